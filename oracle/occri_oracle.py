@@ -1,0 +1,502 @@
+"""Plain FP64 oracle of the occ-RI-K exact-exchange build (test infrastructure).
+
+Conventions (the paper leaves them open; each reading is listed in the design doc):
+* Bloch AOs chi_{mu k}(r) = sum_T e^{i k.T} phi_mu(r - A_mu - T), without the
+  N_k^{-1/2} of Sec. II.A; the cell integral then carries an explicit 1/N_k.
+* Grid r_n = sum_i (n_i/N_i) a_i with n_3 fastest; forward transform
+  e^{-iG.r} with 1/N_g (numpy ``fftn``/N_g); bin m <-> G = sum_i m_i b_i.
+* Pair density of (k,i) with (k',j), q = k - k':
+  rho(r) = conj(psi_{jk'}(r)) psi_{ik}(r) e^{-iq.r}  (Eq. aodf),
+  W(r) = e^{+iq.r} N_g IFFT[v_q . FFT(rho)/N_g]       (Eqs. Vrao, VGao),
+  Y_{ik}(r) += psi_{jk'}(r) W(r)                        (Eq. occrikinterm),
+  K_{mu i}(k) = -(Omega/(N_k N_g)) sum_n conj(chi_{mu k}) Y_{ik}  (Eq. occrik).
+* Kernel per bin: x_i = m_i + q_i reduced to [-N_i/2, N_i/2); at an exact tie
+  x_i = -N_i/2 both aliases are averaged; G+q = 0 takes the value g0.
+* Closed shell: E_x = (1/N_k) sum_k Tr(C_k^H K_{mu i}(k)).
+
+TEST INFRASTRUCTURE: imported only by tests, smoke() and bench.py's CPU legs.
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+
+__all__ = [
+    "cell_volume", "reciprocal_vectors", "grid_points", "SOLID_HARMONICS",
+    "eval_solid_harmonic", "gaussian_moment", "primitive_norms", "image_cutoff",
+    "bloch_aos", "orbitals_on_grid", "grid_phase", "kernel_bins", "kernel_bins_domega",
+    "g0_value", "apply_coulomb_operator", "occri_kc", "contract_kc", "mori_k", "aori_k",
+    "ace_assemble", "exchange_energy", "exchange_energy_parseval", "grad_c",
+    "grad_omega", "grid_overlap", "dft_matrices",
+]
+
+EPS_AO = 1e-16   # AO screening threshold: terms below it are dropped (C10 reading)
+
+
+# ----------------------------------------------------------------------------
+# lattice and grid (Sec. II.A; GPW real-space grid, Sec. II.A eqs. aodf/Vrao)
+# ----------------------------------------------------------------------------
+
+def cell_volume(lattice: np.ndarray) -> float:
+    return float(abs(np.linalg.det(np.asarray(lattice, float))))
+
+
+def reciprocal_vectors(lattice: np.ndarray) -> np.ndarray:
+    """Rows b_j with a_i . b_j = 2 pi delta_ij."""
+    return 2.0 * np.pi * np.linalg.inv(np.asarray(lattice, float)).T
+
+
+def grid_points(lattice: np.ndarray, grid) -> np.ndarray:
+    """r_n = sum_i (n_i/N_i) a_i, flattened with n_3 fastest -> (N_g, 3)."""
+    n1, n2, n3 = grid
+    f = np.stack(np.meshgrid(np.arange(n1) / n1, np.arange(n2) / n2, np.arange(n3) / n3,
+                             indexing="ij"), -1).reshape(-1, 3)
+    return f @ np.asarray(lattice, float)
+
+
+# ----------------------------------------------------------------------------
+# primitives: real solid harmonics x exact normalisation x Gaussian
+# ----------------------------------------------------------------------------
+
+# Unnormalised real solid harmonics P_lm, m = -l..l (p ordered x, y, z), as
+# {(a,b,c): coeff} for x^a y^b z^c.
+SOLID_HARMONICS: Dict[int, List[Dict[Tuple[int, int, int], float]]] = {
+    0: [{(0, 0, 0): 1.0}],
+    1: [{(1, 0, 0): 1.0}, {(0, 1, 0): 1.0}, {(0, 0, 1): 1.0}],
+    2: [{(1, 1, 0): 1.0},                                    # xy
+        {(0, 1, 1): 1.0},                                    # yz
+        {(0, 0, 2): 2.0, (2, 0, 0): -1.0, (0, 2, 0): -1.0},  # 3z^2 - r^2
+        {(1, 0, 1): 1.0},                                    # xz
+        {(2, 0, 0): 1.0, (0, 2, 0): -1.0}],                  # x^2 - y^2
+    3: [{(2, 1, 0): 3.0, (0, 3, 0): -1.0},                   # y(3x^2 - y^2)
+        {(1, 1, 1): 1.0},                                    # xyz
+        {(0, 1, 2): 4.0, (2, 1, 0): -1.0, (0, 3, 0): -1.0},  # y(4z^2 - x^2 - y^2)
+        {(0, 0, 3): 2.0, (2, 0, 1): -3.0, (0, 2, 1): -3.0},  # z(2z^2 - 3x^2 - 3y^2)
+        {(1, 0, 2): 4.0, (3, 0, 0): -1.0, (1, 2, 0): -1.0},  # x(4z^2 - x^2 - y^2)
+        {(2, 0, 1): 1.0, (0, 2, 1): -1.0},                   # z(x^2 - y^2)
+        {(3, 0, 0): 1.0, (1, 2, 0): -3.0}],                  # x(x^2 - 3y^2)
+}
+
+
+def eval_solid_harmonic(l: int, m_index: int, x, y, z):
+    out = 0.0
+    for (a, b, c), coeff in SOLID_HARMONICS[l][m_index].items():
+        out = out + coeff * x ** a * y ** b * z ** c
+    return out
+
+
+def _double_factorial(n: int) -> int:
+    out = 1
+    while n > 1:
+        out *= n
+        n -= 2
+    return out
+
+
+def gaussian_moment(a: int, b: int, c: int, p: float) -> float:
+    """Integral over R^3 of x^a y^b z^c exp(-p r^2)."""
+    out = 1.0
+    for e in (a, b, c):
+        if e % 2:
+            return 0.0
+        out *= _double_factorial(e - 1) / (2.0 * p) ** (e // 2) * math.sqrt(math.pi / p)
+    return out
+
+
+def primitive_norms(l: int, alpha: float) -> np.ndarray:
+    """N_lm with integral of (N_lm P_lm e^{-alpha r^2})^2 equal to 1, for m = -l..l."""
+    out = []
+    for poly in SOLID_HARMONICS[l]:
+        sq = 0.0
+        for e1, c1 in poly.items():
+            for e2, c2 in poly.items():
+                sq += c1 * c2 * gaussian_moment(e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2],
+                                                2.0 * alpha)
+        out.append(1.0 / math.sqrt(sq))
+    return np.array(out)
+
+
+def image_cutoff(l: int, alpha: float, eps: float = EPS_AO) -> float:
+    """Radius beyond which every primitive of the shell is below eps.
+
+    Bound: |N_lm P_lm(d)| <= N_lm sum|coeff| |d|^l, so the radius solves
+    c R^l e^{-alpha R^2} = eps on the decreasing side (R >= sqrt(l/(2 alpha))).
+    """
+    norms = primitive_norms(l, alpha)
+    c = max(n * sum(abs(v) for v in poly.values())
+            for n, poly in zip(norms, SOLID_HARMONICS[l]))
+    lo = math.sqrt(l / (2.0 * alpha)) if l > 0 else 0.0
+    f = lambda r: math.log(c) + l * math.log(max(r, 1e-300)) - alpha * r * r - math.log(eps)
+    hi = max(lo, 1.0)
+    while f(hi) > 0:
+        hi *= 2.0
+    if f(lo) <= 0:
+        return lo
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(mid) > 0:
+            lo = mid
+        else:
+            hi = mid
+    return hi
+
+
+# ----------------------------------------------------------------------------
+# (a) Bloch AOs on the grid (Sec. II.A, first equation; C1 normalisation)
+# ----------------------------------------------------------------------------
+
+def _lattice_images(lattice, centre, radius):
+    """Integer n with |centre + n.lattice| <= radius."""
+    lattice = np.asarray(lattice, float)
+    frac = np.asarray(centre, float) @ np.linalg.inv(lattice)
+    bn = np.linalg.norm(np.linalg.inv(lattice), axis=0)
+    nb = np.ceil(radius * bn).astype(int) + 1
+    axes = [np.arange(int(np.floor(-frac[d])) - nb[d], int(np.ceil(-frac[d])) + nb[d] + 1)
+            for d in range(3)]
+    nn = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    d = centre[None, :] + nn @ lattice
+    return nn[np.linalg.norm(d, axis=1) <= radius]
+
+
+def bloch_aos(lattice, xyz, shell_atom, shell_l, shell_alpha, kfrac, grid=None,
+              points=None, eps: float = EPS_AO) -> np.ndarray:
+    """chi[k, mu, n] = sum_T e^{2 pi i kappa_k . n_T} phi_mu(r_n - A_mu - T).
+
+    The image sum runs over every lattice translation T that brings the shell
+    within its cutoff radius of a point; each (point, image) term below the
+    threshold eps is dropped, per point.
+    """
+    lattice = np.asarray(lattice, float)
+    pts = grid_points(lattice, grid) if points is None else np.asarray(points, float)
+    kfrac = np.asarray(kfrac, float)
+    nk, npts = kfrac.shape[0], pts.shape[0]
+    nao = int(np.sum(2 * np.asarray(shell_l) + 1))
+    chi = np.zeros((nk, nao, npts), dtype=np.complex128)
+    centre = pts.mean(axis=0)
+    rpts = float(np.max(np.linalg.norm(pts - centre, axis=1)))
+    mu0 = 0
+    for s in range(len(shell_l)):
+        l, alpha = int(shell_l[s]), float(shell_alpha[s])
+        a = np.asarray(xyz[shell_atom[s]], float)
+        norms = primitive_norms(l, alpha)
+        rcut = image_cutoff(l, alpha, eps)
+        images = _lattice_images(lattice, a - centre, rcut + rpts)
+        for n_t in images:
+            t = n_t @ lattice
+            d = pts - a[None, :] - t[None, :]
+            r2 = np.einsum("ij,ij->i", d, d)
+            idx = np.nonzero(r2 <= rcut * rcut)[0]
+            if idx.size == 0:
+                continue
+            dx, dy, dz = d[idx, 0], d[idx, 1], d[idx, 2]
+            g = np.exp(-alpha * r2[idx])
+            phase = np.exp(2j * np.pi * (kfrac @ n_t))
+            for m in range(2 * l + 1):
+                val = norms[m] * eval_solid_harmonic(l, m, dx, dy, dz) * g
+                chi[:, mu0 + m, idx] += phase[:, None] * val[None, :]
+        mu0 += 2 * l + 1
+    return chi
+
+
+def orbitals_on_grid(chi: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """psi[k, i, n] = sum_mu C^k_{mu i} chi[k, mu, n]  (Eq. occmo)."""
+    return np.einsum("kmi,kmn->kin", C, chi)
+
+
+def grid_overlap(lattice, chi: np.ndarray, grid) -> np.ndarray:
+    """S^k = (Omega/N_g) sum_n conj(chi_mu) chi_nu (GPW quadrature of the cell overlap)."""
+    ng = int(np.prod(grid))
+    return cell_volume(lattice) / ng * np.einsum("kmn,kvn->kmv", np.conj(chi), chi)
+
+
+# ----------------------------------------------------------------------------
+# (d) Fourier-space kernel per bin (Eqs. VGao, recipcoul; C3, C8)
+# ----------------------------------------------------------------------------
+
+def _frac(x: float, dmax: int = 1 << 20) -> Fraction:
+    return Fraction(float(x)).limit_denominator(dmax)
+
+
+def _axis_reduction(n: int, q: Fraction):
+    """Per bin m: reduced x (first alias), second alias (== first unless tied), zero flag."""
+    xa, xb, zero = [], [], []
+    half = Fraction(n, 2)
+    for m in range(n):
+        x = Fraction(m) + q
+        x = x - n * math.floor(x / n + Fraction(1, 2))
+        tie = (x == -half)
+        xa.append(float(x))
+        xb.append(float(x + n) if tie else float(x))
+        zero.append(x == 0)
+    return np.array(xa), np.array(xb), np.array(zero)
+
+
+def g0_value(kind: str, omega: float, g0_mode: int) -> float:
+    """Value used for the bin G+q = 0 (Eq. VGao's chi; C3 reading)."""
+    if g0_mode == 1:
+        if kind != "erfc":
+            raise ValueError("g0_mode 1 is defined for the erfc kernel only")
+        return math.pi / (omega * omega)
+    return 0.0
+
+
+def _kernel_value(kind: str, omega: float, g2: np.ndarray) -> np.ndarray:
+    """f(|G+q|) of Eq. recipcoul for |G+q|^2 = g2 > 0."""
+    base = 4.0 * np.pi / g2
+    if kind == "coulomb":
+        return base
+    y = g2 / (4.0 * omega * omega)
+    if kind == "erfc":
+        return base * (-np.expm1(-y))
+    if kind == "erf":
+        return base * np.exp(-y)
+    raise ValueError(kind)
+
+
+def _kernel_domega(kind: str, omega: float, g2: np.ndarray) -> np.ndarray:
+    """d f/d omega for |G+q|^2 = g2 > 0."""
+    if kind == "coulomb":
+        return np.zeros_like(g2)
+    e = np.exp(-g2 / (4.0 * omega * omega)) * 2.0 * np.pi / omega ** 3
+    return -e if kind == "erfc" else e
+
+
+def _bins(lattice, grid, qfrac, fn, zero_value):
+    b = reciprocal_vectors(lattice)
+    axes = [_axis_reduction(int(grid[d]), _frac(qfrac[d])) for d in range(3)]
+    zero = axes[0][2][:, None, None] & axes[1][2][None, :, None] & axes[2][2][None, None, :]
+    v = np.zeros(tuple(int(g) for g in grid))
+    for c1 in (0, 1):
+        for c2 in (0, 1):
+            for c3 in (0, 1):
+                x1 = axes[0][c1][:, None, None, None]
+                x2 = axes[1][c2][None, :, None, None]
+                x3 = axes[2][c3][None, None, :, None]
+                gv = x1 * b[0] + x2 * b[1] + x3 * b[2]
+                g2 = np.einsum("abcd,abcd->abc", gv, gv)
+                g2 = np.where(zero, 1.0, g2)
+                v += fn(g2) / 8.0
+    v[zero] = zero_value
+    return v
+
+
+def kernel_bins(lattice, grid, qfrac, kind: str, omega: float, g0: float) -> np.ndarray:
+    """v_q(m) on the FFT bins (tie-averaged); G+q = 0 takes g0."""
+    return _bins(lattice, grid, qfrac, lambda g2: _kernel_value(kind, omega, g2), g0)
+
+
+def kernel_bins_domega(lattice, grid, qfrac, kind: str, omega: float, g0_mode: int):
+    """d v_q(m)/d omega on the bins; G+q = 0 gives d g0/d omega."""
+    dg0 = -2.0 * math.pi / omega ** 3 if (g0_mode == 1 and kind == "erfc") else 0.0
+    return _bins(lattice, grid, qfrac, lambda g2: _kernel_domega(kind, omega, g2), dg0)
+
+
+def grid_phase(grid, qfrac) -> np.ndarray:
+    """e^{i q.r_n} = exp(2 pi i sum_i q_i n_i / N_i) on the grid."""
+    n1, n2, n3 = grid
+    f = (qfrac[0] * np.arange(n1)[:, None, None] / n1 + qfrac[1] * np.arange(n2)[None, :, None] / n2
+         + qfrac[2] * np.arange(n3)[None, None, :] / n3)
+    return np.exp(2j * np.pi * f)
+
+
+def dft_matrices(grid):
+    """Dense 1-D forward DFT matrices F_N[m, n] = e^{-2 pi i m n / N}, one per axis."""
+    out = []
+    for n in grid:
+        j = np.arange(n)
+        out.append(np.exp(-2j * np.pi * np.outer(j, j) / n))
+    return out
+
+
+def apply_coulomb_operator(f: np.ndarray, v: np.ndarray, qfrac, dft: bool = False) -> np.ndarray:
+    """V_q[f](r) = e^{iq.r} N_g IFFT[v_q . FFT(f e^{-iq.r})/N_g]  (Eqs. aodf, Vrao, VGao).
+
+    ``f`` has shape ``grid``. With ``dft=True`` the transforms are explicit
+    separable DFT-matrix products instead of numpy's FFT.
+    """
+    grid = f.shape
+    ng = int(np.prod(grid))
+    ph = grid_phase(grid, qfrac)
+    rho = f * np.conj(ph)
+    if dft:
+        f1, f2, f3 = dft_matrices(grid)
+        rhohat = np.einsum("ai,bj,ck,ijk->abc", f1, f2, f3, rho) / ng
+        u = np.einsum("ai,bj,ck,ijk->abc", np.conj(f1), np.conj(f2), np.conj(f3), v * rhohat)
+    else:
+        rhohat = np.fft.fftn(rho) / ng
+        u = ng * np.fft.ifftn(v * rhohat)
+    return ph * u
+
+
+# ----------------------------------------------------------------------------
+# (c)-(e) occ-RI-K (Algorithm 3) and the conventional builds (Algorithms 1, 2)
+# ----------------------------------------------------------------------------
+
+def occri_kc(lattice, grid, kfrac, psi: np.ndarray, chi: Optional[np.ndarray], kind: str,
+             omega: float, g0: float, dft: bool = False, return_y: bool = False):
+    """AO-occupied block K_{mu i}(k) of Eq. occrik by Algorithm 3.
+
+    psi: (nk, nocc, N_g). For every (k, i) and every (k', j): form the pair
+    density, apply the kernel-fused transform round trip, accumulate
+    Y_{ik} += psi_{jk'} W (Eq. occrikinterm); then contract with conj(chi).
+    If chi is None, only Y is returned.
+    """
+    grid = tuple(int(g) for g in grid)
+    nk, nocc, ng = psi.shape
+    omega_cell = cell_volume(lattice)
+    y = np.zeros_like(psi)
+    for k in range(nk):
+        for kp in range(nk):
+            q = np.asarray(kfrac[k], float) - np.asarray(kfrac[kp], float)
+            v = kernel_bins(lattice, grid, q, kind, omega, g0)
+            for i in range(nocc):
+                for j in range(nocc):
+                    f = (np.conj(psi[kp, j]) * psi[k, i]).reshape(grid)
+                    w = apply_coulomb_operator(f, v, q, dft=dft).reshape(-1)
+                    y[k, i] += psi[kp, j] * w
+    if chi is None:
+        return y
+    kc = contract_kc(lattice, chi, y)
+    return (kc, y) if return_y else kc
+
+
+def contract_kc(lattice, chi: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """K_{mu i}(k) = -(Omega/(N_k N_g)) sum_n conj(chi_{mu k}(r_n)) Y_{ik}(r_n)."""
+    nk, _, ng = chi.shape
+    return -cell_volume(lattice) / (nk * ng) * np.einsum("kmn,kin->kmi", np.conj(chi), y)
+
+
+def mori_k(lattice, grid, kfrac, chi: np.ndarray, psi: np.ndarray, kind: str, omega: float,
+           g0: float) -> np.ndarray:
+    """Conventional GPW exchange K^k_{mu nu} by MO-RI-K (Algorithm 2, Eq. exxmo).
+
+    For every (k, nu) and (k', j): potential of conj(psi_{jk'}) chi_{nu k},
+    accumulate W_nu += psi_{jk'} V, then K_{mu nu} = -c sum_n conj(chi_mu) W_nu.
+    """
+    grid = tuple(int(g) for g in grid)
+    nk, nao, ng = chi.shape
+    nocc = psi.shape[1]
+    c = cell_volume(lattice) / (nk * ng)
+    kmat = np.zeros((nk, nao, nao), dtype=np.complex128)
+    for k in range(nk):
+        wacc = np.zeros((nao, ng), dtype=np.complex128)
+        for kp in range(nk):
+            q = np.asarray(kfrac[k], float) - np.asarray(kfrac[kp], float)
+            v = kernel_bins(lattice, grid, q, kind, omega, g0)
+            for nu in range(nao):
+                for j in range(nocc):
+                    f = (np.conj(psi[kp, j]) * chi[k, nu]).reshape(grid)
+                    wacc[nu] += psi[kp, j] * apply_coulomb_operator(f, v, q).reshape(-1)
+        kmat[k] = -c * np.conj(chi[k]) @ wacc.T
+    return kmat
+
+
+def aori_k(lattice, grid, kfrac, chi: np.ndarray, C: np.ndarray, kind: str, omega: float,
+           g0: float) -> np.ndarray:
+    """Conventional GPW exchange by AO-RI-K (Algorithm 1, Eqs. aointerm, aointerm2, aok).
+
+    psi~_{sigma k'} = sum_lambda P^{k'}_{lambda sigma} chi_{lambda k'} with
+    P^{k'} = C C^H; potentials of conj(chi_{sigma k'}) chi_{nu k} for every AO pair.
+    """
+    grid = tuple(int(g) for g in grid)
+    nk, nao, ng = chi.shape
+    c = cell_volume(lattice) / (nk * ng)
+    pmat = np.einsum("kli,ksi->kls", C, np.conj(C))
+    psit = np.einsum("kls,kln->ksn", pmat, chi)
+    kmat = np.zeros((nk, nao, nao), dtype=np.complex128)
+    for k in range(nk):
+        wacc = np.zeros((nao, ng), dtype=np.complex128)
+        for kp in range(nk):
+            q = np.asarray(kfrac[k], float) - np.asarray(kfrac[kp], float)
+            v = kernel_bins(lattice, grid, q, kind, omega, g0)
+            for nu in range(nao):
+                for s in range(nao):
+                    f = (np.conj(chi[kp, s]) * chi[k, nu]).reshape(grid)
+                    wacc[nu] += psit[kp, s] * apply_coulomb_operator(f, v, q).reshape(-1)
+        kmat[k] = -c * np.conj(chi[k]) @ wacc.T
+    return kmat
+
+
+# ----------------------------------------------------------------------------
+# (f) occ-RI assembly in ACE form and the exchange energy
+# ----------------------------------------------------------------------------
+
+def ace_assemble(C: np.ndarray, kc: np.ndarray):
+    """K_k = KC (C^H KC)^{-1} KC^H via the Cholesky factor of -M (C5, C6 readings).
+
+    Returns (K[nk,nao,nao], M[nk,nocc,nocc], E_x). M is Hermitised before the
+    factorisation; E_x = (1/N_k) sum_k Re Tr M_k.
+    """
+    nk, nao, nocc = C.shape
+    kmat = np.zeros((nk, nao, nao), dtype=np.complex128)
+    mmat = np.zeros((nk, nocc, nocc), dtype=np.complex128)
+    ex = 0.0
+    for k in range(nk):
+        m = np.conj(C[k].T) @ kc[k]
+        m = 0.5 * (m + np.conj(m.T))
+        mmat[k] = m
+        low = np.linalg.cholesky(-m)                       # -M = L L^H
+        xi = np.linalg.solve(np.conj(low), kc[k].T).T      # xi L^H = KC
+        kmat[k] = -xi @ np.conj(xi.T)
+        ex += float(np.real(np.trace(m)))
+    return kmat, mmat, ex / nk
+
+
+def exchange_energy(C: np.ndarray, kc: np.ndarray) -> float:
+    """E_x = (1/N_k) sum_k Re Tr(C_k^H K_{mu i}(k)) (closed shell, C2 reading)."""
+    return float(np.real(np.einsum("kmi,kmi->", np.conj(C), kc))) / C.shape[0]
+
+
+def exchange_energy_parseval(lattice, grid, kfrac, psi: np.ndarray, kind: str, omega: float,
+                             g0: float) -> float:
+    """E_x = -(Omega/N_k^2) sum_{k k' i j} sum_m v_q(m) |rho^hat(m)|^2 (discrete Parseval)."""
+    grid = tuple(int(g) for g in grid)
+    nk, nocc, ng = psi.shape
+    tot = 0.0
+    for k in range(nk):
+        for kp in range(nk):
+            q = np.asarray(kfrac[k], float) - np.asarray(kfrac[kp], float)
+            v = kernel_bins(lattice, grid, q, kind, omega, g0)
+            ph = grid_phase(grid, q)
+            for i in range(nocc):
+                for j in range(nocc):
+                    rho = (np.conj(psi[kp, j]) * psi[k, i]).reshape(grid) * np.conj(ph)
+                    rh = np.fft.fftn(rho) / ng
+                    tot += float(np.sum(v * np.abs(rh) ** 2))
+    return -cell_volume(lattice) / nk ** 2 * tot
+
+
+# ----------------------------------------------------------------------------
+# adjoint of E_x
+# ----------------------------------------------------------------------------
+
+def grad_c(kc: np.ndarray) -> np.ndarray:
+    """Gradient of E_x w.r.t. C_k in the conjugate-Wirtinger convention (2 dE/dC*).
+
+    E_x is quadratic in C and in C*, and every orbital enters once as i and
+    once as j, so dE/dC*_{mu i}(k) = (2/N_k) K_{mu i}(k); the returned value is
+    twice that.
+    """
+    return 4.0 / kc.shape[0] * kc
+
+
+def grad_omega(lattice, grid, kfrac, psi: np.ndarray, kind: str, omega: float,
+               g0_mode: int) -> float:
+    """dE_x/d omega = -(Omega/N_k^2) sum_{k k' i j} sum_m (d v_q(m)/d omega) |rho^hat(m)|^2."""
+    grid = tuple(int(g) for g in grid)
+    nk, nocc, ng = psi.shape
+    tot = 0.0
+    for k in range(nk):
+        for kp in range(nk):
+            q = np.asarray(kfrac[k], float) - np.asarray(kfrac[kp], float)
+            dv = kernel_bins_domega(lattice, grid, q, kind, omega, g0_mode)
+            ph = grid_phase(grid, q)
+            for i in range(nocc):
+                for j in range(nocc):
+                    rho = (np.conj(psi[kp, j]) * psi[k, i]).reshape(grid) * np.conj(ph)
+                    rh = np.fft.fftn(rho) / ng
+                    tot += float(np.sum(dv * np.abs(rh) ** 2))
+    return -cell_volume(lattice) / nk ** 2 * tot

@@ -1,0 +1,348 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test names the passage of arXiv:2207.09028 (or the mathematical fact)
+that fixes the expected value, and is chosen so that a plausible mistake in
+the oracle (a dropped term, a wrong sign, index or normalisation) fails it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import config, small_workload
+from workloads.synthetic import analytic_overlap
+
+
+def _chi(w, grid=None, points=None, kfrac=None):
+    return O.bloch_aos(w.lattice, w.xyz, w.shell_atom, w.shell_l, w.shell_alpha,
+                       w.kfrac if kfrac is None else kfrac, grid=w.grid if grid is None else grid,
+                       points=points)
+
+
+def _g0(w):
+    return O.g0_value(w.kernel, w.omega, w.g0_mode)
+
+
+def _kc(w, chi=None, C=None, dft=False, kind=None, omega=None, g0=None):
+    chi = _chi(w) if chi is None else chi
+    C = w.C if C is None else C
+    psi = O.orbitals_on_grid(chi, C)
+    return O.occri_kc(w.lattice, w.grid, w.kfrac, psi, chi, kind or w.kernel,
+                      w.omega if omega is None else omega, _g0(w) if g0 is None else g0, dft=dft)
+
+
+# ---------------------------------------------------------------- primitives
+
+def _laplacian(poly):
+    out = {}
+    for (a, b, c), v in poly.items():
+        for d, e in enumerate((a, b, c)):
+            if e >= 2:
+                key = [a, b, c]
+                key[d] -= 2
+                out[tuple(key)] = out.get(tuple(key), 0.0) + v * e * (e - 1)
+    return out
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 3])
+def test_solid_harmonics_are_harmonic_and_independent(l):
+    """Real solid harmonics are homogeneous of degree l, harmonic, and 2l+1 independent."""
+    polys = O.SOLID_HARMONICS[l]
+    assert len(polys) == 2 * l + 1
+    for p in polys:
+        assert all(sum(e) == l for e in p)
+        assert all(abs(v) < 1e-14 for v in _laplacian(p).values())
+    # Gram matrix of the polynomials under exp(-r^2) must be diagonal (orthogonal
+    # on the sphere) and positive.
+    gram = np.zeros((2 * l + 1, 2 * l + 1))
+    for i, p in enumerate(polys):
+        for j, q in enumerate(polys):
+            gram[i, j] = sum(c1 * c2 * O.gaussian_moment(e1[0] + e2[0], e1[1] + e2[1],
+                                                         e1[2] + e2[2], 1.0)
+                             for e1, c1 in p.items() for e2, c2 in q.items())
+    assert np.all(np.diag(gram) > 0)
+    assert np.abs(gram - np.diag(np.diag(gram))).max() < 1e-13
+
+
+@pytest.mark.parametrize("l,alpha", [(0, 0.7), (1, 1.3), (2, 0.9), (3, 1.6)])
+def test_primitive_normalisation_by_quadrature(l, alpha):
+    """Integral of phi^2 is 1 by brute-force quadrature (independent of the moment formula)."""
+    h, n = 0.11, 121
+    x = (np.arange(n) - n // 2) * h
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    g = np.exp(-alpha * (X * X + Y * Y + Z * Z))
+    norms = O.primitive_norms(l, alpha)
+    for m in range(2 * l + 1):
+        phi = norms[m] * O.eval_solid_harmonic(l, m, X, Y, Z) * g
+        assert abs(np.sum(phi * phi) * h ** 3 - 1.0) < 1e-10
+
+
+def test_image_cutoff_bounds_every_primitive():
+    for l, alpha in [(0, 0.06), (1, 0.5), (2, 3.0), (3, 40.0)]:
+        r = O.image_cutoff(l, alpha)
+        norms = O.primitive_norms(l, alpha)
+        rng = np.random.default_rng(0)
+        d = rng.standard_normal((2000, 3))
+        d *= r / np.linalg.norm(d, axis=1)[:, None]
+        for m in range(2 * l + 1):
+            v = norms[m] * O.eval_solid_harmonic(l, m, d[:, 0], d[:, 1], d[:, 2]) * math.exp(-alpha * r * r)
+            assert np.abs(v).max() <= 1.0000001e-16
+
+
+# ---------------------------------------------------------------- Bloch AOs
+
+def test_grid_overlap_matches_analytic_obara_saika():
+    """GPW quadrature of <chi_mu k|chi_nu k> equals the analytic lattice-summed overlap.
+
+    On a grid that resolves the products, the trapezoid rule is spectrally
+    exact, so this pins the oracle's AO values (polynomials, normalisation,
+    image sums, Bloch phases) against an independent integral code.
+    """
+    w = small_workload(a_ang=2.6, mesh=(2, 1, 1), counts=(2, 1, 1), lo=0.35, hi=0.9,
+                       grid=(24, 24, 24), nocc=2)
+    chi = _chi(w)
+    s_grid = O.grid_overlap(w.lattice, chi, w.grid)
+    s_ref = analytic_overlap(w.lattice, w.xyz, w.shell_atom, w.shell_l, w.shell_alpha, w.kfrac)
+    assert np.abs(s_grid - s_ref).max() < 1e-9 * np.abs(s_ref).max()
+
+
+def test_bloch_periodicity():
+    """chi_{mu k}(r + a_i) = e^{i k.a_i} chi_{mu k}(r) (Sec. II.A Bloch sum)."""
+    w = small_workload(mesh=(2, 2, 1), counts=(1, 1, 1, 1), grid=(6, 6, 6))
+    rng = np.random.default_rng(3)
+    pts = rng.random((40, 3)) @ w.lattice
+    base = _chi(w, points=pts)
+    for ax in range(3):
+        shifted = _chi(w, points=pts + w.lattice[ax])
+        ph = np.exp(2j * np.pi * w.kfrac[:, ax])
+        assert np.abs(shifted - ph[:, None, None] * base).max() < 1e-13 * np.abs(base).max()
+
+
+# ---------------------------------------------------------------- kernel + transforms
+
+@pytest.mark.parametrize("grid", [(6, 6, 6), (5, 6, 7), (4, 9, 5)])
+@pytest.mark.parametrize("q", [(0.0, 0.0, 0.0), (0.5, -0.5, 0.25), (1 / 3, 0.5, -2 / 3)])
+@pytest.mark.parametrize("kind", ["coulomb", "erfc", "erf"])
+def test_plane_waves_are_eigenfunctions(grid, q, kind):
+    """P8: V_q[e^{i(G_m+q).r}] = v_q(m) e^{i(G_m+q).r} for every bin, ties and G+q=0 included."""
+    w = small_workload()
+    lat = w.lattice
+    v = O.kernel_bins(lat, grid, np.array(q), kind, 0.7, 0.37)
+    n1, n2, n3 = grid
+    n = np.stack(np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij"), -1)
+    rng = np.random.default_rng(1)
+    for _ in range(6):
+        m = [rng.integers(0, g) for g in grid]
+        arg = sum((m[d] + q[d]) * n[..., d] / grid[d] for d in range(3))
+        f = np.exp(2j * np.pi * arg)
+        out = O.apply_coulomb_operator(f, v, np.array(q))
+        assert np.abs(out - v[tuple(m)] * f).max() < 1e-12 * max(1.0, abs(v[tuple(m)]))
+
+
+def test_kernel_bins_inversion_symmetric():
+    """With tie averaging, v_{-q}(-m) = v_q(m), so a real density gives a real potential."""
+    w = config("cfg1")
+    for grid in [(6, 6, 6), (5, 6, 8)]:
+        for q in [(0.0, 0.0, 0.0), (0.5, 0.0, -0.5), (0.25, 0.5, 0.75)]:
+            q = np.array(q)
+            v = O.kernel_bins(w.lattice, grid, q, "coulomb", 0.0, 0.0)
+            vm = O.kernel_bins(w.lattice, grid, -q, "coulomb", 0.0, 0.0)
+            idx = tuple((-np.arange(g)) % g for g in grid)
+            assert np.allclose(vm[np.ix_(*idx)], v, rtol=1e-15, atol=0)
+
+
+def test_kernel_closed_forms_and_g0():
+    """Eq. recipcoul at generic bins; G+q=0 takes g0 = pi/omega^2 for erfc (its x->0 limit)."""
+    w = small_workload()
+    b = O.reciprocal_vectors(w.lattice)
+    grid = (7, 7, 7)
+    omega = 0.45
+    v_c = O.kernel_bins(w.lattice, grid, np.zeros(3), "coulomb", 0.0, 0.0)
+    v_s = O.kernel_bins(w.lattice, grid, np.zeros(3), "erfc", omega, math.pi / omega ** 2)
+    v_l = O.kernel_bins(w.lattice, grid, np.zeros(3), "erf", omega, 0.0)
+    g = b[0] + 2 * b[1] - b[2]
+    g2 = g @ g
+    assert abs(v_c[1, 2, 6] - 4 * math.pi / g2) < 1e-14 * v_c[1, 2, 6]
+    assert abs(v_l[1, 2, 6] - 4 * math.pi / g2 * math.exp(-g2 / (4 * omega ** 2))) < 1e-14
+    assert abs(v_s[1, 2, 6] + v_l[1, 2, 6] - v_c[1, 2, 6]) < 1e-13 * v_c[1, 2, 6]
+    assert v_c[0, 0, 0] == 0.0 and v_l[0, 0, 0] == 0.0
+    assert v_s[0, 0, 0] == math.pi / omega ** 2
+    # the erfc kernel is continuous at the origin: tiny |G+q| approaches g0
+    tiny = O.kernel_bins(w.lattice, grid, np.array([1e-4, 0, 0]), "erfc", omega, 0.0)[0, 0, 0]
+    assert abs(tiny - math.pi / omega ** 2) < 1e-6 * math.pi / omega ** 2
+
+
+def test_explicit_dft_equals_fft():
+    """P12: explicit separable DFT mode agrees with numpy's FFT mode."""
+    w = small_workload(mesh=(1, 1, 2), grid=(6, 5, 4), counts=(2, 1))
+    a = _kc(w)
+    b = _kc(w, dft=True)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+
+
+# ---------------------------------------------------------------- exactness of occ-RI-K
+
+def _conventional(w, chi, which="mo"):
+    psi = O.orbitals_on_grid(chi, w.C)
+    if which == "mo":
+        return O.mori_k(w.lattice, w.grid, w.kfrac, chi, psi, w.kernel, w.omega, _g0(w))
+    return O.aori_k(w.lattice, w.grid, w.kfrac, chi, w.C, w.kernel, w.omega, _g0(w))
+
+
+@pytest.mark.parametrize("mesh,kind", [((1, 1, 1), "coulomb"), ((1, 2, 1), "erfc"),
+                                       ((2, 1, 1), "erf")])
+def test_ace_reproduces_conventional_on_occupied_space(mesh, kind):
+    """P1: K_ACE C = K_conv C; C^H K_ACE C = M; K_ACE Hermitian; K_ACE - K_conv PSD, C in its kernel.
+
+    K_conv is the brute-force MO-RI-K build (Algorithm 2), a separate code path.
+    """
+    omega = {"coulomb": 0.0, "erfc": 0.5, "erf": 0.6}[kind]
+    w = small_workload(mesh=mesh, grid=(8, 8, 8), kernel=kind, omega=omega,
+                       g0_mode=1 if kind == "erfc" else 0)
+    chi = _chi(w)
+    kc = _kc(w, chi=chi)
+    k_conv = _conventional(w, chi)
+    k_ace, m, ex = O.ace_assemble(w.C, kc)
+    scale = np.abs(k_conv).max()
+    for k in range(w.nk):
+        assert np.abs(k_conv[k] @ w.C[k] - kc[k]).max() < 1e-12 * scale
+        assert np.abs(k_ace[k] @ w.C[k] - kc[k]).max() < 1e-12 * scale
+        assert np.abs(np.conj(w.C[k].T) @ k_ace[k] @ w.C[k] - m[k]).max() < 1e-12 * scale
+        assert np.abs(k_ace[k] - np.conj(k_ace[k].T)).max() < 1e-13 * scale
+        d = k_ace[k] - k_conv[k]
+        assert np.linalg.eigvalsh(0.5 * (d + np.conj(d.T))).min() > -1e-12 * scale
+        assert np.abs(d @ w.C[k]).max() < 1e-12 * scale
+
+
+def test_energy_identities_occri_mori_aori():
+    """P2/P3/P4: E_x by trace = by Parseval = by MO-RI-K = by AO-RI-K, and E_x < 0."""
+    w = small_workload(mesh=(1, 1, 2), grid=(8, 8, 8), counts=(2, 1), nocc=2)
+    chi = _chi(w)
+    kc = _kc(w, chi=chi)
+    e_tr = O.exchange_energy(w.C, kc)
+    psi = O.orbitals_on_grid(chi, w.C)
+    e_p = O.exchange_energy_parseval(w.lattice, w.grid, w.kfrac, psi, w.kernel, w.omega, _g0(w))
+    e_mo = float(np.real(np.einsum("kmi,kmv,kvi->", np.conj(w.C), _conventional(w, chi, "mo"),
+                                   w.C))) / w.nk
+    e_ao = float(np.real(np.einsum("kmi,kmv,kvi->", np.conj(w.C), _conventional(w, chi, "ao"),
+                                   w.C))) / w.nk
+    assert e_tr < 0
+    for e in (e_p, e_mo, e_ao):
+        assert abs(e - e_tr) < 1e-12 * abs(e_tr)
+
+
+def test_square_c_makes_ace_exact():
+    """P10: with nocc = nao (square invertible C) the ACE form equals the full K."""
+    w = small_workload(counts=(2, 1), nocc=10, grid=(8, 8, 8))
+    chi = _chi(w)
+    kc = _kc(w, chi=chi)
+    k_ace, _, _ = O.ace_assemble(w.C, kc)
+    k_conv = _conventional(w, chi)
+    assert np.abs(k_ace - k_conv).max() < 1e-11 * np.abs(k_conv).max()
+
+
+def test_gamma_real_orbitals_give_real_symmetric_k():
+    """P6: at Gamma with real C on an fcc cell and even grid, K is real symmetric."""
+    w = config("cfg1")
+    kc = _kc(w)
+    k_ace, _, _ = O.ace_assemble(w.C, kc)
+    assert np.abs(k_ace.imag).max() < 1e-14 * np.abs(k_ace).max()
+    assert np.abs(k_ace[0] - k_ace[0].T).max() < 1e-14 * np.abs(k_ace).max()
+
+
+def test_kmesh_equals_gamma_supercell():
+    """P5: E_x(cell, n-mesh) = E_x(Gamma supercell)/N_k (Tables II/III: k-points vs supercells).
+
+    Supercell orbitals C^sc_{(mu,L),(i,k)} = e^{i k.L} C^k_{mu i}/sqrt(N_k).
+    """
+    w = small_workload(mesh=(1, 1, 2), grid=(6, 6, 6), counts=(2, 1), nocc=2)
+    e_cell = O.exchange_energy(w.C, _kc(w))
+    nk, nao, nocc = w.C.shape
+    sc_lat = w.lattice.copy()
+    sc_lat[2] *= 2
+    offs = [np.array([0, 0, 0]), np.array([0, 0, 1])]
+    xyz = np.concatenate([w.xyz + o @ w.lattice for o in offs])
+    natm = w.xyz.shape[0]
+    sa = np.concatenate([w.shell_atom + natm * j for j in range(2)])
+    sl = np.concatenate([w.shell_l] * 2)
+    sx = np.concatenate([w.shell_alpha] * 2)
+    csc = np.zeros((2 * nao, nk * nocc), dtype=complex)
+    for ik in range(nk):
+        for j, o in enumerate(offs):
+            csc[j * nao:(j + 1) * nao, ik * nocc:(ik + 1) * nocc] = (
+                np.exp(2j * np.pi * w.kfrac[ik] @ o) * w.C[ik] / math.sqrt(nk))
+    gsc = (6, 6, 12)
+    chi_sc = O.bloch_aos(sc_lat, xyz, sa, sl, sx, np.zeros((1, 3)), grid=gsc)
+    psi = O.orbitals_on_grid(chi_sc, csc[None])
+    kc = O.occri_kc(sc_lat, gsc, np.zeros((1, 3)), psi, chi_sc, "coulomb", 0.0, 0.0)
+    e_sc = O.exchange_energy(csc[None], kc)
+    assert abs(e_sc / nk - e_cell) < 1e-12 * abs(e_cell)
+
+
+def test_isolated_gaussian_erfc_closed_form():
+    """P7: one normalised s Gaussian in a large cubic box, erfc kernel with g0 = pi/omega^2.
+
+    The short-range self-exchange of a Gaussian charge of exponent beta = 2 alpha is
+    sqrt(2 beta/pi) - (2/sqrt(pi)) (2/beta + 1/omega^2)^{-1/2} (textbook Gaussian
+    Coulomb integrals), so E_x = minus that.
+    """
+    alpha, omega, box = 0.5, 1.0, 12.0
+    lat = box * np.eye(3)
+    xyz = np.array([[box / 2] * 3])
+    grid = (48, 48, 48)
+    chi = O.bloch_aos(lat, xyz, np.array([0]), np.array([0]), np.array([alpha]),
+                      np.zeros((1, 3)), grid=grid)
+    C = np.ones((1, 1, 1), dtype=complex)
+    psi = O.orbitals_on_grid(chi, C)
+    kc = O.occri_kc(lat, grid, np.zeros((1, 3)), psi, chi, "erfc", omega, math.pi / omega ** 2)
+    beta = 2 * alpha
+    exact = -(math.sqrt(2 * beta / math.pi)
+              - 2 / math.sqrt(math.pi) * (2 / beta + 1 / omega ** 2) ** -0.5)
+    assert abs(O.exchange_energy(C, kc) - exact) < 1e-10
+
+
+def test_kernel_linearity_erfc_plus_erf_is_coulomb():
+    """P11: v_erfc + v_erf = v_Coulomb (Eq. recipcoul), so K is additive (g0 = 0)."""
+    w = small_workload(mesh=(2, 1, 1), grid=(6, 6, 6))
+    chi = _chi(w)
+    a = _kc(w, chi=chi, kind="erfc", omega=0.4, g0=0.0)
+    b = _kc(w, chi=chi, kind="erf", omega=0.4, g0=0.0)
+    c = _kc(w, chi=chi, kind="coulomb", omega=0.0, g0=0.0)
+    assert np.abs(a + b - c).max() < 1e-13 * np.abs(c).max()
+
+
+# ---------------------------------------------------------------- adjoint
+
+def _energy(w, C, chi, omega=None):
+    return O.exchange_energy(C, _kc(w, chi=chi, C=C, omega=omega))
+
+
+def test_grad_c_matches_central_differences():
+    """P9: 2 dE/dC* = (4/N_k) K_{mu i}(k), checked against central differences (h = 1e-5)."""
+    w = small_workload(mesh=(1, 2, 1), grid=(6, 6, 6), nocc=2, kernel="erfc", omega=0.5,
+                       g0_mode=1)
+    chi = _chi(w)
+    g = O.grad_c(_kc(w, chi=chi))
+    rng = np.random.default_rng(11)
+    for _ in range(2):
+        d = rng.standard_normal(w.C.shape) + 1j * rng.standard_normal(w.C.shape)
+        h = 1e-5
+        fd = (_energy(w, w.C + h * d, chi) - _energy(w, w.C - h * d, chi)) / (2 * h)
+        an = float(np.real(np.sum(np.conj(g) * d)))
+        assert abs(fd - an) < 1e-7 * abs(an)
+
+
+@pytest.mark.parametrize("kind,g0_mode", [("erfc", 1), ("erfc", 0), ("erf", 0)])
+def test_grad_omega_matches_central_differences(kind, g0_mode):
+    w = small_workload(mesh=(2, 1, 1), grid=(6, 6, 6), nocc=2, kernel=kind, omega=0.45,
+                       g0_mode=g0_mode)
+    chi = _chi(w)
+    psi = O.orbitals_on_grid(chi, w.C)
+    an = O.grad_omega(w.lattice, w.grid, w.kfrac, psi, kind, 0.45, g0_mode)
+    h = 1e-5
+    ep = O.exchange_energy(w.C, _kc(w, chi=chi, omega=0.45 + h,
+                                    g0=O.g0_value(kind, 0.45 + h, g0_mode)))
+    em = O.exchange_energy(w.C, _kc(w, chi=chi, omega=0.45 - h,
+                                    g0=O.g0_value(kind, 0.45 - h, g0_mode)))
+    assert abs((ep - em) / (2 * h) - an) < 1e-7 * abs(an)
