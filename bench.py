@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Throughput of the occ-RI-K exchange build: K-builds/s at 6x6x6 k, 350 AO.
+
+One step = one full exchange build (steps a-f: AO/orbital evaluation, every
+(k,k',i,j) pair-density FFT round trip with the Coulomb kernel, the contraction
+and the FP64 ACE assembly) on the paper-scale synthetic cell: fcc a = 5.43 A,
+2 atoms, 6x6x6 Gamma-centred k-mesh (216 k), 350 uncontracted s/p/d/f AOs,
+nocc = 8, 60^3 grid, mixed precision. Inputs (C, plan tables) are resident in
+HBM before the timed region; the orbital and accumulator fields (3 GB each)
+exceed L2, so no flush is needed between steps.
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead
+(bounded sample, extrapolated to a full build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "K-builds/s at 6x6x6 k, 350 AO; mixed vs FP64 GPU at |dE_x|<=1e-6 Ha/cell"
+UNIT = "K-builds/s"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample_seconds(w, n_k: int = 2, pts=(256, 1024), seed: int = 0):
+    """Time the FP64 oracle on a bounded sample of one build and scale to a full build.
+
+    Pair stage: the Algorithm-3 loop over n_k k-points (n_k^2 of the N_k^2 (k,k')
+    blocks, each nocc^2 FFT round trips on the full grid); its cost is exactly
+    linear in the number of blocks. AO stage: Bloch AOs for all k-points at two
+    point counts, fitted as a + b*n and evaluated at N_g (the oracle evaluates the
+    AOs once per build and keeps them for the contraction). Returns (seconds per full
+    build, sample description, wall seconds spent sampling).
+    """
+    import oracle as O
+
+    rng = np.random.default_rng(seed)
+    ng = int(np.prod(w.grid))
+    psi = (rng.standard_normal((n_k, w.nocc, ng)) + 1j * rng.standard_normal((n_k, w.nocc, ng)))
+    t0 = time.perf_counter()
+    O.occri_kc(w.lattice, w.grid, w.kfrac[:n_k], psi, None, w.kernel, w.omega,
+               O.g0_value(w.kernel, w.omega, w.g0_mode))
+    t_pairs = time.perf_counter() - t0
+    allpts = O.grid_points(w.lattice, w.grid)
+    ts = []
+    for n in pts:
+        sel = allpts[rng.choice(ng, n, replace=False)]
+        t0 = time.perf_counter()
+        O.bloch_aos(w.lattice, w.xyz, w.shell_atom, w.shell_l, w.shell_alpha, w.kfrac, points=sel)
+        ts.append(time.perf_counter() - t0)
+    slope = max(0.0, (ts[1] - ts[0]) / (pts[1] - pts[0]))
+    t_ao_full = max(ts[0] - slope * pts[0], 0.0) + slope * ng
+    total = t_pairs * (w.nk / n_k) ** 2 + t_ao_full
+    desc = (f"oracle Algorithm-3 loop over {n_k} k-points ({n_k ** 2} of {w.nk ** 2} (k,k') blocks, "
+            f"{n_k ** 2 * w.nocc ** 2} FFT round trips of {w.grid[0]}^3), scaled by blocks; oracle "
+            f"Bloch AOs for all {w.nk} k at {pts[0]} and {pts[1]} points, fitted a+b*n and "
+            f"evaluated at {ng} points, once per build")
+    return total, desc, t_pairs + sum(ts)
+
+
+# ---------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="occri", choices=["occri", "reference"])
+    ap.add_argument("--workload", default="cfg5")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--timing-every", type=int, default=61)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from workloads import config
+    w = config(args.workload)
+    if isinstance(w, list):
+        raise SystemExit("bench workloads are single cells")
+    cfg = {"workload": (f"{args.workload}: fcc a=5.43 A, 2 atoms, {w.nk} k ({round(w.nk ** (1 / 3))}^3 "
+                        f"Gamma-centred), nao {w.nao}, nocc {w.nocc}, grid {w.grid[0]}^3, "
+                        f"{w.kernel} kernel"),
+           "nk": w.nk, "nao": w.nao, "nocc": w.nocc, "grid": list(w.grid), "kernel": w.kernel,
+           "precision": "mixed: FP32 AO/orbitals/FFTs/Y, FP64 contraction sum, assembly, E_x",
+           "l2": "no flush: orbital and accumulator fields (2 x 3 GB) exceed L2",
+           "parallelism": f"replicas x{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        samples = []
+        for _ in range(args.warmup + args.steps):
+            t, desc, wall = oracle_sample_seconds(w)
+            samples.append(t)
+        t = statistics.median(samples[args.warmup:]) if args.steps else samples[-1]
+        val = 1.0 / t
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+                          "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                           "sample": desc},
+                          "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
+
+    import torch
+
+    import paper_2207_09028_gb300 as occri
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    plan = occri.Plan.from_workload(w, precision="mixed")
+    C = torch.from_numpy(w.C).to(dev)
+    KC = torch.empty((w.nk, w.nao, w.nocc), dtype=torch.complex128, device=dev)
+    K = torch.empty((w.nk, w.nao, w.nao), dtype=torch.complex128, device=dev)
+    Ex = torch.zeros(1, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        plan.k_build(C, KC, K, Ex, sync=False)
+    plan.sync()
+    ex_mixed = float(Ex.cpu()[0])
+
+    plan.set_timing(args.timing_every)
+    torch.cuda.synchronize()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.k_build(C, KC, K, Ex, sync=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    plan.sync()
+    stages = plan.stage_times()
+    plan.set_timing(0)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+    info = plan.info()
+
+    # roofline of the dominant kernel (pair-transform passes are HBM/L2-streaming)
+    hbm, peak_kind = _peaks()
+    csz = 8
+    ng = w.ng
+    alg = {"pair_a": csz * ng * (1 + 2.0 / w.nocc), "pair_b": csz * ng * 2.0,
+           "pair_c": csz * ng * (1 + 3.0 / w.nocc)}
+    dom = max(stages, key=lambda s: stages[s]["ms"])
+    roof = None
+    per_build = {s: (stages[s]["ms"] / max(1, stages[s]["launches"])) for s in stages}
+    if dom in alg and stages[dom]["launches"]:
+        st = stages[dom]
+        bytes_total = alg[dom] * st["units"]
+        achieved = bytes_total / (st["ms"] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None,
+                "bytes_per_launch": alg[dom] * st["units"] / st["launches"],
+                "ms_per_launch": st["ms"] / st["launches"]}
+    stage_share = {s: stages[s]["ms"] for s in stages}
+
+    out = {"impl": "occri", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": cfg, "roofline": roof,
+           "gpu_launches": int(info["launches_per_build"]) * args.steps,
+           "stages_ms_sampled": stage_share, "E_x_mixed": ex_mixed}
+    clocks = clk.summary()
+    out["clocks"] = clocks
+
+    # end to end through the host entry point (pinned host buffers, copies timed)
+    if args.e2e_steps > 0:
+        import ctypes
+        Ch = torch.from_numpy(w.C).pin_memory()
+        KCh = torch.empty((w.nk, w.nao, w.nocc), dtype=torch.complex128).pin_memory()
+        Kh = torch.empty((w.nk, w.nao, w.nao), dtype=torch.complex128).pin_memory()
+        Exh = torch.zeros(1, dtype=torch.float64).pin_memory()
+        lib = occri.load_library()
+        plan.set_stream()
+        call = lambda: lib.occri_k_build_host(plan._h, ctypes.c_void_p(Ch.data_ptr()),
+                                              ctypes.c_void_p(KCh.data_ptr()),
+                                              ctypes.c_void_p(Kh.data_ptr()),
+                                              ctypes.c_void_p(Exh.data_ptr()))
+        assert call() == 0
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            assert call() == 0
+        t1 = time.perf_counter()
+        out["e2e"] = {"value": world * args.e2e_steps / (t1 - t0), "unit": UNIT,
+                      "h2d_bytes_per_step": Ch.numel() * 16,
+                      "d2h_bytes_per_step": (KCh.numel() + Kh.numel()) * 16 + 8,
+                      "steps": args.e2e_steps}
+
+    # the plain FP64 GPU path on the same workload
+    if args.fp64_steps > 0:
+        del K
+        torch.cuda.empty_cache()
+        p64 = occri.Plan.from_workload(w, precision="fp64")
+        Ex64 = torch.zeros(1, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            p64.k_build(C, None, None, Ex64, sync=False)
+        e1.record(stream)
+        p64.sync()
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        ex64 = float(Ex64.cpu()[0])
+        out["fp64_gpu"] = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
+                           "steps": args.fp64_steps, "E_x": ex64,
+                           "mixed_speedup": ms64 / ms_per_step,
+                           "abs_dE_x_mixed_vs_fp64": abs(ex_mixed - ex64)}
+        p64.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t, desc, wall = oracle_sample_seconds(w)
+        out["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": desc, "sample_wall_s": wall}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * occri.h -- C ABI of the GB300 occ-RI-K exact-exchange library (liboccri.so).
+ *
+ * The library builds the exact-exchange matrix of a periodic solid in a
+ * Gaussian basis by the occ-RI-K algorithm of Lee, Rettig, Feng, Epifanovsky
+ * and Head-Gordon, arXiv:2207.09028 (Sec. II.D, Algorithm 3, with the
+ * integral-direct AO treatment of Algorithm 4):
+ *   (a) Bloch-summed Gaussian AOs on the real-space grid (Sec. II.A),
+ *   (b) occupied orbitals on the grid (Eq. occmo),
+ *   (c) pair densities conj(psi_jk') psi_ik e^{-iq.r}, q = k - k' (Eq. aodf),
+ *   (d) forward FFT x kernel v(|G+q|) x inverse FFT (Eqs. Vrao, VGao,
+ *       recipcoul), accumulated into Y_ik = sum_{k'j} psi_jk' W (Eq. occrikinterm),
+ *   (e) K_{mu i}(k) = -(Omega/(N_k N_g)) sum_r conj(chi_mu k) Y_ik (Eq. occrik),
+ *   (f) occ-RI assembly in ACE form K_k = KC (C^H KC)^{-1} KC^H, and
+ *       E_x = (1/N_k) sum_k Re Tr(C_k^H KC_k) in Ha per cell (closed shell).
+ *
+ * Conventions.
+ *   Lengths in bohr, exponents in bohr^-2, omega in bohr^-1.
+ *   Lattice rows a_1, a_2, a_3. Grid points r_n = sum_i (n_i/N_i) a_i,
+ *   n = (n1*N2 + n2)*N3 + n3 (n3 fastest).
+ *   Bloch AO chi_{mu k}(r) = sum_T e^{i k.T} phi_mu(r - A_mu - T), without the
+ *   1/sqrt(N_k) of Sec. II.A; the 1/N_k sits in K instead.
+ *   Primitives phi = N_lm P_lm(r) e^{-alpha r^2}, real solid harmonics, unit
+ *   norm. AO order: shell order as given (callers use atom -> l -> exponent),
+ *   m ascending: p = (x, y, z); d = (xy, yz, 3z^2-r^2, xz, x^2-y^2);
+ *   f = (y(3x^2-y^2), xyz, y(4z^2-x^2-y^2), z(2z^2-3x^2-3y^2),
+ *        x(4z^2-x^2-y^2), z(x^2-y^2), x(x^2-3y^2)).
+ *   Kernel per FFT bin m: x_i = m_i + q_i reduced to [-N_i/2, N_i/2); at an
+ *   exact tie x_i = -N_i/2 the two aliases are averaged; the bin G+q = 0
+ *   takes g0 (0, or pi/omega^2 for erfc with g0_mode = 1).
+ *   Complex numbers are interleaved (re, im) doubles ("c128") unless stated.
+ *
+ * Ownership. The caller owns every buffer passed in; the plan owns its
+ * workspaces (orbitals, Y accumulator, transform scratch, tables). Host
+ * structs are copied at plan creation.
+ *
+ * Streams. Every call is asynchronous on the plan's stream except
+ * occri_plan_create (which uploads tables and synchronises), occri_plan_sync,
+ * and the *_host entry points (which synchronise before returning).
+ *
+ * Errors. Every entry point returns an occri_status; none aborts or throws.
+ * Device-side failures (a non-positive-definite C^H K C) are recorded in the
+ * plan and returned by the next occri_plan_sync.
+ */
+#ifndef OCCRI_H
+#define OCCRI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OCCRI_OK = 0,
+  OCCRI_EINVAL = 1,        /* bad argument: shapes, nocc > nao, grid not {2,3,5}-smooth,
+                              l > 3, omega <= 0 for erfc/erf, NULL required pointer */
+  OCCRI_ENOMEM = 2,        /* a workspace allocation failed */
+  OCCRI_ENOTPD = 3,        /* -C^H K C was not positive definite at some k: a Cholesky pivot
+                              fell to <= tol * (largest diagonal), tol = 1e-10 (FP64) or
+                              1e-5 (mixed) */
+  OCCRI_ECUDA = 4,         /* a CUDA runtime call failed */
+  OCCRI_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+  OCCRI_EUNSUPPORTED = 6   /* valid input outside what this build implements */
+} occri_status;
+
+typedef enum { OCCRI_COULOMB = 0, OCCRI_ERFC = 1, OCCRI_ERF = 2 } occri_kernel_kind;
+
+/* OCCRI_FP64: every step in double precision.
+ * OCCRI_MIXED: AO evaluation, orbitals, pair densities, FFTs, the kernel multiply
+ *   and the Y accumulation in FP32; the contraction (e) accumulates per thread in
+ *   FP32 and across threads in FP64; assembly (f) and E_x in FP64. */
+typedef enum { OCCRI_FP64 = 0, OCCRI_MIXED = 1 } occri_precision;
+
+typedef struct {
+  double a[3][3];          /* lattice rows a_1, a_2, a_3 (bohr) */
+  int natm;
+  const double *xyz;       /* host, natm x 3 atom positions (bohr) */
+} occri_cell;
+
+typedef struct {
+  int nshell;
+  const int *atom;         /* host, nshell atom indices in [0, natm) */
+  const int *l;            /* host, nshell angular momenta in [0, 3] */
+  const double *alpha;     /* host, nshell exponents (bohr^-2), > 0 */
+} occri_basis;
+
+typedef struct {
+  int nk;
+  const double *kfrac;     /* host, nk x 3 fractional k-points; every coordinate must be a
+                              rational j/D with D <= 64 on its axis (all Monkhorst-Pack
+                              meshes qualify), else OCCRI_EUNSUPPORTED */
+} occri_kmesh;
+
+typedef struct {
+  int kind;                /* occri_kernel_kind (Eq. recipcoul) */
+  double omega;            /* range-separation parameter (bohr^-1), > 0 for erfc / erf */
+  int g0_mode;             /* 0: drop the G+q = 0 term; 1: use f(x->0) = pi/omega^2 (erfc only) */
+} occri_kernel;
+
+typedef struct {
+  int nk, nao, nocc, natm, nshell;
+  int grid[3];
+  long long ng;
+  int precision;
+  size_t workspace_bytes;  /* device bytes owned by the plan */
+  int fields_per_wave;     /* pair fields transformed per launch group */
+  long long launches_per_build;  /* kernels one occri_k_build launches */
+} occri_plan_info_t;
+
+/* Stages reported by occri_plan_stage_times. */
+enum {
+  OCCRI_STAGE_ORBITALS = 0,  /* (a)+(b) */
+  OCCRI_STAGE_PAIR_A = 1,    /* (c)+(d) pass A: pair density, FFT along n3 and n2 */
+  OCCRI_STAGE_PAIR_B = 2,    /* (d) pass B: FFT along n1, kernel, inverse along m1, m2 */
+  OCCRI_STAGE_PAIR_C = 3,    /* (d) pass C: inverse along m3, accumulate Y */
+  OCCRI_STAGE_CONTRACT = 4,  /* (e) */
+  OCCRI_STAGE_ASSEMBLE = 5,  /* (f) */
+  OCCRI_NSTAGES = 6
+};
+
+typedef struct occri_plan occri_plan;
+
+/* Validate the problem, build image lists and tables, allocate workspaces.
+ * Problem statement: Sec. II.A (cell, Bloch AOs), Eq. recipcoul (kernel).
+ * grid: N1, N2, N3, each {2,3,5}-smooth in [4, 64]; this build requires
+ * N1 = N2 = N3 and nocc <= 32 (else OCCRI_EUNSUPPORTED). cuda_stream: a cudaStream_t or NULL
+ * (legacy default stream). On success *out owns a plan to be destroyed with
+ * occri_plan_destroy; on failure *out is NULL. */
+int occri_plan_create(occri_plan **out, const occri_cell *cell, const occri_kmesh *kmesh,
+                      const occri_basis *basis, int nocc, const int grid[3],
+                      const occri_kernel *kernel, int precision, void *cuda_stream);
+
+int occri_plan_destroy(occri_plan *plan);
+int occri_plan_info(const occri_plan *plan, occri_plan_info_t *info);
+int occri_plan_set_stream(occri_plan *plan, void *cuda_stream);
+
+/* Synchronise the plan's stream and return the first device-side status
+ * recorded since the previous sync (OCCRI_ENOTPD, ...). *bad_k (may be NULL)
+ * receives the k index of an OCCRI_ENOTPD failure, else -1. */
+int occri_plan_sync(occri_plan *plan, int *bad_k);
+
+/* One exchange build, steps (a)-(f) (Algorithm 3 + ACE assembly).
+ * C_dev : device, c128 [nk][nao][nocc] row-major, read only.
+ * KC_dev: device, c128 [nk][nao][nocc] = K_{mu i}(k) (Eq. occrik), or NULL.
+ * K_dev : device, c128 [nk][nao][nao] ACE-form exchange matrix, or NULL.
+ * Ex_dev: device, 1 double, E_x in Ha per cell, or NULL.
+ * Asynchronous; call occri_plan_sync to observe OCCRI_ENOTPD. */
+int occri_k_build(occri_plan *plan, const void *C_dev, void *KC_dev, void *K_dev,
+                  double *Ex_dev);
+
+/* The same build with HOST buffers (same layouts; NULL outputs skipped): copies
+ * C to the device, builds, copies the outputs back, synchronises. */
+int occri_k_build_host(occri_plan *plan, const void *C_host, void *KC_host, void *K_host,
+                       double *Ex_host);
+
+/* Steps (a)+(b) only (Sec. II.A Bloch sums, Eq. occmo): psi_dev receives
+ * c128 [nk][nocc][N_g] occupied orbitals on the grid (computed in the plan's
+ * precision, widened to c128). Asynchronous. */
+int occri_orbitals(occri_plan *plan, const void *C_dev, void *psi_dev);
+
+/* Adjoint of E_x (hand-written, pair densities recomputed, W never stored).
+ * gEx: the incoming gradient dL/dE_x.
+ * gC_dev: device c128 [nk][nao][nocc] receives gEx * 2 dE_x/dC* =
+ *   gEx * (4/N_k) K_{mu i}(k) (PyTorch's conjugate-Wirtinger convention), or NULL.
+ * gomega_dev: device double receives gEx * dE_x/d omega
+ *   = -gEx (Omega/N_k^2) sum_{kk'ij} sum_m (dv_q(m)/d omega) |rho^_{ij}^{kk'}(m)|^2, or NULL
+ *   (zero for the Coulomb kernel).
+ * Requires a preceding occri_k_build with the same C (its K_{mu i} is reused). */
+int occri_vjp(occri_plan *plan, const void *C_dev, double gEx, void *gC_dev,
+              double *gomega_dev);
+
+/* Sampled stage timing with CUDA events on the plan's stream. every > 0 brackets
+ * every `every`-th pair wave (and every orbital, contraction and assembly stage)
+ * with events; every = 0 turns timing off and discards pending samples. */
+int occri_plan_set_timing(occri_plan *plan, int every);
+
+/* Synchronise, resolve pending events and return, per stage, the accumulated
+ * device milliseconds, the number of timed launches and the number of pair
+ * fields (stages 1-3) or k-points (stages 0, 4, 5) those launches covered.
+ * Arrays have OCCRI_NSTAGES entries; the accumulators are then reset. */
+int occri_plan_stage_times(occri_plan *plan, double *ms, long long *launches, double *units);
+
+const char *occri_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCCRI_H */

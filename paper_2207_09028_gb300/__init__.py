@@ -1,0 +1,306 @@
+"""GB300-native occ-RI-K exact-exchange build (arXiv:2207.09028).
+
+Thin Python binding over the C ABI in ``include/occri.h`` (``liboccri.so``).
+Every step of the exchange build runs in the library's CUDA kernels; this
+module only marshals arguments (torch tensors -> device pointers, the current
+CUDA stream). There is no CPU fallback: if the library is missing, importing
+the entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liboccri.so")
+
+OCCRI_OK = 0
+OCCRI_EINVAL = 1
+OCCRI_ENOMEM = 2
+OCCRI_ENOTPD = 3
+OCCRI_ECUDA = 4
+OCCRI_ETIMEOUT = 5
+OCCRI_EUNSUPPORTED = 6
+
+OCCRI_COULOMB, OCCRI_ERFC, OCCRI_ERF = 0, 1, 2
+OCCRI_FP64, OCCRI_MIXED = 0, 1
+KERNELS = {"coulomb": OCCRI_COULOMB, "erfc": OCCRI_ERFC, "erf": OCCRI_ERF}
+PRECISIONS = {"fp64": OCCRI_FP64, "mixed": OCCRI_MIXED}
+
+
+class occri_cell(ctypes.Structure):
+    _fields_ = [("a", (ctypes.c_double * 3) * 3), ("natm", ctypes.c_int),
+                ("xyz", ctypes.POINTER(ctypes.c_double))]
+
+
+class occri_basis(ctypes.Structure):
+    _fields_ = [("nshell", ctypes.c_int), ("atom", ctypes.POINTER(ctypes.c_int)),
+                ("l", ctypes.POINTER(ctypes.c_int)), ("alpha", ctypes.POINTER(ctypes.c_double))]
+
+
+class occri_kmesh(ctypes.Structure):
+    _fields_ = [("nk", ctypes.c_int), ("kfrac", ctypes.POINTER(ctypes.c_double))]
+
+
+class occri_kernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("omega", ctypes.c_double), ("g0_mode", ctypes.c_int)]
+
+
+class occri_plan_info_t(ctypes.Structure):
+    _fields_ = [("nk", ctypes.c_int), ("nao", ctypes.c_int), ("nocc", ctypes.c_int),
+                ("natm", ctypes.c_int), ("nshell", ctypes.c_int), ("grid", ctypes.c_int * 3),
+                ("ng", ctypes.c_longlong), ("precision", ctypes.c_int),
+                ("workspace_bytes", ctypes.c_size_t), ("fields_per_wave", ctypes.c_int),
+                ("launches_per_build", ctypes.c_longlong)]
+
+
+EXPORTED = ["occri_plan_create", "occri_plan_destroy", "occri_plan_info", "occri_plan_set_stream",
+            "occri_plan_sync", "occri_k_build", "occri_k_build_host", "occri_orbitals",
+            "occri_vjp", "occri_plan_set_timing", "occri_plan_stage_times", "occri_status_string"]
+
+STAGES = ["orbitals", "pair_a", "pair_b", "pair_c", "contract", "assemble"]
+
+_lib_handle = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liboccri.so (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                           "g.build()'` (there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    lib.occri_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(occri_cell),
+                                      ctypes.POINTER(occri_kmesh), ctypes.POINTER(occri_basis), ip,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(occri_kernel),
+                                      ip, vp]
+    lib.occri_plan_destroy.argtypes = [vp]
+    lib.occri_plan_info.argtypes = [vp, ctypes.POINTER(occri_plan_info_t)]
+    lib.occri_plan_set_stream.argtypes = [vp, vp]
+    lib.occri_plan_sync.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.occri_k_build.argtypes = [vp, vp, vp, vp, vp]
+    lib.occri_k_build_host.argtypes = [vp, vp, vp, vp, vp]
+    lib.occri_orbitals.argtypes = [vp, vp, vp]
+    lib.occri_vjp.argtypes = [vp, vp, ctypes.c_double, vp, vp]
+    lib.occri_plan_set_timing.argtypes = [vp, ip]
+    lib.occri_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong),
+                                           ctypes.POINTER(ctypes.c_double)]
+    lib.occri_status_string.argtypes = [ip]
+    lib.occri_status_string.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name != "occri_status_string":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib_handle = lib
+    return lib
+
+
+class OccriError(RuntimeError):
+    def __init__(self, status: int, what: str, bad_k: int = -1):
+        msg = load_library().occri_status_string(status).decode()
+        super().__init__(f"{what}: {msg} (status {status}" + (f", k={bad_k})" if bad_k >= 0 else ")"))
+        self.status = status
+        self.bad_k = bad_k
+
+
+def _check(status: int, what: str):
+    if status != OCCRI_OK:
+        raise OccriError(status, what)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Plan:
+    """An exchange-build plan (owns device workspaces; see occri_plan_create)."""
+
+    def __init__(self, lattice, xyz, shell_atom, shell_l, shell_alpha, kfrac, nocc: int, grid,
+                 kernel: str = "coulomb", omega: float = 0.0, g0_mode: int = 0,
+                 precision: str = "mixed", stream=None):
+        lib = load_library()
+        self._lib = lib
+        lattice = np.ascontiguousarray(lattice, dtype=np.float64)
+        self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self._atom = np.ascontiguousarray(shell_atom, dtype=np.int32)
+        self._l = np.ascontiguousarray(shell_l, dtype=np.int32)
+        self._alpha = np.ascontiguousarray(shell_alpha, dtype=np.float64)
+        self._kfrac = np.ascontiguousarray(kfrac, dtype=np.float64).reshape(-1, 3)
+        cell = occri_cell()
+        for i in range(3):
+            for j in range(3):
+                cell.a[i][j] = float(lattice[i, j])
+        cell.natm = self._xyz.shape[0]
+        cell.xyz = self._xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        basis = occri_basis(len(self._l), self._atom.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                            self._l.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                            self._alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        kmesh = occri_kmesh(self._kfrac.shape[0],
+                            self._kfrac.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        kern = occri_kernel(KERNELS[kernel] if isinstance(kernel, str) else int(kernel),
+                            float(omega), int(g0_mode))
+        g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        handle = ctypes.c_void_p()
+        st = lib.occri_plan_create(ctypes.byref(handle), ctypes.byref(cell), ctypes.byref(kmesh),
+                                   ctypes.byref(basis), int(nocc), g, ctypes.byref(kern), prec,
+                                   stream if stream is not None else _current_stream())
+        _check(st, "occri_plan_create")
+        self._h = handle
+        info = occri_plan_info_t()
+        _check(lib.occri_plan_info(self._h, ctypes.byref(info)), "occri_plan_info")
+        self.nk, self.nao, self.nocc = info.nk, info.nao, info.nocc
+        self.grid = tuple(info.grid)
+        self.ng = info.ng
+        self.precision = info.precision
+        self.workspace_bytes = info.workspace_bytes
+        self.fields_per_wave = info.fields_per_wave
+        self.kernel_kind = kern.kind
+
+    @classmethod
+    def from_workload(cls, w, precision: str = "mixed", **kw) -> "Plan":
+        return cls(w.lattice, w.xyz, w.shell_atom, w.shell_l, w.shell_alpha, w.kfrac, w.nocc,
+                   w.grid, w.kernel, w.omega, w.g0_mode, precision, **kw)
+
+    # -- raw entry points -------------------------------------------------------
+    def set_stream(self, stream=None):
+        _check(self._lib.occri_plan_set_stream(self._h, stream or _current_stream()),
+               "occri_plan_set_stream")
+
+    def info(self) -> dict:
+        info = occri_plan_info_t()
+        _check(self._lib.occri_plan_info(self._h, ctypes.byref(info)), "occri_plan_info")
+        return {f: (tuple(getattr(info, f)) if f == "grid" else getattr(info, f))
+                for f, _ in occri_plan_info_t._fields_}
+
+    def set_timing(self, every: int):
+        _check(self._lib.occri_plan_set_timing(self._h, int(every)), "occri_plan_set_timing")
+
+    def stage_times(self) -> dict:
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        units = (ctypes.c_double * n)()
+        _check(self._lib.occri_plan_stage_times(self._h, ms, cnt, units), "occri_plan_stage_times")
+        return {STAGES[i]: dict(ms=ms[i], launches=cnt[i], units=units[i]) for i in range(n)}
+
+    def sync(self):
+        bad = ctypes.c_int(-1)
+        st = self._lib.occri_plan_sync(self._h, ctypes.byref(bad))
+        if st != OCCRI_OK:
+            raise OccriError(st, "occri_plan_sync", bad.value)
+
+    def k_build(self, C, KC=None, K=None, Ex=None, sync: bool = True):
+        """occri_k_build on device tensors (complex128 C [nk,nao,nocc]); returns (KC, K, Ex)."""
+        import torch
+        self._check_c(C)
+        self.set_stream()
+        _check(self._lib.occri_k_build(self._h, _ptr(C), _ptr(KC), _ptr(K), _ptr(Ex)),
+               "occri_k_build")
+        if sync:
+            self.sync()
+        return KC, K, Ex
+
+    def k_build_host(self, C_host: np.ndarray, want_k: bool = True):
+        """occri_k_build_host: host (numpy or pinned torch) buffers in and out."""
+        C_host = np.ascontiguousarray(C_host, dtype=np.complex128)
+        kc = np.empty((self.nk, self.nao, self.nocc), dtype=np.complex128)
+        k = np.empty((self.nk, self.nao, self.nao), dtype=np.complex128) if want_k else None
+        ex = np.zeros(1, dtype=np.float64)
+        _check(self._lib.occri_k_build_host(self._h, C_host.ctypes.data, kc.ctypes.data,
+                                            None if k is None else k.ctypes.data, ex.ctypes.data),
+               "occri_k_build_host")
+        return kc, k, float(ex[0])
+
+    def orbitals(self, C):
+        import torch
+        self._check_c(C)
+        self.set_stream()
+        psi = torch.empty((self.nk, self.nocc) + self.grid, dtype=torch.complex128, device=C.device)
+        _check(self._lib.occri_orbitals(self._h, _ptr(C), _ptr(psi)), "occri_orbitals")
+        self.sync()
+        return psi
+
+    def vjp(self, C, gEx: float, want_c: bool = True, want_omega: bool = True):
+        import torch
+        self.set_stream()
+        gC = torch.empty_like(C) if want_c else None
+        gw = torch.zeros(1, dtype=torch.float64, device=C.device) if want_omega else None
+        _check(self._lib.occri_vjp(self._h, _ptr(C), float(gEx), _ptr(gC), _ptr(gw)), "occri_vjp")
+        self.sync()
+        return gC, gw
+
+    def build(self, C, want_k: bool = True, sync: bool = True):
+        """Allocate outputs and run one build: returns (KC, K or None, Ex[1])."""
+        import torch
+        dev = C.device
+        KC = torch.empty((self.nk, self.nao, self.nocc), dtype=torch.complex128, device=dev)
+        K = torch.empty((self.nk, self.nao, self.nao), dtype=torch.complex128, device=dev) if want_k else None
+        Ex = torch.zeros(1, dtype=torch.float64, device=dev)
+        return self.k_build(C, KC, K, Ex, sync=sync)
+
+    def _check_c(self, C):
+        import torch
+        if C.dtype != torch.complex128 or not C.is_cuda or not C.is_contiguous():
+            raise ValueError("C must be a contiguous complex128 CUDA tensor")
+        if tuple(C.shape) != (self.nk, self.nao, self.nocc):
+            raise ValueError(f"C must have shape {(self.nk, self.nao, self.nocc)}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.occri_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def exchange_energy(plan: Plan, C, omega=None):
+    """E_x(C[, omega]) as a differentiable torch scalar (backward = occri_vjp).
+
+    Gradients: C in the conjugate-Wirtinger convention, (4/N_k) K_{mu i}(k) times
+    the incoming gradient; omega via the hand-written d v/d omega pass. omega
+    must equal the plan's omega (it is an input only so that autograd can
+    route d E_x/d omega).
+    """
+    import torch
+
+    class _ExchangeEnergy(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, Cin, w):
+            KC, _, Ex = plan.build(Cin.detach().contiguous(), want_k=False)
+            ctx.save_for_backward(Cin)
+            ctx.has_w = w is not None
+            ctx.w_device = w.device if w is not None else None
+            return Ex[0].clone()
+
+        @staticmethod
+        def backward(ctx, g):
+            (Cin,) = ctx.saved_tensors
+            gC, gw = plan.vjp(Cin.detach().contiguous(), float(g),
+                              want_c=ctx.needs_input_grad[0],
+                              want_omega=ctx.has_w and ctx.needs_input_grad[1])
+            gw_out = gw[0].to(device=ctx.w_device) if gw is not None else None
+            return gC, gw_out
+
+    return _ExchangeEnergy.apply(C, omega)
+
+
+__all__ = ["Plan", "OccriError", "load_library", "exchange_energy", "EXPORTED", "LIB_PATH"] + [
+    n for n in globals() if n.startswith("OCCRI_")]

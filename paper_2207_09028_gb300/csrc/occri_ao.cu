@@ -1,0 +1,372 @@
+// occri_ao.cu -- Bloch-summed AOs evaluated on the fly (integral-direct, Algorithm 4):
+//   (a)+(b) psi_{ik}(r) = sum_mu C^k_{mu i} chi_{mu k}(r)                  (Eq. occmo)
+//   (e)     K_{mu i}(k) = -(Omega/(N_k N_g)) sum_r conj(chi_{mu k}(r)) Y_{ik}(r)  (Eq. occrik)
+// with chi_{mu k}(r) = sum_T e^{i k.T} phi_mu(r - A - T) (Sec. II.A).
+//
+// The image sum is split as T = T0(r, A) + T': T0 brings r - A into the
+// Wigner-Seitz cell (precomputed per grid point and atom), T' runs over one
+// master list of lattice vectors sorted by length. Every thread of a warp walks
+// the same prefix of that list (a shell's prefix covers its screening radius
+// plus the largest |r - A - T0|), so the image offsets and the phase table
+// e^{i k.T'} are warp-uniform loads. chi itself is never stored.
+//
+// In FP32 the displacement r - A - T is formed from hi/lo float pairs so that
+// it is accurate to an ulp of its own size, not of |T|.
+#include <cuda_runtime.h>
+
+#include "occri_device.cuh"
+#include "occri_internal.h"
+
+namespace occri {
+namespace ao {
+
+using dev::cis_frac;
+using dev::exp_t;
+
+// Unnormalised real solid harmonics, m = -l..l (p: x, y, z).
+template <typename T, int L>
+__device__ __forceinline__ void solid(T x, T y, T z, T (&P)[2 * L + 1]) {
+  if constexpr (L == 0) {
+    P[0] = T(1);
+  } else if constexpr (L == 1) {
+    P[0] = x; P[1] = y; P[2] = z;
+  } else if constexpr (L == 2) {
+    P[0] = x * y;
+    P[1] = y * z;
+    P[2] = T(2) * z * z - x * x - y * y;
+    P[3] = x * z;
+    P[4] = x * x - y * y;
+  } else {
+    const T x2 = x * x, y2 = y * y, z2 = z * z;
+    P[0] = y * (T(3) * x2 - y2);
+    P[1] = x * y * z;
+    P[2] = y * (T(4) * z2 - x2 - y2);
+    P[3] = z * (T(2) * z2 - T(3) * x2 - T(3) * y2);
+    P[4] = x * (T(4) * z2 - x2 - y2);
+    P[5] = z * (x2 - y2);
+    P[6] = x * (x2 - T(3) * y2);
+  }
+}
+
+// r_n - A - T0 for one grid point and atom, in the working precision.
+template <typename T> struct Disp;
+template <> struct Disp<double> { double x, y, z; };
+template <> struct Disp<float> { float xh, yh, zh, xl, yl, zl; };
+
+__device__ __forceinline__ void load_disp(const AOParams& p, int atom, long long n, Disp<double>* d) {
+  const double* b = p.d0_d + (size_t)atom * 3 * p.ng;
+  d->x = b[n];
+  d->y = b[p.ng + n];
+  d->z = b[2 * p.ng + n];
+}
+__device__ __forceinline__ void load_disp(const AOParams& p, int atom, long long n, Disp<float>* d) {
+  const float* h = p.d0_hi + (size_t)atom * 3 * p.ng;
+  const float* l = p.d0_lo + (size_t)atom * 3 * p.ng;
+  d->xh = h[n]; d->yh = h[p.ng + n]; d->zh = h[2 * p.ng + n];
+  d->xl = l[n]; d->yl = l[p.ng + n]; d->zl = l[2 * p.ng + n];
+}
+
+__device__ __forceinline__ void image_disp(const AOParams& p, const Disp<double>& d, int j,
+                                           double* x, double* y, double* z) {
+  *x = d.x - p.img_d[j];
+  *y = d.y - p.img_d[p.nimg + j];
+  *z = d.z - p.img_d[2 * p.nimg + j];
+}
+__device__ __forceinline__ void image_disp(const AOParams& p, const Disp<float>& d, int j,
+                                           float* x, float* y, float* z) {
+  *x = (d.xh - p.img_hi[j]) + (d.xl - p.img_lo[j]);
+  *y = (d.yh - p.img_hi[p.nimg + j]) + (d.yl - p.img_lo[p.nimg + j]);
+  *z = (d.zh - p.img_hi[2 * p.nimg + j]) + (d.zl - p.img_lo[2 * p.nimg + j]);
+}
+
+template <typename T> __device__ __forceinline__ T sh_alpha(const ShellDev& s);
+template <> __device__ __forceinline__ double sh_alpha<double>(const ShellDev& s) { return s.alpha; }
+template <> __device__ __forceinline__ float sh_alpha<float>(const ShellDev& s) { return s.alpha_f; }
+template <typename T> __device__ __forceinline__ T sh_alpha_lo(const ShellDev& s);
+template <> __device__ __forceinline__ double sh_alpha_lo<double>(const ShellDev&) { return 0.0; }
+template <> __device__ __forceinline__ float sh_alpha_lo<float>(const ShellDev& s) { return s.alpha_lo; }
+template <typename T> __device__ __forceinline__ T sh_rcut2(const ShellDev& s);
+template <> __device__ __forceinline__ double sh_rcut2<double>(const ShellDev& s) { return s.rcut2; }
+template <> __device__ __forceinline__ float sh_rcut2<float>(const ShellDev& s) { return s.rcut2_f; }
+
+// e^{i k.T0} for the packed T0 of (atom, n).
+template <typename T>
+__device__ __forceinline__ cplx_t<T> phase_t0(const AOParams& p, int atom, long long n, int k) {
+  int t[3];
+  dev::unpack_t0(p.t0[(size_t)atom * p.ng + n], &t[0], &t[1], &t[2]);
+  long long num = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    num += (long long)p.kint[k * 3 + d] * t[d] * (p.Dc / p.D[d]);
+  return cis_frac<T>(num, p.Dc, +1);
+}
+
+// chi_{mu k}(r_n) / N_mu for the 2L+1 functions of one shell, without the e^{i k.T0}
+// factor (the normalisation is applied in FP64 outside: folded into C for (b), into
+// the reduction for (e)). In FP32 the exponent uses alpha = alpha_f + alpha_lo.
+template <typename T, int L>
+__device__ __forceinline__ void shell_values(const AOParams& p, const ShellDev& sh, int k,
+                                             const Disp<T>& d, T (&cr)[2 * L + 1],
+                                             T (&ci)[2 * L + 1]) {
+  const cplx_t<T>* ph = reinterpret_cast<const cplx_t<T>*>(p.img_phase) + (size_t)k * p.nimg;
+  const T alpha = sh_alpha<T>(sh), alo = sh_alpha_lo<T>(sh), rc2 = sh_rcut2<T>(sh);
+#pragma unroll
+  for (int m = 0; m < 2 * L + 1; ++m) {
+    cr[m] = T(0);
+    ci[m] = T(0);
+  }
+  for (int j = 0; j < sh.nimg; ++j) {
+    T x, y, z;
+    image_disp(p, d, j, &x, &y, &z);
+    const T r2 = x * x + y * y + z * z;
+    if (r2 <= rc2) {
+      const T e = exp_t(-(alpha * r2 + alo * r2));
+      T P[2 * L + 1];
+      solid<T, L>(x, y, z, P);
+      const cplx_t<T> w = ph[j];
+#pragma unroll
+      for (int m = 0; m < 2 * L + 1; ++m) {
+        const T v = P[m] * e;
+        cr[m] += w.x * v;
+        ci[m] += w.y * v;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ (a)+(b)
+
+// psi += (N_mu C_mu i) chi_mu / N_mu; in FP32 the scaled coefficient is a hi/lo pair.
+__device__ __forceinline__ void cmac(const double2* cs, size_t idx, double xr, double xi,
+                                     double& ar, double& ai) {
+  const double2 c = cs[idx];
+  ar += c.x * xr - c.y * xi;
+  ai += c.x * xi + c.y * xr;
+}
+__device__ __forceinline__ void cmac(const float4* cs, size_t idx, float xr, float xi, float& ar,
+                                     float& ai) {
+  const float4 c = cs[idx];
+  ar += (c.x * xr - c.y * xi) + (c.z * xr - c.w * xi);
+  ai += (c.x * xi + c.y * xr) + (c.z * xi + c.w * xr);
+}
+template <typename T> struct CsType;
+template <> struct CsType<double> { using type = double2; };
+template <> struct CsType<float> { using type = float4; };
+
+template <typename T, int L, int NI>
+__device__ __forceinline__ void orbital_shell(const AOParams& p, const ShellDev& sh, int k,
+                                              const Disp<T>& d, cplx_t<T> ph0, int i0,
+                                              T (&ar)[NI], T (&ai)[NI]) {
+  using CS = typename CsType<T>::type;
+  const CS* cs = reinterpret_cast<const CS*>(p.cs);
+  T cr[2 * L + 1], ci[2 * L + 1];
+  shell_values<T, L>(p, sh, k, d, cr, ci);
+#pragma unroll
+  for (int m = 0; m < 2 * L + 1; ++m) {
+    const T xr = cr[m] * ph0.x - ci[m] * ph0.y;
+    const T xi = cr[m] * ph0.y + ci[m] * ph0.x;
+    const size_t row = ((size_t)k * p.nao + sh.ao + m) * p.nocc;
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+      if (i0 + i < p.nocc) cmac(cs, row + i0 + i, xr, xi, ar[i], ai[i]);
+  }
+}
+
+// Scaled coefficients N_mu C^k_{mu i}, formed in FP64 (and split hi/lo for FP32).
+__global__ void scale_c_kernel_d(const double2* __restrict__ C, const double* __restrict__ nrm,
+                                 double2* __restrict__ out, int nao, int nocc, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double s = nrm[(e / nocc) % nao];
+    out[e] = make_double2(s * C[e].x, s * C[e].y);
+  }
+}
+__global__ void scale_c_kernel_f(const double2* __restrict__ C, const double* __restrict__ nrm,
+                                 float4* __restrict__ out, int nao, int nocc, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double s = nrm[(e / nocc) % nao];
+    const double x = s * C[e].x, y = s * C[e].y;
+    const float xh = (float)x, yh = (float)y;
+    out[e] = make_float4(xh, yh, (float)(x - (double)xh), (float)(y - (double)yh));
+  }
+}
+
+template <typename T, int NI>
+__global__ void __launch_bounds__(128)
+orbitals_kernel(AOParams p, cplx_t<T>* __restrict__ psi, int i0) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (n >= p.ng) return;
+  T ar[NI], ai[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) { ar[i] = T(0); ai[i] = T(0); }
+  for (int a = 0; a < p.natm; ++a) {
+    Disp<T> d;
+    load_disp(p, a, n, &d);
+    const cplx_t<T> ph0 = phase_t0<T>(p, a, n, k);
+    for (int s = p.atom_shell0[a]; s < p.atom_shell0[a + 1]; ++s) {
+      const ShellDev sh = p.shells[s];
+      switch (sh.l) {
+        case 0: orbital_shell<T, 0, NI>(p, sh, k, d, ph0, i0, ar, ai); break;
+        case 1: orbital_shell<T, 1, NI>(p, sh, k, d, ph0, i0, ar, ai); break;
+        case 2: orbital_shell<T, 2, NI>(p, sh, k, d, ph0, i0, ar, ai); break;
+        default: orbital_shell<T, 3, NI>(p, sh, k, d, ph0, i0, ar, ai); break;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NI; ++i)
+    if (i0 + i < p.nocc) psi[((size_t)k * p.nocc + i0 + i) * p.ng + n] = cplx_t<T>{ar[i], ai[i]};
+}
+
+// ------------------------------------------------------------------ (e)
+
+template <typename T, int L, int NI>
+__global__ void __launch_bounds__(256)
+contract_kernel(AOParams p, const cplx_t<T>* __restrict__ Y, double2* __restrict__ kc,
+                const int* __restrict__ shell_list, int i0, long long chunk, double scale) {
+  constexpr int NM = 2 * L + 1;
+  constexpr int NV = 2 * NM * NI;
+  const int s = shell_list[blockIdx.z];
+  const int k = blockIdx.y;
+  const ShellDev sh = p.shells[s];
+  const long long start = (long long)blockIdx.x * chunk;
+  const long long end = min(p.ng, start + chunk);
+  T ar[NM][NI], ai[NM][NI];
+#pragma unroll
+  for (int m = 0; m < NM; ++m)
+#pragma unroll
+    for (int i = 0; i < NI; ++i) { ar[m][i] = T(0); ai[m][i] = T(0); }
+  for (long long n = start + threadIdx.x; n < end; n += blockDim.x) {
+    Disp<T> d;
+    load_disp(p, sh.atom, n, &d);
+    const cplx_t<T> ph0 = phase_t0<T>(p, sh.atom, n, k);
+    T cr[NM], ci[NM];
+    shell_values<T, L>(p, sh, k, d, cr, ci);
+    T yr[NI], yi[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      if (i0 + i < p.nocc) {
+        const cplx_t<T> y = Y[((size_t)k * p.nocc + i0 + i) * p.ng + n];
+        yr[i] = y.x; yi[i] = y.y;
+      } else {
+        yr[i] = T(0); yi[i] = T(0);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const T xr = cr[m] * ph0.x - ci[m] * ph0.y;
+      const T xi = cr[m] * ph0.y + ci[m] * ph0.x;
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {  // conj(chi) * y
+        ar[m][i] += xr * yr[i] + xi * yi[i];
+        ai[m][i] += xr * yi[i] - xi * yr[i];
+      }
+    }
+  }
+  __shared__ double red[8][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int m = 0; m < NM; ++m)
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      double vr = double(ar[m][i]), vi = double(ai[m][i]);
+      for (int o = 16; o > 0; o >>= 1) {
+        vr += __shfl_xor_sync(0xffffffffu, vr, o);
+        vi += __shfl_xor_sync(0xffffffffu, vi, o);
+      }
+      if (lane == 0) {
+        red[warp][2 * (m * NI + i)] = vr;
+        red[warp][2 * (m * NI + i) + 1] = vi;
+      }
+    }
+  __syncthreads();
+  for (int v = threadIdx.x; v < NV; v += blockDim.x) {
+    const int mi = v >> 1, m = mi / NI, i = mi - (mi / NI) * NI;
+    if (i0 + i >= p.nocc) continue;
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][v];
+    double* dst = reinterpret_cast<double*>(kc + ((size_t)k * p.nao + sh.ao + m) * p.nocc + i0 + i);
+    atomicAdd(dst + (v & 1), scale * sh.norm[m] * t);
+  }
+}
+
+template <typename T>
+__global__ void widen_kernel(const cplx_t<T>* __restrict__ in, double2* __restrict__ out,
+                             long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = make_double2(double(in[e].x), double(in[e].y));
+}
+
+
+}  // namespace ao
+
+template <>
+cudaError_t launch_scale_c<double>(const Plan& p, const double2* C, cudaStream_t s) {
+  const long long n = (long long)p.nk * p.nao * p.nocc;
+  ao::scale_c_kernel_d<<<2 * 152, 256, 0, s>>>(C, p.ao_norm, (double2*)p.cs, p.nao, p.nocc, n);
+  return cudaGetLastError();
+}
+template <>
+cudaError_t launch_scale_c<float>(const Plan& p, const double2* C, cudaStream_t s) {
+  const long long n = (long long)p.nk * p.nao * p.nocc;
+  ao::scale_c_kernel_f<<<2 * 152, 256, 0, s>>>(C, p.ao_norm, (float4*)p.cs, p.nao, p.nocc, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_orbitals(const Plan& p, cudaStream_t s) {
+  constexpr int NI = kOrbChunk;
+  const AOParams ap = p.ao_params();
+  dim3 grid((unsigned)((p.ng + 127) / 128), p.nk);
+  for (int i0 = 0; i0 < p.nocc; i0 += NI)
+    ao::orbitals_kernel<T, NI><<<grid, 128, 0, s>>>(ap, (cplx_t<T>*)p.psi, i0);
+  return cudaGetLastError();
+}
+
+template <typename T, int L>
+static void launch_contract_l(const Plan& p, const AOParams& ap, cudaStream_t s) {
+  constexpr int NI = contract_chunk<T>();
+  const int ns = (int)p.shells_by_l[L].size();
+  if (ns == 0) return;
+  const long long target = 4LL * 152 * 8;   // CTAs to fill the GPU several times over
+  long long parts = (target + (long long)p.nk * ns - 1) / ((long long)p.nk * ns);
+  const long long maxparts = (p.ng + 1023) / 1024;
+  if (parts > maxparts) parts = maxparts;
+  if (parts < 1) parts = 1;
+  const long long chunk = (p.ng + parts - 1) / parts;
+  // Y carries N_g/(4 pi) (see PairParams), hence -Omega 4 pi / (N_k N_g^2)
+  const double scale = -p.omega_cell * 4.0 * 3.14159265358979323846 /
+                       ((double)p.nk * (double)p.ng * (double)p.ng);
+  for (int i0 = 0; i0 < p.nocc; i0 += NI)
+    ao::contract_kernel<T, L, NI><<<dim3((unsigned)parts, p.nk, ns), 256, 0, s>>>(
+        ap, (const cplx_t<T>*)p.Y, p.kc, p.shell_list_l[L], i0, chunk, scale);
+}
+
+template <typename T>
+cudaError_t launch_contract(const Plan& p, cudaStream_t s) {
+  const AOParams ap = p.ao_params();
+  launch_contract_l<T, 0>(p, ap, s);
+  launch_contract_l<T, 1>(p, ap, s);
+  launch_contract_l<T, 2>(p, ap, s);
+  launch_contract_l<T, 3>(p, ap, s);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s) {
+  const long long n = (long long)p.nk * p.nocc * p.ng;
+  ao::widen_kernel<T><<<4 * 152, 256, 0, s>>>((const cplx_t<T>*)p.psi, (double2*)out, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_orbitals<float>(const Plan&, cudaStream_t);
+template cudaError_t launch_orbitals<double>(const Plan&, cudaStream_t);
+template cudaError_t launch_contract<float>(const Plan&, cudaStream_t);
+template cudaError_t launch_contract<double>(const Plan&, cudaStream_t);
+template cudaError_t launch_widen<float>(const Plan&, void*, cudaStream_t);
+template cudaError_t launch_widen<double>(const Plan&, void*, cudaStream_t);
+
+}  // namespace occri

@@ -1,0 +1,915 @@
+// occri_api.cu -- the C ABI (include/occri.h): plan creation, build orchestration,
+// the FP64 occ-RI (ACE) assembly (step f) and the E_x adjoint.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "occri_device.cuh"
+#include "occri_internal.h"
+
+namespace occri {
+
+static const double kPiD = 3.14159265358979323846;
+
+bool grid_edge_supported(int n) {
+  switch (n) {
+#define OCCRI_EDGE_CASE(NN) case NN:
+    OCCRI_FOR_EACH_N(OCCRI_EDGE_CASE)
+#undef OCCRI_EDGE_CASE
+    return true;
+    default:
+      return false;
+  }
+}
+
+AOParams Plan::ao_params() const {
+  AOParams a;
+  a.nk = nk; a.nao = nao; a.nocc = nocc; a.natm = natm; a.nshell = nshell;
+  a.ng = ng;
+  for (int d = 0; d < 3; ++d) { a.N[d] = N[d]; a.D[d] = D[d]; }
+  a.Dc = D[0] * D[1] * D[2];
+  a.shells = shells;
+  a.atom_shell0 = atom_shell0;
+  a.nimg = nimg;
+  a.img_d = img_d; a.img_hi = img_hi; a.img_lo = img_lo; a.img_phase = img_phase;
+  a.d0_d = d0_d; a.d0_hi = d0_hi; a.d0_lo = d0_lo; a.t0 = t0; a.kint = kint;
+  a.cs = cs;
+  return a;
+}
+
+PairParams Plan::pair_params() const {
+  PairParams q;
+  q.nk = nk; q.nocc = nocc; q.ng = ng; q.N1 = N[0];
+  q.k = 0; q.kp0 = 0; q.nkp = 1;
+  for (int d = 0; d < 3; ++d) q.D[d] = D[d];
+  q.kint = kint;
+  // reciprocal vectors b_i (rows): B = 2 pi (A^{-1})^T
+  double inv[3][3];
+  const double (*a)[3] = lat;
+  const double det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) -
+                     a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                     a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+  inv[0][0] = (a[1][1] * a[2][2] - a[1][2] * a[2][1]) / det;
+  inv[0][1] = (a[0][2] * a[2][1] - a[0][1] * a[2][2]) / det;
+  inv[0][2] = (a[0][1] * a[1][2] - a[0][2] * a[1][1]) / det;
+  inv[1][0] = (a[1][2] * a[2][0] - a[1][0] * a[2][2]) / det;
+  inv[1][1] = (a[0][0] * a[2][2] - a[0][2] * a[2][0]) / det;
+  inv[1][2] = (a[0][2] * a[1][0] - a[0][0] * a[1][2]) / det;
+  inv[2][0] = (a[1][0] * a[2][1] - a[1][1] * a[2][0]) / det;
+  inv[2][1] = (a[0][1] * a[2][0] - a[0][0] * a[2][1]) / det;
+  inv[2][2] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) / det;
+  double b[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) b[i][j] = 2.0 * kPiD * inv[j][i];
+  auto dot = [&](int i, int j) { return b[i][0] * b[j][0] + b[i][1] * b[j][1] + b[i][2] * b[j][2]; };
+  q.g[0] = dot(0, 0); q.g[1] = dot(1, 1); q.g[2] = dot(2, 2);
+  q.g[3] = dot(0, 1); q.g[4] = dot(0, 2); q.g[5] = dot(1, 2);
+  q.kind = kernel.kind;
+  q.omega = kernel.omega;
+  q.inv4w2 = (kernel.kind == OCCRI_COULOMB) ? 0.0 : 1.0 / (4.0 * kernel.omega * kernel.omega);
+  // g0 = pi/omega^2 and d g0/d omega = -2 pi/omega^3, both in units of 4 pi
+  q.g0 = (kernel.g0_mode == 1) ? 0.25 / (kernel.omega * kernel.omega) : 0.0;
+  q.dg0 = (kernel.g0_mode == 1) ? -0.5 / (kernel.omega * kernel.omega * kernel.omega) : 0.0;
+  return q;
+}
+
+// ------------------------------------------------------------------ primitives (host)
+
+namespace {
+
+struct Mono { int a, b, c; double v; };
+
+// Real solid harmonics in AO order as monomial lists.
+const std::vector<std::vector<Mono>>& solid_table(int l) {
+  static const std::vector<std::vector<Mono>> t0 = {{{0, 0, 0, 1.0}}};
+  static const std::vector<std::vector<Mono>> t1 = {
+      {{1, 0, 0, 1.0}}, {{0, 1, 0, 1.0}}, {{0, 0, 1, 1.0}}};
+  static const std::vector<std::vector<Mono>> t2 = {
+      {{1, 1, 0, 1.0}},
+      {{0, 1, 1, 1.0}},
+      {{0, 0, 2, 2.0}, {2, 0, 0, -1.0}, {0, 2, 0, -1.0}},
+      {{1, 0, 1, 1.0}},
+      {{2, 0, 0, 1.0}, {0, 2, 0, -1.0}}};
+  static const std::vector<std::vector<Mono>> t3 = {
+      {{2, 1, 0, 3.0}, {0, 3, 0, -1.0}},
+      {{1, 1, 1, 1.0}},
+      {{0, 1, 2, 4.0}, {2, 1, 0, -1.0}, {0, 3, 0, -1.0}},
+      {{0, 0, 3, 2.0}, {2, 0, 1, -3.0}, {0, 2, 1, -3.0}},
+      {{1, 0, 2, 4.0}, {3, 0, 0, -1.0}, {1, 2, 0, -1.0}},
+      {{2, 0, 1, 1.0}, {0, 2, 1, -1.0}},
+      {{3, 0, 0, 1.0}, {1, 2, 0, -3.0}}};
+  switch (l) {
+    case 0: return t0;
+    case 1: return t1;
+    case 2: return t2;
+    default: return t3;
+  }
+}
+
+double odd_factorial(int n) {  // (n)!! for odd n >= -1
+  double r = 1.0;
+  for (int k = n; k > 1; k -= 2) r *= k;
+  return r;
+}
+
+// integral of x^a y^b z^c exp(-p r^2) over R^3
+double moment(int a, int b, int c, double p) {
+  double r = 1.0;
+  const int e[3] = {a, b, c};
+  for (int d = 0; d < 3; ++d) {
+    if (e[d] % 2) return 0.0;
+    r *= odd_factorial(e[d] - 1) / std::pow(2.0 * p, e[d] / 2) * std::sqrt(kPiD / p);
+  }
+  return r;
+}
+
+void shell_norms(int l, double alpha, double* out) {
+  const auto& tab = solid_table(l);
+  for (size_t m = 0; m < tab.size(); ++m) {
+    double s = 0.0;
+    for (const Mono& x : tab[m])
+      for (const Mono& y : tab[m]) s += x.v * y.v * moment(x.a + y.a, x.b + y.b, x.c + y.c, 2.0 * alpha);
+    out[m] = 1.0 / std::sqrt(s);
+  }
+}
+
+// Radius beyond which N_lm |P_lm| e^{-alpha r^2} < eps for every m (|P_lm| <= sum|coeff| r^l).
+double shell_cutoff(int l, double alpha, double eps) {
+  double nrm[7];
+  shell_norms(l, alpha, nrm);
+  const auto& tab = solid_table(l);
+  double c = 0.0;
+  for (size_t m = 0; m < tab.size(); ++m) {
+    double s = 0.0;
+    for (const Mono& x : tab[m]) s += std::fabs(x.v);
+    c = std::max(c, nrm[m] * s);
+  }
+  auto f = [&](double r) {
+    return std::log(c) + l * std::log(std::max(r, 1e-300)) - alpha * r * r - std::log(eps);
+  };
+  double lo = (l > 0) ? std::sqrt(l / (2.0 * alpha)) : 0.0;
+  if (f(lo) <= 0) return lo;
+  double hi = std::max(lo, 1.0);
+  while (f(hi) > 0) hi *= 2.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (f(mid) > 0) lo = mid; else hi = mid;
+  }
+  return hi;
+}
+
+bool smooth235(int n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  while (n % 5 == 0) n /= 5;
+  return n == 1;
+}
+
+void inv3(const double a[3][3], double inv[3][3]) {
+  const double det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) -
+                     a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                     a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+  inv[0][0] = (a[1][1] * a[2][2] - a[1][2] * a[2][1]) / det;
+  inv[0][1] = (a[0][2] * a[2][1] - a[0][1] * a[2][2]) / det;
+  inv[0][2] = (a[0][1] * a[1][2] - a[0][2] * a[1][1]) / det;
+  inv[1][0] = (a[1][2] * a[2][0] - a[1][0] * a[2][2]) / det;
+  inv[1][1] = (a[0][0] * a[2][2] - a[0][2] * a[2][0]) / det;
+  inv[1][2] = (a[0][2] * a[1][0] - a[0][0] * a[1][2]) / det;
+  inv[2][0] = (a[1][0] * a[2][1] - a[1][1] * a[2][0]) / det;
+  inv[2][1] = (a[0][1] * a[2][0] - a[0][0] * a[2][1]) / det;
+  inv[2][2] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) / det;
+}
+
+template <typename X>
+cudaError_t dalloc(X** p, size_t count, size_t* total) {
+  *total += count * sizeof(X);
+  return cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(X));
+}
+
+template <typename X>
+cudaError_t upload(X** p, const std::vector<X>& v, size_t* total) {
+  cudaError_t e = dalloc(p, v.size(), total);
+  if (e != cudaSuccess) return e;
+  if (v.empty()) return cudaSuccess;
+  return cudaMemcpy(*p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice);
+}
+
+// ------------------------------------------------------------------ step (f) kernels
+
+__device__ void record_status(int* status, int code, int k) {
+  if (atomicCAS(status, 0, code) == 0) status[1] = k;
+}
+
+// One CTA per k: M = C^H KC (Hermitised), -M = L L^H, xi = KC L^{-H},
+// K = -xi xi^H, ek[k] = Re Tr M.
+__global__ void __launch_bounds__(256)
+ace_kernel(const double2* __restrict__ C, const double2* __restrict__ kc, double2* __restrict__ xi,
+           double2* __restrict__ mout, double* __restrict__ ek, double2* __restrict__ K, int nao,
+           int nocc, double pivot_tol, int* status) {
+  extern __shared__ double2 sm[];
+  double2* M = sm;                   // nocc*nocc
+  double2* L = sm + nocc * nocc;     // nocc*nocc
+  __shared__ int ok;
+  const int k = blockIdx.x;
+  const double2* Ck = C + (size_t)k * nao * nocc;
+  const double2* KCk = kc + (size_t)k * nao * nocc;
+  for (int e = threadIdx.x; e < nocc * nocc; e += blockDim.x) {
+    const int i = e / nocc, j = e - (e / nocc) * nocc;
+    double sr = 0.0, si = 0.0;
+    for (int mu = 0; mu < nao; ++mu) {
+      const double2 c = Ck[(size_t)mu * nocc + i], x = KCk[(size_t)mu * nocc + j];
+      sr += c.x * x.x + c.y * x.y;   // conj(c) * x
+      si += c.x * x.y - c.y * x.x;
+    }
+    L[e] = make_double2(sr, si);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nocc * nocc; e += blockDim.x) {
+    const int i = e / nocc, j = e - (e / nocc) * nocc;
+    const double2 a = L[i * nocc + j], b = L[j * nocc + i];
+    M[e] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    double tr = 0.0;
+    for (int i = 0; i < nocc; ++i) tr += M[i * nocc + i].x;
+    ek[k] = tr;
+    for (int e = 0; e < nocc * nocc; ++e) mout[(size_t)k * nocc * nocc + e] = M[e];
+    // Cholesky of A = -M (lower, complex Hermitian); a pivot at or below
+    // pivot_tol * max_j A_jj counts as not positive definite.
+    double amax = 0.0;
+    for (int j = 0; j < nocc; ++j) amax = fmax(amax, -M[j * nocc + j].x);
+    for (int j = 0; j < nocc && ok; ++j) {
+      double d = -M[j * nocc + j].x;
+      for (int l = 0; l < j; ++l) d -= L[j * nocc + l].x * L[j * nocc + l].x + L[j * nocc + l].y * L[j * nocc + l].y;
+      if (!(d > pivot_tol * amax) || !isfinite(d)) { ok = 0; break; }
+      const double ljj = sqrt(d);
+      L[j * nocc + j] = make_double2(ljj, 0.0);
+      for (int i = j + 1; i < nocc; ++i) {
+        double ar = -M[i * nocc + j].x, ai = -M[i * nocc + j].y;
+        for (int l = 0; l < j; ++l) {  // - L_il conj(L_jl)
+          const double2 x = L[i * nocc + l], y = L[j * nocc + l];
+          ar -= x.x * y.x + x.y * y.y;
+          ai -= x.y * y.x - x.x * y.y;
+        }
+        L[i * nocc + j] = make_double2(ar / ljj, ai / ljj);
+      }
+      for (int i = 0; i < j; ++i) L[i * nocc + j] = make_double2(0.0, 0.0);
+    }
+    if (!ok) record_status(status, OCCRI_ENOTPD, k);
+  }
+  __syncthreads();
+  if (!ok) return;
+  // xi L^H = KC  ->  xi_j = (KC_j - sum_{l<j} xi_l conj(L_jl)) / L_jj
+  double2* xik = xi + (size_t)k * nao * nocc;
+  for (int mu = threadIdx.x; mu < nao; mu += blockDim.x) {
+    for (int j = 0; j < nocc; ++j) {
+      double2 v = KCk[(size_t)mu * nocc + j];
+      for (int l = 0; l < j; ++l) {
+        const double2 x = xik[(size_t)mu * nocc + l], y = L[j * nocc + l];
+        v.x -= x.x * y.x + x.y * y.y;
+        v.y -= x.y * y.x - x.x * y.y;
+      }
+      const double ljj = L[j * nocc + j].x;
+      xik[(size_t)mu * nocc + j] = make_double2(v.x / ljj, v.y / ljj);
+    }
+  }
+  __syncthreads();
+  if (K == nullptr) return;
+  double2* Kk = K + (size_t)k * nao * nao;
+  for (size_t e = threadIdx.x; e < (size_t)nao * nao; e += blockDim.x) {
+    const int mu = (int)(e / nao), nu = (int)(e - (e / nao) * nao);
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < nocc; ++j) {  // xi_mu conj(xi_nu)
+      const double2 a = xik[(size_t)mu * nocc + j], b = xik[(size_t)nu * nocc + j];
+      sr += a.x * b.x + a.y * b.y;
+      si += a.y * b.x - a.x * b.y;
+    }
+    Kk[e] = make_double2(-sr, -si);
+  }
+}
+
+__global__ void ex_kernel(const double* __restrict__ ek, int nk, double* __restrict__ ex) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < nk; ++k) s += ek[k];
+    *ex = s / nk;
+  }
+}
+
+__global__ void scale_copy_kernel(const double2* __restrict__ in, double2* __restrict__ out,
+                                  long long n, double s) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = make_double2(s * in[e].x, s * in[e].y);
+}
+
+__global__ void domega_finish_kernel(const double* __restrict__ acc, double s, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = s * acc[0];
+}
+
+void free_plan(Plan* p) {
+  if (!p) return;
+  void* bufs[] = {p->shells, p->atom_shell0, p->img_d, p->img_hi, p->img_lo, p->img_phase,
+                  p->d0_d, p->d0_hi, p->d0_lo, p->t0, p->kint, p->psi, p->Y, p->scratch,
+                  p->kc, p->xi, p->mmat, p->ek, p->dacc, p->status, p->h_c, p->h_kc, p->h_k,
+                  p->h_ex, p->ao_norm, p->cs, p->shell_list_l[0], p->shell_list_l[1], p->shell_list_l[2],
+                  p->shell_list_l[3]};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (cudaEvent_t e : p->ev_used) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_free) cudaEventDestroy(e);
+  delete p;
+}
+
+}  // namespace
+
+}  // namespace occri
+
+using occri::Plan;
+
+struct occri_plan {
+  Plan* p;
+};
+
+namespace occri_impl {
+
+cudaEvent_t take_event(Plan* p) {
+  cudaEvent_t e = nullptr;
+  if (!p->ev_free.empty()) {
+    e = p->ev_free.back();
+    p->ev_free.pop_back();
+  } else if (p->ev_used.size() < 200000) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  } else {
+    return nullptr;
+  }
+  p->ev_used.push_back(e);
+  return e;
+}
+
+// Bracket one stage with a pair of events (no-op when timing is off).
+struct StageTimer {
+  Plan* p;
+  cudaEvent_t a = nullptr;
+  StageTimer(Plan* pl, bool on) : p(pl) {
+    if (on) {
+      a = take_event(p);
+      if (a) cudaEventRecord(a, p->stream);
+    }
+  }
+  void done(int stage, double units) {
+    if (!a) return;
+    cudaEvent_t b = take_event(p);
+    if (!b) return;
+    cudaEventRecord(b, p->stream);
+    p->ev_pending.push_back(Plan::TimedSpan{a, b, stage, units});
+  }
+};
+
+template <typename T>
+int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
+  using namespace occri;
+  cudaStream_t s = p->stream;
+  const bool timed = p->timing_every > 0;
+  long long launches = 0;
+  const size_t orb = (size_t)p->nk * p->nocc * p->ng;
+  if (cudaMemsetAsync(p->Y, 0, orb * sizeof(cplx_t<T>), s) != cudaSuccess) return OCCRI_ECUDA;
+  if (cudaMemsetAsync(p->kc, 0, sizeof(double2) * (size_t)p->nk * p->nao * p->nocc, s) != cudaSuccess)
+    return OCCRI_ECUDA;
+  {
+    StageTimer t(p, timed);
+    if (launch_scale_c<T>(*p, C, s) != cudaSuccess) return OCCRI_ECUDA;
+    if (launch_orbitals<T>(*p, s) != cudaSuccess) return OCCRI_ECUDA;
+    t.done(OCCRI_STAGE_ORBITALS, p->nk);
+    launches += 1 + (p->nocc + kOrbChunk - 1) / kOrbChunk;
+  }
+  long long wave = 0;
+  for (int k = 0; k < p->nk; ++k)
+    for (int kp0 = 0; kp0 < p->nk; kp0 += p->nkp_wave, ++wave) {
+      const int nkp = std::min(p->nkp_wave, p->nk - kp0);
+      cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+      bool sample = timed && (wave % p->timing_every == 0);
+      if (sample)
+        for (int i = 0; i < 4 && sample; ++i) sample = (ev[i] = take_event(p)) != nullptr;
+      if (launch_pair_wave<T>(*p, k, kp0, nkp, s, sample ? ev : nullptr) != cudaSuccess)
+        return OCCRI_ECUDA;
+      launches += 3;
+      if (sample) {
+        const double nf = (double)nkp * p->nocc * p->nocc;
+        p->ev_pending.push_back(Plan::TimedSpan{ev[0], ev[1], OCCRI_STAGE_PAIR_A, nf});
+        p->ev_pending.push_back(Plan::TimedSpan{ev[1], ev[2], OCCRI_STAGE_PAIR_B, nf});
+        p->ev_pending.push_back(Plan::TimedSpan{ev[2], ev[3], OCCRI_STAGE_PAIR_C, nf});
+      }
+    }
+  {
+    StageTimer t(p, timed);
+    if (launch_contract<T>(*p, s) != cudaSuccess) return OCCRI_ECUDA;
+    t.done(OCCRI_STAGE_CONTRACT, p->nk);
+    for (int l = 0; l < 4; ++l)
+      if (!p->shells_by_l[l].empty())
+        launches += (p->nocc + contract_chunk<T>() - 1) / contract_chunk<T>();
+  }
+  {
+    StageTimer t(p, timed);
+    const size_t sm = 2 * sizeof(double2) * (size_t)p->nocc * p->nocc;
+    const double tol = (p->precision == OCCRI_FP64) ? 1e-10 : 1e-5;
+    ace_kernel<<<p->nk, 256, sm, s>>>(C, p->kc, p->xi, p->mmat, p->ek, (double2*)K, p->nao,
+                                      p->nocc, tol, p->status);
+    ++launches;
+    if (Ex) {
+      ex_kernel<<<1, 32, 0, s>>>(p->ek, p->nk, Ex);
+      ++launches;
+    }
+    t.done(OCCRI_STAGE_ASSEMBLE, p->nk);
+  }
+  if (KC &&
+      cudaMemcpyAsync(KC, p->kc, sizeof(double2) * (size_t)p->nk * p->nao * p->nocc,
+                      cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return OCCRI_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return OCCRI_ECUDA;
+  p->have_kc = true;
+  p->launches_per_build = launches;
+  return OCCRI_OK;
+}
+
+template <typename T>
+int vjp_impl(Plan* p, double gEx, void* gC, double* gomega) {
+  using namespace occri;
+  cudaStream_t s = p->stream;
+  const long long nkc = (long long)p->nk * p->nao * p->nocc;
+  if (gC) scale_copy_kernel<<<4 * 152, 256, 0, s>>>(p->kc, (double2*)gC, nkc, gEx * 4.0 / p->nk);
+  if (gomega) {
+    if (cudaMemsetAsync(p->dacc, 0, 2 * sizeof(double), s) != cudaSuccess) return OCCRI_ECUDA;
+    if (p->kernel.kind != OCCRI_COULOMB) {
+      for (int k = 0; k < p->nk; ++k)
+        for (int kp0 = 0; kp0 < p->nk; kp0 += p->nkp_wave) {
+          const int nkp = std::min(p->nkp_wave, p->nk - kp0);
+          if (launch_domega_wave<T>(*p, k, kp0, nkp, s) != cudaSuccess) return OCCRI_ECUDA;
+        }
+    }
+    const double ngd = (double)p->ng;
+    const double sc = -gEx * p->omega_cell * 4.0 * kPiD / ((double)p->nk * p->nk) / (ngd * ngd);
+    domega_finish_kernel<<<1, 32, 0, s>>>(p->dacc, sc, gomega);
+  }
+  return cudaGetLastError() == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* occri_status_string(int status) {
+  switch (status) {
+    case OCCRI_OK: return "ok";
+    case OCCRI_EINVAL: return "invalid argument";
+    case OCCRI_ENOMEM: return "device allocation failed";
+    case OCCRI_ENOTPD: return "-C^H K C is not positive definite";
+    case OCCRI_ECUDA: return "CUDA runtime error";
+    case OCCRI_ETIMEOUT: return "bounded device wait timed out";
+    case OCCRI_EUNSUPPORTED: return "unsupported by this build";
+    default: return "unknown status";
+  }
+}
+
+int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmesh* kmesh,
+                      const occri_basis* basis, int nocc, const int grid[3],
+                      const occri_kernel* kernel, int precision, void* cuda_stream) {
+  using namespace occri;
+  if (!out) return OCCRI_EINVAL;
+  *out = nullptr;
+  if (!cell || !kmesh || !basis || !grid || !kernel) return OCCRI_EINVAL;
+  if (cell->natm < 1 || !cell->xyz) return OCCRI_EINVAL;
+  if (kmesh->nk < 1 || !kmesh->kfrac) return OCCRI_EINVAL;
+  if (basis->nshell < 1 || !basis->atom || !basis->l || !basis->alpha) return OCCRI_EINVAL;
+  if (precision != OCCRI_FP64 && precision != OCCRI_MIXED) return OCCRI_EINVAL;
+  if (kernel->kind < 0 || kernel->kind > 2) return OCCRI_EINVAL;
+  if (kernel->kind != OCCRI_COULOMB && !(kernel->omega > 0.0)) return OCCRI_EINVAL;
+  if (kernel->g0_mode != 0 && kernel->g0_mode != 1) return OCCRI_EINVAL;
+  if (kernel->g0_mode == 1 && kernel->kind != OCCRI_ERFC) return OCCRI_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (grid[d] < 4 || grid[d] > 64 || !smooth235(grid[d])) return OCCRI_EINVAL;
+  int nao = 0;
+  for (int s = 0; s < basis->nshell; ++s) {
+    if (basis->l[s] < 0 || basis->l[s] > 3) return OCCRI_EINVAL;
+    if (basis->atom[s] < 0 || basis->atom[s] >= cell->natm) return OCCRI_EINVAL;
+    if (!(basis->alpha[s] > 0.0) || !std::isfinite(basis->alpha[s])) return OCCRI_EINVAL;
+    if (s > 0 && basis->atom[s] < basis->atom[s - 1]) return OCCRI_EINVAL;  // atom-major order
+    nao += 2 * basis->l[s] + 1;
+  }
+  if (nocc < 1 || nocc > nao) return OCCRI_EINVAL;
+  double lat[3][3], inv[3][3];
+  std::memcpy(lat, cell->a, sizeof(lat));
+  const double det = lat[0][0] * (lat[1][1] * lat[2][2] - lat[1][2] * lat[2][1]) -
+                     lat[0][1] * (lat[1][0] * lat[2][2] - lat[1][2] * lat[2][0]) +
+                     lat[0][2] * (lat[1][0] * lat[2][1] - lat[1][1] * lat[2][0]);
+  if (!(std::fabs(det) > 1e-8) || !std::isfinite(det)) return OCCRI_EINVAL;
+  if (grid[0] != grid[1] || grid[0] != grid[2]) return OCCRI_EUNSUPPORTED;
+  if (nocc > 32) return OCCRI_EUNSUPPORTED;   // assembly keeps C^H KC in shared memory
+  if (!grid_edge_supported(grid[0])) return OCCRI_EUNSUPPORTED;
+  inv3(lat, inv);
+
+  Plan* p = new (std::nothrow) Plan();
+  if (!p) return OCCRI_ENOMEM;
+  p->nk = kmesh->nk; p->nao = nao; p->nocc = nocc; p->natm = cell->natm;
+  p->nshell = basis->nshell; p->precision = precision;
+  for (int d = 0; d < 3; ++d) p->N[d] = grid[d];
+  p->ng = (long long)grid[0] * grid[1] * grid[2];
+  std::memcpy(p->lat, lat, sizeof(lat));
+  p->omega_cell = std::fabs(det);
+  p->kernel = *kernel;
+  p->stream = (cudaStream_t)cuda_stream;
+
+  // k-points as rationals K/D per axis (D <= 64)
+  p->kint_h.assign((size_t)p->nk * 3, 0);
+  for (int d = 0; d < 3; ++d) {
+    int found = 0;
+    for (int D = 1; D <= 64 && !found; ++D) {
+      bool okd = true;
+      for (int k = 0; k < p->nk && okd; ++k) {
+        const double v = kmesh->kfrac[k * 3 + d] * D;
+        if (std::fabs(v - std::nearbyint(v)) > 1e-9) okd = false;
+      }
+      if (okd) found = D;
+    }
+    if (!found) { delete p; return OCCRI_EUNSUPPORTED; }
+    p->D[d] = found;
+    for (int k = 0; k < p->nk; ++k) {
+      long long v = std::llround(kmesh->kfrac[k * 3 + d] * found);
+      v %= found;
+      if (v < 0) v += found;
+      p->kint_h[k * 3 + d] = (int)v;
+    }
+  }
+  const int Dc = p->D[0] * p->D[1] * p->D[2];
+
+  // shells, cutoffs, AO offsets
+  const double eps = (precision == OCCRI_FP64) ? 1e-16 : 1e-11;
+  std::vector<ShellDev> sh(p->nshell);
+  std::vector<double> rcut(p->nshell);
+  double rcut_max = 0.0;
+  int ao = 0;
+  for (int s = 0; s < p->nshell; ++s) {
+    ShellDev& x = sh[s];
+    std::memset(&x, 0, sizeof(x));
+    x.l = basis->l[s];
+    x.atom = basis->atom[s];
+    x.ao = ao;
+    x.alpha = basis->alpha[s];
+    x.alpha_f = (float)x.alpha;
+    x.alpha_lo = (float)(x.alpha - (double)x.alpha_f);
+    shell_norms(x.l, x.alpha, x.norm);
+    for (int m = 0; m < 2 * x.l + 1; ++m) x.norm_f[m] = (float)x.norm[m];
+    rcut[s] = shell_cutoff(x.l, x.alpha, eps);
+    x.rcut2 = rcut[s] * rcut[s];
+    x.rcut2_f = (float)x.rcut2;
+    rcut_max = std::max(rcut_max, rcut[s]);
+    ao += 2 * x.l + 1;
+    p->shells_by_l[x.l].push_back(s);
+  }
+  std::vector<double> ao_norm(nao);
+  for (int s = 0; s < p->nshell; ++s)
+    for (int m = 0; m < 2 * sh[s].l + 1; ++m) ao_norm[sh[s].ao + m] = sh[s].norm[m];
+  std::vector<int> atom_shell0(p->natm + 1, 0);
+  for (int a = 0, s = 0; a <= p->natm; ++a) {
+    while (s < p->nshell && basis->atom[s] < a) ++s;
+    atom_shell0[a] = s;
+  }
+
+  // per (atom, point): T0 bringing r - A into the Wigner-Seitz cell, d0 = r - A - T0
+  const long long ng = p->ng;
+  std::vector<double> d0((size_t)p->natm * 3 * ng);
+  std::vector<int> t0((size_t)p->natm * ng);
+  double rbound = 0.0;
+  for (int a = 0; a < p->natm; ++a) {
+    const double* A = cell->xyz + 3 * a;
+    double af[3];
+    for (int d = 0; d < 3; ++d) af[d] = A[0] * inv[0][d] + A[1] * inv[1][d] + A[2] * inv[2][d];
+    for (long long n = 0; n < ng; ++n) {
+      const int n1 = (int)(n / ((long long)grid[1] * grid[2]));
+      const int n2 = (int)((n / grid[2]) % grid[1]);
+      const int n3 = (int)(n % grid[2]);
+      const double f[3] = {(double)n1 / grid[0] - af[0], (double)n2 / grid[1] - af[1],
+                           (double)n3 / grid[2] - af[2]};
+      int base[3];
+      for (int d = 0; d < 3; ++d) base[d] = (int)std::floor(f[d] + 0.5);
+      double best = 1e300;
+      int bt[3] = {base[0], base[1], base[2]};
+      double bd[3] = {0, 0, 0};
+      for (int e0 = -1; e0 <= 1; ++e0)
+        for (int e1 = -1; e1 <= 1; ++e1)
+          for (int e2 = -1; e2 <= 1; ++e2) {
+            const int t[3] = {base[0] + e0, base[1] + e1, base[2] + e2};
+            const double g[3] = {f[0] - t[0], f[1] - t[1], f[2] - t[2]};
+            double c[3];
+            for (int d = 0; d < 3; ++d) c[d] = g[0] * lat[0][d] + g[1] * lat[1][d] + g[2] * lat[2][d];
+            const double r2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+            if (r2 < best) {
+              best = r2;
+              for (int d = 0; d < 3; ++d) { bt[d] = t[d]; bd[d] = c[d]; }
+            }
+          }
+      rbound = std::max(rbound, std::sqrt(best));
+      for (int d = 0; d < 3; ++d) d0[((size_t)a * 3 + d) * ng + n] = bd[d];
+      t0[(size_t)a * ng + n] = dev::pack_t0(bt[0], bt[1], bt[2]);
+    }
+  }
+  rbound += 1e-9;
+
+  // master image list T' sorted by length, |T'| <= rcut_max + rbound
+  const double rimg = rcut_max + rbound;
+  int nb[3];
+  for (int d = 0; d < 3; ++d) {
+    const double bn = std::sqrt(inv[0][d] * inv[0][d] + inv[1][d] * inv[1][d] + inv[2][d] * inv[2][d]);
+    nb[d] = (int)std::ceil(rimg * bn) + 1;
+  }
+  struct Img { double len, x, y, z; int n[3]; };
+  std::vector<Img> imgs;
+  for (int i = -nb[0]; i <= nb[0]; ++i)
+    for (int j = -nb[1]; j <= nb[1]; ++j)
+      for (int k = -nb[2]; k <= nb[2]; ++k) {
+        Img m;
+        m.x = i * lat[0][0] + j * lat[1][0] + k * lat[2][0];
+        m.y = i * lat[0][1] + j * lat[1][1] + k * lat[2][1];
+        m.z = i * lat[0][2] + j * lat[1][2] + k * lat[2][2];
+        m.len = std::sqrt(m.x * m.x + m.y * m.y + m.z * m.z);
+        m.n[0] = i; m.n[1] = j; m.n[2] = k;
+        if (m.len <= rimg) imgs.push_back(m);
+      }
+  std::sort(imgs.begin(), imgs.end(), [](const Img& a, const Img& b) { return a.len < b.len; });
+  const int nimg = (int)imgs.size();
+  p->nimg = nimg;
+  for (int s = 0; s < p->nshell; ++s) {
+    const double lim = rcut[s] + rbound;
+    int c = 0;
+    while (c < nimg && imgs[c].len <= lim) ++c;
+    sh[s].nimg = c;
+  }
+  std::vector<double> img_d((size_t)3 * nimg);
+  std::vector<float> img_hi((size_t)3 * nimg), img_lo((size_t)3 * nimg);
+  for (int j = 0; j < nimg; ++j) {
+    const double v[3] = {imgs[j].x, imgs[j].y, imgs[j].z};
+    for (int d = 0; d < 3; ++d) {
+      img_d[(size_t)d * nimg + j] = v[d];
+      img_hi[(size_t)d * nimg + j] = (float)v[d];
+      img_lo[(size_t)d * nimg + j] = (float)(v[d] - (double)(float)v[d]);
+    }
+  }
+  // e^{i k.T'} with exact integer reduction of the phase
+  std::vector<double2> ph_d;
+  std::vector<float2> ph_f;
+  if (precision == OCCRI_FP64) ph_d.resize((size_t)p->nk * nimg); else ph_f.resize((size_t)p->nk * nimg);
+  for (int k = 0; k < p->nk; ++k)
+    for (int j = 0; j < nimg; ++j) {
+      long long num = 0;
+      for (int d = 0; d < 3; ++d)
+        num += (long long)p->kint_h[k * 3 + d] * imgs[j].n[d] * (Dc / p->D[d]);
+      num %= Dc;
+      if (num < 0) num += Dc;
+      const double ang = 2.0 * kPiD * (double)num / (double)Dc;
+      if (precision == OCCRI_FP64) ph_d[(size_t)k * nimg + j] = make_double2(std::cos(ang), std::sin(ang));
+      else ph_f[(size_t)k * nimg + j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+
+  // device tables and workspaces
+  size_t tot = 0;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess && x != cudaSuccess) e = x; };
+  chk(upload(&p->shells, sh, &tot));
+  chk(upload(&p->atom_shell0, atom_shell0, &tot));
+  for (int l = 0; l < 4; ++l) chk(upload(&p->shell_list_l[l], p->shells_by_l[l], &tot));
+  chk(upload(&p->kint, p->kint_h, &tot));
+  chk(upload(&p->ao_norm, ao_norm, &tot));
+  {
+    unsigned char* b = nullptr;
+    const size_t csb = (precision == OCCRI_FP64 ? sizeof(double2) : sizeof(float4)) *
+                       (size_t)p->nk * nao * nocc;
+    chk(dalloc(&b, csb, &tot));
+    p->cs = b;
+  }
+  chk(upload(&p->t0, t0, &tot));
+  if (precision == OCCRI_FP64) {
+    chk(upload(&p->img_d, img_d, &tot));
+    chk(upload(&p->d0_d, d0, &tot));
+    double2* ph = nullptr;
+    chk(upload(&ph, ph_d, &tot));
+    p->img_phase = ph;
+  } else {
+    chk(upload(&p->img_hi, img_hi, &tot));
+    chk(upload(&p->img_lo, img_lo, &tot));
+    std::vector<float> hi(d0.size()), lo(d0.size());
+    for (size_t i = 0; i < d0.size(); ++i) {
+      hi[i] = (float)d0[i];
+      lo[i] = (float)(d0[i] - (double)hi[i]);
+    }
+    chk(upload(&p->d0_hi, hi, &tot));
+    chk(upload(&p->d0_lo, lo, &tot));
+    float2* ph = nullptr;
+    chk(upload(&ph, ph_f, &tot));
+    p->img_phase = ph;
+  }
+  const size_t csz = (precision == OCCRI_FP64) ? sizeof(double2) : sizeof(float2);
+  const size_t field_bytes = csz * (size_t)ng;
+  const size_t per_kp = field_bytes * (size_t)nocc * nocc;
+  const size_t budget = (size_t)96 << 20;
+  int nkp = (int)std::max<size_t>(1, budget / per_kp);
+  nkp = std::min(nkp, p->nk);
+  nkp = std::max(1, std::min(nkp, 65535 / (nocc * nocc)));   // grid.y limit of the passes
+  {  // pass C keeps three planes plus two phase rows per k' in shared memory
+    const size_t pitch = (grid[0] % 2 == 0) ? grid[0] + 1 : grid[0];
+    const size_t planes = 3 * (size_t)grid[0] * pitch * csz;
+    const size_t per = 2 * (size_t)grid[0] * csz;
+    const size_t limit = 227 * 1024;
+    nkp = std::max(1, std::min<int>(nkp, (int)((limit - planes) / per)));
+  }
+  p->nkp_wave = nkp;
+  p->fields_cap = nkp * nocc * nocc;
+  const size_t orb = (size_t)p->nk * nocc * ng;
+  {
+    unsigned char* b = nullptr;
+    chk(dalloc(&b, orb * csz, &tot)); p->psi = b; b = nullptr;
+    chk(dalloc(&b, orb * csz, &tot)); p->Y = b; b = nullptr;
+    chk(dalloc(&b, (size_t)p->fields_cap * field_bytes, &tot)); p->scratch = b;
+  }
+  chk(dalloc(&p->kc, (size_t)p->nk * nao * nocc, &tot));
+  chk(dalloc(&p->xi, (size_t)p->nk * nao * nocc, &tot));
+  chk(dalloc(&p->mmat, (size_t)p->nk * nocc * nocc, &tot));
+  chk(dalloc(&p->ek, (size_t)p->nk, &tot));
+  chk(dalloc(&p->dacc, 2, &tot));
+  chk(dalloc(&p->status, 2, &tot));
+  if (e == cudaSuccess) e = cudaMemset(p->status, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? OCCRI_ENOMEM : OCCRI_ECUDA;
+    cudaGetLastError();
+    free_plan(p);
+    return code;
+  }
+  p->workspace_bytes = tot;
+  occri_plan* h = new (std::nothrow) occri_plan;
+  if (!h) { free_plan(p); return OCCRI_ENOMEM; }
+  h->p = p;
+  *out = h;
+  return OCCRI_OK;
+}
+
+int occri_plan_destroy(occri_plan* plan) {
+  if (!plan) return OCCRI_EINVAL;
+  occri::free_plan(plan->p);
+  delete plan;
+  return OCCRI_OK;
+}
+
+int occri_plan_info(const occri_plan* plan, occri_plan_info_t* info) {
+  if (!plan || !info) return OCCRI_EINVAL;
+  const Plan* p = plan->p;
+  info->nk = p->nk; info->nao = p->nao; info->nocc = p->nocc; info->natm = p->natm;
+  info->nshell = p->nshell;
+  for (int d = 0; d < 3; ++d) info->grid[d] = p->N[d];
+  info->ng = p->ng;
+  info->precision = p->precision;
+  info->workspace_bytes = p->workspace_bytes;
+  info->fields_per_wave = p->fields_cap;
+  info->launches_per_build = p->launches_per_build;
+  return OCCRI_OK;
+}
+
+int occri_plan_set_timing(occri_plan* plan, int every) {
+  if (!plan || every < 0) return OCCRI_EINVAL;
+  Plan* p = plan->p;
+  if (every == 0) {
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return OCCRI_ECUDA;
+    p->ev_pending.clear();
+    for (cudaEvent_t e : p->ev_used) p->ev_free.push_back(e);
+    p->ev_used.clear();
+  }
+  p->timing_every = every;
+  return OCCRI_OK;
+}
+
+int occri_plan_stage_times(occri_plan* plan, double* ms, long long* launches, double* units) {
+  if (!plan || !ms || !launches || !units) return OCCRI_EINVAL;
+  Plan* p = plan->p;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return OCCRI_ECUDA;
+  for (const Plan::TimedSpan& sp : p->ev_pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, sp.a, sp.b) != cudaSuccess) return OCCRI_ECUDA;
+    p->stage_ms[sp.stage] += t;
+    p->stage_n[sp.stage] += 1;
+    p->stage_units[sp.stage] += sp.units;
+  }
+  p->ev_pending.clear();
+  for (cudaEvent_t e : p->ev_used) p->ev_free.push_back(e);
+  p->ev_used.clear();
+  for (int i = 0; i < OCCRI_NSTAGES; ++i) {
+    ms[i] = p->stage_ms[i];
+    launches[i] = p->stage_n[i];
+    units[i] = p->stage_units[i];
+    p->stage_ms[i] = 0.0;
+    p->stage_n[i] = 0;
+    p->stage_units[i] = 0.0;
+  }
+  return OCCRI_OK;
+}
+
+int occri_plan_set_stream(occri_plan* plan, void* cuda_stream) {
+  if (!plan) return OCCRI_EINVAL;
+  plan->p->stream = (cudaStream_t)cuda_stream;
+  return OCCRI_OK;
+}
+
+int occri_plan_sync(occri_plan* plan, int* bad_k) {
+  if (bad_k) *bad_k = -1;
+  if (!plan) return OCCRI_EINVAL;
+  Plan* p = plan->p;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return OCCRI_ECUDA;
+  int st[2] = {0, -1};
+  if (cudaMemcpy(st, p->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return OCCRI_ECUDA;
+  if (st[0] != 0) {
+    if (cudaMemset(p->status, 0, sizeof(st)) != cudaSuccess) return OCCRI_ECUDA;
+    if (bad_k) *bad_k = st[1];
+    return st[0];
+  }
+  return OCCRI_OK;
+}
+
+
+int occri_k_build(occri_plan* plan, const void* C_dev, void* KC_dev, void* K_dev, double* Ex_dev) {
+  if (!plan || !C_dev) return OCCRI_EINVAL;
+  Plan* p = plan->p;
+  return p->precision == OCCRI_FP64
+             ? occri_impl::build_impl<double>(p, (const double2*)C_dev, KC_dev, K_dev, Ex_dev)
+             : occri_impl::build_impl<float>(p, (const double2*)C_dev, KC_dev, K_dev, Ex_dev);
+}
+
+int occri_k_build_host(occri_plan* plan, const void* C_host, void* KC_host, void* K_host,
+                       double* Ex_host) {
+  if (!plan || !C_host) return OCCRI_EINVAL;
+  Plan* p = plan->p;
+  const size_t nc = (size_t)p->nk * p->nao * p->nocc;
+  const size_t nkk = (size_t)p->nk * p->nao * p->nao;
+  if (!p->h_c) {
+    if (cudaMalloc((void**)&p->h_c, nc * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void**)&p->h_kc, nc * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void**)&p->h_ex, sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return OCCRI_ENOMEM;
+    }
+  }
+  if (K_host && !p->h_k) {
+    if (cudaMalloc((void**)&p->h_k, nkk * sizeof(double2)) != cudaSuccess) {
+      cudaGetLastError();
+      return OCCRI_ENOMEM;
+    }
+  }
+  cudaStream_t s = p->stream;
+  if (cudaMemcpyAsync(p->h_c, C_host, nc * sizeof(double2), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return OCCRI_ECUDA;
+  int st = occri_k_build(plan, p->h_c, KC_host ? p->h_kc : nullptr, K_host ? p->h_k : nullptr,
+                         Ex_host ? p->h_ex : nullptr);
+  if (st != OCCRI_OK) return st;
+  if (KC_host && cudaMemcpyAsync(KC_host, p->h_kc, nc * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return OCCRI_ECUDA;
+  if (K_host && cudaMemcpyAsync(K_host, p->h_k, nkk * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return OCCRI_ECUDA;
+  if (Ex_host && cudaMemcpyAsync(Ex_host, p->h_ex, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return OCCRI_ECUDA;
+  return occri_plan_sync(plan, nullptr);
+}
+
+int occri_orbitals(occri_plan* plan, const void* C_dev, void* psi_dev) {
+  if (!plan || !C_dev || !psi_dev) return OCCRI_EINVAL;
+  Plan* p = plan->p;
+  cudaError_t e;
+  if (p->precision == OCCRI_FP64) {
+    e = occri::launch_scale_c<double>(*p, (const double2*)C_dev, p->stream);
+    if (e == cudaSuccess) e = occri::launch_orbitals<double>(*p, p->stream);
+    if (e == cudaSuccess) e = occri::launch_widen<double>(*p, psi_dev, p->stream);
+  } else {
+    e = occri::launch_scale_c<float>(*p, (const double2*)C_dev, p->stream);
+    if (e == cudaSuccess) e = occri::launch_orbitals<float>(*p, p->stream);
+    if (e == cudaSuccess) e = occri::launch_widen<float>(*p, psi_dev, p->stream);
+  }
+  return e == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
+}
+
+int occri_vjp(occri_plan* plan, const void* C_dev, double gEx, void* gC_dev, double* gomega_dev) {
+  if (!plan || !C_dev) return OCCRI_EINVAL;
+  Plan* p = plan->p;
+  if (!p->have_kc) return OCCRI_EINVAL;
+  return p->precision == OCCRI_FP64 ? occri_impl::vjp_impl<double>(p, gEx, gC_dev, gomega_dev)
+                                    : occri_impl::vjp_impl<float>(p, gEx, gC_dev, gomega_dev);
+}
+
+}  // extern "C"

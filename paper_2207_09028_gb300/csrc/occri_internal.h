@@ -1,0 +1,163 @@
+// occri_internal.h -- plan layout and kernel launchers shared by the CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "occri.h"
+
+namespace occri {
+
+// Cubic grid edges with a compiled transform (each {2,3,5}-smooth, <= 64).
+#define OCCRI_FOR_EACH_N(X) \
+  X(8) X(9) X(10) X(12) X(15) X(16) X(18) X(20) X(24) X(25) X(27) X(30) X(32) X(36) X(40) \
+  X(45) X(48) X(50) X(54) X(60) X(64)
+
+bool grid_edge_supported(int n);
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+template <typename T> using cplx_t = typename Vec2<T>::type;
+
+// One shell of primitives on the device.
+struct ShellDev {
+  double alpha;
+  double rcut2;      // squared screening radius
+  double norm[7];    // N_lm, m = -l..l
+  float alpha_f, alpha_lo, rcut2_f;   // alpha = alpha_f + alpha_lo
+  float norm_f[7];
+  int l, atom, ao, nimg;   // nimg: prefix of the sorted image list that can reach the cell
+};
+
+// Geometry / AO tables for the AO kernels (steps a, b, e).
+struct AOParams {
+  int nk, nao, nocc, natm, nshell;
+  long long ng;
+  int N[3];
+  int D[3];          // per-axis k denominators: kappa_{k,d} = kint[k][d] / D[d]
+  int Dc;            // D[0]*D[1]*D[2]
+  const ShellDev* shells;
+  const int* atom_shell0;    // [natm+1] shell range per atom (shells are atom-major)
+  int nimg;                  // master image count
+  const double* img_d;       // [3][nimg] Cartesian image offsets T'
+  const float* img_hi;       // [3][nimg] float hi part
+  const float* img_lo;       // [3][nimg] float residual
+  const void* img_phase;     // [nk][nimg] e^{i k.T'} in the plan's precision
+  const double* d0_d;        // [natm][3][ng] r_n - A - T0 (bohr)
+  const float* d0_hi;        // [natm][3][ng]
+  const float* d0_lo;        // [natm][3][ng]
+  const int* t0;             // [natm][ng] packed T0 integer coordinates (3 x 10 bits)
+  const int* kint;           // [nk][3]
+  const void* cs;            // [nk][nao][nocc] N_mu C^k_{mu i}: double2 (FP64) or float4 hi/lo (FP32)
+};
+
+// Parameters of one wave of pair fields (steps c, d): output k, a block of k'.
+struct PairParams {
+  int nk, nocc, N1;          // N1: cubic grid edge
+  long long ng;
+  int k, kp0, nkp;
+  int D[3];
+  const int* kint;           // [nk][3]
+  double g[6];               // reciprocal metric b_i.b_j: 11, 22, 33, 12, 13, 23
+  int kind;                  // occri_kernel_kind
+  double inv4w2;             // 1 / (4 omega^2)
+  double omega;
+  double g0;                 // value at G+q = 0, in units of 4 pi
+  double dg0;                // d g0 / d omega, in units of 4 pi
+};
+// The transforms apply v/(4 pi) between unnormalised forward and inverse FFTs, so
+// Y carries a factor N_g/(4 pi); the contraction restores it in FP64.
+
+struct Plan {
+  // problem
+  int nk, nao, nocc, natm, nshell, precision;
+  int N[3];
+  long long ng;
+  double lat[3][3];
+  double omega_cell;
+  occri_kernel kernel;
+  cudaStream_t stream;
+  int D[3];
+  std::vector<int> kint_h;
+  int fields_cap;            // pair fields held by the transform scratch
+  int nkp_wave;              // k' per wave
+  std::vector<int> shells_by_l[4];
+
+  // device tables
+  ShellDev* shells = nullptr;
+  int* atom_shell0 = nullptr;
+  int* shell_list_l[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* img_d = nullptr;
+  float* img_hi = nullptr;
+  float* img_lo = nullptr;
+  void* img_phase = nullptr;
+  double* d0_d = nullptr;
+  float* d0_hi = nullptr;
+  float* d0_lo = nullptr;
+  int* t0 = nullptr;
+  int* kint = nullptr;
+  int nimg = 0;
+
+  // device workspaces
+  void* psi = nullptr;       // [nk][nocc][ng] cplx_t<T>
+  void* Y = nullptr;         // [nk][nocc][ng] cplx_t<T>
+  void* scratch = nullptr;   // [fields_cap][ng] cplx_t<T>
+  double2* kc = nullptr;     // [nk][nao][nocc]
+  double2* xi = nullptr;     // [nk][nao][nocc]
+  double2* mmat = nullptr;   // [nk][nocc][nocc]
+  double* ek = nullptr;      // [nk]
+  double* dacc = nullptr;    // [2] scratch accumulators (d E/d omega)
+  int* status = nullptr;     // [2]: first device error code, k index
+  bool have_kc = false;
+  double* ao_norm = nullptr; // [nao] N_lm per AO
+  void* cs = nullptr;        // scaled coefficients (see AOParams::cs)
+
+  // host-call staging (allocated on first occri_k_build_host)
+  double2* h_c = nullptr;
+  double2* h_kc = nullptr;
+  double2* h_k = nullptr;
+  double* h_ex = nullptr;
+
+  size_t workspace_bytes = 0;
+  long long launches_per_build = 0;
+
+  // sampled stage timing
+  struct TimedSpan { cudaEvent_t a, b; int stage; double units; };
+  int timing_every = 0;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<TimedSpan> ev_pending;
+  std::vector<cudaEvent_t> ev_used;
+  double stage_ms[6] = {0, 0, 0, 0, 0, 0};
+  long long stage_n[6] = {0, 0, 0, 0, 0, 0};
+  double stage_units[6] = {0, 0, 0, 0, 0, 0};
+
+  AOParams ao_params() const;
+  PairParams pair_params() const;
+};
+
+// orbitals per launch of the orbital kernel, and per launch of the contraction kernel
+constexpr int kOrbChunk = 8;
+template <typename T> constexpr int contract_chunk() { return sizeof(T) == 4 ? 8 : 4; }
+
+// ---- launchers (return cudaError_t of the launch) ----
+template <typename T>
+cudaError_t launch_scale_c(const Plan& p, const double2* C, cudaStream_t s);
+template <typename T>
+cudaError_t launch_orbitals(const Plan& p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_contract(const Plan& p, cudaStream_t s);
+// Pair-wave launches; when ev != nullptr, ev[0..3] are recorded before pass A,
+// before pass B, before pass C and after pass C.
+template <typename T>
+cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, cudaStream_t s,
+                             cudaEvent_t* ev = nullptr);
+template <typename T>
+cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, cudaStream_t s);
+template <typename T>
+cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s);
+
+}  // namespace occri

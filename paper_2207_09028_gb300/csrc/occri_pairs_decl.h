@@ -1,0 +1,19 @@
+// occri_pairs_decl.h -- per-edge entry points of the pair-transform kernels.
+// Definitions live in occri_pairs.cuh and are instantiated, a few grid edges
+// per translation unit, in occri_pairs_<precision>_<group>.cu.
+#pragma once
+
+#include "occri_internal.h"
+
+namespace occri {
+namespace pairs {
+
+template <typename T, int N>
+cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cplx_t<T>* Y,
+                     cudaStream_t st, cudaEvent_t* ev);
+template <typename T, int N>
+cudaError_t run_domega_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S,
+                            double* dacc, cudaStream_t st);
+
+}  // namespace pairs
+}  // namespace occri

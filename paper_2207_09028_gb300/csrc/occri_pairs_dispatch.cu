@@ -1,0 +1,53 @@
+// occri_pairs_dispatch.cu -- runtime grid edge -> compiled pair-transform kernels.
+#include "occri_pairs_decl.h"
+
+namespace occri {
+
+template <typename T>
+cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, cudaStream_t s,
+                             cudaEvent_t* ev) {
+  PairParams pp = p.pair_params();
+  pp.k = k;
+  pp.kp0 = kp0;
+  pp.nkp = nkp;
+  const cplx_t<T>* psi = (const cplx_t<T>*)p.psi;
+  cplx_t<T>* S = (cplx_t<T>*)p.scratch;
+  cplx_t<T>* Y = (cplx_t<T>*)p.Y;
+  switch (p.N[0]) {
+#define OCCRI_PAIR_CASE(NN) \
+  case NN:                  \
+    return pairs::run_wave<T, NN>(pp, psi, S, Y, s, ev);
+    OCCRI_FOR_EACH_N(OCCRI_PAIR_CASE)
+#undef OCCRI_PAIR_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, cudaStream_t s) {
+  PairParams pp = p.pair_params();
+  pp.k = k;
+  pp.kp0 = kp0;
+  pp.nkp = nkp;
+  const cplx_t<T>* psi = (const cplx_t<T>*)p.psi;
+  cplx_t<T>* S = (cplx_t<T>*)p.scratch;
+  switch (p.N[0]) {
+#define OCCRI_DOMEGA_CASE(NN) \
+  case NN:                    \
+    return pairs::run_domega_wave<T, NN>(pp, psi, S, p.dacc, s);
+    OCCRI_FOR_EACH_N(OCCRI_DOMEGA_CASE)
+#undef OCCRI_DOMEGA_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_pair_wave<float>(const Plan&, int, int, int, cudaStream_t,
+                                             cudaEvent_t*);
+template cudaError_t launch_pair_wave<double>(const Plan&, int, int, int, cudaStream_t,
+                                              cudaEvent_t*);
+template cudaError_t launch_domega_wave<float>(const Plan&, int, int, int, cudaStream_t);
+template cudaError_t launch_domega_wave<double>(const Plan&, int, int, int, cudaStream_t);
+
+}  // namespace occri

@@ -1,0 +1,12 @@
+// occri_pairs_f32_g2.cu -- pair-transform kernels for float, grid edges 40 45.
+#include "occri_pairs.cuh"
+#include "occri_pairs_decl.h"
+
+namespace occri {
+namespace pairs {
+template cudaError_t run_wave<float, 40>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t, cudaEvent_t*);
+template cudaError_t run_domega_wave<float, 40>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_wave<float, 45>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t, cudaEvent_t*);
+template cudaError_t run_domega_wave<float, 45>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+}  // namespace pairs
+}  // namespace occri

@@ -1,0 +1,12 @@
+// occri_pairs_f64_g2.cu -- pair-transform kernels for double, grid edges 40 45.
+#include "occri_pairs.cuh"
+#include "occri_pairs_decl.h"
+
+namespace occri {
+namespace pairs {
+template cudaError_t run_wave<double, 40>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, cplx_t<double>*, cudaStream_t, cudaEvent_t*);
+template cudaError_t run_domega_wave<double, 40>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, double*, cudaStream_t);
+template cudaError_t run_wave<double, 45>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, cplx_t<double>*, cudaStream_t, cudaEvent_t*);
+template cudaError_t run_domega_wave<double, 45>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, double*, cudaStream_t);
+}  // namespace pairs
+}  // namespace occri

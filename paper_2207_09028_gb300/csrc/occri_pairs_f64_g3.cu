@@ -1,0 +1,12 @@
+// occri_pairs_f64_g3.cu -- pair-transform kernels for double, grid edges 48 50.
+#include "occri_pairs.cuh"
+#include "occri_pairs_decl.h"
+
+namespace occri {
+namespace pairs {
+template cudaError_t run_wave<double, 48>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, cplx_t<double>*, cudaStream_t, cudaEvent_t*);
+template cudaError_t run_domega_wave<double, 48>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, double*, cudaStream_t);
+template cudaError_t run_wave<double, 50>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, cplx_t<double>*, cudaStream_t, cudaEvent_t*);
+template cudaError_t run_domega_wave<double, 50>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, double*, cudaStream_t);
+}  // namespace pairs
+}  // namespace occri

@@ -1,0 +1,10 @@
+// occri_pairs_f64_g6.cu -- pair-transform kernels for double, grid edges 64.
+#include "occri_pairs.cuh"
+#include "occri_pairs_decl.h"
+
+namespace occri {
+namespace pairs {
+template cudaError_t run_wave<double, 64>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, cplx_t<double>*, cudaStream_t, cudaEvent_t*);
+template cudaError_t run_domega_wave<double, 64>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, double*, cudaStream_t);
+}  // namespace pairs
+}  // namespace occri
