@@ -181,6 +181,28 @@ int occri_plan_set_timing(occri_plan *plan, int every);
  * Arrays have OCCRI_NSTAGES entries; the accumulators are then reset. */
 int occri_plan_stage_times(occri_plan *plan, double *ms, long long *launches, double *units);
 
+/* Bytes of device memory behind occri_orbitals_noalloc (one array per GPU that loads
+ * the library, held until the process exits). */
+#define OCCRI_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* occri_orbitals for callers that cannot allocate device memory at call time -- for
+ * example code running while a stream is being captured into a CUDA graph, or hosts
+ * whose device memory is owned by another allocator. No counterpart in the paper.
+ * Same inputs, output and result as occri_orbitals, but the call's scratch (the
+ * normalised coefficients and the orbitals before widening) lives in one static
+ * device array of OCCRI_STATIC_SCRATCH_BYTES instead of the plan's workspaces; the
+ * call makes no cudaMalloc, cudaFree or other allocating call.
+ * A call needs 16*nk*nao*nocc bytes (rounded up to 256) plus 16*nk*nocc*N_g (FP64)
+ * or 8*nk*nocc*N_g (mixed) bytes of it; larger problems return OCCRI_EINVAL before
+ * anything is launched.
+ * The first call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture. All calls share the one
+ * array and it keeps the previous call's contents (every byte a call reads it has
+ * written first, so nothing needs clearing); calls whose work overlaps on the GPU --
+ * on different streams, or from different host threads -- race on it and must be
+ * serialised by the caller. */
+int occri_orbitals_noalloc(const occri_plan *plan, const void *C_dev, void *psi_dev);
+
 const char *occri_status_string(int status);
 
 #ifdef __cplusplus

@@ -59,7 +59,8 @@ class occri_plan_info_t(ctypes.Structure):
 
 EXPORTED = ["occri_plan_create", "occri_plan_destroy", "occri_plan_info", "occri_plan_set_stream",
             "occri_plan_sync", "occri_k_build", "occri_k_build_host", "occri_orbitals",
-            "occri_vjp", "occri_plan_set_timing", "occri_plan_stage_times", "occri_status_string"]
+            "occri_vjp", "occri_plan_set_timing", "occri_plan_stage_times", "occri_orbitals_noalloc",
+            "occri_status_string"]
 
 STAGES = ["orbitals", "pair_a", "pair_b", "pair_c", "contract", "assemble"]
 
@@ -92,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.occri_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong),
                                            ctypes.POINTER(ctypes.c_double)]
+    lib.occri_orbitals_noalloc.argtypes = [vp, vp, vp]
     lib.occri_status_string.argtypes = [ip]
     lib.occri_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -231,6 +233,20 @@ class Plan:
         self.set_stream()
         psi = torch.empty((self.nk, self.nocc) + self.grid, dtype=torch.complex128, device=C.device)
         _check(self._lib.occri_orbitals(self._h, _ptr(C), _ptr(psi)), "occri_orbitals")
+        self.sync()
+        return psi
+
+    def orbitals_noalloc(self, C, psi=None):
+        """occri_orbitals_noalloc: as orbitals(), with the call's scratch in the library's
+        static device array instead of the plan's workspaces (no allocation in the call)."""
+        import torch
+        self._check_c(C)
+        self.set_stream()
+        if psi is None:
+            psi = torch.empty((self.nk, self.nocc) + self.grid, dtype=torch.complex128,
+                              device=C.device)
+        _check(self._lib.occri_orbitals_noalloc(self._h, _ptr(C), _ptr(psi)),
+               "occri_orbitals_noalloc")
         self.sync()
         return psi
 

@@ -14,6 +14,8 @@
 // it is accurate to an ulp of its own size, not of |T|.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "occri_device.cuh"
 #include "occri_internal.h"
 
@@ -370,3 +372,82 @@ template cudaError_t launch_widen<float>(const Plan&, void*, cudaStream_t);
 template cudaError_t launch_widen<double>(const Plan&, void*, cudaStream_t);
 
 }  // namespace occri
+
+// ------------------------------------------------------------------ orbitals without allocation
+//
+// occri_orbitals_noalloc runs the same kernels as occri_orbitals but keeps its
+// scratch -- the normalised coefficients N_mu C^k_{mu i} and the orbitals in the
+// plan's working precision before widening -- in this file-scope device array
+// instead of the plan's workspaces. Every GPU that loads the library reserves
+// OCCRI_STATIC_SCRATCH_BYTES of device memory for it until the process exits.
+static __device__ __align__(256) unsigned char occri_static_scratch[OCCRI_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mutex;
+
+size_t round_up_256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Device address of the static array for the current device (looked up once per device,
+// with that device current; the host-side symbol itself is not a device address).
+int static_scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return OCCRI_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return OCCRI_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, occri_static_scratch) != cudaSuccess || ptr == nullptr) {
+      cudaGetLastError();
+      return OCCRI_ECUDA;
+    }
+    g_scratch_addr[dev] = ptr;
+  }
+  *out = g_scratch_addr[dev];
+  return OCCRI_OK;
+}
+
+template <typename T>
+int orbitals_noalloc_impl(const occri::Plan& p, const double2* C, void* psi_out, void* base) {
+  using namespace occri;
+  using CS = typename ao::CsType<T>::type;
+  const long long ncs = (long long)p.nk * p.nao * p.nocc;
+  const long long npsi = (long long)p.nk * p.nocc * p.ng;
+  CS* cs = reinterpret_cast<CS*>(base);
+  cplx_t<T>* psi = reinterpret_cast<cplx_t<T>*>(static_cast<unsigned char*>(base) +
+                                                round_up_256(sizeof(CS) * ncs));
+  cudaStream_t s = p.stream;
+  if constexpr (sizeof(T) == 8)
+    ao::scale_c_kernel_d<<<2 * 152, 256, 0, s>>>(C, p.ao_norm, cs, p.nao, p.nocc, ncs);
+  else
+    ao::scale_c_kernel_f<<<2 * 152, 256, 0, s>>>(C, p.ao_norm, cs, p.nao, p.nocc, ncs);
+  AOParams ap = p.ao_params();
+  ap.cs = cs;
+  const dim3 grid((unsigned)((p.ng + 127) / 128), p.nk);
+  for (int i0 = 0; i0 < p.nocc; i0 += kOrbChunk)
+    ao::orbitals_kernel<T, kOrbChunk><<<grid, 128, 0, s>>>(ap, psi, i0);
+  ao::widen_kernel<T><<<4 * 152, 256, 0, s>>>(psi, (double2*)psi_out, npsi);
+  return cudaGetLastError() == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
+}
+
+}  // namespace
+
+extern "C" int occri_orbitals_noalloc(const occri_plan* plan, const void* C_dev, void* psi_dev) {
+  if (!plan || !C_dev || !psi_dev) return OCCRI_EINVAL;
+  const occri::Plan& p = *plan->p;
+  const bool fp64 = p.precision == OCCRI_FP64;
+  const size_t ncs = (size_t)p.nk * p.nao * p.nocc;
+  const size_t npsi = (size_t)p.nk * p.nocc * p.ng;
+  const size_t need = round_up_256((fp64 ? sizeof(double2) : sizeof(float4)) * ncs) +
+                      (fp64 ? sizeof(double2) : sizeof(float2)) * npsi;
+  if (need > (size_t)OCCRI_STATIC_SCRATCH_BYTES) return OCCRI_EINVAL;
+  void* base = nullptr;
+  const int st = static_scratch_address(&base);
+  if (st != OCCRI_OK) return st;
+  return fp64 ? orbitals_noalloc_impl<double>(p, (const double2*)C_dev, psi_dev, base)
+              : orbitals_noalloc_impl<float>(p, (const double2*)C_dev, psi_dev, base);
+}

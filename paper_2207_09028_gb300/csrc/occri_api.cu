@@ -336,10 +336,6 @@ void free_plan(Plan* p) {
 
 using occri::Plan;
 
-struct occri_plan {
-  Plan* p;
-};
-
 namespace occri_impl {
 
 cudaEvent_t take_event(Plan* p) {

@@ -161,3 +161,8 @@ template <typename T>
 cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s);
 
 }  // namespace occri
+
+// The opaque handle behind occri_plan*.
+struct occri_plan {
+  occri::Plan* p;
+};
