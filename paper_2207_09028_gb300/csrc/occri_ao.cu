@@ -91,11 +91,21 @@ template <typename T> __device__ __forceinline__ T sh_rcut2(const ShellDev& s);
 template <> __device__ __forceinline__ double sh_rcut2<double>(const ShellDev& s) { return s.rcut2; }
 template <> __device__ __forceinline__ float sh_rcut2<float>(const ShellDev& s) { return s.rcut2_f; }
 
-// e^{i k.T0} for the packed T0 of (atom, n).
+// Grid point of `lane` in point block `blk` (2 x 4 x 4 points, ragged at the grid edge);
+// lanes outside the grid get a clamped in-range point and *valid = false.
+__device__ __forceinline__ long long block_point(const AOParams& p, int blk, int lane, bool* valid) {
+  const int b3 = blk % p.nb[2], b2 = (blk / p.nb[2]) % p.nb[1], b1 = blk / (p.nb[1] * p.nb[2]);
+  const int n1 = 2 * b1 + (lane >> 4), n2 = 4 * b2 + ((lane >> 2) & 3), n3 = 4 * b3 + (lane & 3);
+  *valid = n1 < p.N[0] && n2 < p.N[1] && n3 < p.N[2];
+  return ((long long)min(n1, p.N[0] - 1) * p.N[1] + min(n2, p.N[1] - 1)) * p.N[2] +
+         min(n3, p.N[2] - 1);
+}
+
+// e^{i k.T0} for the T0 shared by the points of block `blk` for this atom.
 template <typename T>
-__device__ __forceinline__ cplx_t<T> phase_t0(const AOParams& p, int atom, long long n, int k) {
+__device__ __forceinline__ cplx_t<T> phase_t0(const AOParams& p, int atom, int blk, int k) {
   int t[3];
-  dev::unpack_t0(p.t0[(size_t)atom * p.ng + n], &t[0], &t[1], &t[2]);
+  dev::unpack_t0(p.t0[(size_t)atom * p.nblk + blk], &t[0], &t[1], &t[2]);
   long long num = 0;
 #pragma unroll
   for (int d = 0; d < 3; ++d)
@@ -105,11 +115,12 @@ __device__ __forceinline__ cplx_t<T> phase_t0(const AOParams& p, int atom, long 
 
 // chi_{mu k}(r_n) / N_mu for the 2L+1 functions of one shell, without the e^{i k.T0}
 // factor (the normalisation is applied in FP64 outside: folded into C for (b), into
-// the reduction for (e)). In FP32 the exponent uses alpha = alpha_f + alpha_lo.
+// the reduction for (e)). The images are the first np entries of the block's list,
+// identical for all lanes of the warp. In FP32 the exponent uses alpha = alpha_f + alpha_lo.
 template <typename T, int L>
 __device__ __forceinline__ void shell_values(const AOParams& p, const ShellDev& sh, int k,
-                                             const Disp<T>& d, T (&cr)[2 * L + 1],
-                                             T (&ci)[2 * L + 1]) {
+                                             const Disp<T>& d, const unsigned short* list, int np,
+                                             T (&cr)[2 * L + 1], T (&ci)[2 * L + 1]) {
   const cplx_t<T>* ph = reinterpret_cast<const cplx_t<T>*>(p.img_phase) + (size_t)k * p.nimg;
   const T alpha = sh_alpha<T>(sh), alo = sh_alpha_lo<T>(sh), rc2 = sh_rcut2<T>(sh);
 #pragma unroll
@@ -117,15 +128,16 @@ __device__ __forceinline__ void shell_values(const AOParams& p, const ShellDev& 
     cr[m] = T(0);
     ci[m] = T(0);
   }
-  for (int j = 0; j < sh.nimg; ++j) {
+  for (int j = 0; j < np; ++j) {
+    const int idx = list[j];
     T x, y, z;
-    image_disp(p, d, j, &x, &y, &z);
+    image_disp(p, d, idx, &x, &y, &z);
     const T r2 = x * x + y * y + z * z;
     if (r2 <= rc2) {
       const T e = exp_t(-(alpha * r2 + alo * r2));
       T P[2 * L + 1];
       solid<T, L>(x, y, z, P);
-      const cplx_t<T> w = ph[j];
+      const cplx_t<T> w = ph[idx];
 #pragma unroll
       for (int m = 0; m < 2 * L + 1; ++m) {
         const T v = P[m] * e;
@@ -136,7 +148,46 @@ __device__ __forceinline__ void shell_values(const AOParams& p, const ShellDev& 
   }
 }
 
-// ------------------------------------------------------------------ (a)+(b)
+// chi_{mu k}(r_n)/N_mu for KB consecutive k-points (rows k0..k0+KB-1 of the padded
+// phase table); the image geometry, exponential and polynomial are computed once.
+template <typename T, int L, int KB>
+__device__ __forceinline__ void shell_values_kb(const AOParams& p, const ShellDev& sh, int k0,
+                                                const Disp<T>& d, const unsigned short* list,
+                                                int np, T (&cr)[KB][2 * L + 1],
+                                                T (&ci)[KB][2 * L + 1]) {
+  const cplx_t<T>* ph = reinterpret_cast<const cplx_t<T>*>(p.img_phase) + (size_t)k0 * p.nimg;
+  const T alpha = sh_alpha<T>(sh), alo = sh_alpha_lo<T>(sh), rc2 = sh_rcut2<T>(sh);
+#pragma unroll
+  for (int b = 0; b < KB; ++b)
+#pragma unroll
+    for (int m = 0; m < 2 * L + 1; ++m) {
+      cr[b][m] = T(0);
+      ci[b][m] = T(0);
+    }
+  for (int j = 0; j < np; ++j) {
+    const int idx = list[j];
+    T x, y, z;
+    image_disp(p, d, idx, &x, &y, &z);
+    const T r2 = x * x + y * y + z * z;
+    if (r2 <= rc2) {
+      const T e = exp_t(-(alpha * r2 + alo * r2));
+      T P[2 * L + 1];
+      solid<T, L>(x, y, z, P);
+#pragma unroll
+      for (int m = 0; m < 2 * L + 1; ++m) P[m] *= e;
+#pragma unroll
+      for (int b = 0; b < KB; ++b) {
+        const cplx_t<T> w = ph[(size_t)b * p.nimg + idx];
+#pragma unroll
+        for (int m = 0; m < 2 * L + 1; ++m) {
+          cr[b][m] += w.x * P[m];
+          ci[b][m] += w.y * P[m];
+        }
+      }
+    }
+  }
+}
+
 
 // psi += (N_mu C_mu i) chi_mu / N_mu; in FP32 the scaled coefficient is a hi/lo pair.
 __device__ __forceinline__ void cmac(const double2* cs, size_t idx, double xr, double xi,
@@ -155,22 +206,27 @@ template <typename T> struct CsType;
 template <> struct CsType<double> { using type = double2; };
 template <> struct CsType<float> { using type = float4; };
 
-template <typename T, int L, int NI>
-__device__ __forceinline__ void orbital_shell(const AOParams& p, const ShellDev& sh, int k,
-                                              const Disp<T>& d, cplx_t<T> ph0, int i0,
-                                              T (&ar)[NI], T (&ai)[NI]) {
+template <typename T, int L, int NI, int KB>
+__device__ __forceinline__ void orbital_shell(const AOParams& p, const ShellDev& sh, int k0,
+                                              const Disp<T>& d, const unsigned short* list,
+                                              int np, const cplx_t<T> (&ph0)[KB], int i0,
+                                              T (&ar)[KB][NI], T (&ai)[KB][NI]) {
   using CS = typename CsType<T>::type;
   const CS* cs = reinterpret_cast<const CS*>(p.cs);
-  T cr[2 * L + 1], ci[2 * L + 1];
-  shell_values<T, L>(p, sh, k, d, cr, ci);
+  T cr[KB][2 * L + 1], ci[KB][2 * L + 1];
+  shell_values_kb<T, L, KB>(p, sh, k0, d, list, np, cr, ci);
 #pragma unroll
-  for (int m = 0; m < 2 * L + 1; ++m) {
-    const T xr = cr[m] * ph0.x - ci[m] * ph0.y;
-    const T xi = cr[m] * ph0.y + ci[m] * ph0.x;
-    const size_t row = ((size_t)k * p.nao + sh.ao + m) * p.nocc;
+  for (int b = 0; b < KB; ++b) {
+    if (k0 + b >= p.nk) break;
 #pragma unroll
-    for (int i = 0; i < NI; ++i)
-      if (i0 + i < p.nocc) cmac(cs, row + i0 + i, xr, xi, ar[i], ai[i]);
+    for (int m = 0; m < 2 * L + 1; ++m) {
+      const T xr = cr[b][m] * ph0[b].x - ci[b][m] * ph0[b].y;
+      const T xi = cr[b][m] * ph0[b].y + ci[b][m] * ph0[b].x;
+      const size_t row = ((size_t)(k0 + b) * p.nao + sh.ao + m) * p.nocc;
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+        if (i0 + i < p.nocc) cmac(cs, row + i0 + i, xr, xi, ar[b][i], ai[b][i]);
+    }
   }
 }
 
@@ -194,32 +250,51 @@ __global__ void scale_c_kernel_f(const double2* __restrict__ C, const double* __
   }
 }
 
-template <typename T, int NI>
+// One warp per point block, four blocks per CTA; KB k-points per thread.
+template <typename T, int NI, int KB>
 __global__ void __launch_bounds__(128)
 orbitals_kernel(AOParams p, cplx_t<T>* __restrict__ psi, int i0) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = blockIdx.y;
-  if (n >= p.ng) return;
-  T ar[NI], ai[NI];
+  const int blk = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (blk >= p.nblk) return;
+  bool valid;
+  const long long n = block_point(p, blk, threadIdx.x & 31, &valid);
+  const int k0 = blockIdx.y * KB;
+  T ar[KB][NI], ai[KB][NI];
 #pragma unroll
-  for (int i = 0; i < NI; ++i) { ar[i] = T(0); ai[i] = T(0); }
+  for (int b = 0; b < KB; ++b)
+#pragma unroll
+    for (int i = 0; i < NI; ++i) { ar[b][i] = T(0); ai[b][i] = T(0); }
   for (int a = 0; a < p.natm; ++a) {
     Disp<T> d;
     load_disp(p, a, n, &d);
-    const cplx_t<T> ph0 = phase_t0<T>(p, a, n, k);
-    for (int s = p.atom_shell0[a]; s < p.atom_shell0[a + 1]; ++s) {
+    cplx_t<T> ph0[KB];
+#pragma unroll
+    for (int b = 0; b < KB; ++b)
+      ph0[b] = (k0 + b < p.nk) ? phase_t0<T>(p, a, blk, k0 + b) : cplx_t<T>{T(0), T(0)};
+    const size_t ab = (size_t)a * p.nblk + blk;
+    const unsigned short* list = p.blist + ab * p.lmax;
+    const unsigned short* pre = p.bpre + ab * p.nsa;
+    const int s0 = p.atom_shell0[a];
+    for (int s = s0; s < p.atom_shell0[a + 1]; ++s) {
       const ShellDev sh = p.shells[s];
+      const int np = pre[s - s0];
       switch (sh.l) {
-        case 0: orbital_shell<T, 0, NI>(p, sh, k, d, ph0, i0, ar, ai); break;
-        case 1: orbital_shell<T, 1, NI>(p, sh, k, d, ph0, i0, ar, ai); break;
-        case 2: orbital_shell<T, 2, NI>(p, sh, k, d, ph0, i0, ar, ai); break;
-        default: orbital_shell<T, 3, NI>(p, sh, k, d, ph0, i0, ar, ai); break;
+        case 0: orbital_shell<T, 0, NI, KB>(p, sh, k0, d, list, np, ph0, i0, ar, ai); break;
+        case 1: orbital_shell<T, 1, NI, KB>(p, sh, k0, d, list, np, ph0, i0, ar, ai); break;
+        case 2: orbital_shell<T, 2, NI, KB>(p, sh, k0, d, list, np, ph0, i0, ar, ai); break;
+        default: orbital_shell<T, 3, NI, KB>(p, sh, k0, d, list, np, ph0, i0, ar, ai); break;
       }
     }
   }
+  if (!valid) return;
 #pragma unroll
-  for (int i = 0; i < NI; ++i)
-    if (i0 + i < p.nocc) psi[((size_t)k * p.nocc + i0 + i) * p.ng + n] = cplx_t<T>{ar[i], ai[i]};
+  for (int b = 0; b < KB; ++b) {
+    if (k0 + b >= p.nk) break;
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+      if (i0 + i < p.nocc)
+        psi[((size_t)(k0 + b) * p.nocc + i0 + i) * p.ng + n] = cplx_t<T>{ar[b][i], ai[b][i]};
+  }
 }
 
 // ------------------------------------------------------------------ (e)
@@ -233,23 +308,27 @@ contract_kernel(AOParams p, const cplx_t<T>* __restrict__ Y, double2* __restrict
   const int s = shell_list[blockIdx.z];
   const int k = blockIdx.y;
   const ShellDev sh = p.shells[s];
-  const long long start = (long long)blockIdx.x * chunk;
-  const long long end = min(p.ng, start + chunk);
+  const int start = blockIdx.x * (int)chunk;
+  const int end = min(p.nblk, start + (int)chunk);
+  const int s0 = p.atom_shell0[sh.atom];
   T ar[NM][NI], ai[NM][NI];
 #pragma unroll
   for (int m = 0; m < NM; ++m)
 #pragma unroll
     for (int i = 0; i < NI; ++i) { ar[m][i] = T(0); ai[m][i] = T(0); }
-  for (long long n = start + threadIdx.x; n < end; n += blockDim.x) {
+  for (int blk = start + (int)(threadIdx.x >> 5); blk < end; blk += (int)(blockDim.x >> 5)) {
+    bool valid;
+    const long long n = block_point(p, blk, threadIdx.x & 31, &valid);
     Disp<T> d;
     load_disp(p, sh.atom, n, &d);
-    const cplx_t<T> ph0 = phase_t0<T>(p, sh.atom, n, k);
+    const cplx_t<T> ph0 = phase_t0<T>(p, sh.atom, blk, k);
+    const size_t ab = (size_t)sh.atom * p.nblk + blk;
     T cr[NM], ci[NM];
-    shell_values<T, L>(p, sh, k, d, cr, ci);
+    shell_values<T, L>(p, sh, k, d, p.blist + ab * p.lmax, p.bpre[ab * p.nsa + (s - s0)], cr, ci);
     T yr[NI], yi[NI];
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
-      if (i0 + i < p.nocc) {
+      if (valid && i0 + i < p.nocc) {
         const cplx_t<T> y = Y[((size_t)k * p.nocc + i0 + i) * p.ng + n];
         yr[i] = y.x; yi[i] = y.y;
       } else {
@@ -320,11 +399,11 @@ cudaError_t launch_scale_c<float>(const Plan& p, const double2* C, cudaStream_t 
 
 template <typename T>
 cudaError_t launch_orbitals(const Plan& p, cudaStream_t s) {
-  constexpr int NI = kOrbChunk;
+  constexpr int NI = kOrbChunk, KB = orbital_kbatch<T>();
   const AOParams ap = p.ao_params();
-  dim3 grid((unsigned)((p.ng + 127) / 128), p.nk);
+  dim3 grid((unsigned)((p.nblk + 3) / 4), (p.nk + KB - 1) / KB);
   for (int i0 = 0; i0 < p.nocc; i0 += NI)
-    ao::orbitals_kernel<T, NI><<<grid, 128, 0, s>>>(ap, (cplx_t<T>*)p.psi, i0);
+    ao::orbitals_kernel<T, NI, KB><<<grid, 128, 0, s>>>(ap, (cplx_t<T>*)p.psi, i0);
   return cudaGetLastError();
 }
 
@@ -335,10 +414,10 @@ static void launch_contract_l(const Plan& p, const AOParams& ap, cudaStream_t s)
   if (ns == 0) return;
   const long long target = 4LL * 152 * 8;   // CTAs to fill the GPU several times over
   long long parts = (target + (long long)p.nk * ns - 1) / ((long long)p.nk * ns);
-  const long long maxparts = (p.ng + 1023) / 1024;
+  const long long maxparts = (p.nblk + 31) / 32;   // at least 32 point blocks per CTA
   if (parts > maxparts) parts = maxparts;
   if (parts < 1) parts = 1;
-  const long long chunk = (p.ng + parts - 1) / parts;
+  const long long chunk = (p.nblk + parts - 1) / parts;
   // Y carries N_g/(4 pi) (see PairParams), hence -Omega 4 pi / (N_k N_g^2)
   const double scale = -p.omega_cell * 4.0 * 3.14159265358979323846 /
                        ((double)p.nk * (double)p.ng * (double)p.ng);
@@ -427,9 +506,10 @@ int orbitals_noalloc_impl(const occri::Plan& p, const double2* C, void* psi_out,
     ao::scale_c_kernel_f<<<2 * 152, 256, 0, s>>>(C, p.ao_norm, cs, p.nao, p.nocc, ncs);
   AOParams ap = p.ao_params();
   ap.cs = cs;
-  const dim3 grid((unsigned)((p.ng + 127) / 128), p.nk);
+  constexpr int KB = orbital_kbatch<T>();
+  const dim3 grid((unsigned)((p.nblk + 3) / 4), (p.nk + KB - 1) / KB);
   for (int i0 = 0; i0 < p.nocc; i0 += kOrbChunk)
-    ao::orbitals_kernel<T, kOrbChunk><<<grid, 128, 0, s>>>(ap, psi, i0);
+    ao::orbitals_kernel<T, kOrbChunk, KB><<<grid, 128, 0, s>>>(ap, psi, i0);
   ao::widen_kernel<T><<<4 * 152, 256, 0, s>>>(psi, (double2*)psi_out, npsi);
   return cudaGetLastError() == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
 }

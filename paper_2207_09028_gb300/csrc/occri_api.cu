@@ -39,6 +39,8 @@ AOParams Plan::ao_params() const {
   a.nimg = nimg;
   a.img_d = img_d; a.img_hi = img_hi; a.img_lo = img_lo; a.img_phase = img_phase;
   a.d0_d = d0_d; a.d0_hi = d0_hi; a.d0_lo = d0_lo; a.t0 = t0; a.kint = kint;
+  for (int d = 0; d < 3; ++d) a.nb[d] = nb[d];
+  a.nblk = nblk; a.lmax = lmax; a.nsa = nsa; a.blist = blist; a.bpre = bpre;
   a.cs = cs;
   return a;
 }
@@ -46,7 +48,7 @@ AOParams Plan::ao_params() const {
 PairParams Plan::pair_params() const {
   PairParams q;
   q.nk = nk; q.nocc = nocc; q.ng = ng; q.N1 = N[0];
-  q.k = 0; q.kp0 = 0; q.nkp = 1;
+  q.k = 0; q.kp0 = 0; q.nkp = 1; q.diag = 0;
   for (int d = 0; d < 3; ++d) q.D[d] = D[d];
   q.kint = kint;
   // reciprocal vectors b_i (rows): B = 2 pi (A^{-1})^T
@@ -321,7 +323,7 @@ void free_plan(Plan* p) {
   void* bufs[] = {p->shells, p->atom_shell0, p->img_d, p->img_hi, p->img_lo, p->img_phase,
                   p->d0_d, p->d0_hi, p->d0_lo, p->t0, p->kint, p->psi, p->Y, p->scratch,
                   p->kc, p->xi, p->mmat, p->ek, p->dacc, p->status, p->h_c, p->h_kc, p->h_k,
-                  p->h_ex, p->ao_norm, p->cs, p->shell_list_l[0], p->shell_list_l[1], p->shell_list_l[2],
+                  p->h_ex, p->ao_norm, p->cs, p->blist, p->bpre, p->shell_list_l[0], p->shell_list_l[1], p->shell_list_l[2],
                   p->shell_list_l[3]};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -393,21 +395,23 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
   }
   long long wave = 0;
   for (int k = 0; k < p->nk; ++k)
-    for (int kp0 = 0; kp0 < p->nk; kp0 += p->nkp_wave, ++wave) {
-      const int nkp = std::min(p->nkp_wave, p->nk - kp0);
+    for (int kp0 = k; kp0 < p->nk; ++wave) {   // unordered pairs: (k, k), then k' > k
+      const int diag = (kp0 == k) ? 1 : 0;
+      const int nkp = diag ? 1 : std::min(p->nkp_wave, p->nk - kp0);
       cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
       bool sample = timed && (wave % p->timing_every == 0);
       if (sample)
         for (int i = 0; i < 4 && sample; ++i) sample = (ev[i] = take_event(p)) != nullptr;
-      if (launch_pair_wave<T>(*p, k, kp0, nkp, s, sample ? ev : nullptr) != cudaSuccess)
+      if (launch_pair_wave<T>(*p, k, kp0, nkp, diag, s, sample ? ev : nullptr) != cudaSuccess)
         return OCCRI_ECUDA;
       launches += 3;
       if (sample) {
-        const double nf = (double)nkp * p->nocc * p->nocc;
+        const double nf = (double)wave_fields(p->nocc, nkp, diag);
         p->ev_pending.push_back(Plan::TimedSpan{ev[0], ev[1], OCCRI_STAGE_PAIR_A, nf});
         p->ev_pending.push_back(Plan::TimedSpan{ev[1], ev[2], OCCRI_STAGE_PAIR_B, nf});
         p->ev_pending.push_back(Plan::TimedSpan{ev[2], ev[3], OCCRI_STAGE_PAIR_C, nf});
       }
+      kp0 += nkp;
     }
   {
     StageTimer t(p, timed);
@@ -450,9 +454,11 @@ int vjp_impl(Plan* p, double gEx, void* gC, double* gomega) {
     if (cudaMemsetAsync(p->dacc, 0, 2 * sizeof(double), s) != cudaSuccess) return OCCRI_ECUDA;
     if (p->kernel.kind != OCCRI_COULOMB) {
       for (int k = 0; k < p->nk; ++k)
-        for (int kp0 = 0; kp0 < p->nk; kp0 += p->nkp_wave) {
-          const int nkp = std::min(p->nkp_wave, p->nk - kp0);
-          if (launch_domega_wave<T>(*p, k, kp0, nkp, s) != cudaSuccess) return OCCRI_ECUDA;
+        for (int kp0 = k; kp0 < p->nk;) {
+          const int diag = (kp0 == k) ? 1 : 0;
+          const int nkp = diag ? 1 : std::min(p->nkp_wave, p->nk - kp0);
+          if (launch_domega_wave<T>(*p, k, kp0, nkp, diag, s) != cudaSuccess) return OCCRI_ECUDA;
+          kp0 += nkp;
         }
     }
     const double ngd = (double)p->ng;
@@ -583,43 +589,67 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     atom_shell0[a] = s;
   }
 
-  // per (atom, point): T0 bringing r - A into the Wigner-Seitz cell, d0 = r - A - T0
+  // Point blocks of 2 x 4 x 4 grid points (one warp each, ragged at the edges). Every
+  // point of a block shares the block's T0, the lattice vector that brings the block
+  // centre minus A into the Wigner-Seitz cell; d0 = r - A - T0 per (atom, point).
   const long long ng = p->ng;
+  const int BD[3] = {2, 4, 4};
+  for (int d = 0; d < 3; ++d) p->nb[d] = (grid[d] + BD[d] - 1) / BD[d];
+  const int nblk = p->nb[0] * p->nb[1] * p->nb[2];
+  p->nblk = nblk;
   std::vector<double> d0((size_t)p->natm * 3 * ng);
-  std::vector<int> t0((size_t)p->natm * ng);
+  std::vector<int> t0((size_t)p->natm * nblk);
+  std::vector<double> bcen((size_t)p->natm * nblk * 3);  // block centre - A - T0
+  std::vector<double> brad(nblk, 0.0);                     // max |r - centre| in the block
   double rbound = 0.0;
   for (int a = 0; a < p->natm; ++a) {
     const double* A = cell->xyz + 3 * a;
     double af[3];
     for (int d = 0; d < 3; ++d) af[d] = A[0] * inv[0][d] + A[1] * inv[1][d] + A[2] * inv[2][d];
-    for (long long n = 0; n < ng; ++n) {
-      const int n1 = (int)(n / ((long long)grid[1] * grid[2]));
-      const int n2 = (int)((n / grid[2]) % grid[1]);
-      const int n3 = (int)(n % grid[2]);
-      const double f[3] = {(double)n1 / grid[0] - af[0], (double)n2 / grid[1] - af[1],
-                           (double)n3 / grid[2] - af[2]};
-      int base[3];
-      for (int d = 0; d < 3; ++d) base[d] = (int)std::floor(f[d] + 0.5);
-      double best = 1e300;
-      int bt[3] = {base[0], base[1], base[2]};
-      double bd[3] = {0, 0, 0};
-      for (int e0 = -1; e0 <= 1; ++e0)
-        for (int e1 = -1; e1 <= 1; ++e1)
-          for (int e2 = -1; e2 <= 1; ++e2) {
-            const int t[3] = {base[0] + e0, base[1] + e1, base[2] + e2};
-            const double g[3] = {f[0] - t[0], f[1] - t[1], f[2] - t[2]};
-            double c[3];
-            for (int d = 0; d < 3; ++d) c[d] = g[0] * lat[0][d] + g[1] * lat[1][d] + g[2] * lat[2][d];
-            const double r2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-            if (r2 < best) {
-              best = r2;
-              for (int d = 0; d < 3; ++d) { bt[d] = t[d]; bd[d] = c[d]; }
-            }
-          }
-      rbound = std::max(rbound, std::sqrt(best));
-      for (int d = 0; d < 3; ++d) d0[((size_t)a * 3 + d) * ng + n] = bd[d];
-      t0[(size_t)a * ng + n] = dev::pack_t0(bt[0], bt[1], bt[2]);
-    }
+    for (int b1 = 0; b1 < p->nb[0]; ++b1)
+      for (int b2 = 0; b2 < p->nb[1]; ++b2)
+        for (int b3 = 0; b3 < p->nb[2]; ++b3) {
+          const int blk = (b1 * p->nb[1] + b2) * p->nb[2] + b3;
+          const int lo[3] = {BD[0] * b1, BD[1] * b2, BD[2] * b3};
+          int hi[3];
+          for (int d = 0; d < 3; ++d) hi[d] = std::min(lo[d] + BD[d], grid[d]) - 1;
+          double fc[3];
+          for (int d = 0; d < 3; ++d) fc[d] = 0.5 * (lo[d] + hi[d]) / grid[d] - af[d];
+          int base[3];
+          for (int d = 0; d < 3; ++d) base[d] = (int)std::floor(fc[d] + 0.5);
+          double best = 1e300;
+          int bt[3] = {base[0], base[1], base[2]};
+          double bc[3] = {0, 0, 0};
+          for (int e0 = -1; e0 <= 1; ++e0)
+            for (int e1 = -1; e1 <= 1; ++e1)
+              for (int e2 = -1; e2 <= 1; ++e2) {
+                const int t[3] = {base[0] + e0, base[1] + e1, base[2] + e2};
+                const double g[3] = {fc[0] - t[0], fc[1] - t[1], fc[2] - t[2]};
+                double c[3];
+                for (int d = 0; d < 3; ++d) c[d] = g[0] * lat[0][d] + g[1] * lat[1][d] + g[2] * lat[2][d];
+                const double r2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+                if (r2 < best) {
+                  best = r2;
+                  for (int d = 0; d < 3; ++d) { bt[d] = t[d]; bc[d] = c[d]; }
+                }
+              }
+          t0[(size_t)a * nblk + blk] = dev::pack_t0(bt[0], bt[1], bt[2]);
+          for (int d = 0; d < 3; ++d) bcen[((size_t)a * nblk + blk) * 3 + d] = bc[d];
+          for (int n1 = lo[0]; n1 <= hi[0]; ++n1)
+            for (int n2 = lo[1]; n2 <= hi[1]; ++n2)
+              for (int n3 = lo[2]; n3 <= hi[2]; ++n3) {
+                const long long n = ((long long)n1 * grid[1] + n2) * grid[2] + n3;
+                const double f[3] = {(double)n1 / grid[0] - af[0] - bt[0],
+                                     (double)n2 / grid[1] - af[1] - bt[1],
+                                     (double)n3 / grid[2] - af[2] - bt[2]};
+                double c[3];
+                for (int d = 0; d < 3; ++d) c[d] = f[0] * lat[0][d] + f[1] * lat[1][d] + f[2] * lat[2][d];
+                for (int d = 0; d < 3; ++d) d0[((size_t)a * 3 + d) * ng + n] = c[d];
+                rbound = std::max(rbound, std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]));
+                const double e[3] = {c[0] - bc[0], c[1] - bc[1], c[2] - bc[2]};
+                brad[blk] = std::max(brad[blk], std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]));
+              }
+        }
   }
   rbound += 1e-9;
 
@@ -652,6 +682,47 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     while (c < nimg && imgs[c].len <= lim) ++c;
     sh[s].nimg = c;
   }
+  // per (atom, block): master images sorted by distance from the block centre, and
+  // per shell the prefix within the shell's radius plus the block radius
+  int nsa = 0;
+  for (int a = 0; a < p->natm; ++a) nsa = std::max(nsa, atom_shell0[a + 1] - atom_shell0[a]);
+  p->nsa = nsa;
+  std::vector<std::vector<unsigned short>> lists((size_t)p->natm * nblk);
+  std::vector<unsigned short> bpre((size_t)p->natm * nblk * std::max(nsa, 1), 0);
+  int lmax = 1;
+  {
+    std::vector<std::pair<double, int>> cand;
+    for (int a = 0; a < p->natm; ++a) {
+      double rmax_a = 0.0;
+      for (int s2 = atom_shell0[a]; s2 < atom_shell0[a + 1]; ++s2) rmax_a = std::max(rmax_a, rcut[s2]);
+      for (int blk = 0; blk < nblk; ++blk) {
+        const double* c = &bcen[((size_t)a * nblk + blk) * 3];
+        const double reach = rmax_a + brad[blk] + 1e-9;
+        cand.clear();
+        for (int j = 0; j < nimg; ++j) {
+          const double e[3] = {c[0] - imgs[j].x, c[1] - imgs[j].y, c[2] - imgs[j].z};
+          const double dist = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+          if (dist <= reach) cand.push_back({dist, j});
+        }
+        std::sort(cand.begin(), cand.end());
+        auto& L = lists[(size_t)a * nblk + blk];
+        L.resize(cand.size());
+        for (size_t u = 0; u < cand.size(); ++u) L[u] = (unsigned short)cand[u].second;
+        for (int s2 = atom_shell0[a]; s2 < atom_shell0[a + 1]; ++s2) {
+          const double lim = rcut[s2] + brad[blk] + 1e-9;
+          int cnt = 0;
+          while (cnt < (int)cand.size() && cand[cnt].first <= lim) ++cnt;
+          bpre[((size_t)a * nblk + blk) * nsa + (s2 - atom_shell0[a])] = (unsigned short)cnt;
+        }
+        lmax = std::max(lmax, (int)cand.size());
+      }
+    }
+  }
+  p->lmax = lmax;
+  std::vector<unsigned short> blist((size_t)p->natm * nblk * lmax, 0);
+  for (size_t q = 0; q < lists.size(); ++q)
+    std::copy(lists[q].begin(), lists[q].end(), blist.begin() + q * lmax);
+  if (nimg >= 65536) { delete p; return OCCRI_EUNSUPPORTED; }
   std::vector<double> img_d((size_t)3 * nimg);
   std::vector<float> img_hi((size_t)3 * nimg), img_lo((size_t)3 * nimg);
   for (int j = 0; j < nimg; ++j) {
@@ -665,7 +736,9 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
   // e^{i k.T'} with exact integer reduction of the phase
   std::vector<double2> ph_d;
   std::vector<float2> ph_f;
-  if (precision == OCCRI_FP64) ph_d.resize((size_t)p->nk * nimg); else ph_f.resize((size_t)p->nk * nimg);
+  const int nk_pad = (p->nk + kPhasePadK - 1) / kPhasePadK * kPhasePadK;   // zero rows past nk
+  if (precision == OCCRI_FP64) ph_d.assign((size_t)nk_pad * nimg, make_double2(0.0, 0.0));
+  else ph_f.assign((size_t)nk_pad * nimg, make_float2(0.f, 0.f));
   for (int k = 0; k < p->nk; ++k)
     for (int j = 0; j < nimg; ++j) {
       long long num = 0;
@@ -695,6 +768,8 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     p->cs = b;
   }
   chk(upload(&p->t0, t0, &tot));
+  chk(upload(&p->blist, blist, &tot));
+  chk(upload(&p->bpre, bpre, &tot));
   if (precision == OCCRI_FP64) {
     chk(upload(&p->img_d, img_d, &tot));
     chk(upload(&p->d0_d, d0, &tot));

@@ -50,8 +50,14 @@ struct AOParams {
   const double* d0_d;        // [natm][3][ng] r_n - A - T0 (bohr)
   const float* d0_hi;        // [natm][3][ng]
   const float* d0_lo;        // [natm][3][ng]
-  const int* t0;             // [natm][ng] packed T0 integer coordinates (3 x 10 bits)
+  const int* t0;             // [natm][nblk] packed T0 of each point block (3 x 10 bits)
   const int* kint;           // [nk][3]
+  // point blocks of 2 x 4 x 4 grid points (one warp each) sharing one Wigner-Seitz
+  // shift T0; per (atom, block) the master images sorted by distance from the block
+  // centre, and per shell the prefix of that list that reaches every point of the block
+  int nb[3], nblk, lmax, nsa;
+  const unsigned short* blist;   // [natm][nblk][lmax] master-list indices
+  const unsigned short* bpre;    // [natm][nblk][nsa] per-shell prefix lengths
   const void* cs;            // [nk][nao][nocc] N_mu C^k_{mu i}: double2 (FP64) or float4 hi/lo (FP32)
 };
 
@@ -60,6 +66,7 @@ struct PairParams {
   int nk, nocc, N1;          // N1: cubic grid edge
   long long ng;
   int k, kp0, nkp;
+  int diag;                  // 1: the wave is (k, k) and holds the fields i <= j only
   int D[3];
   const int* kint;           // [nk][3]
   double g[6];               // reciprocal metric b_i.b_j: 11, 22, 33, 12, 13, 23
@@ -101,6 +108,9 @@ struct Plan {
   int* t0 = nullptr;
   int* kint = nullptr;
   int nimg = 0;
+  int nb[3] = {0, 0, 0}, nblk = 0, lmax = 0, nsa = 0;
+  unsigned short* blist = nullptr;
+  unsigned short* bpre = nullptr;
 
   // device workspaces
   void* psi = nullptr;       // [nk][nocc][ng] cplx_t<T>
@@ -141,6 +151,10 @@ struct Plan {
 
 // orbitals per launch of the orbital kernel, and per launch of the contraction kernel
 constexpr int kOrbChunk = 8;
+// k-points per thread in the orbital kernel (the image geometry is shared by them);
+// the phase table e^{i k.T'} has its k rows padded with zeros to a multiple of 4.
+template <typename T> constexpr int orbital_kbatch() { return sizeof(T) == 4 ? 4 : 2; }
+constexpr int kPhasePadK = 4;
 template <typename T> constexpr int contract_chunk() { return sizeof(T) == 4 ? 8 : 4; }
 
 // ---- launchers (return cudaError_t of the launch) ----
@@ -150,13 +164,21 @@ template <typename T>
 cudaError_t launch_orbitals(const Plan& p, cudaStream_t s);
 template <typename T>
 cudaError_t launch_contract(const Plan& p, cudaStream_t s);
-// Pair-wave launches; when ev != nullptr, ev[0..3] are recorded before pass A,
-// before pass B, before pass C and after pass C.
+// Pair-wave launches over unordered pairs: diag = 1 is the wave (k, k) with fields
+// i <= j; diag = 0 covers k' in [kp0, kp0 + nkp), all kp0 > k, with every (i, j).
+// When ev != nullptr, ev[0..3] are recorded before pass A, before pass B, before
+// pass C and after pass C.
 template <typename T>
-cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, cudaStream_t s,
+cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s,
                              cudaEvent_t* ev = nullptr);
 template <typename T>
-cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, cudaStream_t s);
+cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s);
+
+// fields and pass-C targets of a wave
+inline int wave_fields(int nocc, int nkp, int diag) {
+  return diag ? nocc * (nocc + 1) / 2 : nkp * nocc * nocc;
+}
+inline int wave_targets(int nocc, int nkp, int diag) { return diag ? nocc : nocc + nkp * nocc; }
 template <typename T>
 cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s);
 

@@ -2,9 +2,12 @@
 //
 // For output k-point k, a block of k' and every occupied pair (i, j), the field
 //   rho(r) = conj(psi_{jk'}(r)) psi_{ik}(r) e^{-iq.r},   q = k - k'      (Eq. aodf)
-// is transformed, multiplied by v(|G+q|)/N_g (Eqs. VGao, recipcoul) and
+// is transformed, multiplied by v(|G+q|)/(4 pi) (Eqs. VGao, recipcoul) and
 // transformed back; the potential W = e^{iq.r} u accumulates into
 //   Y_{ik}(r) += psi_{jk'}(r) W(r)                                       (Eq. occrikinterm).
+// The reversed pair (k', k, j, i) has the conjugate field and potential, so each
+// unordered pair is transformed once and also feeds Y_{jk'} += psi_{ik} conj(W)
+// (the tie-averaged kernel is inversion-symmetric, v_{-q}(-m) = v_q(m)).
 //
 // A cubic N^3 field does not fit on one SM, so a round trip takes three passes
 // over a scratch field stored as S[f][m3][n1][m2] (third axis outermost):
@@ -32,34 +35,9 @@ using dev::expm1_t;
 
 constexpr int pitch(int n) { return (n % 2 == 0) ? n + 1 : n; }
 constexpr int threads_for(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : 128); }
-
-// Integer reduction of x = m + Q/D into [-N/2, N/2): returns X = x*D (exact),
-// and whether it is an exact tie at -N/2.
-__device__ __forceinline__ long long reduce_axis(int m, int Q, int D, int N, bool* tie) {
-  const long long P = (long long)N * D;
-  long long X = (long long)m * D + Q;
-  // floor((2X + P) / (2P))
-  long long num = 2 * X + P, den = 2 * P;
-  long long fl = num / den;
-  if ((num % den != 0) && ((num < 0) != (den < 0))) --fl;
-  X -= P * fl;
-  *tie = (2 * X == -P);
-  return X;
-}
-
-struct AxisVal {
-  double xa, xb;   // reduced coordinate and its second alias (== xa unless tied)
-  bool zero;
-};
-
-__device__ __forceinline__ AxisVal axis_val(int m, int Q, int D, int N) {
-  bool tie;
-  long long X = reduce_axis(m, Q, D, N, &tie);
-  AxisVal a;
-  a.xa = double(X) / double(D);
-  a.xb = tie ? double(X + (long long)N * D) / double(D) : a.xa;
-  a.zero = (X == 0);
-  return a;
+// resident CTAs per SM requested from the register allocator (one line per thread)
+constexpr int min_blocks(int n, int elem_bytes) {
+  return elem_bytes > 8 ? (n <= 32 ? 4 : 2) : (n <= 32 ? 8 : 5);
 }
 
 // f(|G+q|)/(4 pi) of Eq. recipcoul for |G+q|^2 = g2 > 0.
@@ -80,14 +58,23 @@ __device__ __forceinline__ T kernel_df(T g2, int kind, T inv4w2, T omega) {
   return kind == OCCRI_ERFC ? -e : e;
 }
 
-// field f of the wave -> (k' offset, i, j)
+// field f of the wave -> (k' offset, i, j); diagonal waves list i <= j row by row
 struct FieldIdx { int kpl, i, j; };
-__device__ __forceinline__ FieldIdx field_idx(int f, int nocc) {
+__device__ __forceinline__ FieldIdx field_idx(int f, int nocc, int diag) {
   FieldIdx r;
+  if (diag) {
+    int i = 0, row = nocc;
+    while (f >= row) { f -= row; ++i; --row; }
+    r.kpl = 0; r.i = i; r.j = i + f;
+    return r;
+  }
   r.j = f % nocc;
   r.i = (f / nocc) % nocc;
   r.kpl = f / (nocc * nocc);
   return r;
+}
+__device__ __forceinline__ int diag_field(int i, int j, int nocc) {  // i <= j
+  return i * nocc - i * (i - 1) / 2 + (j - i);
 }
 
 // ------------------------------------------------------------------ async plane staging
@@ -116,74 +103,168 @@ __device__ __forceinline__ void stage_plane(cplx_t<T>* dst, const cplx_t<T>* src
   }
 }
 
+// ------------------------------------------------------------------ one line transform
+// Forward DFT (e^{-2 pi i m n / N}) of the N elements at base[m * stride], in place,
+// with the whole line in registers. With conj_io the line is conjugated on load and
+// on store, which gives the unnormalised inverse transform. post(k, re, im) sees
+// output index k before the store (store is skipped when !store). Each kernel
+// calls this once, inside a runtime loop, so the unrolled transform exists once
+// in the instruction stream.
+template <typename T, int N, typename Post>
+__device__ __forceinline__ void line_fft(cplx_t<T>* base, int stride, bool conj_io, bool store,
+                                         Post&& post) {
+  T re[N], im[N];
+  const T sg = conj_io ? T(-1) : T(1);
+  fft::static_for<N>([&](auto I) {
+    constexpr int m = decltype(I)::value;
+    const cplx_t<T> v = base[m * stride];
+    re[m] = v.x;
+    im[m] = sg * v.y;
+  });
+  fft::fft_dif<N, -1>(re, im);
+  fft::static_for<N>([&](auto I) {
+    constexpr int q = decltype(I)::value;
+    constexpr int k = fft::dif_rev(N, q);
+    post(k, re[q], im[q]);
+    if (store) base[k * stride] = mk<T>(re[q], sg * im[q]);
+  });
+}
+
 // ------------------------------------------------------------------ kernel values per bin
-// Axis tables: reduced coordinate x (first alias), flags bit0 = tie, bit1 = x == 0.
-// For axis 1 also g11 x^2 split hi/lo, so that |G+q|^2 costs a few FMAs per bin:
-//   g2(m1) = a1(m1) + x1(m1) * beta + gamma,  beta = 2 (g12 x2 + g13 x3),
-//   gamma = g22 x2^2 + 2 g23 x2 x3 + g33 x3^2 (per column, FP64 split hi/lo).
+// Per-CTA table for axis 1 and per-column constants for axes 2, 3 give, for the first
+// alias of every axis,
+//   |G+q|^2 = a1(m1) + x1(m1) * beta + gamma,  a1 = g11 x1^2,
+//   beta = 2 (g12 x2 + g13 x3),  gamma = g22 x2^2 + 2 g23 x2 x3 + g33 x3^2,
+// all formed in the working precision: in FP32 the metric is a hi/lo pair and every
+// product is error-free (two-product by FMA), so no rounding biases all bins alike and
+// no FP64 instruction (1/64 rate) is issued. Bins with an exact tie on some axis, or
+// G+q = 0, go to one out-of-line function (flags: bit0 tie, bit1 zero coordinate).
+
+// Reduced coordinate of bin m on one axis as the exact integer X = x*D in
+// [-N*D/2, N*D/2), plus tie and zero flags (all integer, |X| < 2^12).
+struct AxisInt {
+  int X, D, N;
+  bool tie, zero;
+};
+__device__ __forceinline__ AxisInt axis_int(int m, int Q, int D, int N) {
+  const int P = N * D;
+  int X = m * D + Q;           // |Q| < D, so X in (-P, 2P)
+  // subtract P*floor(X/P + 1/2)
+  const int twice = 2 * X + P;
+  const int fl = (twice >= 0) ? twice / (2 * P) : -((-twice + 2 * P - 1) / (2 * P));
+  X -= P * fl;
+  AxisInt r;
+  r.X = X; r.D = D; r.N = N;
+  r.tie = (2 * X == -P);
+  r.zero = (X == 0);
+  return r;
+}
+template <typename T> __device__ __forceinline__ T axis_x(const AxisInt& a, bool second) {
+  return T(second ? a.X + a.N * a.D : a.X) / T(a.D);
+}
+
+// hi/lo parts of the reciprocal metric g_ij (lo = 0 in FP64)
+template <typename T>
+struct MetricHL {
+  T h[6], l[6];
+  __device__ __forceinline__ explicit MetricHL(const PairParams& p) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      h[i] = T(p.g[i]);
+      l[i] = T(p.g[i] - double(h[i]));
+    }
+  }
+};
+
+// s (hi, lo) += g * a * b with g = (gh, gl), error-free in the product a*b.
+template <typename T>
+__device__ __forceinline__ void acc_gab(T gh, T gl, T a, T b, T& hi, T& lo) {
+  const T ph = a * b;
+  const T pl = fma(a, b, -ph);
+  const T t = gh * ph;
+  lo += fma(gh, ph, -t) + gh * pl + gl * ph;
+  const T s = hi + t;                       // two-sum of hi + t
+  const T bb = s - hi;
+  lo += (hi - (s - bb)) + (t - bb);
+  hi = s;
+}
+
 template <typename T>
 struct Axis1 {
   T x, ah, al;
   int flags;
 };
 
-__device__ __forceinline__ int axis_flags(const AxisVal& a) {
-  return (a.xa != a.xb ? 1 : 0) | (a.zero ? 2 : 0);
-}
-
-// Rare bins (an exact tie on some axis, or G+q = 0): full tie-averaged evaluation.
-template <typename T, bool DERIV>
-__device__ __noinline__ T slow_bin(const PairParams& p, int m1, int m2, int m3, const int* Q) {
-  const AxisVal a = axis_val(m1, Q[0], p.D[0], p.N1);
-  const AxisVal b = axis_val(m2, Q[1], p.D[1], p.N1);
-  const AxisVal c = axis_val(m3, Q[2], p.D[2], p.N1);
-  if (a.zero && b.zero && c.zero) return DERIV ? T(p.dg0) : T(p.g0);
-  double s = 0.0;
-  for (int k = 0; k < 8; ++k) {
-    const double x1 = (k & 1) ? a.xb : a.xa, x2 = (k & 2) ? b.xb : b.xa, x3 = (k & 4) ? c.xb : c.xa;
-    const double g2 = p.g[0] * x1 * x1 + p.g[1] * x2 * x2 + p.g[2] * x3 * x3 +
-                      2.0 * (p.g[3] * x1 * x2 + p.g[4] * x1 * x3 + p.g[5] * x2 * x3);
-    s += DERIV ? kernel_df<double>(g2, p.kind, p.inv4w2, p.omega)
-               : kernel_f<double>(g2, p.kind, p.inv4w2);
-  }
-  return T(0.125 * s);
+template <typename T>
+__device__ __forceinline__ Axis1<T> axis1_entry(const MetricHL<T>& g, const AxisInt& a) {
+  Axis1<T> r;
+  r.x = axis_x<T>(a, false);
+  T hi = T(0), lo = T(0);
+  acc_gab<T>(g.h[0], g.l[0], r.x, r.x, hi, lo);
+  r.ah = hi;
+  r.al = lo;
+  r.flags = (a.tie ? 1 : 0) | (a.zero ? 2 : 0);
+  return r;
 }
 
 template <typename T>
 struct ColumnConst {
   T bh, bl, ch, cl;
-  int flags;  // bit0: tie on axis 2 or 3; bit1: x2 == 0 and x3 == 0
+  int flags;
 };
 
 template <typename T>
-__device__ __forceinline__ ColumnConst<T> column_const(const PairParams& p, const AxisVal& b,
-                                                       const AxisVal& c) {
-  const double beta = 2.0 * (p.g[3] * b.xa + p.g[4] * c.xa);
-  const double gam = p.g[1] * b.xa * b.xa + p.g[2] * c.xa * c.xa + 2.0 * p.g[5] * b.xa * c.xa;
+__device__ __forceinline__ ColumnConst<T> column_const(const MetricHL<T>& g, const AxisInt& b,
+                                                       const AxisInt& c) {
   ColumnConst<T> r;
-  r.bh = T(beta);
-  r.bl = T(beta - double(r.bh));
-  r.ch = T(gam);
-  r.cl = T(gam - double(r.ch));
-  r.flags = ((b.xa != b.xb) || (c.xa != c.xb) ? 1 : 0) | ((b.zero && c.zero) ? 2 : 0);
+  const T x2 = axis_x<T>(b, false), x3 = axis_x<T>(c, false);
+  T bh = T(0), bl = T(0);   // beta = 2 g12 x2 + 2 g13 x3
+  acc_gab<T>(g.h[3], g.l[3], T(2), x2, bh, bl);
+  acc_gab<T>(g.h[4], g.l[4], T(2), x3, bh, bl);
+  T ch = T(0), cl = T(0);   // gamma = g22 x2^2 + g33 x3^2 + 2 g23 x2 x3
+  acc_gab<T>(g.h[1], g.l[1], x2, x2, ch, cl);
+  acc_gab<T>(g.h[2], g.l[2], x3, x3, ch, cl);
+  acc_gab<T>(g.h[5], g.l[5], T(2) * x2, x3, ch, cl);
+  r.bh = bh; r.bl = bl; r.ch = ch; r.cl = cl;
+  r.flags = ((b.tie || c.tie) ? 1 : 0) | ((b.zero && c.zero) ? 2 : 0);
   return r;
 }
 
-template <typename T>
-__device__ __forceinline__ Axis1<T> axis1_entry(const PairParams& p, const AxisVal& a) {
-  const double a1 = p.g[0] * a.xa * a.xa;
-  Axis1<T> r;
-  r.x = T(a.xa);
-  r.ah = T(a1);
-  r.al = T(a1 - double(r.ah));
-  r.flags = axis_flags(a);
-  return r;
+// Tie-averaged value on a rare bin (working precision, out of line).
+template <typename T, bool DERIV>
+__device__ __noinline__ T bin_value_rare(const PairParams& p, int m1, int m2, int m3, int q1,
+                                         int q2, int q3) {
+  const AxisInt a = axis_int(m1, q1, p.D[0], p.N1);
+  const AxisInt b = axis_int(m2, q2, p.D[1], p.N1);
+  const AxisInt c = axis_int(m3, q3, p.D[2], p.N1);
+  if (a.zero && b.zero && c.zero) return DERIV ? T(p.dg0) : T(p.g0);
+  const MetricHL<T> g(p);
+  const T i4 = T(p.inv4w2), om = T(p.omega);
+  T s = T(0);
+  int n = 0;
+  for (int u = 0; u < 8; ++u) {
+    if (((u & 1) && !a.tie) || ((u & 2) && !b.tie) || ((u & 4) && !c.tie)) continue;
+    const T x1 = axis_x<T>(a, u & 1), x2 = axis_x<T>(b, u & 2), x3 = axis_x<T>(c, u & 4);
+    T hi = T(0), lo = T(0);
+    acc_gab<T>(g.h[0], g.l[0], x1, x1, hi, lo);
+    acc_gab<T>(g.h[1], g.l[1], x2, x2, hi, lo);
+    acc_gab<T>(g.h[2], g.l[2], x3, x3, hi, lo);
+    acc_gab<T>(g.h[3], g.l[3], T(2) * x1, x2, hi, lo);
+    acc_gab<T>(g.h[4], g.l[4], T(2) * x1, x3, hi, lo);
+    acc_gab<T>(g.h[5], g.l[5], T(2) * x2, x3, hi, lo);
+    const T g2 = hi + lo;
+    s += DERIV ? kernel_df<T>(g2, p.kind, i4, om) : kernel_f<T>(g2, p.kind, i4);
+    ++n;
+  }
+  return s / T(n);
 }
 
 template <typename T, bool DERIV>
-__device__ __forceinline__ T fast_bin(const PairParams& p, const Axis1<T>& a, const ColumnConst<T>& c,
-                                      int m1, int m2, int m3, const int* Q) {
-  if ((a.flags | c.flags) & 1 || ((a.flags & c.flags) & 2)) return slow_bin<T, DERIV>(p, m1, m2, m3, Q);
+__device__ __forceinline__ T bin_value(const PairParams& p, const Axis1<T>& a,
+                                       const ColumnConst<T>& c, int m1, int m2, int m3,
+                                       const int* Q) {
+  if (((a.flags | c.flags) & 1) || ((a.flags & c.flags) & 2))
+    return bin_value_rare<T, DERIV>(p, m1, m2, m3, Q[0], Q[1], Q[2]);
   const T g2 = (a.ah + a.x * c.bh + c.ch) + (a.al + a.x * c.bl + c.cl);
   return DERIV ? kernel_df<T>(g2, p.kind, T(p.inv4w2), T(p.omega))
                : kernel_f<T>(g2, p.kind, T(p.inv4w2));
@@ -192,22 +273,18 @@ __device__ __forceinline__ T fast_bin(const PairParams& p, const Axis1<T>& a, co
 // ------------------------------------------------------------------ pass A
 // plane n1 of field (i, j): rho = conj(psi_j) psi_i e^{-iq.r}; FFT along n3, then n2.
 template <typename T, int N>
-__global__ void __launch_bounds__(threads_for(N))
+__global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
 pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams p) {
   using C2 = cplx_t<T>;
   constexpr int P = pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2* pl = reinterpret_cast<C2*>(smem_raw);   // psi_i plane, then rho / its transform
-  C2* qj = pl + N * P;                         // psi_j plane
-  C2* ph2 = qj + N * P;
+  C2* pl = reinterpret_cast<C2*>(smem_raw);   // rho, then its 2-D transform
+  C2* ph2 = pl + N * P;
   C2* ph3 = ph2 + N;
   const int n1 = blockIdx.x;
   const int f = blockIdx.y;
-  const FieldIdx fi = field_idx(f, p.nocc);
+  const FieldIdx fi = field_idx(f, p.nocc, p.diag);
   const int kp = p.kp0 + fi.kpl;
-  stage_plane<T, N, P>(pl, psi + (size_t)(p.k * p.nocc + fi.i) * p.ng + (size_t)n1 * N * N);
-  stage_plane<T, N, P>(qj, psi + (size_t)(kp * p.nocc + fi.j) * p.ng + (size_t)n1 * N * N);
-  cp_async_commit();
   int Q[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
@@ -216,39 +293,25 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
     ph3[t] = cis_frac<T>((long long)Q[2] * t, (long long)p.D[2] * N, -1);
   }
   const C2 ph1 = cis_frac<T>((long long)Q[0] * n1, (long long)p.D[0] * N, -1);
-  cp_async_wait<0>();
   __syncthreads();
-  if (threadIdx.x < N) {  // rows (fixed n2 = r): form rho, FFT along n3
-    const int r = threadIdx.x;
-    const C2 ph12 = cmul<T>(ph1, ph2[r]);
-    T re[N], im[N];
-    fft::static_for<N>([&](auto I) {
-      constexpr int m = decltype(I)::value;
-      const C2 v = cmul<T>(cmulc<T>(qj[r * P + m], pl[r * P + m]), cmul<T>(ph12, ph3[m]));
-      re[m] = v.x; im[m] = v.y;
-    });
-    fft::fft_dif<N, -1>(re, im);
-    fft::static_for<N>([&](auto I) {
-      constexpr int q = decltype(I)::value;
-      pl[r * P + fft::dif_rev(N, q)] = mk<T>(re[q], im[q]);
-    });
+  const C2* pi = psi + (size_t)(p.k * p.nocc + fi.i) * p.ng + (size_t)n1 * N * N;
+  const C2* pj = psi + (size_t)(kp * p.nocc + fi.j) * p.ng + (size_t)n1 * N * N;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int n2 = e / N, n3 = e - (e / N) * N;
+    const C2 r = cmulc<T>(__ldg(pj + e), __ldg(pi + e));
+    pl[n2 * P + n3] = cmul<T>(r, cmul<T>(ph1, cmul<T>(ph2[n2], ph3[n3])));
   }
   __syncthreads();
-  if (threadIdx.x < N) {  // columns: along n2
-    const int c = threadIdx.x;
-    T re[N], im[N];
-    fft::static_for<N>([&](auto I) {
-      constexpr int m = decltype(I)::value;
-      const C2 v = pl[m * P + c];
-      re[m] = v.x; im[m] = v.y;
-    });
-    fft::fft_dif<N, -1>(re, im);
-    fft::static_for<N>([&](auto I) {
-      constexpr int q = decltype(I)::value;
-      pl[fft::dif_rev(N, q) * P + c] = mk<T>(re[q], im[q]);
-    });
+#pragma unroll 1
+  for (int job = 0; job < 2; ++job) {   // rows (along n3), then columns (along n2)
+    if (threadIdx.x < N) {
+      const int t = threadIdx.x;
+      line_fft<T, N>(job == 0 ? pl + t * P : pl + t, job == 0 ? 1 : P, false, true,
+                     [](int, T&, T&) {});
+    }
+    __syncthreads();
   }
-  __syncthreads();
   C2* out = S + (size_t)f * p.ng;
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int m3 = e / N, m2 = e - (e / N) * N;
@@ -258,6 +321,7 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
 
 // ------------------------------------------------------------------ pass B
 // plane m3 of a field: FFT along n1, multiply by v/(4 pi), inverse along m1, inverse along m2.
+// With DOMEGA: the forward part only, accumulating sum_m (dv/d omega)/(4 pi) |rho^(m)|^2.
 template <typename T, int N, bool DOMEGA>
 __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const PairParams& p,
                                             double* dacc) {
@@ -266,10 +330,11 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* plane = reinterpret_cast<C2*>(smem_raw);                 // [n1][m2]
   Axis1<T>* ax1 = reinterpret_cast<Axis1<T>*>(plane + N * P);  // [m1]
+  T* vtab = reinterpret_cast<T*>(ax1 + N);                     // [m1][m2] v/(4 pi) or dv
   __shared__ double red[4];
   const int m3 = blockIdx.x;
   const int f = blockIdx.y;
-  const FieldIdx fi = field_idx(f, p.nocc);
+  const FieldIdx fi = field_idx(f, p.nocc, p.diag);
   const int kp = p.kp0 + fi.kpl;
   C2* buf = S + (size_t)f * p.ng + (size_t)m3 * N * N;
   stage_plane<T, N, P>(plane, buf);
@@ -277,74 +342,55 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
   int Q[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
+  const MetricHL<T> gm(p);
   for (int t = threadIdx.x; t < N; t += blockDim.x)
-    ax1[t] = axis1_entry<T>(p, axis_val(t, Q[0], p.D[0], N));
-  const AxisVal a3 = axis_val(m3, Q[2], p.D[2], N);
+    ax1[t] = axis1_entry<T>(gm, axis_int(t, Q[0], p.D[0], N));
+  const AxisInt a3 = axis_int(m3, Q[2], p.D[2], N);
+  __syncthreads();
+  if (threadIdx.x < N) {  // kernel values of this column, one rolled loop
+    const int c = threadIdx.x;
+    const ColumnConst<T> cc = column_const<T>(gm, axis_int(c, Q[1], p.D[1], N), a3);
+#pragma unroll 1
+    for (int m1 = 0; m1 < N; ++m1) vtab[m1 * N + c] = bin_value<T, DOMEGA>(p, ax1[m1], cc, m1, c, m3, Q);
+  }
   cp_async_wait<0>();
   __syncthreads();
-  double part = 0.0;
-  if (threadIdx.x < N) {  // columns (fixed m2 = c): along n1, kernel, back along m1
-    const int c = threadIdx.x;
-    const ColumnConst<T> cc = column_const<T>(p, axis_val(c, Q[1], p.D[1], N), a3);
-    T re[N], im[N];
-    fft::static_for<N>([&](auto I) {
-      constexpr int m = decltype(I)::value;
-      const C2 v = plane[m * P + c];
-      re[m] = v.x; im[m] = v.y;
-    });
-    fft::fft_dif<N, -1>(re, im);
-    if constexpr (DOMEGA) {
-      T s = T(0);
-      fft::static_for<N>([&](auto I) {
-        constexpr int q = decltype(I)::value;
-        constexpr int m1 = fft::dif_rev(N, q);
-        const T dv = fast_bin<T, true>(p, ax1[m1], cc, m1, c, m3, Q);
-        s += dv * (re[q] * re[q] + im[q] * im[q]);
-      });
-      part = double(s);
-    } else {
-      fft::static_for<N>([&](auto I) {
-        constexpr int q = decltype(I)::value;
-        constexpr int m1 = fft::dif_rev(N, q);
-        const T v = fast_bin<T, false>(p, ax1[m1], cc, m1, c, m3, Q);
-        re[q] *= v;
-        im[q] *= v;
-      });
-      fft::dif_to_natural<N>(re, im);
-      fft::fft_dif<N, +1>(re, im);
-      fft::static_for<N>([&](auto I) {
-        constexpr int q = decltype(I)::value;
-        plane[fft::dif_rev(N, q) * P + c] = mk<T>(re[q], im[q]);
+  T dsum = T(0);
+  constexpr int NJOB = DOMEGA ? 1 : 3;
+#pragma unroll 1
+  for (int job = 0; job < NJOB; ++job) {
+    // job 0: columns (m2 = t), forward along n1, x v; job 1: columns, inverse along m1;
+    // job 2: rows (n1 = t), inverse along m2
+    if (threadIdx.x < N) {
+      const int t = threadIdx.x;
+      C2* base = (job < 2) ? plane + t : plane + t * P;
+      line_fft<T, N>(base, job < 2 ? P : 1, job > 0, !DOMEGA, [&](int k, T& re, T& im) {
+        if (job == 0) {
+          const T v = vtab[k * N + t];
+          if constexpr (DOMEGA) {
+            dsum += v * (re * re + im * im);
+          } else {
+            re *= v;
+            im *= v;
+          }
+        }
       });
     }
+    __syncthreads();
   }
   if constexpr (DOMEGA) {
+    double part = double(dsum);
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-      atomicAdd(dacc, t);
+      // an unordered pair stands for itself and its reverse, except (k, k, i, i)
+      atomicAdd(dacc, (p.diag && fi.i == fi.j) ? t : 2.0 * t);
     }
     return;
   }
-  __syncthreads();
-  if (threadIdx.x < N) {  // rows: back along m2
-    const int r = threadIdx.x;
-    T re[N], im[N];
-    fft::static_for<N>([&](auto I) {
-      constexpr int m = decltype(I)::value;
-      const C2 v = plane[r * P + m];
-      re[m] = v.x; im[m] = v.y;
-    });
-    fft::fft_dif<N, +1>(re, im);
-    fft::static_for<N>([&](auto I) {
-      constexpr int q = decltype(I)::value;
-      plane[r * P + fft::dif_rev(N, q)] = mk<T>(re[q], im[q]);
-    });
-  }
-  __syncthreads();
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int r = e / N, c = e - (e / N) * N;
     buf[e] = plane[r * P + c];
@@ -352,21 +398,20 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(threads_for(N)) pass_b(cplx_t<T>* __restrict__ S, PairParams p) {
+__global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>))) pass_b(cplx_t<T>* __restrict__ S, PairParams p) {
   pass_b_body<T, N, false>(S, p, nullptr);
 }
 
-// d E/d omega: the forward half of pass B, accumulating sum_m (dv/d omega)(m) |rho^(m)|^2.
 template <typename T, int N>
-__global__ void __launch_bounds__(threads_for(N))
+__global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
 pass_b_domega(cplx_t<T>* __restrict__ S, PairParams p, double* dacc) {
   pass_b_body<T, N, true>(S, p, dacc);
 }
 
 // ------------------------------------------------------------------ pass C
-// plane n1, orbital i: for every j of the wave, inverse along m3, multiply by
-// e^{iq.r} psi_{jk'} and accumulate; the gather of field j+1 is in flight while
-// field j is transformed (double buffer).
+// plane n1, orbital i: for every (k', j) of the wave, inverse along m3, multiply by
+// e^{iq.r} psi_{jk'} and accumulate; the gather of the next field is in flight while
+// the current one is transformed (double buffer).
 template <typename T, int N, int P>
 __device__ __forceinline__ void stage_gather(cplx_t<T>* dst, const cplx_t<T>* src, int n1) {
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
@@ -375,8 +420,40 @@ __device__ __forceinline__ void stage_gather(cplx_t<T>* dst, const cplx_t<T>* sr
   }
 }
 
+// Pass-C target t of a wave and its u-th contributing field:
+//   t < nocc: Y_{k,i=t} += psi_{j,k'} W_f over (k', j)       (field (k', i, j), as is)
+//   else    : Y_{k',j}   += psi_{i,k} conj(W_f) over i        (field (k', i, j), reversed)
+//   diag    : Y_{k,i=t}  += psi_{j,k} W over all j, from field (min, max) (reversed if j < i)
+struct CTerm { int f, kpl, other_orb, other_k; bool rev; };
+__device__ __forceinline__ CTerm c_term(const PairParams& p, int t, int u) {
+  CTerm c;
+  if (p.diag) {
+    const int i = t, j = u;
+    c.kpl = 0;
+    c.rev = j < i;
+    c.f = c.rev ? diag_field(j, i, p.nocc) : diag_field(i, j, p.nocc);
+    c.other_orb = j;
+    c.other_k = p.k;
+  } else if (t < p.nocc) {
+    const int i = t, kpl = u / p.nocc, j = u - (u / p.nocc) * p.nocc;
+    c.kpl = kpl;
+    c.rev = false;
+    c.f = (kpl * p.nocc + i) * p.nocc + j;
+    c.other_orb = j;
+    c.other_k = p.kp0 + kpl;
+  } else {
+    const int tt = t - p.nocc, kpl = tt / p.nocc, j = tt - (tt / p.nocc) * p.nocc, i = u;
+    c.kpl = kpl;
+    c.rev = true;
+    c.f = (kpl * p.nocc + i) * p.nocc + j;
+    c.other_orb = i;
+    c.other_k = p.k;
+  }
+  return c;
+}
+
 template <typename T, int N>
-__global__ void __launch_bounds__(threads_for(N))
+__global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
 pass_c(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
        cplx_t<T>* __restrict__ Y, PairParams p) {
   using C2 = cplx_t<T>;
@@ -385,61 +462,63 @@ pass_c(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
   C2* g0 = reinterpret_cast<C2*>(smem_raw);   // gather buffers [m3][n2] pitch P
   C2* g1 = g0 + N * P;
   C2* acc = g1 + N * P;                        // [n2][n3] pitch P
-  C2* ph2 = acc + N * P;                       // [nkp][N]
+  C2* ph2 = acc + N * P;                       // [nkp][N]  e^{+i q2 n2 ...}
   C2* ph3 = ph2 + p.nkp * N;                   // [nkp][N]
   const int n1 = blockIdx.x;
-  const int i = blockIdx.y;
-  const int nf = p.nkp * p.nocc;               // fields (k', j) summed into this target
-  stage_gather<T, N, P>(g0, S + (size_t)(i * p.nocc) * p.ng, n1);   // kpl = 0, j = 0
+  const int t = blockIdx.y;
+  const int nu = p.diag ? p.nocc : (t < p.nocc ? p.nkp * p.nocc : p.nocc);
+  stage_gather<T, N, P>(g0, S + (size_t)c_term(p, t, 0).f * p.ng, n1);
   cp_async_commit();
   for (int e = threadIdx.x; e < N * P; e += blockDim.x) acc[e] = mk<T>(T(0), T(0));
-  for (int t = threadIdx.x; t < p.nkp * N; t += blockDim.x) {
-    const int kpl = t / N, x = t - (t / N) * N, kp = p.kp0 + kpl;
+  for (int x = threadIdx.x; x < p.nkp * N; x += blockDim.x) {
+    const int kpl = x / N, m = x - (x / N) * N, kp = p.kp0 + kpl;
     const int q2 = p.kint[p.k * 3 + 1] - p.kint[kp * 3 + 1];
     const int q3 = p.kint[p.k * 3 + 2] - p.kint[kp * 3 + 2];
-    ph2[t] = cis_frac<T>((long long)q2 * x, (long long)p.D[1] * N, +1);
-    ph3[t] = cis_frac<T>((long long)q3 * x, (long long)p.D[2] * N, +1);
+    ph2[x] = cis_frac<T>((long long)q2 * m, (long long)p.D[1] * N, +1);
+    ph3[x] = cis_frac<T>((long long)q3 * m, (long long)p.D[2] * N, +1);
   }
-  for (int u = 0; u < nf; ++u) {
-    const int kpl = u / p.nocc, j = u - (u / p.nocc) * p.nocc;
+  for (int u = 0; u < nu; ++u) {
+    const CTerm ct = c_term(p, t, u);
     C2* cur = (u & 1) ? g1 : g0;
-    if (u + 1 < nf) {
-      const int kpl2 = (u + 1) / p.nocc, j2 = (u + 1) - kpl2 * p.nocc;
-      const int f2 = (kpl2 * p.nocc + i) * p.nocc + j2;
-      stage_gather<T, N, P>((u & 1) ? g0 : g1, S + (size_t)f2 * p.ng, n1);
-    }
+    if (u + 1 < nu) stage_gather<T, N, P>((u & 1) ? g0 : g1, S + (size_t)c_term(p, t, u + 1).f * p.ng, n1);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
     if (threadIdx.x < N) {
       const int c = threadIdx.x;  // n2
-      const int kp = p.kp0 + kpl;
+      const int kp = p.kp0 + ct.kpl;
       const int q1 = p.kint[p.k * 3] - p.kint[kp * 3];
-      T re[N], im[N];
-      fft::static_for<N>([&](auto I) {
-        constexpr int m = decltype(I)::value;
-        const C2 v = cur[m * P + c];
-        re[m] = v.x; im[m] = v.y;
-      });
-      fft::fft_dif<N, +1>(re, im);
       const C2 ph12 = cmul<T>(cis_frac<T>((long long)q1 * n1, (long long)p.D[0] * N, +1),
-                              ph2[kpl * N + c]);
-      const C2* pj = psi + (size_t)(kp * p.nocc + j) * p.ng + ((size_t)n1 * N + c) * N;
-      const C2* p3 = ph3 + kpl * N;
-      fft::static_for<N>([&](auto I) {
-        constexpr int q = decltype(I)::value;
-        constexpr int n3 = fft::dif_rev(N, q);
-        const C2 w = cmul<T>(mk<T>(re[q], im[q]), cmul<T>(ph12, p3[n3]));
-        const C2 t = cmul<T>(__ldg(pj + n3), w);
-        C2 a = acc[c * P + n3];
-        a.x += t.x;
-        a.y += t.y;
-        acc[c * P + n3] = a;
+                              ph2[ct.kpl * N + c]);
+      const C2* pj = psi + (size_t)(ct.other_k * p.nocc + ct.other_orb) * p.ng +
+                     ((size_t)n1 * N + c) * N;
+      const C2* p3 = ph3 + ct.kpl * N;
+      const T cs = ct.rev ? T(-1) : T(1);
+      C2* arow = acc + c * P;
+      line_fft<T, N>(cur + c, P, true, false, [&](int n3, T& re, T& im) {
+        // W = e^{iq.r} u with u = (re, -im); the reversed pair uses conj(W)
+        const C2 w0 = cmul<T>(mk<T>(re, -im), cmul<T>(ph12, p3[n3]));
+        const C2 w = mk<T>(w0.x, cs * w0.y);
+        C2 pv;
+        if constexpr (sizeof(C2) == 8 && N % 2 == 0) {  // two elements per 16-byte load
+          const float4 q4 = __ldg(reinterpret_cast<const float4*>(pj) + n3 / 2);
+          pv = (n3 & 1) ? mk<T>(q4.z, q4.w) : mk<T>(q4.x, q4.y);
+        } else {
+          pv = __ldg(pj + n3);
+        }
+        const C2 r = cmul<T>(pv, w);
+        C2 a = arow[n3];
+        a.x += r.x;
+        a.y += r.y;
+        arow[n3] = a;
       });
     }
     __syncthreads();
   }
-  C2* y = Y + (size_t)(p.k * p.nocc + i) * p.ng + (size_t)n1 * N * N;
+  int yk, yi;
+  if (p.diag || t < p.nocc) { yk = p.k; yi = t; }
+  else { const int tt = t - p.nocc; yk = p.kp0 + tt / p.nocc; yi = tt - (tt / p.nocc) * p.nocc; }
+  C2* y = Y + (size_t)(yk * p.nocc + yi) * p.ng + (size_t)n1 * N * N;
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int n2 = e / N, n3 = e - (e / N) * N;
     C2 v = y[e];
@@ -450,8 +529,10 @@ pass_c(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
   }
 }
 
-template <int N> constexpr size_t smem_a(size_t csz) { return csz * (2 * N * pitch(N) + 2 * N); }
-template <int N> constexpr size_t smem_b(size_t csz, size_t tab) { return csz * N * pitch(N) + N * tab; }
+template <int N> constexpr size_t smem_a(size_t csz) { return csz * (N * pitch(N) + 2 * N); }
+template <int N> constexpr size_t smem_b(size_t csz, size_t tab) {
+  return csz * N * pitch(N) + N * tab + csz / 2 * N * N;
+}
 inline size_t smem_c(int N, int nkp, size_t csz) {
   return csz * (3 * (size_t)N * pitch(N) + 2 * (size_t)nkp * N);
 }
@@ -461,7 +542,8 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
                      cudaStream_t st, cudaEvent_t* ev) {
   using C2 = cplx_t<T>;
   const int nt = threads_for(N);
-  const int nf = p.nkp * p.nocc * p.nocc;
+  const int nf = wave_fields(p.nocc, p.nkp, p.diag);
+  const int ntg = wave_targets(p.nocc, p.nkp, p.diag);
   const size_t sa = smem_a<N>(sizeof(C2));
   const size_t sb = smem_b<N>(sizeof(C2), sizeof(Axis1<T>));
   const size_t sc = smem_c(N, p.nkp, sizeof(C2));
@@ -481,7 +563,7 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   if (ev) cudaEventRecord(ev[1], st);
   pass_b<T, N><<<dim3(N, nf), nt, sb, st>>>(S, p);
   if (ev) cudaEventRecord(ev[2], st);
-  pass_c<T, N><<<dim3(N, p.nocc), nt, sc, st>>>(S, psi, Y, p);
+  pass_c<T, N><<<dim3(N, ntg), nt, sc, st>>>(S, psi, Y, p);
   if (ev) cudaEventRecord(ev[3], st);
   return cudaGetLastError();
 }
@@ -491,7 +573,7 @@ cudaError_t run_domega_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>
                             double* dacc, cudaStream_t st) {
   using C2 = cplx_t<T>;
   const int nt = threads_for(N);
-  const int nf = p.nkp * p.nocc * p.nocc;
+  const int nf = wave_fields(p.nocc, p.nkp, p.diag);
   const size_t sa = smem_a<N>(sizeof(C2));
   const size_t sb = smem_b<N>(sizeof(C2), sizeof(Axis1<T>));
   static bool configured = false;

@@ -4,12 +4,13 @@
 namespace occri {
 
 template <typename T>
-cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, cudaStream_t s,
+cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s,
                              cudaEvent_t* ev) {
   PairParams pp = p.pair_params();
   pp.k = k;
   pp.kp0 = kp0;
   pp.nkp = nkp;
+  pp.diag = diag;
   const cplx_t<T>* psi = (const cplx_t<T>*)p.psi;
   cplx_t<T>* S = (cplx_t<T>*)p.scratch;
   cplx_t<T>* Y = (cplx_t<T>*)p.Y;
@@ -25,11 +26,13 @@ cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, cudaStream_
 }
 
 template <typename T>
-cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, cudaStream_t s) {
+cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag,
+                               cudaStream_t s) {
   PairParams pp = p.pair_params();
   pp.k = k;
   pp.kp0 = kp0;
   pp.nkp = nkp;
+  pp.diag = diag;
   const cplx_t<T>* psi = (const cplx_t<T>*)p.psi;
   cplx_t<T>* S = (cplx_t<T>*)p.scratch;
   switch (p.N[0]) {
@@ -43,11 +46,11 @@ cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, cudaStrea
   }
 }
 
-template cudaError_t launch_pair_wave<float>(const Plan&, int, int, int, cudaStream_t,
+template cudaError_t launch_pair_wave<float>(const Plan&, int, int, int, int, cudaStream_t,
                                              cudaEvent_t*);
-template cudaError_t launch_pair_wave<double>(const Plan&, int, int, int, cudaStream_t,
+template cudaError_t launch_pair_wave<double>(const Plan&, int, int, int, int, cudaStream_t,
                                               cudaEvent_t*);
-template cudaError_t launch_domega_wave<float>(const Plan&, int, int, int, cudaStream_t);
-template cudaError_t launch_domega_wave<double>(const Plan&, int, int, int, cudaStream_t);
+template cudaError_t launch_domega_wave<float>(const Plan&, int, int, int, int, cudaStream_t);
+template cudaError_t launch_domega_wave<double>(const Plan&, int, int, int, int, cudaStream_t);
 
 }  // namespace occri
