@@ -81,6 +81,46 @@ __device__ __forceinline__ void image_disp(const AOParams& p, const Disp<float>&
   *z = (d.zh - p.img_hi[2 * p.nimg + j]) + (d.zl - p.img_lo[2 * p.nimg + j]);
 }
 
+// Exact-argument Gaussian for FP32: x = (d0 - T') as an unevaluated hi + lo sum (two-diff
+// of the hi parts plus the lo parts), r^2 and alpha r^2 as hi + lo pairs (FMA
+// two-products, two-sums), and e^{-alpha r^2} = e^{-ah} (1 - al). Returns r^2 (hi) for
+// the cutoff test and the coordinates rounded to FP32 for the polynomial.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ float exact_gauss(const AOParams& p, const Disp<float>& d, int j,
+                                             float ah_, float al_, float* r2h, float* x,
+                                             float* y, float* z) {
+  float c[3], cl[3];
+  const float dh[3] = {d.xh, d.yh, d.zh}, dl[3] = {d.xl, d.yl, d.zl};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    float s, e;
+    two_sum(dh[q], -p.img_hi[q * p.nimg + j], s, e);
+    c[q] = s;
+    cl[q] = e + (dl[q] - p.img_lo[q * p.nimg + j]);
+  }
+  float ph[3], pl[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    ph[q] = c[q] * c[q];
+    pl[q] = fmaf(c[q], c[q], -ph[q]) + 2.0f * c[q] * cl[q];
+  }
+  float s1, e1, s2, e2;
+  two_sum(ph[0], ph[1], s1, e1);
+  two_sum(s1, ph[2], s2, e2);
+  const float rl = (e1 + e2) + (pl[0] + pl[1] + pl[2]);
+  *r2h = s2;
+  const float ah = ah_ * s2;
+  const float al = fmaf(ah_, s2, -ah) + ah_ * rl + al_ * s2;
+  *x = c[0] + cl[0];
+  *y = c[1] + cl[1];
+  *z = c[2] + cl[2];
+  return expf(-ah) * (1.0f - al);
+}
+
 template <typename T> __device__ __forceinline__ T sh_alpha(const ShellDev& s);
 template <> __device__ __forceinline__ double sh_alpha<double>(const ShellDev& s) { return s.alpha; }
 template <> __device__ __forceinline__ float sh_alpha<float>(const ShellDev& s) { return s.alpha_f; }
@@ -128,13 +168,24 @@ __device__ __forceinline__ void shell_values(const AOParams& p, const ShellDev& 
     cr[m] = T(0);
     ci[m] = T(0);
   }
+  const bool exact = (sizeof(T) == 4) && sh.exact_arg;
   for (int j = 0; j < np; ++j) {
     const int idx = list[j];
-    T x, y, z;
-    image_disp(p, d, idx, &x, &y, &z);
-    const T r2 = x * x + y * y + z * z;
+    T x, y, z, r2, e;
+    if constexpr (sizeof(T) == 4) {
+      if (exact) {
+        e = exact_gauss(p, d, idx, alpha, alo, &r2, &x, &y, &z);
+      } else {
+        image_disp(p, d, idx, &x, &y, &z);
+        r2 = x * x + y * y + z * z;
+        e = exp_t(-(alpha * r2 + alo * r2));
+      }
+    } else {
+      image_disp(p, d, idx, &x, &y, &z);
+      r2 = x * x + y * y + z * z;
+      e = exp_t(-(alpha * r2 + alo * r2));
+    }
     if (r2 <= rc2) {
-      const T e = exp_t(-(alpha * r2 + alo * r2));
       T P[2 * L + 1];
       solid<T, L>(x, y, z, P);
       const cplx_t<T> w = ph[idx];
@@ -164,13 +215,24 @@ __device__ __forceinline__ void shell_values_kb(const AOParams& p, const ShellDe
       cr[b][m] = T(0);
       ci[b][m] = T(0);
     }
+  const bool exact = (sizeof(T) == 4) && sh.exact_arg;
   for (int j = 0; j < np; ++j) {
     const int idx = list[j];
-    T x, y, z;
-    image_disp(p, d, idx, &x, &y, &z);
-    const T r2 = x * x + y * y + z * z;
+    T x, y, z, r2, e;
+    if constexpr (sizeof(T) == 4) {
+      if (exact) {
+        e = exact_gauss(p, d, idx, alpha, alo, &r2, &x, &y, &z);
+      } else {
+        image_disp(p, d, idx, &x, &y, &z);
+        r2 = x * x + y * y + z * z;
+        e = exp_t(-(alpha * r2 + alo * r2));
+      }
+    } else {
+      image_disp(p, d, idx, &x, &y, &z);
+      r2 = x * x + y * y + z * z;
+      e = exp_t(-(alpha * r2 + alo * r2));
+    }
     if (r2 <= rc2) {
-      const T e = exp_t(-(alpha * r2 + alo * r2));
       T P[2 * L + 1];
       solid<T, L>(x, y, z, P);
 #pragma unroll

@@ -78,6 +78,14 @@ PairParams Plan::pair_params() const {
   // g0 = pi/omega^2 and d g0/d omega = -2 pi/omega^3, both in units of 4 pi
   q.g0 = (kernel.g0_mode == 1) ? 0.25 / (kernel.omega * kernel.omega) : 0.0;
   q.dg0 = (kernel.g0_mode == 1) ? -0.5 / (kernel.omega * kernel.omega * kernel.omega) : 0.0;
+  for (int i = 0; i < 6; ++i) {
+    q.gh[i] = (float)q.g[i];
+    q.gl[i] = (float)(q.g[i] - (double)q.gh[i]);
+  }
+  q.inv4w2_f = (float)q.inv4w2;
+  q.omega_f = (float)q.omega;
+  q.g0_f = (float)q.g0;
+  q.dg0_f = (float)q.dg0;
   return q;
 }
 
@@ -571,6 +579,9 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     x.alpha = basis->alpha[s];
     x.alpha_f = (float)x.alpha;
     x.alpha_lo = (float)(x.alpha - (double)x.alpha_f);
+    // Tight primitives reach one or two images per point, so FP32 rounding of
+    // r^2 and alpha r^2 does not average out there; they get a double-float exponent.
+    x.exact_arg = (precision == OCCRI_MIXED && x.alpha >= 0.5) ? 1 : 0;
     shell_norms(x.l, x.alpha, x.norm);
     for (int m = 0; m < 2 * x.l + 1; ++m) x.norm_f[m] = (float)x.norm[m];
     rcut[s] = shell_cutoff(x.l, x.alpha, eps);
@@ -797,9 +808,9 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
   int nkp = (int)std::max<size_t>(1, budget / per_kp);
   nkp = std::min(nkp, p->nk);
   nkp = std::max(1, std::min(nkp, 65535 / (nocc * nocc)));   // grid.y limit of the passes
-  {  // pass C keeps three planes plus two phase rows per k' in shared memory
+  {  // pass C keeps one plane plus two phase rows per k' in shared memory
     const size_t pitch = (grid[0] % 2 == 0) ? grid[0] + 1 : grid[0];
-    const size_t planes = 3 * (size_t)grid[0] * pitch * csz;
+    const size_t planes = (size_t)grid[0] * pitch * csz;
     const size_t per = 2 * (size_t)grid[0] * csz;
     const size_t limit = 227 * 1024;
     nkp = std::max(1, std::min<int>(nkp, (int)((limit - planes) / per)));

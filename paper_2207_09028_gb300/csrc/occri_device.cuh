@@ -37,6 +37,17 @@ __device__ __forceinline__ cplx_t<T> cis_frac(long long num, long long den, int 
   return {c, T(sgn) * s};
 }
 
+// Same for small arguments (|num|, den < 2^24): 32-bit integer reduction only.
+template <typename T>
+__device__ __forceinline__ cplx_t<T> cis_frac_i(int num, int den, int sgn) {
+  int r = num % den;
+  if (r < 0) r += den;
+  if (2 * r >= den) r -= den;
+  T s, c;
+  sincospi_t(T(2 * r) / T(den), &s, &c);
+  return {c, T(sgn) * s};
+}
+
 // T0 packing: three signed 10-bit lattice coordinates in one int.
 __host__ __device__ __forceinline__ int pack_t0(int a, int b, int c) {
   return (a & 1023) | ((b & 1023) << 10) | ((c & 1023) << 20);

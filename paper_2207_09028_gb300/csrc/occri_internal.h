@@ -31,6 +31,7 @@ struct ShellDev {
   float alpha_f, alpha_lo, rcut2_f;   // alpha = alpha_f + alpha_lo
   float norm_f[7];
   int l, atom, ao, nimg;   // nimg: prefix of the sorted image list that can reach the cell
+  int exact_arg;           // FP32: form r - A - T, r^2 and alpha r^2 in double-float
 };
 
 // Geometry / AO tables for the AO kernels (steps a, b, e).
@@ -75,6 +76,10 @@ struct PairParams {
   double omega;
   double g0;                 // value at G+q = 0, in units of 4 pi
   double dg0;                // d g0 / d omega, in units of 4 pi
+  // FP32 copies (hi/lo for the metric) made on the host, so FP32 kernels never
+  // convert from double on the device (FP64 issue is 1/64 rate)
+  float gh[6], gl[6];
+  float inv4w2_f, omega_f, g0_f, dg0_f;
 };
 // The transforms apply v/(4 pi) between unnormalised forward and inverse FFTs, so
 // Y carries a factor N_g/(4 pi); the contraction restores it in FP64.

@@ -30,14 +30,19 @@ using dev::mk;
 using dev::cmul;
 using dev::cmulc;
 using dev::cis_frac;
+using dev::cis_frac_i;
 using dev::exp_t;
 using dev::expm1_t;
 
 constexpr int pitch(int n) { return (n % 2 == 0) ? n + 1 : n; }
-constexpr int threads_for(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : 128); }
+// Even edges use two threads per line (radix-2 split, see line_fft2), odd edges one.
+constexpr int line_split(int n) { return (n % 2 == 0) ? 2 : 1; }
+constexpr int threads_for(int n) {
+  return ((line_split(n) * n + 31) / 32) * 32;
+}
 // resident CTAs per SM requested from the register allocator (one line per thread)
 constexpr int min_blocks(int n, int elem_bytes) {
-  return elem_bytes > 8 ? (n <= 32 ? 4 : 2) : (n <= 32 ? 8 : 5);
+  return elem_bytes > 8 ? (n <= 32 ? 4 : 2) : (n <= 32 ? 8 : 4);
 }
 
 // f(|G+q|)/(4 pi) of Eq. recipcoul for |G+q|^2 = g2 > 0.
@@ -130,6 +135,61 @@ __device__ __forceinline__ void line_fft(cplx_t<T>* base, int stride, bool conj_
   });
 }
 
+// Two threads per line (even N). Thread h of the pair forms
+//   y_h[n] = (x[n] + (-1)^h x[n + N/2]) e^{-2 pi i h n / N},   n < N/2,
+// from the whole line in shared memory and transforms it with an N/2-point register
+// FFT, which gives the outputs X[2k + h] (radix-2 decimation in frequency). conj_io,
+// store and post as in line_fft; `valid` is false for padding threads, which compute
+// on a duplicate line but neither store nor call post. The pair sits in one warp and
+// synchronises between its loads and its stores.
+template <typename T, int N, typename Post>
+__device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool conj_io, bool store,
+                                          int h, bool valid, Post&& post) {
+  constexpr int M = N / 2;
+  T re[M], im[M];
+  const T sg = conj_io ? T(-1) : T(1);
+  const T hs = h ? T(-1) : T(1);
+  fft::static_for<M>([&](auto I) {
+    constexpr int n = decltype(I)::value;
+    constexpr fft::CS w = fft::cs2pi(n, N);     // e^{-2 pi i n / N} = (c, -s)
+    const cplx_t<T> a = base[n * stride], b = base[(n + M) * stride];
+    const T yr = a.x + hs * b.x, yi = sg * (a.y + hs * b.y);
+    const T c = h ? T(w.c) : T(1), sn = h ? T(-w.s) : T(0);
+    re[n] = yr * c - yi * sn;
+    im[n] = yr * sn + yi * c;
+  });
+  __syncwarp();
+  fft::fft_dif<M, -1>(re, im);
+  fft::static_for<M>([&](auto I) {
+    constexpr int q = decltype(I)::value;
+    const int k = 2 * fft::dif_rev(M, q) + h;
+    if (valid) {
+      post(k, re[q], im[q]);
+      if (store) base[k * stride] = mk<T>(re[q], sg * im[q]);
+    }
+  });
+}
+
+// One transform job over the N lines of a plane (rows: along the contiguous index;
+// columns: along the pitched index); every thread of the CTA must call it.
+template <typename T, int N, typename Post>
+__device__ __forceinline__ void run_lines(cplx_t<T>* plane, int P, bool rows, bool conj_io,
+                                          bool store, Post&& post) {
+  if constexpr (line_split(N) == 2) {
+    const int t = threadIdx.x;
+    const bool valid = (t >> 1) < N;
+    const int line = valid ? (t >> 1) : N - 1;
+    line_fft2<T, N>(rows ? plane + line * P : plane + line, rows ? 1 : P, conj_io, store,
+                    t & 1, valid, [&](int k, T& re, T& im) { post(line, k, re, im); });
+  } else {
+    if (threadIdx.x < N) {
+      const int line = threadIdx.x;
+      line_fft<T, N>(rows ? plane + line * P : plane + line, rows ? 1 : P, conj_io, store,
+                     [&](int k, T& re, T& im) { post(line, k, re, im); });
+    }
+  }
+}
+
 // ------------------------------------------------------------------ kernel values per bin
 // Per-CTA table for axis 1 and per-column constants for axes 2, 3 give, for the first
 // alias of every axis,
@@ -163,18 +223,26 @@ template <typename T> __device__ __forceinline__ T axis_x(const AxisInt& a, bool
   return T(second ? a.X + a.N * a.D : a.X) / T(a.D);
 }
 
-// hi/lo parts of the reciprocal metric g_ij (lo = 0 in FP64)
-template <typename T>
-struct MetricHL {
-  T h[6], l[6];
-  __device__ __forceinline__ explicit MetricHL(const PairParams& p) {
+// hi/lo parts of the reciprocal metric g_ij (lo = 0 in FP64), and the other launch
+// constants in the working precision, read without any double -> float conversion
+template <typename T> struct Consts;
+template <> struct Consts<double> {
+  double h[6], l[6], inv4w2, omega, g0, dg0;
+  __device__ __forceinline__ explicit Consts(const PairParams& p) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      h[i] = T(p.g[i]);
-      l[i] = T(p.g[i] - double(h[i]));
-    }
+    for (int i = 0; i < 6; ++i) { h[i] = p.g[i]; l[i] = 0.0; }
+    inv4w2 = p.inv4w2; omega = p.omega; g0 = p.g0; dg0 = p.dg0;
   }
 };
+template <> struct Consts<float> {
+  float h[6], l[6], inv4w2, omega, g0, dg0;
+  __device__ __forceinline__ explicit Consts(const PairParams& p) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { h[i] = p.gh[i]; l[i] = p.gl[i]; }
+    inv4w2 = p.inv4w2_f; omega = p.omega_f; g0 = p.g0_f; dg0 = p.dg0_f;
+  }
+};
+template <typename T> using MetricHL = Consts<T>;
 
 // s (hi, lo) += g * a * b with g = (gh, gl), error-free in the product a*b.
 template <typename T>
@@ -191,83 +259,77 @@ __device__ __forceinline__ void acc_gab(T gh, T gl, T a, T b, T& hi, T& lo) {
 
 template <typename T>
 struct Axis1 {
-  T x, ah, al;
-  int flags;
+  T x, ah, al;     // first alias: x and g11 x^2 (hi, lo)
+  T xb, bh, bl;    // second alias (== first unless tied)
+  int flags;       // bit0 tie, bit1 x == 0
 };
 
 template <typename T>
-__device__ __forceinline__ Axis1<T> axis1_entry(const MetricHL<T>& g, const AxisInt& a) {
+__device__ __forceinline__ Axis1<T> axis1_entry(const Consts<T>& g, const AxisInt& a) {
   Axis1<T> r;
   r.x = axis_x<T>(a, false);
+  r.xb = axis_x<T>(a, a.tie);
   T hi = T(0), lo = T(0);
   acc_gab<T>(g.h[0], g.l[0], r.x, r.x, hi, lo);
-  r.ah = hi;
-  r.al = lo;
+  r.ah = hi; r.al = lo;
+  hi = T(0); lo = T(0);
+  acc_gab<T>(g.h[0], g.l[0], r.xb, r.xb, hi, lo);
+  r.bh = hi; r.bl = lo;
   r.flags = (a.tie ? 1 : 0) | (a.zero ? 2 : 0);
   return r;
 }
 
+// Column constants for up to four (x2, x3) alias variants; nv distinct ones first.
 template <typename T>
 struct ColumnConst {
-  T bh, bl, ch, cl;
-  int flags;
+  T bh[4], bl[4], ch[4], cl[4];
+  int nv;
+  int zero;  // x2 == 0 and x3 == 0
 };
 
 template <typename T>
-__device__ __forceinline__ ColumnConst<T> column_const(const MetricHL<T>& g, const AxisInt& b,
+__device__ __forceinline__ ColumnConst<T> column_const(const Consts<T>& g, const AxisInt& b,
                                                        const AxisInt& c) {
   ColumnConst<T> r;
-  const T x2 = axis_x<T>(b, false), x3 = axis_x<T>(c, false);
-  T bh = T(0), bl = T(0);   // beta = 2 g12 x2 + 2 g13 x3
-  acc_gab<T>(g.h[3], g.l[3], T(2), x2, bh, bl);
-  acc_gab<T>(g.h[4], g.l[4], T(2), x3, bh, bl);
-  T ch = T(0), cl = T(0);   // gamma = g22 x2^2 + g33 x3^2 + 2 g23 x2 x3
-  acc_gab<T>(g.h[1], g.l[1], x2, x2, ch, cl);
-  acc_gab<T>(g.h[2], g.l[2], x3, x3, ch, cl);
-  acc_gab<T>(g.h[5], g.l[5], T(2) * x2, x3, ch, cl);
-  r.bh = bh; r.bl = bl; r.ch = ch; r.cl = cl;
-  r.flags = ((b.tie || c.tie) ? 1 : 0) | ((b.zero && c.zero) ? 2 : 0);
+  r.nv = (b.tie ? 2 : 1) * (c.tie ? 2 : 1);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    // u -> (alias of x2, alias of x3), listing only the tied axes' second aliases
+    const bool s2 = b.tie && (u & 1);
+    const bool s3 = c.tie && (b.tie ? (u & 2) : (u & 1));
+    const T x2 = axis_x<T>(b, s2), x3 = axis_x<T>(c, s3);
+    T bh = T(0), bl = T(0);   // beta = 2 g12 x2 + 2 g13 x3
+    acc_gab<T>(g.h[3], g.l[3], T(2), x2, bh, bl);
+    acc_gab<T>(g.h[4], g.l[4], T(2), x3, bh, bl);
+    T ch = T(0), cl = T(0);   // gamma = g22 x2^2 + g33 x3^2 + 2 g23 x2 x3
+    acc_gab<T>(g.h[1], g.l[1], x2, x2, ch, cl);
+    acc_gab<T>(g.h[2], g.l[2], x3, x3, ch, cl);
+    acc_gab<T>(g.h[5], g.l[5], T(2) * x2, x3, ch, cl);
+    r.bh[u] = bh; r.bl[u] = bl; r.ch[u] = ch; r.cl[u] = cl;
+  }
+  r.zero = (b.zero && c.zero) ? 1 : 0;
   return r;
 }
 
-// Tie-averaged value on a rare bin (working precision, out of line).
+// v/(4 pi) (or its omega-derivative) on one bin, averaged over tied aliases. Called from
+// a rolled loop, so the variant handling is inline without growing the unrolled code.
 template <typename T, bool DERIV>
-__device__ __noinline__ T bin_value_rare(const PairParams& p, int m1, int m2, int m3, int q1,
-                                         int q2, int q3) {
-  const AxisInt a = axis_int(m1, q1, p.D[0], p.N1);
-  const AxisInt b = axis_int(m2, q2, p.D[1], p.N1);
-  const AxisInt c = axis_int(m3, q3, p.D[2], p.N1);
-  if (a.zero && b.zero && c.zero) return DERIV ? T(p.dg0) : T(p.g0);
-  const MetricHL<T> g(p);
-  const T i4 = T(p.inv4w2), om = T(p.omega);
+__device__ __forceinline__ T bin_value(const PairParams& p, const Consts<T>& k,
+                                       const Axis1<T>& a, const ColumnConst<T>& c) {
+  if ((a.flags & 2) && c.zero) return DERIV ? k.dg0 : k.g0;
+  auto f = [&](T g2) {
+    return DERIV ? kernel_df<T>(g2, p.kind, k.inv4w2, k.omega) : kernel_f<T>(g2, p.kind, k.inv4w2);
+  };
+  const bool t1 = (a.flags & 1) != 0;
   T s = T(0);
-  int n = 0;
-  for (int u = 0; u < 8; ++u) {
-    if (((u & 1) && !a.tie) || ((u & 2) && !b.tie) || ((u & 4) && !c.tie)) continue;
-    const T x1 = axis_x<T>(a, u & 1), x2 = axis_x<T>(b, u & 2), x3 = axis_x<T>(c, u & 4);
-    T hi = T(0), lo = T(0);
-    acc_gab<T>(g.h[0], g.l[0], x1, x1, hi, lo);
-    acc_gab<T>(g.h[1], g.l[1], x2, x2, hi, lo);
-    acc_gab<T>(g.h[2], g.l[2], x3, x3, hi, lo);
-    acc_gab<T>(g.h[3], g.l[3], T(2) * x1, x2, hi, lo);
-    acc_gab<T>(g.h[4], g.l[4], T(2) * x1, x3, hi, lo);
-    acc_gab<T>(g.h[5], g.l[5], T(2) * x2, x3, hi, lo);
-    const T g2 = hi + lo;
-    s += DERIV ? kernel_df<T>(g2, p.kind, i4, om) : kernel_f<T>(g2, p.kind, i4);
-    ++n;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (u < c.nv) {
+      s += f((a.ah + a.x * c.bh[u] + c.ch[u]) + (a.al + a.x * c.bl[u] + c.cl[u]));
+      if (t1) s += f((a.bh + a.xb * c.bh[u] + c.ch[u]) + (a.bl + a.xb * c.bl[u] + c.cl[u]));
+    }
   }
-  return s / T(n);
-}
-
-template <typename T, bool DERIV>
-__device__ __forceinline__ T bin_value(const PairParams& p, const Axis1<T>& a,
-                                       const ColumnConst<T>& c, int m1, int m2, int m3,
-                                       const int* Q) {
-  if (((a.flags | c.flags) & 1) || ((a.flags & c.flags) & 2))
-    return bin_value_rare<T, DERIV>(p, m1, m2, m3, Q[0], Q[1], Q[2]);
-  const T g2 = (a.ah + a.x * c.bh + c.ch) + (a.al + a.x * c.bl + c.cl);
-  return DERIV ? kernel_df<T>(g2, p.kind, T(p.inv4w2), T(p.omega))
-               : kernel_f<T>(g2, p.kind, T(p.inv4w2));
+  return (c.nv == 1 && !t1) ? s : s / T(c.nv * (t1 ? 2 : 1));
 }
 
 // ------------------------------------------------------------------ pass A
@@ -289,10 +351,10 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
 #pragma unroll
   for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
-    ph2[t] = cis_frac<T>((long long)Q[1] * t, (long long)p.D[1] * N, -1);
-    ph3[t] = cis_frac<T>((long long)Q[2] * t, (long long)p.D[2] * N, -1);
+    ph2[t] = cis_frac_i<T>(Q[1] * t, p.D[1] * N, -1);
+    ph3[t] = cis_frac_i<T>(Q[2] * t, p.D[2] * N, -1);
   }
-  const C2 ph1 = cis_frac<T>((long long)Q[0] * n1, (long long)p.D[0] * N, -1);
+  const C2 ph1 = cis_frac_i<T>(Q[0] * n1, p.D[0] * N, -1);
   __syncthreads();
   const C2* pi = psi + (size_t)(p.k * p.nocc + fi.i) * p.ng + (size_t)n1 * N * N;
   const C2* pj = psi + (size_t)(kp * p.nocc + fi.j) * p.ng + (size_t)n1 * N * N;
@@ -305,11 +367,7 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
   __syncthreads();
 #pragma unroll 1
   for (int job = 0; job < 2; ++job) {   // rows (along n3), then columns (along n2)
-    if (threadIdx.x < N) {
-      const int t = threadIdx.x;
-      line_fft<T, N>(job == 0 ? pl + t * P : pl + t, job == 0 ? 1 : P, false, true,
-                     [](int, T&, T&) {});
-    }
+    run_lines<T, N>(pl, P, job == 0, false, true, [](int, int, T&, T&) {});
     __syncthreads();
   }
   C2* out = S + (size_t)f * p.ng;
@@ -347,11 +405,15 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
     ax1[t] = axis1_entry<T>(gm, axis_int(t, Q[0], p.D[0], N));
   const AxisInt a3 = axis_int(m3, Q[2], p.D[2], N);
   __syncthreads();
-  if (threadIdx.x < N) {  // kernel values of this column, one rolled loop
-    const int c = threadIdx.x;
-    const ColumnConst<T> cc = column_const<T>(gm, axis_int(c, Q[1], p.D[1], N), a3);
+  {  // kernel values, one rolled loop per column (split between the line's threads)
+    constexpr int SP = line_split(N);
+    const int c = (int)threadIdx.x / SP, h = (int)threadIdx.x % SP;
+    if (c < N) {
+      const ColumnConst<T> cc = column_const<T>(gm, axis_int(c, Q[1], p.D[1], N), a3);
 #pragma unroll 1
-    for (int m1 = 0; m1 < N; ++m1) vtab[m1 * N + c] = bin_value<T, DOMEGA>(p, ax1[m1], cc, m1, c, m3, Q);
+      for (int m1 = h; m1 < N; m1 += SP)
+        vtab[m1 * N + c] = bin_value<T, DOMEGA>(p, gm, ax1[m1], cc);
+    }
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -359,14 +421,12 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
   constexpr int NJOB = DOMEGA ? 1 : 3;
 #pragma unroll 1
   for (int job = 0; job < NJOB; ++job) {
-    // job 0: columns (m2 = t), forward along n1, x v; job 1: columns, inverse along m1;
-    // job 2: rows (n1 = t), inverse along m2
-    if (threadIdx.x < N) {
-      const int t = threadIdx.x;
-      C2* base = (job < 2) ? plane + t : plane + t * P;
-      line_fft<T, N>(base, job < 2 ? P : 1, job > 0, !DOMEGA, [&](int k, T& re, T& im) {
+    // job 0: columns (m2 = line), forward along n1, x v; job 1: columns, inverse along m1;
+    // job 2: rows (n1 = line), inverse along m2
+    {
+      run_lines<T, N>(plane, P, job == 2, job > 0, !DOMEGA, [&](int line, int k, T& re, T& im) {
         if (job == 0) {
-          const T v = vtab[k * N + t];
+          const T v = vtab[k * N + line];
           if constexpr (DOMEGA) {
             dsum += v * (re * re + im * im);
           } else {
@@ -459,73 +519,52 @@ pass_c(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
   using C2 = cplx_t<T>;
   constexpr int P = pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2* g0 = reinterpret_cast<C2*>(smem_raw);   // gather buffers [m3][n2] pitch P
-  C2* g1 = g0 + N * P;
-  C2* acc = g1 + N * P;                        // [n2][n3] pitch P
-  C2* ph2 = acc + N * P;                       // [nkp][N]  e^{+i q2 n2 ...}
+  C2* cur = reinterpret_cast<C2*>(smem_raw);  // gathered field plane [m3][n2], pitch P
+  C2* ph2 = cur + N * P;                       // [nkp][N]  e^{+i q2 n2 ...}
   C2* ph3 = ph2 + p.nkp * N;                   // [nkp][N]
   const int n1 = blockIdx.x;
   const int t = blockIdx.y;
   const int nu = p.diag ? p.nocc : (t < p.nocc ? p.nkp * p.nocc : p.nocc);
-  stage_gather<T, N, P>(g0, S + (size_t)c_term(p, t, 0).f * p.ng, n1);
-  cp_async_commit();
-  for (int e = threadIdx.x; e < N * P; e += blockDim.x) acc[e] = mk<T>(T(0), T(0));
   for (int x = threadIdx.x; x < p.nkp * N; x += blockDim.x) {
     const int kpl = x / N, m = x - (x / N) * N, kp = p.kp0 + kpl;
     const int q2 = p.kint[p.k * 3 + 1] - p.kint[kp * 3 + 1];
     const int q3 = p.kint[p.k * 3 + 2] - p.kint[kp * 3 + 2];
-    ph2[x] = cis_frac<T>((long long)q2 * m, (long long)p.D[1] * N, +1);
-    ph3[x] = cis_frac<T>((long long)q3 * m, (long long)p.D[2] * N, +1);
-  }
-  for (int u = 0; u < nu; ++u) {
-    const CTerm ct = c_term(p, t, u);
-    C2* cur = (u & 1) ? g1 : g0;
-    if (u + 1 < nu) stage_gather<T, N, P>((u & 1) ? g0 : g1, S + (size_t)c_term(p, t, u + 1).f * p.ng, n1);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    if (threadIdx.x < N) {
-      const int c = threadIdx.x;  // n2
-      const int kp = p.kp0 + ct.kpl;
-      const int q1 = p.kint[p.k * 3] - p.kint[kp * 3];
-      const C2 ph12 = cmul<T>(cis_frac<T>((long long)q1 * n1, (long long)p.D[0] * N, +1),
-                              ph2[ct.kpl * N + c]);
-      const C2* pj = psi + (size_t)(ct.other_k * p.nocc + ct.other_orb) * p.ng +
-                     ((size_t)n1 * N + c) * N;
-      const C2* p3 = ph3 + ct.kpl * N;
-      const T cs = ct.rev ? T(-1) : T(1);
-      C2* arow = acc + c * P;
-      line_fft<T, N>(cur + c, P, true, false, [&](int n3, T& re, T& im) {
-        // W = e^{iq.r} u with u = (re, -im); the reversed pair uses conj(W)
-        const C2 w0 = cmul<T>(mk<T>(re, -im), cmul<T>(ph12, p3[n3]));
-        const C2 w = mk<T>(w0.x, cs * w0.y);
-        C2 pv;
-        if constexpr (sizeof(C2) == 8 && N % 2 == 0) {  // two elements per 16-byte load
-          const float4 q4 = __ldg(reinterpret_cast<const float4*>(pj) + n3 / 2);
-          pv = (n3 & 1) ? mk<T>(q4.z, q4.w) : mk<T>(q4.x, q4.y);
-        } else {
-          pv = __ldg(pj + n3);
-        }
-        const C2 r = cmul<T>(pv, w);
-        C2 a = arow[n3];
-        a.x += r.x;
-        a.y += r.y;
-        arow[n3] = a;
-      });
-    }
-    __syncthreads();
+    ph2[x] = cis_frac_i<T>(q2 * m, p.D[1] * N, +1);
+    ph3[x] = cis_frac_i<T>(q3 * m, p.D[2] * N, +1);
   }
   int yk, yi;
   if (p.diag || t < p.nocc) { yk = p.k; yi = t; }
   else { const int tt = t - p.nocc; yk = p.kp0 + tt / p.nocc; yi = tt - (tt / p.nocc) * p.nocc; }
   C2* y = Y + (size_t)(yk * p.nocc + yi) * p.ng + (size_t)n1 * N * N;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int n2 = e / N, n3 = e - (e / N) * N;
-    C2 v = y[e];
-    const C2 a = acc[n2 * P + n3];
-    v.x += a.x;
-    v.y += a.y;
-    y[e] = v;
+  for (int u = 0; u < nu; ++u) {
+    const CTerm ct = c_term(p, t, u);
+    stage_gather<T, N, P>(cur, S + (size_t)ct.f * p.ng, n1);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    // columns (n2 = line): inverse along m3, result u(n3) back into cur
+    run_lines<T, N>(cur, P, false, true, true, [](int, int, T&, T&) {});
+    __syncthreads();
+    // Y(n1, n2, n3) += psi_other * W, W = e^{iq.r} u (conj(W) for the reversed pair);
+    // this CTA is the only writer of the target plane, and the wave's targets stay in L2
+    const int kp = p.kp0 + ct.kpl;
+    const int q1 = p.kint[p.k * 3] - p.kint[kp * 3];
+    const C2 ph1 = cis_frac_i<T>(q1 * n1, p.D[0] * N, +1);
+    const C2* po = psi + (size_t)(ct.other_k * p.nocc + ct.other_orb) * p.ng + (size_t)n1 * N * N;
+    const C2* p2 = ph2 + ct.kpl * N;
+    const C2* p3 = ph3 + ct.kpl * N;
+    const T cs = ct.rev ? T(-1) : T(1);
+#pragma unroll 4
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+      const int n2 = e / N, n3 = e - (e / N) * N;
+      const C2 w0 = cmul<T>(cur[n3 * P + n2], cmul<T>(ph1, cmul<T>(p2[n2], p3[n3])));
+      const C2 r = cmul<T>(__ldg(po + e), mk<T>(w0.x, cs * w0.y));
+      C2 v = y[e];
+      v.x += r.x;
+      v.y += r.y;
+      y[e] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -534,7 +573,7 @@ template <int N> constexpr size_t smem_b(size_t csz, size_t tab) {
   return csz * N * pitch(N) + N * tab + csz / 2 * N * N;
 }
 inline size_t smem_c(int N, int nkp, size_t csz) {
-  return csz * (3 * (size_t)N * pitch(N) + 2 * (size_t)nkp * N);
+  return csz * ((size_t)N * pitch(N) + 2 * (size_t)nkp * N);
 }
 
 template <typename T, int N>
