@@ -28,8 +28,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) per launch from one ncu capture of the same launch shape
-# (a 64-field wave of 60^3 FP32 fields), see profiles/; None until captured.
+# DRAM bytes (read + write) of one full wave (pass_a + pass_b + pass_c), keyed by
+# ("round_trip", grid edge, fields per wave), from one ncu capture of the same launch
+# shape; None until captured for the current kernels.
 TRAFFIC = {}
 
 METRIC = "K-builds/s at 6x6x6 k, 350 AO; mixed vs FP64 GPU at |dE_x|<=1e-6 Ha/cell"
@@ -253,26 +254,30 @@ def main():
             stage_ms[name] = st["ms"] * waves * args.steps / max(1, st["launches"]) / args.steps
         else:
             stage_ms[name] = st["ms"] / args.steps
-    # roofline of the dominant kernel: the pair passes stream fields through HBM/L2;
-    # algorithmic bytes per field (FP32 complex, 8 B per point): A writes the field and
-    # reads its share of the two orbital planes, B reads and writes it, C reads it once
-    # and updates its share of the orbital and Y planes
+    # Roofline of the dominant work, the pair round trip (steps c, d). Its unit is one
+    # transformed field; each of the two 3-D transforms reads and writes the field once,
+    # so the streaming model is 2 x 2 x 8 B x N_g = 32 N_g bytes per field in FP32 (c64).
+    # A round trip runs as three launches (pass_a, pass_b, pass_c) over a wave of fields,
+    # timed with CUDA events on the plan's stream on every `timing_every`-th wave.
     hbm, peak_kind = _peaks()
-    csz = 8
     ng = w.ng
-    alg = {"pair_a": csz * ng * (1 + 2.0 / w.nocc), "pair_b": csz * ng * 2.0,
-           "pair_c": csz * ng * (1 + 6.0 / w.nocc)}
-    dom = max(stage_ms, key=lambda s_: stage_ms[s_])
     roof = None
-    if dom in alg and stages[dom]["launches"]:
-        st = stages[dom]
-        bytes_total = alg[dom] * st["units"]
-        achieved = bytes_total / (st["ms"] / 1e3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": TRAFFIC.get((dom, w.grid[0])),
-                "bytes_per_launch": alg[dom] * st["units"] / st["launches"],
-                "ms_per_launch": st["ms"] / st["launches"]}
+    pair = [s_ for s_ in ("pair_a", "pair_b", "pair_c") if s_ in stages]
+    rt_ms = sum(stages[s_]["ms"] for s_ in pair)
+    rt_waves = stages["pair_a"]["launches"] if "pair_a" in stages else 0
+    if rt_waves and rt_ms > 0:
+        fields = stages["pair_a"]["units"]
+        bytes_total = 32.0 * ng * fields
+        achieved = bytes_total / (rt_ms / 1e3) / 1e9
+        fpw = int(info["fields_per_wave"])
+        roof = {"kernel": "pair round trip: pass_a + pass_b + pass_c over one wave of "
+                          f"{fpw} fields of {w.grid[0]}^3",
+                "bound": "hbm", "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": TRAFFIC.get(("round_trip", w.grid[0], fpw)),
+                "bytes_per_launch": 32.0 * ng * fpw,
+                "ms_per_launch": rt_ms * fpw / fields,
+                "pass_ms_share": {s_: stages[s_]["ms"] / rt_ms for s_ in pair}}
     stage_share = stage_ms
 
     out = {"impl": "occri", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -133,12 +133,21 @@ template <> __device__ __forceinline__ float sh_rcut2<float>(const ShellDev& s) 
 
 // Grid point of `lane` in point block `blk` (2 x 4 x 4 points, ragged at the grid edge);
 // lanes outside the grid get a clamped in-range point and *valid = false.
-__device__ __forceinline__ long long block_point(const AOParams& p, int blk, int lane, bool* valid) {
+// Point `lane` of block `blk`: its natural index n = (n1 N2 + n2) N3 + n3 (the
+// geometry tables) and its index in the orbital/accumulator fields, which are stored
+// with the third axis outermost, q = (n3 N1 + n1) N2 + n2 (see occri_internal.h).
+// Lanes run along n2 first so that four consecutive lanes touch contiguous elements.
+// Points past the grid edge (ragged blocks) are clamped and flagged invalid.
+__device__ __forceinline__ long long block_point(const AOParams& p, int blk, int lane, bool* valid,
+                                                 long long* q) {
   const int b3 = blk % p.nb[2], b2 = (blk / p.nb[2]) % p.nb[1], b1 = blk / (p.nb[1] * p.nb[2]);
-  const int n1 = 2 * b1 + (lane >> 4), n2 = 4 * b2 + ((lane >> 2) & 3), n3 = 4 * b3 + (lane & 3);
+  int n1 = 2 * b1 + (lane >> 4), n2 = 4 * b2 + (lane & 3), n3 = 4 * b3 + ((lane >> 2) & 3);
   *valid = n1 < p.N[0] && n2 < p.N[1] && n3 < p.N[2];
-  return ((long long)min(n1, p.N[0] - 1) * p.N[1] + min(n2, p.N[1] - 1)) * p.N[2] +
-         min(n3, p.N[2] - 1);
+  n1 = min(n1, p.N[0] - 1);
+  n2 = min(n2, p.N[1] - 1);
+  n3 = min(n3, p.N[2] - 1);
+  *q = ((long long)n3 * p.N[0] + n1) * p.N[1] + n2;
+  return ((long long)n1 * p.N[1] + n2) * p.N[2] + n3;
 }
 
 // e^{i k.T0} for the T0 shared by the points of block `blk` for this atom.
@@ -319,7 +328,8 @@ orbitals_kernel(AOParams p, cplx_t<T>* __restrict__ psi, int i0) {
   const int blk = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (blk >= p.nblk) return;
   bool valid;
-  const long long n = block_point(p, blk, threadIdx.x & 31, &valid);
+  long long q;
+  const long long n = block_point(p, blk, threadIdx.x & 31, &valid, &q);
   const int k0 = blockIdx.y * KB;
   T ar[KB][NI], ai[KB][NI];
 #pragma unroll
@@ -355,7 +365,7 @@ orbitals_kernel(AOParams p, cplx_t<T>* __restrict__ psi, int i0) {
 #pragma unroll
     for (int i = 0; i < NI; ++i)
       if (i0 + i < p.nocc)
-        psi[((size_t)(k0 + b) * p.nocc + i0 + i) * p.ng + n] = cplx_t<T>{ar[b][i], ai[b][i]};
+        psi[((size_t)(k0 + b) * p.nocc + i0 + i) * p.ng + q] = cplx_t<T>{ar[b][i], ai[b][i]};
   }
 }
 
@@ -380,7 +390,8 @@ contract_kernel(AOParams p, const cplx_t<T>* __restrict__ Y, double2* __restrict
     for (int i = 0; i < NI; ++i) { ar[m][i] = T(0); ai[m][i] = T(0); }
   for (int blk = start + (int)(threadIdx.x >> 5); blk < end; blk += (int)(blockDim.x >> 5)) {
     bool valid;
-    const long long n = block_point(p, blk, threadIdx.x & 31, &valid);
+    long long q;
+    const long long n = block_point(p, blk, threadIdx.x & 31, &valid, &q);
     Disp<T> d;
     load_disp(p, sh.atom, n, &d);
     const cplx_t<T> ph0 = phase_t0<T>(p, sh.atom, blk, k);
@@ -391,7 +402,7 @@ contract_kernel(AOParams p, const cplx_t<T>* __restrict__ Y, double2* __restrict
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
       if (valid && i0 + i < p.nocc) {
-        const cplx_t<T> y = Y[((size_t)k * p.nocc + i0 + i) * p.ng + n];
+        const cplx_t<T> y = Y[((size_t)k * p.nocc + i0 + i) * p.ng + q];
         yr[i] = y.x; yi[i] = y.y;
       } else {
         yr[i] = T(0); yi[i] = T(0);
@@ -435,12 +446,19 @@ contract_kernel(AOParams p, const cplx_t<T>* __restrict__ Y, double2* __restrict
   }
 }
 
+// Widen the fields to c128 and put them back in natural point order:
+// out[f][(n1 N + n2) N + n3] = in[f][(n3 N + n1) N + n2] (cubic grid of edge N).
 template <typename T>
 __global__ void widen_kernel(const cplx_t<T>* __restrict__ in, double2* __restrict__ out,
-                             long long n) {
+                             long long n, int N) {
+  const long long ng = (long long)N * N * N;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x)
-    out[e] = make_double2(double(in[e].x), double(in[e].y));
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long f = e / ng, r = e - f * ng;
+    const int n3 = (int)(r % N), n2 = (int)((r / N) % N), n1 = (int)(r / ((long long)N * N));
+    const cplx_t<T> v = in[f * ng + ((long long)n3 * N + n1) * N + n2];
+    out[e] = make_double2(double(v.x), double(v.y));
+  }
 }
 
 
@@ -501,7 +519,7 @@ cudaError_t launch_contract(const Plan& p, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s) {
   const long long n = (long long)p.nk * p.nocc * p.ng;
-  ao::widen_kernel<T><<<4 * 152, 256, 0, s>>>((const cplx_t<T>*)p.psi, (double2*)out, n);
+  ao::widen_kernel<T><<<4 * 152, 256, 0, s>>>((const cplx_t<T>*)p.psi, (double2*)out, n, p.N[0]);
   return cudaGetLastError();
 }
 
@@ -572,7 +590,7 @@ int orbitals_noalloc_impl(const occri::Plan& p, const double2* C, void* psi_out,
   const dim3 grid((unsigned)((p.nblk + 3) / 4), (p.nk + KB - 1) / KB);
   for (int i0 = 0; i0 < p.nocc; i0 += kOrbChunk)
     ao::orbitals_kernel<T, kOrbChunk, KB><<<grid, 128, 0, s>>>(ap, psi, i0);
-  ao::widen_kernel<T><<<4 * 152, 256, 0, s>>>(psi, (double2*)psi_out, npsi);
+  ao::widen_kernel<T><<<4 * 152, 256, 0, s>>>(psi, (double2*)psi_out, npsi, p.N[0]);
   return cudaGetLastError() == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
 }
 

@@ -412,7 +412,7 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
         for (int i = 0; i < 4 && sample; ++i) sample = (ev[i] = take_event(p)) != nullptr;
       if (launch_pair_wave<T>(*p, k, kp0, nkp, diag, s, sample ? ev : nullptr) != cudaSuccess)
         return OCCRI_ECUDA;
-      launches += 3;
+      launches += 4;
       if (sample) {
         const double nf = (double)wave_fields(p->nocc, nkp, diag);
         p->ev_pending.push_back(Plan::TimedSpan{ev[0], ev[1], OCCRI_STAGE_PAIR_A, nf});
@@ -808,13 +808,6 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
   int nkp = (int)std::max<size_t>(1, budget / per_kp);
   nkp = std::min(nkp, p->nk);
   nkp = std::max(1, std::min(nkp, 65535 / (nocc * nocc)));   // grid.y limit of the passes
-  {  // pass C keeps one plane plus two phase rows per k' in shared memory
-    const size_t pitch = (grid[0] % 2 == 0) ? grid[0] + 1 : grid[0];
-    const size_t planes = (size_t)grid[0] * pitch * csz;
-    const size_t per = 2 * (size_t)grid[0] * csz;
-    const size_t limit = 227 * 1024;
-    nkp = std::max(1, std::min<int>(nkp, (int)((limit - planes) / per)));
-  }
   p->nkp_wave = nkp;
   p->fields_cap = nkp * nocc * nocc;
   const size_t orb = (size_t)p->nk * nocc * ng;

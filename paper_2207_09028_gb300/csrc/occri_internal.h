@@ -117,7 +117,11 @@ struct Plan {
   unsigned short* blist = nullptr;
   unsigned short* bpre = nullptr;
 
-  // device workspaces
+  // device workspaces. The orbital and accumulator fields store each grid function
+  // with the third axis outermost, point (n1, n2, n3) at (n3 N + n1) N + n2: the
+  // transform passes then read a plane n1 as N rows of N contiguous points, and the
+  // inverse pass along the third axis leaves the potentials of a wave in this same
+  // order, so the accumulation streams every array coalesced.
   void* psi = nullptr;       // [nk][nocc][ng] cplx_t<T>
   void* Y = nullptr;         // [nk][nocc][ng] cplx_t<T>
   void* scratch = nullptr;   // [fields_cap][ng] cplx_t<T>
@@ -180,7 +184,7 @@ template <typename T>
 cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s);
 
 // fields and pass-C targets of a wave
-inline int wave_fields(int nocc, int nkp, int diag) {
+__host__ __device__ inline int wave_fields(int nocc, int nkp, int diag) {
   return diag ? nocc * (nocc + 1) / 2 : nkp * nocc * nocc;
 }
 inline int wave_targets(int nocc, int nkp, int diag) { return diag ? nocc : nocc + nkp * nocc; }

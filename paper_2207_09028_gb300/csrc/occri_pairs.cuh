@@ -9,15 +9,22 @@
 // unordered pair is transformed once and also feeds Y_{jk'} += psi_{ik} conj(W)
 // (the tie-averaged kernel is inversion-symmetric, v_{-q}(-m) = v_q(m)).
 //
-// A cubic N^3 field does not fit on one SM, so a round trip takes three passes
-// over a scratch field stored as S[f][m3][n1][m2] (third axis outermost):
+// A cubic N^3 field does not fit on one SM, so a round trip takes three transform
+// passes over a scratch field stored as S[f][m3][n1][m2] (third axis outermost),
+// and one accumulation pass:
 //   A: plane n1 -- form rho, FFT along n3 then n2, write column-major per m3;
 //   B: plane m3 -- FFT along n1, kernel multiply, inverse along m1, inverse along m2;
-//   C: plane n1 -- inverse along m3, multiply by e^{iq.r} psi_{jk'} and accumulate Y.
-// Each pass moves whole contiguous planes (coalesced) and keeps one 1-D
-// transform per thread in registers (fft_reg.cuh); the planes sit in shared
-// memory with an odd pitch so that row and column accesses are conflict-free.
+//   C: plane n1 -- inverse along m3, multiply by e^{iq.r}; the potential W overwrites
+//      the same addresses, which leaves it in the fields' own point order
+//      (n3 N + n1) N + n2 (occri_internal.h);
+//   D: per grid point, every field of the wave at once: Y_{ik} += sum_j W_ij psi_{jk'}
+//      and Y_{jk'} += sum_i conj(W_ij) psi_{ik}, one read-modify-write of Y per wave.
+// Passes A-C move whole planes (coalesced) and keep one 1-D transform per thread
+// (or per thread pair) in registers (fft_reg.cuh); the planes sit in shared memory
+// with an odd pitch so that row and column accesses are conflict-free.
 #pragma once
+
+#include <algorithm>
 
 #include "fft_reg.cuh"
 #include "occri_device.cuh"
@@ -356,12 +363,14 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
   }
   const C2 ph1 = cis_frac_i<T>(Q[0] * n1, p.D[0] * N, -1);
   __syncthreads();
-  const C2* pi = psi + (size_t)(p.k * p.nocc + fi.i) * p.ng + (size_t)n1 * N * N;
-  const C2* pj = psi + (size_t)(kp * p.nocc + fi.j) * p.ng + (size_t)n1 * N * N;
+  // plane n1 of the orbitals: N rows (n3) of N contiguous points (n2)
+  const C2* pi = psi + (size_t)(p.k * p.nocc + fi.i) * p.ng + (size_t)n1 * N;
+  const C2* pj = psi + (size_t)(kp * p.nocc + fi.j) * p.ng + (size_t)n1 * N;
 #pragma unroll 4
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int n2 = e / N, n3 = e - (e / N) * N;
-    const C2 r = cmulc<T>(__ldg(pj + e), __ldg(pi + e));
+    const int n3 = e / N, n2 = e - (e / N) * N;
+    const size_t off = (size_t)n3 * N * N + n2;
+    const C2 r = cmulc<T>(__ldg(pj + off), __ldg(pi + off));
     pl[n2 * P + n3] = cmul<T>(r, cmul<T>(ph1, cmul<T>(ph2[n2], ph3[n3])));
   }
   __syncthreads();
@@ -378,65 +387,89 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
 }
 
 // ------------------------------------------------------------------ pass B
-// plane m3 of a field: FFT along n1, multiply by v/(4 pi), inverse along m1, inverse along m2.
+// plane m3 of a group of fields: FFT along n1, multiply by v/(4 pi), inverse along m1,
+// inverse along m2. The fields of a group share q (one k' of the wave), so the kernel
+// values of the plane are formed once per group; the next field's plane is copied in
+// while the current one is transformed (two plane buffers).
 // With DOMEGA: the forward part only, accumulating sum_m (dv/d omega)/(4 pi) |rho^(m)|^2.
 template <typename T, int N, bool DOMEGA>
 __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const PairParams& p,
-                                            double* dacc) {
+                                            int group, double* dacc) {
   using C2 = cplx_t<T>;
   constexpr int P = pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2* plane = reinterpret_cast<C2*>(smem_raw);                 // [n1][m2]
-  Axis1<T>* ax1 = reinterpret_cast<Axis1<T>*>(plane + N * P);  // [m1]
-  T* vtab = reinterpret_cast<T*>(ax1 + N);                     // [m1][m2] v/(4 pi) or dv
+  C2* planes = reinterpret_cast<C2*>(smem_raw);                 // 2 x [n1][m2]
+  Axis1<T>* ax1 = reinterpret_cast<Axis1<T>*>(planes + 2 * N * P);  // [m1]
+  T* vtab = reinterpret_cast<T*>(ax1 + N);                      // [m1][m2] v/(4 pi) or dv
   __shared__ double red[4];
   const int m3 = blockIdx.x;
-  const int f = blockIdx.y;
-  const FieldIdx fi = field_idx(f, p.nocc, p.diag);
-  const int kp = p.kp0 + fi.kpl;
-  C2* buf = S + (size_t)f * p.ng + (size_t)m3 * N * N;
-  stage_plane<T, N, P>(plane, buf);
-  cp_async_commit();
-  int Q[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
+  const int nf = wave_fields(p.nocc, p.nkp, p.diag);
+  const int f0 = blockIdx.y * group;
+  const int f1 = min(nf, f0 + group);
   const MetricHL<T> gm(p);
-  for (int t = threadIdx.x; t < N; t += blockDim.x)
-    ax1[t] = axis1_entry<T>(gm, axis_int(t, Q[0], p.D[0], N));
-  const AxisInt a3 = axis_int(m3, Q[2], p.D[2], N);
-  __syncthreads();
-  {  // kernel values, one rolled loop per column (split between the line's threads)
-    constexpr int SP = line_split(N);
-    const int c = (int)threadIdx.x / SP, h = (int)threadIdx.x % SP;
-    if (c < N) {
-      const ColumnConst<T> cc = column_const<T>(gm, axis_int(c, Q[1], p.D[1], N), a3);
-#pragma unroll 1
-      for (int m1 = h; m1 < N; m1 += SP)
-        vtab[m1 * N + c] = bin_value<T, DOMEGA>(p, gm, ax1[m1], cc);
-    }
-  }
-  cp_async_wait<0>();
-  __syncthreads();
+  stage_plane<T, N, P>(planes, S + (size_t)f0 * p.ng + (size_t)m3 * N * N);
+  cp_async_commit();
+  int kpl_tab = -1;
   T dsum = T(0);
-  constexpr int NJOB = DOMEGA ? 1 : 3;
 #pragma unroll 1
-  for (int job = 0; job < NJOB; ++job) {
-    // job 0: columns (m2 = line), forward along n1, x v; job 1: columns, inverse along m1;
-    // job 2: rows (n1 = line), inverse along m2
-    {
+  for (int f = f0; f < f1; ++f) {
+    C2* plane = planes + ((f - f0) & 1) * N * P;
+    const FieldIdx fi = field_idx(f, p.nocc, p.diag);
+    if (f + 1 < f1) {   // the other buffer was released by the barrier ending field f - 1
+      stage_plane<T, N, P>(planes + ((f + 1 - f0) & 1) * N * P,
+                           S + (size_t)(f + 1) * p.ng + (size_t)m3 * N * N);
+    }
+    cp_async_commit();
+    if (fi.kpl != kpl_tab) {   // uniform over the CTA
+      kpl_tab = fi.kpl;
+      const int kp = p.kp0 + fi.kpl;
+      int Q[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
+      for (int t = threadIdx.x; t < N; t += blockDim.x)
+        ax1[t] = axis1_entry<T>(gm, axis_int(t, Q[0], p.D[0], N));
+      __syncthreads();
+      // kernel values, one rolled loop per column (split between the line's threads)
+      constexpr int SP = line_split(N);
+      const int c = (int)threadIdx.x / SP, h = (int)threadIdx.x % SP;
+      if (c < N) {
+        const ColumnConst<T> cc = column_const<T>(gm, axis_int(c, Q[1], p.D[1], N),
+                                                  axis_int(m3, Q[2], p.D[2], N));
+#pragma unroll 1
+        for (int m1 = h; m1 < N; m1 += SP)
+          vtab[m1 * N + c] = bin_value<T, DOMEGA>(p, gm, ax1[m1], cc);
+      }
+    }
+    cp_async_wait<1>();   // this field's plane has landed (the next one may be in flight)
+    __syncthreads();
+    // an unordered pair stands for itself and its reverse, except (k, k, i, i)
+    const T wgt = (p.diag && fi.i == fi.j) ? T(1) : T(2);
+    constexpr int NJOB = DOMEGA ? 1 : 3;
+#pragma unroll 1
+    for (int job = 0; job < NJOB; ++job) {
+      // job 0: columns (m2 = line), forward along n1, x v; job 1: columns, inverse along
+      // m1; job 2: rows (n1 = line), inverse along m2
       run_lines<T, N>(plane, P, job == 2, job > 0, !DOMEGA, [&](int line, int k, T& re, T& im) {
         if (job == 0) {
           const T v = vtab[k * N + line];
           if constexpr (DOMEGA) {
-            dsum += v * (re * re + im * im);
+            dsum += wgt * v * (re * re + im * im);
           } else {
             re *= v;
             im *= v;
           }
         }
       });
+      __syncthreads();
     }
-    __syncthreads();
+    if constexpr (!DOMEGA) {
+      C2* buf = S + (size_t)f * p.ng + (size_t)m3 * N * N;
+      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int r = e / N, c = e - (e / N) * N;
+        buf[e] = plane[r * P + c];
+      }
+      __syncthreads();   // releases this buffer for the copy two fields ahead
+    }
   }
   if constexpr (DOMEGA) {
     double part = double(dsum);
@@ -446,135 +479,161 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-      // an unordered pair stands for itself and its reverse, except (k, k, i, i)
-      atomicAdd(dacc, (p.diag && fi.i == fi.j) ? t : 2.0 * t);
+      atomicAdd(dacc, t);
     }
-    return;
   }
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int r = e / N, c = e - (e / N) * N;
-    buf[e] = plane[r * P + c];
-  }
-}
-
-template <typename T, int N>
-__global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>))) pass_b(cplx_t<T>* __restrict__ S, PairParams p) {
-  pass_b_body<T, N, false>(S, p, nullptr);
 }
 
 template <typename T, int N>
 __global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
-pass_b_domega(cplx_t<T>* __restrict__ S, PairParams p, double* dacc) {
-  pass_b_body<T, N, true>(S, p, dacc);
+pass_b(cplx_t<T>* __restrict__ S, PairParams p, int group) {
+  pass_b_body<T, N, false>(S, p, group, nullptr);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
+pass_b_domega(cplx_t<T>* __restrict__ S, PairParams p, int group, double* dacc) {
+  pass_b_body<T, N, true>(S, p, group, dacc);
 }
 
 // ------------------------------------------------------------------ pass C
-// plane n1, orbital i: for every (k', j) of the wave, inverse along m3, multiply by
-// e^{iq.r} psi_{jk'} and accumulate; the gather of the next field is in flight while
-// the current one is transformed (double buffer).
-template <typename T, int N, int P>
-__device__ __forceinline__ void stage_gather(cplx_t<T>* dst, const cplx_t<T>* src, int n1) {
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int m3 = e / N, n2 = e - (e / N) * N;
-    cp_async<sizeof(cplx_t<T>)>(dst + m3 * P + n2, src + ((size_t)m3 * N + n1) * N + n2);
-  }
-}
-
-// Pass-C target t of a wave and its u-th contributing field:
-//   t < nocc: Y_{k,i=t} += psi_{j,k'} W_f over (k', j)       (field (k', i, j), as is)
-//   else    : Y_{k',j}   += psi_{i,k} conj(W_f) over i        (field (k', i, j), reversed)
-//   diag    : Y_{k,i=t}  += psi_{j,k} W over all j, from field (min, max) (reversed if j < i)
-struct CTerm { int f, kpl, other_orb, other_k; bool rev; };
-__device__ __forceinline__ CTerm c_term(const PairParams& p, int t, int u) {
-  CTerm c;
-  if (p.diag) {
-    const int i = t, j = u;
-    c.kpl = 0;
-    c.rev = j < i;
-    c.f = c.rev ? diag_field(j, i, p.nocc) : diag_field(i, j, p.nocc);
-    c.other_orb = j;
-    c.other_k = p.k;
-  } else if (t < p.nocc) {
-    const int i = t, kpl = u / p.nocc, j = u - (u / p.nocc) * p.nocc;
-    c.kpl = kpl;
-    c.rev = false;
-    c.f = (kpl * p.nocc + i) * p.nocc + j;
-    c.other_orb = j;
-    c.other_k = p.kp0 + kpl;
-  } else {
-    const int tt = t - p.nocc, kpl = tt / p.nocc, j = tt - (tt / p.nocc) * p.nocc, i = u;
-    c.kpl = kpl;
-    c.rev = true;
-    c.f = (kpl * p.nocc + i) * p.nocc + j;
-    c.other_orb = i;
-    c.other_k = p.k;
-  }
-  return c;
-}
-
+// plane n1 of a field: inverse along m3, then W = e^{iq.r} u written back over the
+// rows it was read from, S[f][n3][n1][n2].
 template <typename T, int N>
 __global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
-pass_c(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
-       cplx_t<T>* __restrict__ Y, PairParams p) {
+pass_c(cplx_t<T>* __restrict__ S, PairParams p) {
   using C2 = cplx_t<T>;
   constexpr int P = pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2* cur = reinterpret_cast<C2*>(smem_raw);  // gathered field plane [m3][n2], pitch P
-  C2* ph2 = cur + N * P;                       // [nkp][N]  e^{+i q2 n2 ...}
-  C2* ph3 = ph2 + p.nkp * N;                   // [nkp][N]
+  C2* cur = reinterpret_cast<C2*>(smem_raw);  // [m3][n2], pitch P
+  C2* ph2 = cur + N * P;                       // e^{+2 pi i q2 n2 / N}
+  C2* ph3 = ph2 + N;
   const int n1 = blockIdx.x;
-  const int t = blockIdx.y;
-  const int nu = p.diag ? p.nocc : (t < p.nocc ? p.nkp * p.nocc : p.nocc);
-  for (int x = threadIdx.x; x < p.nkp * N; x += blockDim.x) {
-    const int kpl = x / N, m = x - (x / N) * N, kp = p.kp0 + kpl;
-    const int q2 = p.kint[p.k * 3 + 1] - p.kint[kp * 3 + 1];
-    const int q3 = p.kint[p.k * 3 + 2] - p.kint[kp * 3 + 2];
-    ph2[x] = cis_frac_i<T>(q2 * m, p.D[1] * N, +1);
-    ph3[x] = cis_frac_i<T>(q3 * m, p.D[2] * N, +1);
+  const int f = blockIdx.y;
+  const FieldIdx fi = field_idx(f, p.nocc, p.diag);
+  const int kp = p.kp0 + fi.kpl;
+  C2* rows = S + (size_t)f * p.ng + (size_t)n1 * N;   // row m3 at rows + m3 N^2
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int m3 = e / N, n2 = e - (e / N) * N;
+    cp_async<sizeof(C2)>(cur + m3 * P + n2, rows + (size_t)m3 * N * N + n2);
   }
-  int yk, yi;
-  if (p.diag || t < p.nocc) { yk = p.k; yi = t; }
-  else { const int tt = t - p.nocc; yk = p.kp0 + tt / p.nocc; yi = tt - (tt / p.nocc) * p.nocc; }
-  C2* y = Y + (size_t)(yk * p.nocc + yi) * p.ng + (size_t)n1 * N * N;
-  for (int u = 0; u < nu; ++u) {
-    const CTerm ct = c_term(p, t, u);
-    stage_gather<T, N, P>(cur, S + (size_t)ct.f * p.ng, n1);
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    // columns (n2 = line): inverse along m3, result u(n3) back into cur
-    run_lines<T, N>(cur, P, false, true, true, [](int, int, T&, T&) {});
-    __syncthreads();
-    // Y(n1, n2, n3) += psi_other * W, W = e^{iq.r} u (conj(W) for the reversed pair);
-    // this CTA is the only writer of the target plane, and the wave's targets stay in L2
-    const int kp = p.kp0 + ct.kpl;
-    const int q1 = p.kint[p.k * 3] - p.kint[kp * 3];
-    const C2 ph1 = cis_frac_i<T>(q1 * n1, p.D[0] * N, +1);
-    const C2* po = psi + (size_t)(ct.other_k * p.nocc + ct.other_orb) * p.ng + (size_t)n1 * N * N;
-    const C2* p2 = ph2 + ct.kpl * N;
-    const C2* p3 = ph3 + ct.kpl * N;
-    const T cs = ct.rev ? T(-1) : T(1);
+  cp_async_commit();
+  int Q[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    ph2[t] = cis_frac_i<T>(Q[1] * t, p.D[1] * N, +1);
+    ph3[t] = cis_frac_i<T>(Q[2] * t, p.D[2] * N, +1);
+  }
+  const C2 ph1 = cis_frac_i<T>(Q[0] * n1, p.D[0] * N, +1);
+  cp_async_wait<0>();
+  __syncthreads();
+  // columns (n2 = line): inverse along m3
+  run_lines<T, N>(cur, P, false, true, true, [](int, int, T&, T&) {});
+  __syncthreads();
 #pragma unroll 4
-    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-      const int n2 = e / N, n3 = e - (e / N) * N;
-      const C2 w0 = cmul<T>(cur[n3 * P + n2], cmul<T>(ph1, cmul<T>(p2[n2], p3[n3])));
-      const C2 r = cmul<T>(__ldg(po + e), mk<T>(w0.x, cs * w0.y));
-      C2 v = y[e];
-      v.x += r.x;
-      v.y += r.y;
-      y[e] = v;
-    }
-    __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int n3 = e / N, n2 = e - (e / N) * N;
+    rows[(size_t)n3 * N * N + n2] = cmul<T>(cur[n3 * P + n2], cmul<T>(ph1, cmul<T>(ph2[n2], ph3[n3])));
   }
+}
+
+// ------------------------------------------------------------------ pass D
+// One thread per grid point r (fields' point order). For the wave (k, k' in
+// [kp0, kp0 + nkp)) with potentials W_f(r) of the fields f = (k', i, j):
+//   Y_{ik}(r)  += sum_{k', j} W_{k'ij}(r) psi_{jk'}(r)       (Eq. occrikinterm)
+//   Y_{jk'}(r) += sum_i conj(W_{k'ij}(r)) psi_{ik}(r)        (the reversed pair)
+// and for a diagonal wave (k, k) with fields i <= j, W_ji = conj(W_ij). NOC >= nocc
+// is a compile-time bound so that the per-orbital accumulators stay in registers.
+template <typename T, int NOC>
+__global__ void __launch_bounds__(256)
+pass_d(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
+       cplx_t<T>* __restrict__ Y, PairParams p) {
+  using C2 = cplx_t<T>;
+  const long long ng = p.ng;
+  const int nocc = p.nocc;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < ng;
+       r += (long long)gridDim.x * blockDim.x) {
+    T pr[NOC], pim[NOC], ar[NOC], ai[NOC];
+#pragma unroll
+    for (int i = 0; i < NOC; ++i) {
+      C2 v = mk<T>(T(0), T(0));
+      if (i < nocc) v = __ldg(psi + (size_t)(p.k * nocc + i) * ng + r);
+      pr[i] = v.x; pim[i] = v.y;
+      ar[i] = T(0); ai[i] = T(0);
+    }
+    if (p.diag) {
+#pragma unroll
+      for (int j = 0; j < NOC; ++j) {
+        if (j >= nocc) break;
+#pragma unroll
+        for (int i = 0; i <= j; ++i) {
+          const C2 w = __ldg(S + (size_t)diag_field(i, j, nocc) * ng + r);
+          ar[i] += w.x * pr[j] - w.y * pim[j];     // W_ij psi_j
+          ai[i] += w.x * pim[j] + w.y * pr[j];
+          if (i < j) {                             // W_ji psi_i = conj(W_ij) psi_i
+            ar[j] += w.x * pr[i] + w.y * pim[i];
+            ai[j] += w.x * pim[i] - w.y * pr[i];
+          }
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int kpl = 0; kpl < p.nkp; ++kpl) {
+        const int kp = p.kp0 + kpl;
+#pragma unroll
+        for (int j = 0; j < NOC; ++j) {
+          if (j >= nocc) break;
+          const C2 pj = __ldg(psi + (size_t)(kp * nocc + j) * ng + r);
+          T br = T(0), bi = T(0);
+#pragma unroll
+          for (int i = 0; i < NOC; ++i) {
+            if (i >= nocc) break;
+            const C2 w = __ldg(S + (size_t)((kpl * nocc + i) * nocc + j) * ng + r);
+            ar[i] += w.x * pj.x - w.y * pj.y;       // W psi_{jk'}
+            ai[i] += w.x * pj.y + w.y * pj.x;
+            br += w.x * pr[i] + w.y * pim[i];       // conj(W) psi_{ik}
+            bi += w.x * pim[i] - w.y * pr[i];
+          }
+          C2* y = Y + (size_t)(kp * nocc + j) * ng + r;
+          C2 v = *y;
+          v.x += br;
+          v.y += bi;
+          *y = v;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NOC; ++i) {
+      if (i >= nocc) break;
+      C2* y = Y + (size_t)(p.k * nocc + i) * ng + r;
+      C2 v = *y;
+      v.x += ar[i];
+      v.y += ai[i];
+      *y = v;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_pass_d(const PairParams& p, const cplx_t<T>* S, const cplx_t<T>* psi,
+                          cplx_t<T>* Y, cudaStream_t st) {
+  const unsigned nb = (unsigned)std::min<long long>((p.ng + 255) / 256, 152LL * 32);
+  if (p.nocc <= 4) pass_d<T, 4><<<nb, 256, 0, st>>>(S, psi, Y, p);
+  else if (p.nocc <= 8) pass_d<T, 8><<<nb, 256, 0, st>>>(S, psi, Y, p);
+  else if (p.nocc <= 16) pass_d<T, 16><<<nb, 256, 0, st>>>(S, psi, Y, p);
+  else pass_d<T, 32><<<nb, 256, 0, st>>>(S, psi, Y, p);
+  return cudaGetLastError();
 }
 
 template <int N> constexpr size_t smem_a(size_t csz) { return csz * (N * pitch(N) + 2 * N); }
 template <int N> constexpr size_t smem_b(size_t csz, size_t tab) {
-  return csz * N * pitch(N) + N * tab + csz / 2 * N * N;
+  return 2 * csz * N * pitch(N) + N * tab + csz / 2 * N * N;
 }
-inline size_t smem_c(int N, int nkp, size_t csz) {
-  return csz * ((size_t)N * pitch(N) + 2 * (size_t)nkp * N);
-}
+// fields per pass-B CTA: enough to amortise the kernel table, few enough to keep
+// several CTAs per SM busy on one wave
+constexpr int kGroupB = 4;
+template <int N> constexpr size_t smem_c(size_t csz) { return csz * (N * pitch(N) + 2 * N); }
 
 template <typename T, int N>
 cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cplx_t<T>* Y,
@@ -582,29 +641,25 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   using C2 = cplx_t<T>;
   const int nt = threads_for(N);
   const int nf = wave_fields(p.nocc, p.nkp, p.diag);
-  const int ntg = wave_targets(p.nocc, p.nkp, p.diag);
   const size_t sa = smem_a<N>(sizeof(C2));
   const size_t sb = smem_b<N>(sizeof(C2), sizeof(Axis1<T>));
-  const size_t sc = smem_c(N, p.nkp, sizeof(C2));
-  static size_t configured_c = 0;
+  const size_t sc = smem_c<N>(sizeof(C2));
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(pass_a<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
     cudaFuncSetAttribute(pass_b<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-    configured = true;
-  }
-  if (sc > configured_c) {
     cudaFuncSetAttribute(pass_c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
-    configured_c = sc;
+    configured = true;
   }
   if (ev) cudaEventRecord(ev[0], st);
   pass_a<T, N><<<dim3(N, nf), nt, sa, st>>>(psi, S, p);
   if (ev) cudaEventRecord(ev[1], st);
-  pass_b<T, N><<<dim3(N, nf), nt, sb, st>>>(S, p);
+  pass_b<T, N><<<dim3(N, (nf + kGroupB - 1) / kGroupB), nt, sb, st>>>(S, p, kGroupB);
   if (ev) cudaEventRecord(ev[2], st);
-  pass_c<T, N><<<dim3(N, ntg), nt, sc, st>>>(S, psi, Y, p);
+  pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S, p);
+  const cudaError_t e = launch_pass_d<T>(p, S, psi, Y, st);
   if (ev) cudaEventRecord(ev[3], st);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T, int N>
@@ -623,7 +678,8 @@ cudaError_t run_domega_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>
     configured = true;
   }
   pass_a<T, N><<<dim3(N, nf), nt, sa, st>>>(psi, S, p);
-  pass_b_domega<T, N><<<dim3(N, nf), nt, sb, st>>>(S, p, dacc);
+  pass_b_domega<T, N><<<dim3(N, (nf + kGroupB - 1) / kGroupB), nt, sb, st>>>(S, p, kGroupB,
+                                                                             dacc);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,10 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 TOL = {"fp64": dict(k_rel=1e-10, e_rel=1e-10), "mixed": dict(k_abs=1e-5, e_abs=1e-6)}
+# The mixed-precision bar |dE_x| <= 1e-6 Ha per cell is set for the 6x6x6-k, 350-AO cell,
+# whose |E_x| is about 2.5 Ha. FP32 rounding error is relative, so cells with a larger
+# |E_x| (many occupied orbitals in a small basis) get the same relative bar.
+E_X_BAR_SCALE = 2.5
 
 
 @pytest.fixture(scope="module")
@@ -49,7 +53,8 @@ def _gpu(torch, w, precision):
     return out
 
 
-def _assert_close(got, ref, precision, what=""):
+def _assert_close(got, ref, precision, what="", strict_e=False):
+    """strict_e: the absolute 1e-6 Ha bar whatever |E_x| (the paper-scale cells)."""
     t = TOL[precision]
     if precision == "fp64":
         scale = np.abs(ref["k"]).max()
@@ -58,7 +63,8 @@ def _assert_close(got, ref, precision, what=""):
         assert abs(got["ex"] - ref["ex"]) <= t["e_rel"] * abs(ref["ex"]), what
     else:
         assert np.abs(got["k"] - ref["k"]).max() <= t["k_abs"], (what, np.abs(got["k"] - ref["k"]).max())
-        assert abs(got["ex"] - ref["ex"]) <= t["e_abs"], (what, got["ex"], ref["ex"])
+        tol_e = t["e_abs"] * (1.0 if strict_e else max(1.0, abs(ref["ex"]) / E_X_BAR_SCALE))
+        assert abs(got["ex"] - ref["ex"]) <= tol_e, (what, got["ex"], ref["ex"])
 
 
 # ------------------------------------------------------------------ steps (a)+(b)
@@ -89,6 +95,10 @@ SMALL = [
     dict(mesh=(1, 2, 1), grid=(16, 16, 16), counts=(2, 1), nocc=2, kernel="erf", omega=0.6),
     dict(mesh=(1, 1, 1), grid=(25, 25, 25), counts=(1, 1), nocc=1),
     dict(mesh=(1, 1, 1), grid=(27, 27, 27), counts=(1, 1, 1), nocc=4),
+    # more than 8 and more than 16 occupied orbitals (wider register blocks of the
+    # accumulation pass), with off-diagonal (k, k') waves
+    dict(mesh=(1, 1, 2), grid=(8, 8, 8), counts=(3, 2, 1), nocc=12),
+    dict(mesh=(2, 1, 1), grid=(9, 9, 9), counts=(3, 2, 1), nocc=20),
 ]
 
 
@@ -158,7 +168,7 @@ def test_config_matches_golden(torch_cuda, name, precision):
     g = _golden(name)
     k_ref, _, ex_ref = O.ace_assemble(w.C, g["kc"])
     got = _gpu(torch_cuda, w, precision)
-    _assert_close(got, dict(k=k_ref, kc=g["kc"], ex=float(g["ex"])), precision, name)
+    _assert_close(got, dict(k=k_ref, kc=g["kc"], ex=float(g["ex"])), precision, name, strict_e=True)
 
 
 @pytest.mark.parametrize("name", ["cfg3_erfc", "cfg3_erf"])
@@ -167,7 +177,7 @@ def test_config3_mixed_matches_golden(torch_cuda, name):
     g = _golden(name)
     k_ref, _, ex_ref = O.ace_assemble(w.C, g["kc"])
     got = _gpu(torch_cuda, w, "mixed")
-    _assert_close(got, dict(k=k_ref, kc=g["kc"], ex=float(g["ex"])), "mixed", name)
+    _assert_close(got, dict(k=k_ref, kc=g["kc"], ex=float(g["ex"])), "mixed", name, strict_e=True)
 
 
 @pytest.mark.parametrize("cell", range(5))
@@ -177,7 +187,8 @@ def test_config4_cells_match_golden(torch_cuda, cell, precision):
     g = _golden(w.name)
     k_ref, _, _ = O.ace_assemble(w.C, g["kc"])
     got = _gpu(torch_cuda, w, precision)
-    _assert_close(got, dict(k=k_ref, kc=g["kc"], ex=float(g["ex"])), precision, w.name)
+    _assert_close(got, dict(k=k_ref, kc=g["kc"], ex=float(g["ex"])), precision, w.name,
+                  strict_e=True)
     # the E_x adjoint: d E_x / d omega against the oracle, d E_x / d C = (4/N_k) KC
     gC, gw = got["plan"].vjp(got["C"], 1.0)
     tol = 1e-9 if precision == "fp64" else 1e-5
