@@ -462,6 +462,35 @@ __global__ void widen_kernel(const cplx_t<T>* __restrict__ in, double2* __restri
 }
 
 
+// F[k][i][q] *= e^{sign i k.r_q} for every orbital field of every k-point (fields'
+// point order q = (n3 N + n1) N + n2, cubic grid of edge N). With sign = -1 this turns
+// the Bloch orbitals psi_ik into their periodic parts u_ik = e^{-ik.r} psi_ik, with
+// sign = +1 it turns the accumulated periodic parts back into Y_ik. The phase is
+// 2 pi sum_d kint_d n_d / (D_d N), reduced exactly in integers.
+template <typename T>
+__global__ void phase_fields_kernel(cplx_t<T>* __restrict__ F, const int* __restrict__ kint,
+                                    int nk, int nocc, int N, int D0, int D1, int D2, int sign) {
+  const long long ng = (long long)N * N * N;
+  const long long Dc = (long long)D0 * D1 * D2;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nk * ng;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / ng);
+    const long long q = e - (long long)k * ng;
+    const int n3 = (int)(q / ((long long)N * N));
+    const int rem = (int)(q - (long long)n3 * N * N);
+    const int n1 = rem / N, n2 = rem - (rem / N) * N;
+    const long long num = (long long)kint[3 * k] * n1 * (Dc / D0) +
+                          (long long)kint[3 * k + 1] * n2 * (Dc / D1) +
+                          (long long)kint[3 * k + 2] * n3 * (Dc / D2);
+    const cplx_t<T> ph = dev::cis_frac<T>(num, Dc * N, sign);
+    cplx_t<T>* f = F + (size_t)k * nocc * ng + q;
+    for (int i = 0; i < nocc; ++i) {
+      const cplx_t<T> v = f[(size_t)i * ng];
+      f[(size_t)i * ng] = cplx_t<T>{v.x * ph.x - v.y * ph.y, v.x * ph.y + v.y * ph.x};
+    }
+  }
+}
+
 }  // namespace ao
 
 template <>
@@ -476,6 +505,15 @@ cudaError_t launch_scale_c<float>(const Plan& p, const double2* C, cudaStream_t 
   ao::scale_c_kernel_f<<<2 * 152, 256, 0, s>>>(C, p.ao_norm, (float4*)p.cs, p.nao, p.nocc, n);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_phase_fields(const Plan& p, void* F, int sign, cudaStream_t s) {
+  ao::phase_fields_kernel<T><<<8 * 152, 256, 0, s>>>((cplx_t<T>*)F, p.kint, p.nk, p.nocc, p.N[0],
+                                                      p.D[0], p.D[1], p.D[2], sign);
+  return cudaGetLastError();
+}
+template cudaError_t launch_phase_fields<float>(const Plan&, void*, int, cudaStream_t);
+template cudaError_t launch_phase_fields<double>(const Plan&, void*, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_orbitals(const Plan& p, cudaStream_t s) {

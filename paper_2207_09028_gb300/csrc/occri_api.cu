@@ -47,7 +47,7 @@ AOParams Plan::ao_params() const {
 
 PairParams Plan::pair_params() const {
   PairParams q;
-  q.nk = nk; q.nocc = nocc; q.ng = ng; q.N1 = N[0];
+  q.nk = nk; q.nocc = nocc; q.ng = ng; q.fs = fs; q.N1 = N[0];
   q.k = 0; q.kp0 = 0; q.nkp = 1; q.diag = 0;
   for (int d = 0; d < 3; ++d) q.D[d] = D[d];
   q.kint = kint;
@@ -398,8 +398,12 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
     StageTimer t(p, timed);
     if (launch_scale_c<T>(*p, C, s) != cudaSuccess) return OCCRI_ECUDA;
     if (launch_orbitals<T>(*p, s) != cudaSuccess) return OCCRI_ECUDA;
+    // the pair passes work on the periodic parts u = e^{-ik.r} psi: the pair density
+    // conj(u_jk') u_ik is then periodic as it stands, and the accumulated periodic part
+    // e^{-ik.r} Y_ik needs no phase either (Y is restored below)
+    if (launch_phase_fields<T>(*p, p->psi, -1, s) != cudaSuccess) return OCCRI_ECUDA;
     t.done(OCCRI_STAGE_ORBITALS, p->nk);
-    launches += 1 + (p->nocc + kOrbChunk - 1) / kOrbChunk;
+    launches += 2 + (p->nocc + kOrbChunk - 1) / kOrbChunk;
   }
   long long wave = 0;
   for (int k = 0; k < p->nk; ++k)
@@ -423,6 +427,8 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
     }
   {
     StageTimer t(p, timed);
+    if (launch_phase_fields<T>(*p, p->Y, +1, s) != cudaSuccess) return OCCRI_ECUDA;
+    ++launches;
     if (launch_contract<T>(*p, s) != cudaSuccess) return OCCRI_ECUDA;
     t.done(OCCRI_STAGE_CONTRACT, p->nk);
     for (int l = 0; l < 4; ++l)
@@ -453,7 +459,7 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
 }
 
 template <typename T>
-int vjp_impl(Plan* p, double gEx, void* gC, double* gomega) {
+int vjp_impl(Plan* p, const double2* C, double gEx, void* gC, double* gomega) {
   using namespace occri;
   cudaStream_t s = p->stream;
   const long long nkc = (long long)p->nk * p->nao * p->nocc;
@@ -461,6 +467,11 @@ int vjp_impl(Plan* p, double gEx, void* gC, double* gomega) {
   if (gomega) {
     if (cudaMemsetAsync(p->dacc, 0, 2 * sizeof(double), s) != cudaSuccess) return OCCRI_ECUDA;
     if (p->kernel.kind != OCCRI_COULOMB) {
+      // periodic parts of the orbitals of C (the plan's copy may have been replaced by
+      // an occri_orbitals call since the build)
+      if (launch_scale_c<T>(*p, C, s) != cudaSuccess) return OCCRI_ECUDA;
+      if (launch_orbitals<T>(*p, s) != cudaSuccess) return OCCRI_ECUDA;
+      if (launch_phase_fields<T>(*p, p->psi, -1, s) != cudaSuccess) return OCCRI_ECUDA;
       for (int k = 0; k < p->nk; ++k)
         for (int kp0 = k; kp0 < p->nk;) {
           const int diag = (kp0 == k) ? 1 : 0;
@@ -802,7 +813,8 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     p->img_phase = ph;
   }
   const size_t csz = (precision == OCCRI_FP64) ? sizeof(double2) : sizeof(float2);
-  const size_t field_bytes = csz * (size_t)ng;
+  p->fs = (ng + 63) / 64 * 64;
+  const size_t field_bytes = csz * (size_t)p->fs;
   const size_t per_kp = field_bytes * (size_t)nocc * nocc;
   const size_t budget = (size_t)96 << 20;
   int nkp = (int)std::max<size_t>(1, budget / per_kp);
@@ -983,8 +995,9 @@ int occri_vjp(occri_plan* plan, const void* C_dev, double gEx, void* gC_dev, dou
   if (!plan || !C_dev) return OCCRI_EINVAL;
   Plan* p = plan->p;
   if (!p->have_kc) return OCCRI_EINVAL;
-  return p->precision == OCCRI_FP64 ? occri_impl::vjp_impl<double>(p, gEx, gC_dev, gomega_dev)
-                                    : occri_impl::vjp_impl<float>(p, gEx, gC_dev, gomega_dev);
+  const double2* C = (const double2*)C_dev;
+  return p->precision == OCCRI_FP64 ? occri_impl::vjp_impl<double>(p, C, gEx, gC_dev, gomega_dev)
+                                    : occri_impl::vjp_impl<float>(p, C, gEx, gC_dev, gomega_dev);
 }
 
 }  // extern "C"

@@ -66,6 +66,8 @@ struct AOParams {
 struct PairParams {
   int nk, nocc, N1;          // N1: cubic grid edge
   long long ng;
+  long long fs;              // scratch field stride in points: ng rounded up to 64, so that
+                             // every field starts 512-byte aligned
   int k, kp0, nkp;
   int diag;                  // 1: the wave is (k, k) and holds the fields i <= j only
   int D[3];
@@ -96,6 +98,7 @@ struct Plan {
   int D[3];
   std::vector<int> kint_h;
   int fields_cap;            // pair fields held by the transform scratch
+  long long fs;              // scratch field stride in points (ng rounded up to 64)
   int nkp_wave;              // k' per wave
   std::vector<int> shells_by_l[4];
 
@@ -124,7 +127,7 @@ struct Plan {
   // order, so the accumulation streams every array coalesced.
   void* psi = nullptr;       // [nk][nocc][ng] cplx_t<T>
   void* Y = nullptr;         // [nk][nocc][ng] cplx_t<T>
-  void* scratch = nullptr;   // [fields_cap][ng] cplx_t<T>
+  void* scratch = nullptr;   // [fields_cap][fs] cplx_t<T>
   double2* kc = nullptr;     // [nk][nao][nocc]
   double2* xi = nullptr;     // [nk][nao][nocc]
   double2* mmat = nullptr;   // [nk][nocc][nocc]
@@ -173,6 +176,10 @@ template <typename T>
 cudaError_t launch_orbitals(const Plan& p, cudaStream_t s);
 template <typename T>
 cudaError_t launch_contract(const Plan& p, cudaStream_t s);
+// F[k][i][.] *= e^{sign i k.r} over the orbital-shaped field F (psi -> periodic parts
+// with sign -1 before the pair passes, accumulated periodic parts -> Y with +1 after).
+template <typename T>
+cudaError_t launch_phase_fields(const Plan& p, void* F, int sign, cudaStream_t s);
 // Pair-wave launches over unordered pairs: diag = 1 is the wave (k, k) with fields
 // i <= j; diag = 0 covers k' in [kp0, kp0 + nkp), all kp0 > k, with every (i, j).
 // When ev != nullptr, ev[0..3] are recorded before pass A, before pass B, before

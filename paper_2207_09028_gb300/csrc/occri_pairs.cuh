@@ -14,11 +14,14 @@
 // and one accumulation pass:
 //   A: plane n1 -- form rho, FFT along n3 then n2, write column-major per m3;
 //   B: plane m3 -- FFT along n1, kernel multiply, inverse along m1, inverse along m2;
-//   C: plane n1 -- inverse along m3, multiply by e^{iq.r}; the potential W overwrites
-//      the same addresses, which leaves it in the fields' own point order
-//      (n3 N + n1) N + n2 (occri_internal.h);
+//   C: plane n1 -- inverse along m3; the potential W overwrites the same addresses,
+//      which leaves it in the fields' own point order (n3 N + n1) N + n2
+//      (occri_internal.h);
 //   D: per grid point, every field of the wave at once: Y_{ik} += sum_j W_ij psi_{jk'}
 //      and Y_{jk'} += sum_i conj(W_ij) psi_{ik}, one read-modify-write of Y per wave.
+// The orbitals and the accumulators are held as periodic parts (u_ik = e^{-ik.r} psi_ik,
+// e^{-ik.r} Y_ik), so no pass multiplies by e^{-+iq.r}: the density conj(u_jk') u_ik is
+// periodic, and so is the potential that comes back.
 // Passes A-C move whole planes (coalesced) and keep one 1-D transform per thread
 // (or per thread pair) in registers (fft_reg.cuh); the planes sit in shared memory
 // with an odd pitch so that row and column accesses are conflict-free.
@@ -44,14 +47,14 @@ using dev::expm1_t;
 constexpr int pitch(int n) { return (n % 2 == 0) ? n + 1 : n; }
 // Even edges use two threads per line (radix-2 split, see line_fft2), odd edges one.
 constexpr int line_split(int n) { return (n % 2 == 0) ? 2 : 1; }
-constexpr int threads_for(int n) {
-  return ((line_split(n) * n + 31) / 32) * 32;
-}
-// resident CTAs per SM requested from the register allocator (one line per thread)
+constexpr int round32(int n) { return (n + 31) / 32 * 32; }
+// With the split, the two halves of lines 32w..32w+31 sit in warps 2w (h = 0) and
+// 2w + 1 (h = 1), so the half-dependent code is uniform over each warp.
+constexpr int threads_for(int n) { return line_split(n) * round32(n); }
+// resident CTAs per SM requested from the register allocator
 constexpr int min_blocks(int n, int elem_bytes) {
   return elem_bytes > 8 ? (n <= 32 ? 4 : 2) : (n <= 32 ? 8 : 4);
 }
-
 // f(|G+q|)/(4 pi) of Eq. recipcoul for |G+q|^2 = g2 > 0.
 template <typename T>
 __device__ __forceinline__ T kernel_f(T g2, int kind, T inv4w2) {
@@ -116,63 +119,80 @@ __device__ __forceinline__ void stage_plane(cplx_t<T>* dst, const cplx_t<T>* src
 }
 
 // ------------------------------------------------------------------ one line transform
-// Forward DFT (e^{-2 pi i m n / N}) of the N elements at base[m * stride], in place,
-// with the whole line in registers. With conj_io the line is conjugated on load and
-// on store, which gives the unnormalised inverse transform. post(k, re, im) sees
-// output index k before the store (store is skipped when !store). Each kernel
-// calls this once, inside a runtime loop, so the unrolled transform exists once
-// in the instruction stream.
+// DFT (e^{-2 pi i m n / N}) of the N elements at base[m * stride], in place, with the
+// whole line in registers. The unnormalised inverse (e^{+2 pi i m n / N}) is the same
+// transform with output k stored at index (N - k) mod N. post(k, re, im) sees output
+// index k (after that reversal) before the store (store is skipped when !store). Each
+// kernel calls this once, inside a runtime loop, so the unrolled transform exists
+// once in the instruction stream.
 template <typename T, int N, typename Post>
-__device__ __forceinline__ void line_fft(cplx_t<T>* base, int stride, bool conj_io, bool store,
+__device__ __forceinline__ void line_fft(cplx_t<T>* base, int stride, bool inverse, bool store,
                                          Post&& post) {
   T re[N], im[N];
-  const T sg = conj_io ? T(-1) : T(1);
   fft::static_for<N>([&](auto I) {
     constexpr int m = decltype(I)::value;
     const cplx_t<T> v = base[m * stride];
     re[m] = v.x;
-    im[m] = sg * v.y;
+    im[m] = v.y;
   });
   fft::fft_dif<N, -1>(re, im);
   fft::static_for<N>([&](auto I) {
     constexpr int q = decltype(I)::value;
     constexpr int k = fft::dif_rev(N, q);
-    post(k, re[q], im[q]);
-    if (store) base[k * stride] = mk<T>(re[q], sg * im[q]);
+    constexpr int kr = (N - k) % N;
+    const int ks = inverse ? kr : k;
+    post(ks, re[q], im[q]);
+    if (store) base[ks * stride] = mk<T>(re[q], im[q]);
   });
 }
 
-// Two threads per line (even N). Thread h of the pair forms
+// Two threads per line (even N), in two different warps. Half h forms
 //   y_h[n] = (x[n] + (-1)^h x[n + N/2]) e^{-2 pi i h n / N},   n < N/2,
 // from the whole line in shared memory and transforms it with an N/2-point register
-// FFT, which gives the outputs X[2k + h] (radix-2 decimation in frequency). conj_io,
+// FFT, which gives the outputs X[2k + h] (radix-2 decimation in frequency). inverse,
 // store and post as in line_fft; `valid` is false for padding threads, which compute
-// on a duplicate line but neither store nor call post. The pair sits in one warp and
-// synchronises between its loads and its stores.
+// on a duplicate line but neither store nor call post. The two warps of the pair meet
+// at named barrier `bar` (1 or 2: at most two pairs of warps per CTA, N <= 64) between
+// their loads and their stores.
 template <typename T, int N, typename Post>
-__device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool conj_io, bool store,
-                                          int h, bool valid, Post&& post) {
+__device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool inverse, bool store,
+                                          int h, bool valid, int bar, Post&& post) {
   constexpr int M = N / 2;
   T re[M], im[M];
-  const T sg = conj_io ? T(-1) : T(1);
-  const T hs = h ? T(-1) : T(1);
-  fft::static_for<M>([&](auto I) {
-    constexpr int n = decltype(I)::value;
-    constexpr fft::CS w = fft::cs2pi(n, N);     // e^{-2 pi i n / N} = (c, -s)
-    const cplx_t<T> a = base[n * stride], b = base[(n + M) * stride];
-    const T yr = a.x + hs * b.x, yi = sg * (a.y + hs * b.y);
-    const T c = h ? T(w.c) : T(1), sn = h ? T(-w.s) : T(0);
-    re[n] = yr * c - yi * sn;
-    im[n] = yr * sn + yi * c;
-  });
-  __syncwarp();
+  if (h == 0) {
+    fft::static_for<M>([&](auto I) {
+      constexpr int n = decltype(I)::value;
+      const cplx_t<T> a = base[n * stride], b = base[(n + M) * stride];
+      re[n] = a.x + b.x;
+      im[n] = a.y + b.y;
+    });
+  } else {
+    fft::static_for<M>([&](auto I) {
+      constexpr int n = decltype(I)::value;
+      constexpr fft::CS w = fft::cs2pi(n, N);     // e^{-2 pi i n / N} = c - i s
+      const cplx_t<T> a = base[n * stride], b = base[(n + M) * stride];
+      const T yr = a.x - b.x, yi = a.y - b.y;
+      if constexpr (n == 0) {
+        re[n] = yr;
+        im[n] = yi;
+      } else {
+        re[n] = yr * T(w.c) + yi * T(w.s);
+        im[n] = yi * T(w.c) - yr * T(w.s);
+      }
+    });
+  }
+  if (bar == 1)   // warp-uniform; immediate barrier ids
+    asm volatile("bar.sync 1, 64;\n" ::: "memory");
+  else
+    asm volatile("bar.sync 2, 64;\n" ::: "memory");
   fft::fft_dif<M, -1>(re, im);
   fft::static_for<M>([&](auto I) {
     constexpr int q = decltype(I)::value;
     const int k = 2 * fft::dif_rev(M, q) + h;
+    const int ks = inverse ? (k == 0 ? 0 : N - k) : k;
     if (valid) {
-      post(k, re[q], im[q]);
-      if (store) base[k * stride] = mk<T>(re[q], sg * im[q]);
+      post(ks, re[q], im[q]);
+      if (store) base[ks * stride] = mk<T>(re[q], im[q]);
     }
   });
 }
@@ -180,18 +200,19 @@ __device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool conj
 // One transform job over the N lines of a plane (rows: along the contiguous index;
 // columns: along the pitched index); every thread of the CTA must call it.
 template <typename T, int N, typename Post>
-__device__ __forceinline__ void run_lines(cplx_t<T>* plane, int P, bool rows, bool conj_io,
+__device__ __forceinline__ void run_lines(cplx_t<T>* plane, int P, bool rows, bool inverse,
                                           bool store, Post&& post) {
   if constexpr (line_split(N) == 2) {
-    const int t = threadIdx.x;
-    const bool valid = (t >> 1) < N;
-    const int line = valid ? (t >> 1) : N - 1;
-    line_fft2<T, N>(rows ? plane + line * P : plane + line, rows ? 1 : P, conj_io, store,
-                    t & 1, valid, [&](int k, T& re, T& im) { post(line, k, re, im); });
+    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int line0 = (w >> 1) * 32 + lane;
+    const bool valid = line0 < N;
+    const int line = valid ? line0 : N - 1;
+    line_fft2<T, N>(rows ? plane + line * P : plane + line, rows ? 1 : P, inverse, store, w & 1,
+                    valid, 1 + (w >> 1), [&](int k, T& re, T& im) { post(line, k, re, im); });
   } else {
     if (threadIdx.x < N) {
       const int line = threadIdx.x;
-      line_fft<T, N>(rows ? plane + line * P : plane + line, rows ? 1 : P, conj_io, store,
+      line_fft<T, N>(rows ? plane + line * P : plane + line, rows ? 1 : P, inverse, store,
                      [&](int k, T& re, T& im) { post(line, k, re, im); });
     }
   }
@@ -340,7 +361,8 @@ __device__ __forceinline__ T bin_value(const PairParams& p, const Consts<T>& k,
 }
 
 // ------------------------------------------------------------------ pass A
-// plane n1 of field (i, j): rho = conj(psi_j) psi_i e^{-iq.r}; FFT along n3, then n2.
+// plane n1 of field (i, j): rho = conj(u_jk') u_ik (= conj(psi_jk') psi_ik e^{-iq.r}, the
+// orbitals being held as their periodic parts u); FFT along n3, then n2.
 template <typename T, int N>
 __global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
 pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams p) {
@@ -348,30 +370,18 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
   constexpr int P = pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* pl = reinterpret_cast<C2*>(smem_raw);   // rho, then its 2-D transform
-  C2* ph2 = pl + N * P;
-  C2* ph3 = ph2 + N;
   const int n1 = blockIdx.x;
   const int f = blockIdx.y;
   const FieldIdx fi = field_idx(f, p.nocc, p.diag);
   const int kp = p.kp0 + fi.kpl;
-  int Q[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
-  for (int t = threadIdx.x; t < N; t += blockDim.x) {
-    ph2[t] = cis_frac_i<T>(Q[1] * t, p.D[1] * N, -1);
-    ph3[t] = cis_frac_i<T>(Q[2] * t, p.D[2] * N, -1);
-  }
-  const C2 ph1 = cis_frac_i<T>(Q[0] * n1, p.D[0] * N, -1);
-  __syncthreads();
-  // plane n1 of the orbitals: N rows (n3) of N contiguous points (n2)
+  // plane n1 of the periodic parts: N rows (n3) of N contiguous points (n2)
   const C2* pi = psi + (size_t)(p.k * p.nocc + fi.i) * p.ng + (size_t)n1 * N;
   const C2* pj = psi + (size_t)(kp * p.nocc + fi.j) * p.ng + (size_t)n1 * N;
 #pragma unroll 4
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int n3 = e / N, n2 = e - (e / N) * N;
     const size_t off = (size_t)n3 * N * N + n2;
-    const C2 r = cmulc<T>(__ldg(pj + off), __ldg(pi + off));
-    pl[n2 * P + n3] = cmul<T>(r, cmul<T>(ph1, cmul<T>(ph2[n2], ph3[n3])));
+    pl[n2 * P + n3] = cmulc<T>(__ldg(pj + off), __ldg(pi + off));
   }
   __syncthreads();
 #pragma unroll 1
@@ -379,7 +389,7 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
     run_lines<T, N>(pl, P, job == 0, false, true, [](int, int, T&, T&) {});
     __syncthreads();
   }
-  C2* out = S + (size_t)f * p.ng;
+  C2* out = S + (size_t)f * p.fs;
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int m3 = e / N, m2 = e - (e / N) * N;
     out[((size_t)m3 * N + n1) * N + m2] = pl[m2 * P + m3];
@@ -387,41 +397,48 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
 }
 
 // ------------------------------------------------------------------ pass B
-// plane m3 of a group of fields: FFT along n1, multiply by v/(4 pi), inverse along m1,
-// inverse along m2. The fields of a group share q (one k' of the wave), so the kernel
-// values of the plane are formed once per group; the next field's plane is copied in
-// while the current one is transformed (two plane buffers).
+// Items (m3, field), m3-major; CTA b takes the contiguous chunk [b c, (b + 1) c) of
+// them (c = ceil(items / grid), the grid being the SMs' resident CTA slots), so there is
+// no partly filled last round of CTAs. Per item: FFT along n1, multiply by v/(4 pi),
+// inverse along m1, inverse along m2. Consecutive items share m3 and (mostly) q, so the
+// kernel values of a plane are formed only when (m3, k') changes; the next item's plane
+// is copied in while the current one is transformed (two plane buffers).
 // With DOMEGA: the forward part only, accumulating sum_m (dv/d omega)/(4 pi) |rho^(m)|^2.
 template <typename T, int N, bool DOMEGA>
 __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const PairParams& p,
-                                            int group, double* dacc) {
+                                            double* dacc) {
   using C2 = cplx_t<T>;
   constexpr int P = pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2* planes = reinterpret_cast<C2*>(smem_raw);                 // 2 x [n1][m2]
+  C2* planes = reinterpret_cast<C2*>(smem_raw);                      // 2 x [n1][m2]
   Axis1<T>* ax1 = reinterpret_cast<Axis1<T>*>(planes + 2 * N * P);  // [m1]
-  T* vtab = reinterpret_cast<T*>(ax1 + N);                      // [m1][m2] v/(4 pi) or dv
+  T* vtab = reinterpret_cast<T*>(ax1 + N);                           // [m1][m2] v or dv
   __shared__ double red[4];
-  const int m3 = blockIdx.x;
   const int nf = wave_fields(p.nocc, p.nkp, p.diag);
-  const int f0 = blockIdx.y * group;
-  const int f1 = min(nf, f0 + group);
+  const int items = N * nf;
+  const int per = (items + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int i0 = min(items, (int)blockIdx.x * per);
+  const int i1 = min(items, i0 + per);
   const MetricHL<T> gm(p);
-  stage_plane<T, N, P>(planes, S + (size_t)f0 * p.ng + (size_t)m3 * N * N);
+  auto plane_src = [&](int it) {
+    const int m3 = it / nf, f = it - (it / nf) * nf;
+    return S + (size_t)f * p.fs + (size_t)m3 * N * N;
+  };
+  if (i0 < i1) stage_plane<T, N, P>(planes, plane_src(i0));
   cp_async_commit();
-  int kpl_tab = -1;
+  int m3_tab = -1, kpl_tab = -1;
   T dsum = T(0);
 #pragma unroll 1
-  for (int f = f0; f < f1; ++f) {
-    C2* plane = planes + ((f - f0) & 1) * N * P;
+  for (int it = i0; it < i1; ++it) {
+    C2* plane = planes + ((it - i0) & 1) * N * P;
+    const int m3 = it / nf, f = it - (it / nf) * nf;
     const FieldIdx fi = field_idx(f, p.nocc, p.diag);
-    if (f + 1 < f1) {   // the other buffer was released by the barrier ending field f - 1
-      stage_plane<T, N, P>(planes + ((f + 1 - f0) & 1) * N * P,
-                           S + (size_t)(f + 1) * p.ng + (size_t)m3 * N * N);
-    }
+    if (it + 1 < i1)   // the other buffer was released by the barrier ending item it - 1
+      stage_plane<T, N, P>(planes + ((it + 1 - i0) & 1) * N * P, plane_src(it + 1));
     cp_async_commit();
-    if (fi.kpl != kpl_tab) {   // uniform over the CTA
+    if (fi.kpl != kpl_tab || m3 != m3_tab) {   // uniform over the CTA
       kpl_tab = fi.kpl;
+      m3_tab = m3;
       const int kp = p.kp0 + fi.kpl;
       int Q[3];
 #pragma unroll
@@ -440,35 +457,37 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
           vtab[m1 * N + c] = bin_value<T, DOMEGA>(p, gm, ax1[m1], cc);
       }
     }
-    cp_async_wait<1>();   // this field's plane has landed (the next one may be in flight)
+    cp_async_wait<1>();   // this item's plane has landed (the next one may be in flight)
     __syncthreads();
     // an unordered pair stands for itself and its reverse, except (k, k, i, i)
     const T wgt = (p.diag && fi.i == fi.j) ? T(1) : T(2);
-    constexpr int NJOB = DOMEGA ? 1 : 3;
+    // columns (m2 = line): forward along n1, times v (the only forward transform, so its
+    // output indices are constants)
+    run_lines<T, N>(plane, P, false, false, !DOMEGA, [&](int line, int k, T& re, T& im) {
+      const T v = vtab[k * N + line];
+      if constexpr (DOMEGA) {
+        dsum += wgt * v * (re * re + im * im);
+      } else {
+        re *= v;
+        im *= v;
+      }
+    });
+    __syncthreads();
+    if constexpr (!DOMEGA) {
+      // inverse along m1 (columns), then along m2 (rows)
 #pragma unroll 1
-    for (int job = 0; job < NJOB; ++job) {
-      // job 0: columns (m2 = line), forward along n1, x v; job 1: columns, inverse along
-      // m1; job 2: rows (n1 = line), inverse along m2
-      run_lines<T, N>(plane, P, job == 2, job > 0, !DOMEGA, [&](int line, int k, T& re, T& im) {
-        if (job == 0) {
-          const T v = vtab[k * N + line];
-          if constexpr (DOMEGA) {
-            dsum += wgt * v * (re * re + im * im);
-          } else {
-            re *= v;
-            im *= v;
-          }
-        }
-      });
-      __syncthreads();
+      for (int job = 1; job < 3; ++job) {
+        run_lines<T, N>(plane, P, job == 2, true, true, [](int, int, T&, T&) {});
+        __syncthreads();
+      }
     }
     if constexpr (!DOMEGA) {
-      C2* buf = S + (size_t)f * p.ng + (size_t)m3 * N * N;
+      C2* buf = S + (size_t)f * p.fs + (size_t)m3 * N * N;
       for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
         const int r = e / N, c = e - (e / N) * N;
         buf[e] = plane[r * P + c];
       }
-      __syncthreads();   // releases this buffer for the copy two fields ahead
+      __syncthreads();   // releases this buffer for the copy two items ahead
     }
   }
   if constexpr (DOMEGA) {
@@ -486,19 +505,30 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
 
 template <typename T, int N>
 __global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
-pass_b(cplx_t<T>* __restrict__ S, PairParams p, int group) {
-  pass_b_body<T, N, false>(S, p, group, nullptr);
+pass_b(cplx_t<T>* __restrict__ S, PairParams p) {
+  pass_b_body<T, N, false>(S, p, nullptr);
 }
 
 template <typename T, int N>
 __global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
-pass_b_domega(cplx_t<T>* __restrict__ S, PairParams p, int group, double* dacc) {
-  pass_b_body<T, N, true>(S, p, group, dacc);
+pass_b_domega(cplx_t<T>* __restrict__ S, PairParams p, double* dacc) {
+  pass_b_body<T, N, true>(S, p, dacc);
+}
+
+// Resident CTA slots of a kernel on this device (SMs x CTAs per SM), at least 1.
+template <typename K>
+int resident_slots(K kernel, int threads, size_t smem) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+  return std::max(1, nsm * std::max(1, per));
 }
 
 // ------------------------------------------------------------------ pass C
-// plane n1 of a field: inverse along m3, then W = e^{iq.r} u written back over the
-// rows it was read from, S[f][n3][n1][n2].
+// plane n1 of a field: inverse along m3, written back over the rows it was read from,
+// S[f][n3][n1][n2]. This is the periodic part e^{-iq.r} W of the potential, which is
+// what the accumulation of periodic parts needs.
 template <typename T, int N>
 __global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
 pass_c(cplx_t<T>* __restrict__ S, PairParams p) {
@@ -506,26 +536,14 @@ pass_c(cplx_t<T>* __restrict__ S, PairParams p) {
   constexpr int P = pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* cur = reinterpret_cast<C2*>(smem_raw);  // [m3][n2], pitch P
-  C2* ph2 = cur + N * P;                       // e^{+2 pi i q2 n2 / N}
-  C2* ph3 = ph2 + N;
   const int n1 = blockIdx.x;
   const int f = blockIdx.y;
-  const FieldIdx fi = field_idx(f, p.nocc, p.diag);
-  const int kp = p.kp0 + fi.kpl;
-  C2* rows = S + (size_t)f * p.ng + (size_t)n1 * N;   // row m3 at rows + m3 N^2
+  C2* rows = S + (size_t)f * p.fs + (size_t)n1 * N;   // row m3 at rows + m3 N^2
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int m3 = e / N, n2 = e - (e / N) * N;
     cp_async<sizeof(C2)>(cur + m3 * P + n2, rows + (size_t)m3 * N * N + n2);
   }
   cp_async_commit();
-  int Q[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
-  for (int t = threadIdx.x; t < N; t += blockDim.x) {
-    ph2[t] = cis_frac_i<T>(Q[1] * t, p.D[1] * N, +1);
-    ph3[t] = cis_frac_i<T>(Q[2] * t, p.D[2] * N, +1);
-  }
-  const C2 ph1 = cis_frac_i<T>(Q[0] * n1, p.D[0] * N, +1);
   cp_async_wait<0>();
   __syncthreads();
   // columns (n2 = line): inverse along m3
@@ -534,7 +552,7 @@ pass_c(cplx_t<T>* __restrict__ S, PairParams p) {
 #pragma unroll 4
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int n3 = e / N, n2 = e - (e / N) * N;
-    rows[(size_t)n3 * N * N + n2] = cmul<T>(cur[n3 * P + n2], cmul<T>(ph1, cmul<T>(ph2[n2], ph3[n3])));
+    rows[(size_t)n3 * N * N + n2] = cur[n3 * P + n2];
   }
 }
 
@@ -543,10 +561,13 @@ pass_c(cplx_t<T>* __restrict__ S, PairParams p) {
 // [kp0, kp0 + nkp)) with potentials W_f(r) of the fields f = (k', i, j):
 //   Y_{ik}(r)  += sum_{k', j} W_{k'ij}(r) psi_{jk'}(r)       (Eq. occrikinterm)
 //   Y_{jk'}(r) += sum_i conj(W_{k'ij}(r)) psi_{ik}(r)        (the reversed pair)
-// and for a diagonal wave (k, k) with fields i <= j, W_ji = conj(W_ij). NOC >= nocc
-// is a compile-time bound so that the per-orbital accumulators stay in registers.
+// and for a diagonal wave (k, k) with fields i <= j, W_ji = conj(W_ij). All of it runs on
+// periodic parts (u = e^{-ik.r} psi, e^{-iq.r} W, e^{-ik.r} Y), for which the same
+// relations hold with every phase factor cancelled. NOC >= nocc
+// is a compile-time bound so that both sets of per-orbital sums stay in registers;
+// the loop body is loads and FMAs only, so the loads of many fields are in flight.
 template <typename T, int NOC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, NOC <= 8 ? 2 : 1)
 pass_d(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
        cplx_t<T>* __restrict__ Y, PairParams p) {
   using C2 = cplx_t<T>;
@@ -568,7 +589,7 @@ pass_d(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
         if (j >= nocc) break;
 #pragma unroll
         for (int i = 0; i <= j; ++i) {
-          const C2 w = __ldg(S + (size_t)diag_field(i, j, nocc) * ng + r);
+          const C2 w = __ldg(S + (size_t)diag_field(i, j, nocc) * p.fs + r);
           ar[i] += w.x * pr[j] - w.y * pim[j];     // W_ij psi_j
           ai[i] += w.x * pim[j] + w.y * pr[j];
           if (i < j) {                             // W_ji psi_i = conj(W_ij) psi_i
@@ -581,24 +602,35 @@ pass_d(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
 #pragma unroll 1
       for (int kpl = 0; kpl < p.nkp; ++kpl) {
         const int kp = p.kp0 + kpl;
+        const C2* wk = S + (size_t)kpl * nocc * nocc * p.fs + r;
+        T qr[NOC], qi[NOC], br[NOC], bi[NOC];
+#pragma unroll
+        for (int j = 0; j < NOC; ++j) {
+          C2 v = mk<T>(T(0), T(0));
+          if (j < nocc) v = __ldg(psi + (size_t)(kp * nocc + j) * ng + r);
+          qr[j] = v.x; qi[j] = v.y;
+          br[j] = T(0); bi[j] = T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < NOC; ++i) {
+          if (i >= nocc) break;
+#pragma unroll
+          for (int j = 0; j < NOC; ++j) {
+            if (j >= nocc) break;
+            const C2 w = __ldg(wk + (size_t)(i * nocc + j) * p.fs);
+            ar[i] += w.x * qr[j] - w.y * qi[j];     // W psi_{jk'}
+            ai[i] += w.x * qi[j] + w.y * qr[j];
+            br[j] += w.x * pr[i] + w.y * pim[i];    // conj(W) psi_{ik}
+            bi[j] += w.x * pim[i] - w.y * pr[i];
+          }
+        }
 #pragma unroll
         for (int j = 0; j < NOC; ++j) {
           if (j >= nocc) break;
-          const C2 pj = __ldg(psi + (size_t)(kp * nocc + j) * ng + r);
-          T br = T(0), bi = T(0);
-#pragma unroll
-          for (int i = 0; i < NOC; ++i) {
-            if (i >= nocc) break;
-            const C2 w = __ldg(S + (size_t)((kpl * nocc + i) * nocc + j) * ng + r);
-            ar[i] += w.x * pj.x - w.y * pj.y;       // W psi_{jk'}
-            ai[i] += w.x * pj.y + w.y * pj.x;
-            br += w.x * pr[i] + w.y * pim[i];       // conj(W) psi_{ik}
-            bi += w.x * pim[i] - w.y * pr[i];
-          }
           C2* y = Y + (size_t)(kp * nocc + j) * ng + r;
           C2 v = *y;
-          v.x += br;
-          v.y += bi;
+          v.x += br[j];
+          v.y += bi[j];
           *y = v;
         }
       }
@@ -615,25 +647,31 @@ pass_d(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
   }
 }
 
-template <typename T>
-cudaError_t launch_pass_d(const PairParams& p, const cplx_t<T>* S, const cplx_t<T>* psi,
-                          cplx_t<T>* Y, cudaStream_t st) {
-  const unsigned nb = (unsigned)std::min<long long>((p.ng + 255) / 256, 152LL * 32);
-  if (p.nocc <= 4) pass_d<T, 4><<<nb, 256, 0, st>>>(S, psi, Y, p);
-  else if (p.nocc <= 8) pass_d<T, 8><<<nb, 256, 0, st>>>(S, psi, Y, p);
-  else if (p.nocc <= 16) pass_d<T, 16><<<nb, 256, 0, st>>>(S, psi, Y, p);
-  else pass_d<T, 32><<<nb, 256, 0, st>>>(S, psi, Y, p);
+template <typename T, int NOC>
+cudaError_t launch_pass_d_noc(const PairParams& p, const cplx_t<T>* S, const cplx_t<T>* psi,
+                              cplx_t<T>* Y, cudaStream_t st) {
+  static int slots = 0;
+  if (!slots) slots = resident_slots(pass_d<T, NOC>, 256, 0);
+  const unsigned nb = (unsigned)std::min<long long>((p.ng + 255) / 256, slots);
+  pass_d<T, NOC><<<nb, 256, 0, st>>>(S, psi, Y, p);
   return cudaGetLastError();
 }
 
-template <int N> constexpr size_t smem_a(size_t csz) { return csz * (N * pitch(N) + 2 * N); }
+template <typename T>
+cudaError_t launch_pass_d(const PairParams& p, const cplx_t<T>* S, const cplx_t<T>* psi,
+                          cplx_t<T>* Y, cudaStream_t st) {
+  if (p.nocc <= 4) return launch_pass_d_noc<T, 4>(p, S, psi, Y, st);
+  if (p.nocc <= 8) return launch_pass_d_noc<T, 8>(p, S, psi, Y, st);
+  if (p.nocc <= 16) return launch_pass_d_noc<T, 16>(p, S, psi, Y, st);
+  return launch_pass_d_noc<T, 32>(p, S, psi, Y, st);
+}
+
+template <int N> constexpr size_t smem_a(size_t csz) { return csz * N * pitch(N); }
 template <int N> constexpr size_t smem_b(size_t csz, size_t tab) {
   return 2 * csz * N * pitch(N) + N * tab + csz / 2 * N * N;
 }
-// fields per pass-B CTA: enough to amortise the kernel table, few enough to keep
-// several CTAs per SM busy on one wave
-constexpr int kGroupB = 4;
-template <int N> constexpr size_t smem_c(size_t csz) { return csz * (N * pitch(N) + 2 * N); }
+
+template <int N> constexpr size_t smem_c(size_t csz) { return csz * N * pitch(N); }
 
 template <typename T, int N>
 cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cplx_t<T>* Y,
@@ -645,16 +683,18 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   const size_t sb = smem_b<N>(sizeof(C2), sizeof(Axis1<T>));
   const size_t sc = smem_c<N>(sizeof(C2));
   static bool configured = false;
+  static int slots_b = 1;
   if (!configured) {
     cudaFuncSetAttribute(pass_a<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
     cudaFuncSetAttribute(pass_b<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
     cudaFuncSetAttribute(pass_c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+    slots_b = resident_slots(pass_b<T, N>, nt, sb);
     configured = true;
   }
   if (ev) cudaEventRecord(ev[0], st);
   pass_a<T, N><<<dim3(N, nf), nt, sa, st>>>(psi, S, p);
   if (ev) cudaEventRecord(ev[1], st);
-  pass_b<T, N><<<dim3(N, (nf + kGroupB - 1) / kGroupB), nt, sb, st>>>(S, p, kGroupB);
+  pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S, p);
   if (ev) cudaEventRecord(ev[2], st);
   pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S, p);
   const cudaError_t e = launch_pass_d<T>(p, S, psi, Y, st);
@@ -671,15 +711,16 @@ cudaError_t run_domega_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>
   const size_t sa = smem_a<N>(sizeof(C2));
   const size_t sb = smem_b<N>(sizeof(C2), sizeof(Axis1<T>));
   static bool configured = false;
+  static int slots_b = 1;
   if (!configured) {
     cudaFuncSetAttribute(pass_a<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
     cudaFuncSetAttribute(pass_b_domega<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sb);
+    slots_b = resident_slots(pass_b_domega<T, N>, nt, sb);
     configured = true;
   }
   pass_a<T, N><<<dim3(N, nf), nt, sa, st>>>(psi, S, p);
-  pass_b_domega<T, N><<<dim3(N, (nf + kGroupB - 1) / kGroupB), nt, sb, st>>>(S, p, kGroupB,
-                                                                             dacc);
+  pass_b_domega<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S, p, dacc);
   return cudaGetLastError();
 }
 
