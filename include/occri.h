@@ -192,9 +192,9 @@ int occri_plan_stage_times(occri_plan *plan, double *ms, long long *launches, do
  * normalised coefficients and the orbitals before widening) lives in one static
  * device array of OCCRI_STATIC_SCRATCH_BYTES instead of the plan's workspaces; the
  * call makes no cudaMalloc, cudaFree or other allocating call.
- * A call needs 16*nk*nao*nocc bytes (rounded up to 256) plus 16*nk*nocc*N_g (FP64)
- * or 8*nk*nocc*N_g (mixed) bytes of it; larger problems return OCCRI_EINVAL before
- * anything is launched.
+ * A call needs 16*nk*nao*nocc bytes (rounded up to 256) plus 16*nk*nocc*F (FP64)
+ * or 8*nk*nocc*F (mixed) bytes of it, F being N_g rounded up to a multiple of 64;
+ * larger problems return OCCRI_EINVAL before anything is launched.
  * The first call on each device looks up the array's device address (with that device
  * current); make that first call before any stream capture. All calls share the one
  * array and it keeps the previous call's contents (every byte a call reads it has

@@ -243,5 +243,171 @@ OCCRI_HDI void dif_to_natural(T (&re)[N], T (&im)[N]) {
   });
 }
 
+// ---------------------------------------------------------------- packed FP32 form
+// The same decimation-in-frequency recursion for FP32 with each complex value held as
+// one 64-bit register pair {re, im}. Operations that act alike on both halves (sums,
+// differences, scaling by a real constant) are single packed f32x2 instructions
+// (add/sub/mul/fma.rn.f32x2, sm_100 and later); products with +-i and the twiddles,
+// which mix the halves, are scalar operations on the pair's halves. Every packed
+// instruction rounds each half exactly as the scalar instruction would.
+#if defined(__CUDACC__)
+namespace pk {
+using u64 = unsigned long long;
+__device__ __forceinline__ u64 pack(float re, float im) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(re), "f"(im));
+  return r;
+}
+__device__ __forceinline__ void unpack(u64 v, float& re, float& im) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(re), "=f"(im) : "l"(v));
+}
+__device__ __forceinline__ u64 add(u64 a, u64 b) {
+  u64 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 sub(u64 a, u64 b) {
+  u64 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 mul(u64 a, u64 b) {
+  u64 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 fma(u64 a, u64 b, u64 c) {   // a * b + c
+  u64 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ u64 splat(float c) { return pack(c, c); }
+// SGN * i * x = (-SGN x.im, SGN x.re)
+template <int SGN>
+__device__ __forceinline__ u64 mul_i(u64 x) {
+  float r, i;
+  unpack(x, r, i);
+  return SGN > 0 ? pack(-i, r) : pack(i, -r);
+}
+// x * (c + i s), scalar on the halves so that c and s stay instruction immediates
+__device__ __forceinline__ u64 cmul_const(u64 x, float c, float s) {
+  float r, i;
+  unpack(x, r, i);
+  return pack(r * c - i * s, r * s + i * c);
+}
+}  // namespace pk
+
+template <int SIGN, int A, int S, int TOT>
+__device__ __forceinline__ void pdft2(pk::u64 (&x)[TOT]) {
+  const pk::u64 a = x[A], b = x[A + S];
+  x[A] = pk::add(a, b);
+  x[A + S] = pk::sub(a, b);
+}
+
+template <int SIGN, int A, int S, int TOT>
+__device__ __forceinline__ void pdft3(pk::u64 (&x)[TOT]) {
+  constexpr double h = 0.86602540378443864676372317075293618;  // sqrt(3)/2
+  const pk::u64 a = x[A];
+  const pk::u64 t1 = pk::add(x[A + S], x[A + 2 * S]);
+  const pk::u64 d = pk::sub(x[A + S], x[A + 2 * S]);
+  const pk::u64 t2 = pk::fma(t1, pk::splat(-0.5f), a);
+  float dr, di;
+  pk::unpack(d, dr, di);
+  // i * SIGN * h * d = (-SIGN h di, SIGN h dr)
+  const pk::u64 u = pk::pack(float(-SIGN * h) * di, float(SIGN * h) * dr);
+  x[A] = pk::add(a, t1);
+  x[A + S] = pk::add(t2, u);
+  x[A + 2 * S] = pk::sub(t2, u);
+}
+
+template <int SIGN, int A, int S, int TOT>
+__device__ __forceinline__ void pdft4(pk::u64 (&x)[TOT]) {
+  const pk::u64 s0 = pk::add(x[A], x[A + 2 * S]);
+  const pk::u64 d0 = pk::sub(x[A], x[A + 2 * S]);
+  const pk::u64 s1 = pk::add(x[A + S], x[A + 3 * S]);
+  const pk::u64 d1 = pk::sub(x[A + S], x[A + 3 * S]);
+  const pk::u64 j = pk::mul_i<SIGN>(d1);   // SIGN * i * d1
+  x[A] = pk::add(s0, s1);
+  x[A + 2 * S] = pk::sub(s0, s1);
+  x[A + S] = pk::add(d0, j);
+  x[A + 3 * S] = pk::sub(d0, j);
+}
+
+template <int SIGN, int A, int S, int TOT>
+__device__ __forceinline__ void pdft5(pk::u64 (&x)[TOT]) {
+  constexpr CS w1 = cs2pi(1, 5), w2 = cs2pi(2, 5);
+  const pk::u64 a = x[A];
+  const pk::u64 t1 = pk::add(x[A + S], x[A + 4 * S]);
+  const pk::u64 t2 = pk::add(x[A + 2 * S], x[A + 3 * S]);
+  const pk::u64 t3 = pk::sub(x[A + S], x[A + 4 * S]);
+  const pk::u64 t4 = pk::sub(x[A + 2 * S], x[A + 3 * S]);
+  const pk::u64 c1 = pk::splat(float(w1.c)), c2 = pk::splat(float(w2.c));
+  const pk::u64 s1 = pk::splat(float(SIGN * w1.s)), s2 = pk::splat(float(SIGN * w2.s));
+  const pk::u64 p1 = pk::fma(t2, c2, pk::fma(t1, c1, a));
+  const pk::u64 p2 = pk::fma(t2, c1, pk::fma(t1, c2, a));
+  const pk::u64 q1 = pk::fma(t4, s2, pk::mul(t3, s1));                       // times i below
+  const pk::u64 q2 = pk::fma(t4, pk::splat(float(-SIGN * w1.s)), pk::mul(t3, s2));
+  const pk::u64 iq1 = pk::mul_i<1>(q1), iq2 = pk::mul_i<1>(q2);
+  x[A] = pk::add(pk::add(a, t1), t2);
+  x[A + S] = pk::add(p1, iq1);
+  x[A + 4 * S] = pk::sub(p1, iq1);
+  x[A + 2 * S] = pk::add(p2, iq2);
+  x[A + 3 * S] = pk::sub(p2, iq2);
+}
+
+template <int R, int SIGN, int A, int S, int TOT>
+__device__ __forceinline__ void psmall_dft(pk::u64 (&x)[TOT]) {
+  if constexpr (R == 2) pdft2<SIGN, A, S>(x);
+  else if constexpr (R == 3) pdft3<SIGN, A, S>(x);
+  else if constexpr (R == 4) pdft4<SIGN, A, S>(x);
+  else if constexpr (R == 5) pdft5<SIGN, A, S>(x);
+}
+
+// x[P] *= e^{SIGN 2 pi i E / N}
+template <int N, int SIGN, int E, int P, int TOT>
+__device__ __forceinline__ void ptwiddle(pk::u64 (&x)[TOT]) {
+  constexpr int e = E % N;
+  if constexpr (e == 0) {
+  } else if constexpr (2 * e == N) {
+    x[P] = pk::sub(pk::splat(0.0f), x[P]);
+  } else if constexpr (4 * e == N || 4 * e == 3 * N) {
+    constexpr int sgn = (4 * e == N) ? SIGN : -SIGN;
+    x[P] = pk::mul_i<sgn>(x[P]);
+  } else {
+    constexpr CS w = cs2pi(e, N);
+    x[P] = pk::cmul_const(x[P], float(w.c), float(SIGN * w.s));
+  }
+}
+
+template <int N, int SIGN, int A, int S, int TOT>
+__device__ __forceinline__ void pdif(pk::u64 (&x)[TOT]) {
+  if constexpr (N == 1) {
+  } else if constexpr (is_base(N)) {
+    psmall_dft<N, SIGN, A, S>(x);
+  } else {
+    constexpr int R = pick_radix(N), M = N / R;
+    static_for<M>([&](auto I1) {
+      constexpr int n1 = decltype(I1)::value;
+      psmall_dft<R, SIGN, A + S * n1, S * M>(x);
+      static_for<R>([&](auto K1) {
+        constexpr int k1 = decltype(K1)::value;
+        ptwiddle<N, SIGN, n1 * k1, A + S * (n1 + M * k1)>(x);
+      });
+    });
+    static_for<R>([&](auto K1) {
+      constexpr int k1 = decltype(K1)::value;
+      pdif<M, SIGN, A + S * M * k1, S>(x);
+    });
+  }
+}
+
+// Packed FP32 transform: after the call, x[p] holds X[dif_rev(N, p)].
+template <int N, int SIGN>
+__device__ __forceinline__ void pfft_dif(pk::u64 (&x)[N]) {
+  static_assert(smooth235(N), "FFT length must be {2,3,5}-smooth");
+  pdif<N, SIGN, 0, 1>(x);
+}
+#endif
+
 }  // namespace fft
 }  // namespace occri

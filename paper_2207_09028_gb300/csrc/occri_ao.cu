@@ -365,7 +365,7 @@ orbitals_kernel(AOParams p, cplx_t<T>* __restrict__ psi, int i0) {
 #pragma unroll
     for (int i = 0; i < NI; ++i)
       if (i0 + i < p.nocc)
-        psi[((size_t)(k0 + b) * p.nocc + i0 + i) * p.ng + q] = cplx_t<T>{ar[b][i], ai[b][i]};
+        psi[((size_t)(k0 + b) * p.nocc + i0 + i) * p.fs + q] = cplx_t<T>{ar[b][i], ai[b][i]};
   }
 }
 
@@ -402,7 +402,7 @@ contract_kernel(AOParams p, const cplx_t<T>* __restrict__ Y, double2* __restrict
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
       if (valid && i0 + i < p.nocc) {
-        const cplx_t<T> y = Y[((size_t)k * p.nocc + i0 + i) * p.ng + q];
+        const cplx_t<T> y = Y[((size_t)k * p.nocc + i0 + i) * p.fs + q];
         yr[i] = y.x; yi[i] = y.y;
       } else {
         yr[i] = T(0); yi[i] = T(0);
@@ -447,16 +447,17 @@ contract_kernel(AOParams p, const cplx_t<T>* __restrict__ Y, double2* __restrict
 }
 
 // Widen the fields to c128 and put them back in natural point order:
-// out[f][(n1 N + n2) N + n3] = in[f][(n3 N + n1) N + n2] (cubic grid of edge N).
+// out[f][(n1 N + n2) N + n3] = in[f][(n3 N + n1) N + n2] (cubic grid of edge N; input
+// fields fs points apart, output fields N^3 apart).
 template <typename T>
 __global__ void widen_kernel(const cplx_t<T>* __restrict__ in, double2* __restrict__ out,
-                             long long n, int N) {
+                             long long n, int N, long long fs) {
   const long long ng = (long long)N * N * N;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const long long f = e / ng, r = e - f * ng;
     const int n3 = (int)(r % N), n2 = (int)((r / N) % N), n1 = (int)(r / ((long long)N * N));
-    const cplx_t<T> v = in[f * ng + ((long long)n3 * N + n1) * N + n2];
+    const cplx_t<T> v = in[f * fs + ((long long)n3 * N + n1) * N + n2];
     out[e] = make_double2(double(v.x), double(v.y));
   }
 }
@@ -469,7 +470,8 @@ __global__ void widen_kernel(const cplx_t<T>* __restrict__ in, double2* __restri
 // 2 pi sum_d kint_d n_d / (D_d N), reduced exactly in integers.
 template <typename T>
 __global__ void phase_fields_kernel(cplx_t<T>* __restrict__ F, const int* __restrict__ kint,
-                                    int nk, int nocc, int N, int D0, int D1, int D2, int sign) {
+                                    int nk, int nocc, int N, long long fs, int D0, int D1, int D2,
+                                    int sign) {
   const long long ng = (long long)N * N * N;
   const long long Dc = (long long)D0 * D1 * D2;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nk * ng;
@@ -483,10 +485,10 @@ __global__ void phase_fields_kernel(cplx_t<T>* __restrict__ F, const int* __rest
                           (long long)kint[3 * k + 1] * n2 * (Dc / D1) +
                           (long long)kint[3 * k + 2] * n3 * (Dc / D2);
     const cplx_t<T> ph = dev::cis_frac<T>(num, Dc * N, sign);
-    cplx_t<T>* f = F + (size_t)k * nocc * ng + q;
+    cplx_t<T>* f = F + (size_t)k * nocc * fs + q;
     for (int i = 0; i < nocc; ++i) {
-      const cplx_t<T> v = f[(size_t)i * ng];
-      f[(size_t)i * ng] = cplx_t<T>{v.x * ph.x - v.y * ph.y, v.x * ph.y + v.y * ph.x};
+      const cplx_t<T> v = f[(size_t)i * fs];
+      f[(size_t)i * fs] = cplx_t<T>{v.x * ph.x - v.y * ph.y, v.x * ph.y + v.y * ph.x};
     }
   }
 }
@@ -509,7 +511,7 @@ cudaError_t launch_scale_c<float>(const Plan& p, const double2* C, cudaStream_t 
 template <typename T>
 cudaError_t launch_phase_fields(const Plan& p, void* F, int sign, cudaStream_t s) {
   ao::phase_fields_kernel<T><<<8 * 152, 256, 0, s>>>((cplx_t<T>*)F, p.kint, p.nk, p.nocc, p.N[0],
-                                                      p.D[0], p.D[1], p.D[2], sign);
+                                                      p.fs, p.D[0], p.D[1], p.D[2], sign);
   return cudaGetLastError();
 }
 template cudaError_t launch_phase_fields<float>(const Plan&, void*, int, cudaStream_t);
@@ -557,7 +559,8 @@ cudaError_t launch_contract(const Plan& p, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s) {
   const long long n = (long long)p.nk * p.nocc * p.ng;
-  ao::widen_kernel<T><<<4 * 152, 256, 0, s>>>((const cplx_t<T>*)p.psi, (double2*)out, n, p.N[0]);
+  ao::widen_kernel<T><<<4 * 152, 256, 0, s>>>((const cplx_t<T>*)p.psi, (double2*)out, n, p.N[0],
+                                               p.fs);
   return cudaGetLastError();
 }
 
@@ -613,7 +616,7 @@ int orbitals_noalloc_impl(const occri::Plan& p, const double2* C, void* psi_out,
   using namespace occri;
   using CS = typename ao::CsType<T>::type;
   const long long ncs = (long long)p.nk * p.nao * p.nocc;
-  const long long npsi = (long long)p.nk * p.nocc * p.ng;
+  const long long npsi = (long long)p.nk * p.nocc * p.ng;   // outputs (natural order)
   CS* cs = reinterpret_cast<CS*>(base);
   cplx_t<T>* psi = reinterpret_cast<cplx_t<T>*>(static_cast<unsigned char*>(base) +
                                                 round_up_256(sizeof(CS) * ncs));
@@ -628,7 +631,7 @@ int orbitals_noalloc_impl(const occri::Plan& p, const double2* C, void* psi_out,
   const dim3 grid((unsigned)((p.nblk + 3) / 4), (p.nk + KB - 1) / KB);
   for (int i0 = 0; i0 < p.nocc; i0 += kOrbChunk)
     ao::orbitals_kernel<T, kOrbChunk, KB><<<grid, 128, 0, s>>>(ap, psi, i0);
-  ao::widen_kernel<T><<<4 * 152, 256, 0, s>>>(psi, (double2*)psi_out, npsi, p.N[0]);
+  ao::widen_kernel<T><<<4 * 152, 256, 0, s>>>(psi, (double2*)psi_out, npsi, p.N[0], p.fs);
   return cudaGetLastError() == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
 }
 
@@ -639,7 +642,7 @@ extern "C" int occri_orbitals_noalloc(const occri_plan* plan, const void* C_dev,
   const occri::Plan& p = *plan->p;
   const bool fp64 = p.precision == OCCRI_FP64;
   const size_t ncs = (size_t)p.nk * p.nao * p.nocc;
-  const size_t npsi = (size_t)p.nk * p.nocc * p.ng;
+  const size_t npsi = (size_t)p.nk * p.nocc * p.fs;   // internal fields, fs points apart
   const size_t need = round_up_256((fp64 ? sizeof(double2) : sizeof(float4)) * ncs) +
                       (fp64 ? sizeof(double2) : sizeof(float2)) * npsi;
   if (need > (size_t)OCCRI_STATIC_SCRATCH_BYTES) return OCCRI_EINVAL;

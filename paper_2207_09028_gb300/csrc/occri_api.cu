@@ -32,6 +32,7 @@ AOParams Plan::ao_params() const {
   AOParams a;
   a.nk = nk; a.nao = nao; a.nocc = nocc; a.natm = natm; a.nshell = nshell;
   a.ng = ng;
+  a.fs = fs;
   for (int d = 0; d < 3; ++d) { a.N[d] = N[d]; a.D[d] = D[d]; }
   a.Dc = D[0] * D[1] * D[2];
   a.shells = shells;
@@ -48,6 +49,7 @@ AOParams Plan::ao_params() const {
 PairParams Plan::pair_params() const {
   PairParams q;
   q.nk = nk; q.nocc = nocc; q.ng = ng; q.fs = fs; q.N1 = N[0];
+  q.status = status;
   q.k = 0; q.kp0 = 0; q.nkp = 1; q.diag = 0;
   for (int d = 0; d < 3; ++d) q.D[d] = D[d];
   q.kint = kint;
@@ -390,7 +392,7 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
   cudaStream_t s = p->stream;
   const bool timed = p->timing_every > 0;
   long long launches = 0;
-  const size_t orb = (size_t)p->nk * p->nocc * p->ng;
+  const size_t orb = (size_t)p->nk * p->nocc * p->fs;
   if (cudaMemsetAsync(p->Y, 0, orb * sizeof(cplx_t<T>), s) != cudaSuccess) return OCCRI_ECUDA;
   if (cudaMemsetAsync(p->kc, 0, sizeof(double2) * (size_t)p->nk * p->nao * p->nocc, s) != cudaSuccess)
     return OCCRI_ECUDA;
@@ -822,7 +824,7 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
   nkp = std::max(1, std::min(nkp, 65535 / (nocc * nocc)));   // grid.y limit of the passes
   p->nkp_wave = nkp;
   p->fields_cap = nkp * nocc * nocc;
-  const size_t orb = (size_t)p->nk * nocc * ng;
+  const size_t orb = (size_t)p->nk * nocc * p->fs;
   {
     unsigned char* b = nullptr;
     chk(dalloc(&b, orb * csz, &tot)); p->psi = b; b = nullptr;

@@ -38,6 +38,7 @@ struct ShellDev {
 struct AOParams {
   int nk, nao, nocc, natm, nshell;
   long long ng;
+  long long fs;      // stride of the orbital-shaped fields: ng rounded up to 64
   int N[3];
   int D[3];          // per-axis k denominators: kappa_{k,d} = kint[k][d] / D[d]
   int Dc;            // D[0]*D[1]*D[2]
@@ -66,10 +67,11 @@ struct AOParams {
 struct PairParams {
   int nk, nocc, N1;          // N1: cubic grid edge
   long long ng;
-  long long fs;              // scratch field stride in points: ng rounded up to 64, so that
-                             // every field starts 512-byte aligned
+  long long fs;              // field stride in points (orbital, accumulator and scratch
+                             // fields): ng rounded up to 64, every field 512-byte aligned
   int k, kp0, nkp;
   int diag;                  // 1: the wave is (k, k) and holds the fields i <= j only
+  int* status;               // plan status word (first device error, k), for bounded waits
   int D[3];
   const int* kint;           // [nk][3]
   double g[6];               // reciprocal metric b_i.b_j: 11, 22, 33, 12, 13, 23
@@ -125,8 +127,10 @@ struct Plan {
   // transform passes then read a plane n1 as N rows of N contiguous points, and the
   // inverse pass along the third axis leaves the potentials of a wave in this same
   // order, so the accumulation streams every array coalesced.
-  void* psi = nullptr;       // [nk][nocc][ng] cplx_t<T>
-  void* Y = nullptr;         // [nk][nocc][ng] cplx_t<T>
+  // Every field (orbital, accumulator or scratch) is fs = ng rounded up to 64 points
+  // long, so each starts 512-byte aligned (whole-tile bulk copies).
+  void* psi = nullptr;       // [nk][nocc][fs] cplx_t<T>
+  void* Y = nullptr;         // [nk][nocc][fs] cplx_t<T>
   void* scratch = nullptr;   // [fields_cap][fs] cplx_t<T>
   double2* kc = nullptr;     // [nk][nao][nocc]
   double2* xi = nullptr;     // [nk][nao][nocc]

@@ -28,6 +28,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "fft_reg.cuh"
 #include "occri_device.cuh"
@@ -92,6 +93,11 @@ __device__ __forceinline__ int diag_field(int i, int j, int nocc) {  // i <= j
   return i * nocc - i * (i - 1) / 2 + (j - i);
 }
 
+// First device error wins: record a bounded wait that gave up.
+__device__ __forceinline__ void record_timeout(int* status) {
+  if (status && atomicCAS(status, 0, (int)OCCRI_ETIMEOUT) == 0) status[1] = -1;
+}
+
 // ------------------------------------------------------------------ async plane staging
 // cp.async copies global -> shared without staging through registers, so a whole
 // plane is in flight per CTA. Element size 8 B (FP32 complex) or 16 B (FP64 complex).
@@ -128,22 +134,42 @@ __device__ __forceinline__ void stage_plane(cplx_t<T>* dst, const cplx_t<T>* src
 template <typename T, int N, typename Post>
 __device__ __forceinline__ void line_fft(cplx_t<T>* base, int stride, bool inverse, bool store,
                                          Post&& post) {
-  T re[N], im[N];
-  fft::static_for<N>([&](auto I) {
-    constexpr int m = decltype(I)::value;
-    const cplx_t<T> v = base[m * stride];
-    re[m] = v.x;
-    im[m] = v.y;
-  });
-  fft::fft_dif<N, -1>(re, im);
-  fft::static_for<N>([&](auto I) {
-    constexpr int q = decltype(I)::value;
-    constexpr int k = fft::dif_rev(N, q);
-    constexpr int kr = (N - k) % N;
-    const int ks = inverse ? kr : k;
-    post(ks, re[q], im[q]);
-    if (store) base[ks * stride] = mk<T>(re[q], im[q]);
-  });
+  if constexpr (std::is_same<T, float>::value) {   // packed FP32 core
+    fft::pk::u64 x[N];
+    fft::static_for<N>([&](auto I) {
+      constexpr int m = decltype(I)::value;
+      const float2 v = base[m * stride];
+      x[m] = fft::pk::pack(v.x, v.y);
+    });
+    fft::pfft_dif<N, -1>(x);
+    fft::static_for<N>([&](auto I) {
+      constexpr int q = decltype(I)::value;
+      constexpr int k = fft::dif_rev(N, q);
+      constexpr int kr = (N - k) % N;
+      const int ks = inverse ? kr : k;
+      float re, im;
+      fft::pk::unpack(x[q], re, im);
+      post(ks, re, im);
+      if (store) base[ks * stride] = mk<T>(re, im);
+    });
+  } else {
+    T re[N], im[N];
+    fft::static_for<N>([&](auto I) {
+      constexpr int m = decltype(I)::value;
+      const cplx_t<T> v = base[m * stride];
+      re[m] = v.x;
+      im[m] = v.y;
+    });
+    fft::fft_dif<N, -1>(re, im);
+    fft::static_for<N>([&](auto I) {
+      constexpr int q = decltype(I)::value;
+      constexpr int k = fft::dif_rev(N, q);
+      constexpr int kr = (N - k) % N;
+      const int ks = inverse ? kr : k;
+      post(ks, re[q], im[q]);
+      if (store) base[ks * stride] = mk<T>(re[q], im[q]);
+    });
+  }
 }
 
 // Two threads per line (even N), in two different warps. Half h forms
@@ -158,43 +184,82 @@ template <typename T, int N, typename Post>
 __device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool inverse, bool store,
                                           int h, bool valid, int bar, Post&& post) {
   constexpr int M = N / 2;
-  T re[M], im[M];
-  if (h == 0) {
+  auto pair_barrier = [&]() {
+    if (bar == 1)   // warp-uniform; immediate barrier ids
+      asm volatile("bar.sync 1, 64;\n" ::: "memory");
+    else
+      asm volatile("bar.sync 2, 64;\n" ::: "memory");
+  };
+  if constexpr (std::is_same<T, float>::value) {   // packed FP32 core
+    using fft::pk::u64;
+    u64 x[M];
+    if (h == 0) {
+      fft::static_for<M>([&](auto I) {
+        constexpr int n = decltype(I)::value;
+        const float2 a = base[n * stride], b = base[(n + M) * stride];
+        x[n] = fft::pk::add(fft::pk::pack(a.x, a.y), fft::pk::pack(b.x, b.y));
+      });
+    } else {
+      fft::static_for<M>([&](auto I) {
+        constexpr int n = decltype(I)::value;
+        constexpr fft::CS w = fft::cs2pi(n, N);     // e^{-2 pi i n / N} = c - i s
+        const float2 a = base[n * stride], b = base[(n + M) * stride];
+        const u64 d = fft::pk::sub(fft::pk::pack(a.x, a.y), fft::pk::pack(b.x, b.y));
+        if constexpr (n == 0)
+          x[n] = d;
+        else
+          x[n] = fft::pk::cmul_const(d, float(w.c), float(-w.s));
+      });
+    }
+    pair_barrier();
+    fft::pfft_dif<M, -1>(x);
     fft::static_for<M>([&](auto I) {
-      constexpr int n = decltype(I)::value;
-      const cplx_t<T> a = base[n * stride], b = base[(n + M) * stride];
-      re[n] = a.x + b.x;
-      im[n] = a.y + b.y;
+      constexpr int q = decltype(I)::value;
+      const int k = 2 * fft::dif_rev(M, q) + h;
+      const int ks = inverse ? (k == 0 ? 0 : N - k) : k;
+      if (valid) {
+        float re, im;
+        fft::pk::unpack(x[q], re, im);
+        post(ks, re, im);
+        if (store) base[ks * stride] = mk<T>(re, im);
+      }
     });
   } else {
+    T re[M], im[M];
+    if (h == 0) {
+      fft::static_for<M>([&](auto I) {
+        constexpr int n = decltype(I)::value;
+        const cplx_t<T> a = base[n * stride], b = base[(n + M) * stride];
+        re[n] = a.x + b.x;
+        im[n] = a.y + b.y;
+      });
+    } else {
+      fft::static_for<M>([&](auto I) {
+        constexpr int n = decltype(I)::value;
+        constexpr fft::CS w = fft::cs2pi(n, N);     // e^{-2 pi i n / N} = c - i s
+        const cplx_t<T> a = base[n * stride], b = base[(n + M) * stride];
+        const T yr = a.x - b.x, yi = a.y - b.y;
+        if constexpr (n == 0) {
+          re[n] = yr;
+          im[n] = yi;
+        } else {
+          re[n] = yr * T(w.c) + yi * T(w.s);
+          im[n] = yi * T(w.c) - yr * T(w.s);
+        }
+      });
+    }
+    pair_barrier();
+    fft::fft_dif<M, -1>(re, im);
     fft::static_for<M>([&](auto I) {
-      constexpr int n = decltype(I)::value;
-      constexpr fft::CS w = fft::cs2pi(n, N);     // e^{-2 pi i n / N} = c - i s
-      const cplx_t<T> a = base[n * stride], b = base[(n + M) * stride];
-      const T yr = a.x - b.x, yi = a.y - b.y;
-      if constexpr (n == 0) {
-        re[n] = yr;
-        im[n] = yi;
-      } else {
-        re[n] = yr * T(w.c) + yi * T(w.s);
-        im[n] = yi * T(w.c) - yr * T(w.s);
+      constexpr int q = decltype(I)::value;
+      const int k = 2 * fft::dif_rev(M, q) + h;
+      const int ks = inverse ? (k == 0 ? 0 : N - k) : k;
+      if (valid) {
+        post(ks, re[q], im[q]);
+        if (store) base[ks * stride] = mk<T>(re[q], im[q]);
       }
     });
   }
-  if (bar == 1)   // warp-uniform; immediate barrier ids
-    asm volatile("bar.sync 1, 64;\n" ::: "memory");
-  else
-    asm volatile("bar.sync 2, 64;\n" ::: "memory");
-  fft::fft_dif<M, -1>(re, im);
-  fft::static_for<M>([&](auto I) {
-    constexpr int q = decltype(I)::value;
-    const int k = 2 * fft::dif_rev(M, q) + h;
-    const int ks = inverse ? (k == 0 ? 0 : N - k) : k;
-    if (valid) {
-      post(ks, re[q], im[q]);
-      if (store) base[ks * stride] = mk<T>(re[q], im[q]);
-    }
-  });
 }
 
 // One transform job over the N lines of a plane (rows: along the contiguous index;
@@ -375,8 +440,8 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
   const FieldIdx fi = field_idx(f, p.nocc, p.diag);
   const int kp = p.kp0 + fi.kpl;
   // plane n1 of the periodic parts: N rows (n3) of N contiguous points (n2)
-  const C2* pi = psi + (size_t)(p.k * p.nocc + fi.i) * p.ng + (size_t)n1 * N;
-  const C2* pj = psi + (size_t)(kp * p.nocc + fi.j) * p.ng + (size_t)n1 * N;
+  const C2* pi = psi + (size_t)(p.k * p.nocc + fi.i) * p.fs + (size_t)n1 * N;
+  const C2* pj = psi + (size_t)(kp * p.nocc + fi.j) * p.fs + (size_t)n1 * N;
 #pragma unroll 4
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int n3 = e / N, n2 = e - (e / N) * N;
@@ -579,7 +644,7 @@ pass_d(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
 #pragma unroll
     for (int i = 0; i < NOC; ++i) {
       C2 v = mk<T>(T(0), T(0));
-      if (i < nocc) v = __ldg(psi + (size_t)(p.k * nocc + i) * ng + r);
+      if (i < nocc) v = __ldg(psi + (size_t)(p.k * nocc + i) * p.fs + r);
       pr[i] = v.x; pim[i] = v.y;
       ar[i] = T(0); ai[i] = T(0);
     }
@@ -607,7 +672,7 @@ pass_d(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
 #pragma unroll
         for (int j = 0; j < NOC; ++j) {
           C2 v = mk<T>(T(0), T(0));
-          if (j < nocc) v = __ldg(psi + (size_t)(kp * nocc + j) * ng + r);
+          if (j < nocc) v = __ldg(psi + (size_t)(kp * nocc + j) * p.fs + r);
           qr[j] = v.x; qi[j] = v.y;
           br[j] = T(0); bi[j] = T(0);
         }
@@ -627,7 +692,7 @@ pass_d(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
 #pragma unroll
         for (int j = 0; j < NOC; ++j) {
           if (j >= nocc) break;
-          C2* y = Y + (size_t)(kp * nocc + j) * ng + r;
+          C2* y = Y + (size_t)(kp * nocc + j) * p.fs + r;
           C2 v = *y;
           v.x += br[j];
           v.y += bi[j];
@@ -638,7 +703,7 @@ pass_d(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
 #pragma unroll
     for (int i = 0; i < NOC; ++i) {
       if (i >= nocc) break;
-      C2* y = Y + (size_t)(p.k * nocc + i) * ng + r;
+      C2* y = Y + (size_t)(p.k * nocc + i) * p.fs + r;
       C2 v = *y;
       v.x += ar[i];
       v.y += ai[i];
@@ -647,9 +712,240 @@ pass_d(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
   }
 }
 
+// ------------------------------------------------------------------ pass D, bulk-copy form
+// The same accumulation with every operand moved by the bulk-copy (TMA) engine. Tiles of
+// kBulkTile consecutive points; for a tile, one producer thread (the last warp) copies, per field and
+// per orbital plane, the tile's contiguous tp points into shared memory:
+//   W: nf fields, u_k: nocc planes, u_k': nkp nocc planes, Y_k and Y_k': as many,
+// counting the bytes on the buffer's `full` mbarrier. The consumer warps (one point per
+// thread) wait for it, compute, store Y with plain coalesced stores and arrive on the
+// buffer's `free` mbarrier, after which the producer refills it with the tile kBulkStages
+// ahead.
+// The bytes in flight therefore sit in shared memory, not in registers. Every wait is
+// bounded: on timeout the kernel records OCCRI_ETIMEOUT in the plan status and leaves.
+namespace tma {
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes,
+                                         unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+}  // namespace tma
+
+constexpr int kBulkTile = 128;   // points per tile = consumer threads (four warps)
+constexpr int kBulkStages = 2;   // tile buffers per CTA (one in use, one filling)
+
+template <typename T, int NOC>
+__global__ void __launch_bounds__(kBulkTile + 32, 1)
+pass_d_bulk(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
+            cplx_t<T>* __restrict__ Y, PairParams p) {
+  using C2 = cplx_t<T>;
+  constexpr int TP = kBulkTile, NS = kBulkStages;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw);  // full[NS], free[NS]
+  C2* buf0 = reinterpret_cast<C2*>(smem_raw + 128);
+  const int nocc = p.nocc;
+  const int nf = wave_fields(nocc, p.nkp, p.diag);
+  const int nkq = p.diag ? 0 : p.nkp * nocc;   // orbital planes at k'
+  const int planes = nf + 2 * nocc + 2 * nkq;  // W, u_k, u_k', Y_k, Y_k'
+  const long long ng = p.ng;
+  const long long tiles = (ng + TP - 1) / TP;
+  const unsigned full0 = tma::smem_u32(&bars[0]), free0 = tma::smem_u32(&bars[NS]);
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < NS; ++b) {
+      tma::mbar_init(full0 + 8 * b, 1);
+      tma::mbar_init(free0 + 8 * b, TP);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  // plane offsets inside a buffer (in points): W | u_k | u_k' | Y_k | Y_k'
+  const int oPk = nf * TP, oPq = oPk + nocc * TP, oYk = oPq + nkq * TP, oYq = oYk + nocc * TP;
+  auto buf = [&](int b) { return buf0 + (size_t)b * planes * TP; };
+
+  if (threadIdx.x >= TP) {   // producer warp
+    if (threadIdx.x != TP) return;
+    long long it = 0;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+      const int b = (int)(it % NS);
+      // the buffer's previous tile (it - NS) must have been consumed
+      if (it >= NS && !tma::mbar_wait(free0 + 8 * b, (unsigned)((it / NS - 1) & 1))) {
+        record_timeout(p.status);
+        return;
+      }
+      const long long r0 = tile * TP;
+      const long long npts = std::min<long long>(TP, ng - r0);
+      // bytes per plane, a multiple of 16 (the last tile may read into the field padding)
+      const unsigned bytes = (unsigned)(((npts * (long long)sizeof(C2)) + 15) / 16 * 16);
+      const unsigned fb = full0 + 8 * b;
+      tma::mbar_expect_tx(fb, bytes * (unsigned)planes);
+      C2* d = buf(b);
+      for (int f = 0; f < nf; ++f)
+        tma::bulk_g2s(tma::smem_u32(d + f * TP), S + (size_t)f * p.fs + r0, bytes, fb);
+      for (int i = 0; i < nocc; ++i) {
+        const size_t src = (size_t)(p.k * nocc + i) * p.fs + r0;
+        tma::bulk_g2s(tma::smem_u32(d + oPk + i * TP), psi + src, bytes, fb);
+        tma::bulk_g2s(tma::smem_u32(d + oYk + i * TP), Y + src, bytes, fb);
+      }
+      for (int j = 0; j < nkq; ++j) {
+        const size_t src = (size_t)(p.kp0 * nocc + j) * p.fs + r0;
+        tma::bulk_g2s(tma::smem_u32(d + oPq + j * TP), psi + src, bytes, fb);
+        tma::bulk_g2s(tma::smem_u32(d + oYq + j * TP), Y + src, bytes, fb);
+      }
+    }
+    // every issued copy completes before the consumers release its buffer; wait for the
+    // last NS releases so that no copy is in flight when the CTA exits
+    for (long long last = std::max<long long>(0, it - NS); last < it; ++last) {
+      const int b = (int)(last % NS);
+      if (!tma::mbar_wait(free0 + 8 * b, (unsigned)((last / NS) & 1))) {
+        record_timeout(p.status);
+        return;
+      }
+    }
+    return;
+  }
+
+  // consumer warps
+  const int t = threadIdx.x;
+  long long it = 0;
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+    const int b = (int)(it % NS);
+    if (!tma::mbar_wait(full0 + 8 * b, (unsigned)((it / NS) & 1))) {
+      record_timeout(p.status);
+      return;
+    }
+    const C2* d = buf(b);
+    const long long r = tile * TP + t;
+    if (r < ng) {
+      T pr[NOC], pim[NOC], ar[NOC], ai[NOC];
+#pragma unroll
+      for (int i = 0; i < NOC; ++i) {
+        C2 v = mk<T>(T(0), T(0));
+        if (i < nocc) v = d[oPk + i * TP + t];
+        pr[i] = v.x; pim[i] = v.y;
+        ar[i] = T(0); ai[i] = T(0);
+      }
+      if (p.diag) {
+#pragma unroll
+        for (int j = 0; j < NOC; ++j) {
+          if (j >= nocc) break;
+#pragma unroll
+          for (int i = 0; i <= j; ++i) {
+            const C2 w = d[diag_field(i, j, nocc) * TP + t];
+            ar[i] += w.x * pr[j] - w.y * pim[j];     // W_ij u_j
+            ai[i] += w.x * pim[j] + w.y * pr[j];
+            if (i < j) {                             // W_ji u_i = conj(W_ij) u_i
+              ar[j] += w.x * pr[i] + w.y * pim[i];
+              ai[j] += w.x * pim[i] - w.y * pr[i];
+            }
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int kpl = 0; kpl < p.nkp; ++kpl) {
+          T qr[NOC], qi[NOC], br[NOC], bi[NOC];
+#pragma unroll
+          for (int j = 0; j < NOC; ++j) {
+            C2 v = mk<T>(T(0), T(0));
+            if (j < nocc) v = d[oPq + (kpl * nocc + j) * TP + t];
+            qr[j] = v.x; qi[j] = v.y;
+            br[j] = T(0); bi[j] = T(0);
+          }
+          const C2* wk = d + (size_t)kpl * nocc * nocc * TP + t;
+#pragma unroll
+          for (int i = 0; i < NOC; ++i) {
+            if (i >= nocc) break;
+#pragma unroll
+            for (int j = 0; j < NOC; ++j) {
+              if (j >= nocc) break;
+              const C2 w = wk[(i * nocc + j) * TP];
+              ar[i] += w.x * qr[j] - w.y * qi[j];     // W u_{jk'}
+              ai[i] += w.x * qi[j] + w.y * qr[j];
+              br[j] += w.x * pr[i] + w.y * pim[i];    // conj(W) u_{ik}
+              bi[j] += w.x * pim[i] - w.y * pr[i];
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < NOC; ++j) {
+            if (j >= nocc) break;
+            const C2 y = d[oYq + (kpl * nocc + j) * TP + t];
+            Y[(size_t)((p.kp0 + kpl) * nocc + j) * p.fs + r] = mk<T>(y.x + br[j], y.y + bi[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NOC; ++i) {
+        if (i >= nocc) break;
+        const C2 y = d[oYk + i * TP + t];
+        Y[(size_t)(p.k * nocc + i) * p.fs + r] = mk<T>(y.x + ar[i], y.y + ai[i]);
+      }
+    }
+    tma::mbar_arrive(free0 + 8 * b);
+  }
+}
+
+// Bytes of shared memory of pass_d_bulk for a wave (two buffers and the barriers), or 0
+// when they would not fit next to nothing else on an SM (the register form runs then).
+inline size_t bulk_smem(int nocc, int nkp, int diag, size_t csz) {
+  const int nf = wave_fields(nocc, nkp, diag);
+  const int planes = nf + 2 * nocc + 2 * (diag ? 0 : nkp * nocc);
+  const size_t bytes = 128 + (size_t)kBulkStages * planes * kBulkTile * csz;
+  return bytes <= 226 * 1024 ? bytes : 0;
+}
+
 template <typename T, int NOC>
 cudaError_t launch_pass_d_noc(const PairParams& p, const cplx_t<T>* S, const cplx_t<T>* psi,
                               cplx_t<T>* Y, cudaStream_t st) {
+  const size_t sm = bulk_smem(p.nocc, p.nkp, p.diag, sizeof(cplx_t<T>));
+  if (sm) {
+    static size_t sm_set = 0;
+    static int nsm = 0;
+    if (sm > sm_set) {
+      cudaFuncSetAttribute(pass_d_bulk<T, NOC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm);
+      sm_set = sm;
+    }
+    if (!nsm) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      nsm = std::max(1, nsm);
+    }
+    const long long tiles = (p.ng + kBulkTile - 1) / kBulkTile;
+    pass_d_bulk<T, NOC><<<(unsigned)std::min<long long>(tiles, nsm), kBulkTile + 32, sm, st>>>(
+        S, psi, Y, p);
+    return cudaGetLastError();
+  }
   static int slots = 0;
   if (!slots) slots = resident_slots(pass_d<T, NOC>, 256, 0);
   const unsigned nb = (unsigned)std::min<long long>((p.ng + 255) / 256, slots);
