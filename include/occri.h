@@ -113,10 +113,11 @@ enum {
   OCCRI_STAGE_ORBITALS = 0,  /* (a)+(b) */
   OCCRI_STAGE_PAIR_A = 1,    /* (c)+(d) pass A: pair density, FFT along n3 and n2 */
   OCCRI_STAGE_PAIR_B = 2,    /* (d) pass B: FFT along n1, kernel, inverse along m1, m2 */
-  OCCRI_STAGE_PAIR_C = 3,    /* (d) pass C: inverse along m3, accumulate Y */
+  OCCRI_STAGE_PAIR_C = 3,    /* (d) pass C: inverse along m3; pass D: accumulate Y */
   OCCRI_STAGE_CONTRACT = 4,  /* (e) */
   OCCRI_STAGE_ASSEMBLE = 5,  /* (f) */
-  OCCRI_NSTAGES = 6
+  OCCRI_STAGE_PAIRS = 6,     /* (c)+(d): the whole loop over pair waves, wall time */
+  OCCRI_NSTAGES = 7
 };
 
 typedef struct occri_plan occri_plan;

@@ -62,7 +62,7 @@ EXPORTED = ["occri_plan_create", "occri_plan_destroy", "occri_plan_info", "occri
             "occri_vjp", "occri_plan_set_timing", "occri_plan_stage_times", "occri_orbitals_noalloc",
             "occri_status_string"]
 
-STAGES = ["orbitals", "pair_a", "pair_b", "pair_c", "contract", "assemble"]
+STAGES = ["orbitals", "pair_a", "pair_b", "pair_c", "contract", "assemble", "pairs"]
 
 _lib_handle = None
 

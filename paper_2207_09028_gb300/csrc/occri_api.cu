@@ -337,6 +337,10 @@ void free_plan(Plan* p) {
                   p->shell_list_l[3]};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  if (p->scratch2) cudaFree(p->scratch2);
+  for (cudaEvent_t e : {p->ev_fork, p->ev_join, p->ev_y, p->ev_iso})
+    if (e) cudaEventDestroy(e);
+  if (p->aux) cudaStreamDestroy(p->aux);
   for (cudaEvent_t e : p->ev_used) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev_free) cudaEventDestroy(e);
   delete p;
@@ -407,26 +411,50 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
     t.done(OCCRI_STAGE_ORBITALS, p->nk);
     launches += 2 + (p->nocc + kOrbChunk - 1) / kOrbChunk;
   }
-  long long wave = 0;
-  for (int k = 0; k < p->nk; ++k)
-    for (int kp0 = k; kp0 < p->nk; ++wave) {   // unordered pairs: (k, k), then k' > k
-      const int diag = (kp0 == k) ? 1 : 0;
-      const int nkp = diag ? 1 : std::min(p->nkp_wave, p->nk - kp0);
-      cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-      bool sample = timed && (wave % p->timing_every == 0);
-      if (sample)
-        for (int i = 0; i < 4 && sample; ++i) sample = (ev[i] = take_event(p)) != nullptr;
-      if (launch_pair_wave<T>(*p, k, kp0, nkp, diag, s, sample ? ev : nullptr) != cudaSuccess)
-        return OCCRI_ECUDA;
-      launches += 4;
-      if (sample) {
+  {
+    // Waves alternate between the plan's stream and the auxiliary one, each with its own
+    // scratch; the accumulation passes (which update Y_k) are chained across the two
+    // streams by ev_y. A sampled wave runs alone (both streams wait for each other
+    // around it) so that its pass times are not mixed with the other stream's work.
+    StageTimer all(p, timed);
+    cudaStream_t st[2] = {s, p->aux};
+    void* sc[2] = {p->scratch, p->scratch2};
+    if (cudaEventRecord(p->ev_fork, s) != cudaSuccess) return OCCRI_ECUDA;
+    if (cudaStreamWaitEvent(p->aux, p->ev_fork, 0) != cudaSuccess) return OCCRI_ECUDA;
+    double fields = 0.0;
+    long long wave = 0;
+    for (int k = 0; k < p->nk; ++k)
+      for (int kp0 = k; kp0 < p->nk; ++wave) {   // unordered pairs: (k, k), then k' > k
+        const int diag = (kp0 == k) ? 1 : 0;
+        const int nkp = diag ? 1 : std::min(p->nkp_wave, p->nk - kp0);
+        const int w = (int)(wave & 1);
+        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+        bool sample = timed && (wave % p->timing_every == 0);
+        if (sample)
+          for (int i = 0; i < 4 && sample; ++i) sample = (ev[i] = take_event(p)) != nullptr;
+        if (sample) {   // wait for the other stream's work
+          cudaEventRecord(p->ev_iso, st[w ^ 1]);
+          cudaStreamWaitEvent(st[w], p->ev_iso, 0);
+        }
+        if (launch_pair_wave<T>(*p, k, kp0, nkp, diag, st[w], sc[w], sample ? ev : nullptr,
+                                p->ev_y) != cudaSuccess)
+          return OCCRI_ECUDA;
+        launches += 4;
         const double nf = (double)wave_fields(p->nocc, nkp, diag);
-        p->ev_pending.push_back(Plan::TimedSpan{ev[0], ev[1], OCCRI_STAGE_PAIR_A, nf});
-        p->ev_pending.push_back(Plan::TimedSpan{ev[1], ev[2], OCCRI_STAGE_PAIR_B, nf});
-        p->ev_pending.push_back(Plan::TimedSpan{ev[2], ev[3], OCCRI_STAGE_PAIR_C, nf});
+        fields += nf;
+        if (sample) {   // and keep the other stream waiting until this wave is done
+          cudaEventRecord(p->ev_iso, st[w]);
+          cudaStreamWaitEvent(st[w ^ 1], p->ev_iso, 0);
+          p->ev_pending.push_back(Plan::TimedSpan{ev[0], ev[1], OCCRI_STAGE_PAIR_A, nf});
+          p->ev_pending.push_back(Plan::TimedSpan{ev[1], ev[2], OCCRI_STAGE_PAIR_B, nf});
+          p->ev_pending.push_back(Plan::TimedSpan{ev[2], ev[3], OCCRI_STAGE_PAIR_C, nf});
+        }
+        kp0 += nkp;
       }
-      kp0 += nkp;
-    }
+    if (cudaEventRecord(p->ev_join, p->aux) != cudaSuccess) return OCCRI_ECUDA;
+    if (cudaStreamWaitEvent(s, p->ev_join, 0) != cudaSuccess) return OCCRI_ECUDA;
+    all.done(OCCRI_STAGE_PAIRS, fields);
+  }
   {
     StageTimer t(p, timed);
     if (launch_phase_fields<T>(*p, p->Y, +1, s) != cudaSuccess) return OCCRI_ECUDA;
@@ -829,8 +857,12 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     unsigned char* b = nullptr;
     chk(dalloc(&b, orb * csz, &tot)); p->psi = b; b = nullptr;
     chk(dalloc(&b, orb * csz, &tot)); p->Y = b; b = nullptr;
-    chk(dalloc(&b, (size_t)p->fields_cap * field_bytes, &tot)); p->scratch = b;
+    chk(dalloc(&b, (size_t)p->fields_cap * field_bytes, &tot)); p->scratch = b; b = nullptr;
+    chk(dalloc(&b, (size_t)p->fields_cap * field_bytes, &tot)); p->scratch2 = b;
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
+  for (cudaEvent_t* ev : {&p->ev_fork, &p->ev_join, &p->ev_y, &p->ev_iso})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   chk(dalloc(&p->kc, (size_t)p->nk * nao * nocc, &tot));
   chk(dalloc(&p->xi, (size_t)p->nk * nao * nocc, &tot));
   chk(dalloc(&p->mmat, (size_t)p->nk * nocc * nocc, &tot));

@@ -131,7 +131,13 @@ struct Plan {
   // long, so each starts 512-byte aligned (whole-tile bulk copies).
   void* psi = nullptr;       // [nk][nocc][fs] cplx_t<T>
   void* Y = nullptr;         // [nk][nocc][fs] cplx_t<T>
-  void* scratch = nullptr;   // [fields_cap][fs] cplx_t<T>
+  void* scratch = nullptr;   // [fields_cap][fs] cplx_t<T>, waves on the plan's stream
+  void* scratch2 = nullptr;  // the same for the waves on the second stream
+  // Consecutive waves alternate between the plan's stream and `aux`, each with its own
+  // scratch, so one wave's passes overlap the next one's; only the accumulation passes,
+  // which both update Y_k, are ordered across the two streams (event ev_y).
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_y = nullptr, ev_iso = nullptr;
   double2* kc = nullptr;     // [nk][nao][nocc]
   double2* xi = nullptr;     // [nk][nao][nocc]
   double2* mmat = nullptr;   // [nk][nocc][nocc]
@@ -157,9 +163,9 @@ struct Plan {
   std::vector<cudaEvent_t> ev_free;
   std::vector<TimedSpan> ev_pending;
   std::vector<cudaEvent_t> ev_used;
-  double stage_ms[6] = {0, 0, 0, 0, 0, 0};
-  long long stage_n[6] = {0, 0, 0, 0, 0, 0};
-  double stage_units[6] = {0, 0, 0, 0, 0, 0};
+  double stage_ms[OCCRI_NSTAGES] = {};
+  long long stage_n[OCCRI_NSTAGES] = {};
+  double stage_units[OCCRI_NSTAGES] = {};
 
   AOParams ao_params() const;
   PairParams pair_params() const;
@@ -186,11 +192,12 @@ template <typename T>
 cudaError_t launch_phase_fields(const Plan& p, void* F, int sign, cudaStream_t s);
 // Pair-wave launches over unordered pairs: diag = 1 is the wave (k, k) with fields
 // i <= j; diag = 0 covers k' in [kp0, kp0 + nkp), all kp0 > k, with every (i, j).
-// When ev != nullptr, ev[0..3] are recorded before pass A, before pass B, before
-// pass C and after pass C.
+// S is the wave's scratch. When ev != nullptr, ev[0..3] are recorded before pass A,
+// before pass B, before pass C and after pass D. When ev_y != nullptr, pass D first
+// waits for it and then records it (orders the Y updates of waves on two streams).
 template <typename T>
 cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s,
-                             cudaEvent_t* ev = nullptr);
+                             void* S, cudaEvent_t* ev = nullptr, cudaEvent_t ev_y = nullptr);
 template <typename T>
 cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s);
 

@@ -462,6 +462,9 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
 }
 
 // ------------------------------------------------------------------ pass B
+// Plane buffers per pass-B CTA: 2 copies the next item in while the current one is
+// transformed; 1 leaves room for a fourth CTA per SM, whose warps cover the copies.
+constexpr int kPassBBuffers = 1;
 // Items (m3, field), m3-major; CTA b takes the contiguous chunk [b c, (b + 1) c) of
 // them (c = ceil(items / grid), the grid being the SMs' resident CTA slots), so there is
 // no partly filled last round of CTAs. Per item: FFT along n1, multiply by v/(4 pi),
@@ -476,7 +479,8 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
   constexpr int P = pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* planes = reinterpret_cast<C2*>(smem_raw);                      // 2 x [n1][m2]
-  Axis1<T>* ax1 = reinterpret_cast<Axis1<T>*>(planes + 2 * N * P);  // [m1]
+  constexpr int NB = kPassBBuffers;
+  Axis1<T>* ax1 = reinterpret_cast<Axis1<T>*>(planes + NB * N * P);  // [m1]
   T* vtab = reinterpret_cast<T*>(ax1 + N);                           // [m1][m2] v or dv
   __shared__ double red[4];
   const int nf = wave_fields(p.nocc, p.nkp, p.diag);
@@ -495,12 +499,14 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
   T dsum = T(0);
 #pragma unroll 1
   for (int it = i0; it < i1; ++it) {
-    C2* plane = planes + ((it - i0) & 1) * N * P;
+    C2* plane = planes + ((it - i0) % NB) * N * P;
     const int m3 = it / nf, f = it - (it / nf) * nf;
     const FieldIdx fi = field_idx(f, p.nocc, p.diag);
-    if (it + 1 < i1)   // the other buffer was released by the barrier ending item it - 1
-      stage_plane<T, N, P>(planes + ((it + 1 - i0) & 1) * N * P, plane_src(it + 1));
-    cp_async_commit();
+    if constexpr (NB == 2) {
+      if (it + 1 < i1)   // the other buffer was released by the barrier ending item it - 1
+        stage_plane<T, N, P>(planes + ((it + 1 - i0) & 1) * N * P, plane_src(it + 1));
+      cp_async_commit();
+    }
     if (fi.kpl != kpl_tab || m3 != m3_tab) {   // uniform over the CTA
       kpl_tab = fi.kpl;
       m3_tab = m3;
@@ -522,7 +528,8 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
           vtab[m1 * N + c] = bin_value<T, DOMEGA>(p, gm, ax1[m1], cc);
       }
     }
-    cp_async_wait<1>();   // this item's plane has landed (the next one may be in flight)
+    // this item's plane has landed (with two buffers the next one may be in flight)
+    if constexpr (NB == 2) cp_async_wait<1>(); else cp_async_wait<0>();
     __syncthreads();
     // an unordered pair stands for itself and its reverse, except (k, k, i, i)
     const T wgt = (p.diag && fi.i == fi.j) ? T(1) : T(2);
@@ -552,7 +559,11 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
         const int r = e / N, c = e - (e / N) * N;
         buf[e] = plane[r * P + c];
       }
-      __syncthreads();   // releases this buffer for the copy two items ahead
+      __syncthreads();   // releases this buffer for the copy NB items ahead
+    }
+    if constexpr (NB == 1) {   // one buffer: the next plane is copied in only now
+      if (it + 1 < i1) stage_plane<T, N, P>(planes, plane_src(it + 1));
+      cp_async_commit();
     }
   }
   if constexpr (DOMEGA) {
@@ -964,14 +975,14 @@ cudaError_t launch_pass_d(const PairParams& p, const cplx_t<T>* S, const cplx_t<
 
 template <int N> constexpr size_t smem_a(size_t csz) { return csz * N * pitch(N); }
 template <int N> constexpr size_t smem_b(size_t csz, size_t tab) {
-  return 2 * csz * N * pitch(N) + N * tab + csz / 2 * N * N;
+  return kPassBBuffers * csz * N * pitch(N) + N * tab + csz / 2 * N * N;
 }
 
 template <int N> constexpr size_t smem_c(size_t csz) { return csz * N * pitch(N); }
 
 template <typename T, int N>
 cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cplx_t<T>* Y,
-                     cudaStream_t st, cudaEvent_t* ev) {
+                     cudaStream_t st, cudaEvent_t* ev, cudaEvent_t ev_y) {
   using C2 = cplx_t<T>;
   const int nt = threads_for(N);
   const int nf = wave_fields(p.nocc, p.nkp, p.diag);
@@ -993,7 +1004,9 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S, p);
   if (ev) cudaEventRecord(ev[2], st);
   pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S, p);
+  if (ev_y) cudaStreamWaitEvent(st, ev_y, 0);   // the previous wave's Y updates
   const cudaError_t e = launch_pass_d<T>(p, S, psi, Y, st);
+  if (ev_y) cudaEventRecord(ev_y, st);
   if (ev) cudaEventRecord(ev[3], st);
   return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -10,7 +10,7 @@ namespace pairs {
 
 template <typename T, int N>
 cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cplx_t<T>* Y,
-                     cudaStream_t st, cudaEvent_t* ev);
+                     cudaStream_t st, cudaEvent_t* ev, cudaEvent_t ev_y);
 template <typename T, int N>
 cudaError_t run_domega_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S,
                             double* dacc, cudaStream_t st);

@@ -5,19 +5,19 @@ namespace occri {
 
 template <typename T>
 cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s,
-                             cudaEvent_t* ev) {
+                             void* scratch, cudaEvent_t* ev, cudaEvent_t ev_y) {
   PairParams pp = p.pair_params();
   pp.k = k;
   pp.kp0 = kp0;
   pp.nkp = nkp;
   pp.diag = diag;
   const cplx_t<T>* psi = (const cplx_t<T>*)p.psi;
-  cplx_t<T>* S = (cplx_t<T>*)p.scratch;
+  cplx_t<T>* S = (cplx_t<T>*)scratch;
   cplx_t<T>* Y = (cplx_t<T>*)p.Y;
   switch (p.N[0]) {
 #define OCCRI_PAIR_CASE(NN) \
   case NN:                  \
-    return pairs::run_wave<T, NN>(pp, psi, S, Y, s, ev);
+    return pairs::run_wave<T, NN>(pp, psi, S, Y, s, ev, ev_y);
     OCCRI_FOR_EACH_N(OCCRI_PAIR_CASE)
 #undef OCCRI_PAIR_CASE
     default:
@@ -46,10 +46,10 @@ cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag,
   }
 }
 
-template cudaError_t launch_pair_wave<float>(const Plan&, int, int, int, int, cudaStream_t,
-                                             cudaEvent_t*);
-template cudaError_t launch_pair_wave<double>(const Plan&, int, int, int, int, cudaStream_t,
-                                              cudaEvent_t*);
+template cudaError_t launch_pair_wave<float>(const Plan&, int, int, int, int, cudaStream_t, void*,
+                                             cudaEvent_t*, cudaEvent_t);
+template cudaError_t launch_pair_wave<double>(const Plan&, int, int, int, int, cudaStream_t, void*,
+                                              cudaEvent_t*, cudaEvent_t);
 template cudaError_t launch_domega_wave<float>(const Plan&, int, int, int, int, cudaStream_t);
 template cudaError_t launch_domega_wave<double>(const Plan&, int, int, int, int, cudaStream_t);
 
