@@ -49,9 +49,15 @@ constexpr int pitch(int n) { return (n % 2 == 0) ? n + 1 : n; }
 // Even edges use two threads per line (radix-2 split, see line_fft2), odd edges one.
 constexpr int line_split(int n) { return (n % 2 == 0) ? 2 : 1; }
 constexpr int round32(int n) { return (n + 31) / 32 * 32; }
-// With the split, the two halves of lines 32w..32w+31 sit in warps 2w (h = 0) and
-// 2w + 1 (h = 1), so the half-dependent code is uniform over each warp.
-constexpr int threads_for(int n) { return line_split(n) * round32(n); }
+// Where the two halves of a split line live. true: adjacent lanes of one warp, so that
+// both halves' loads of the same element are one shared-memory broadcast (the
+// half-dependent twiddle is then computed by both and selected). false: the halves of
+// lines 32w..32w+31 in warps 2w (h = 0) and 2w + 1 (h = 1), half-dependent code uniform
+// over each warp, every load its own shared-memory access.
+constexpr bool kPairLanes = false;
+constexpr int threads_for(int n) {
+  return line_split(n) == 1 ? round32(n) : (kPairLanes ? round32(2 * n) : 2 * round32(n));
+}
 // resident CTAs per SM requested from the register allocator
 constexpr int min_blocks(int n, int elem_bytes) {
   return elem_bytes > 8 ? (n <= 32 ? 4 : 2) : (n <= 32 ? 8 : 4);
@@ -172,28 +178,44 @@ __device__ __forceinline__ void line_fft(cplx_t<T>* base, int stride, bool inver
   }
 }
 
-// Two threads per line (even N), in two different warps. Half h forms
+// Two threads per line (even N), adjacent lanes or two warps (kPairLanes). Half h forms
 //   y_h[n] = (x[n] + (-1)^h x[n + N/2]) e^{-2 pi i h n / N},   n < N/2,
 // from the whole line in shared memory and transforms it with an N/2-point register
 // FFT, which gives the outputs X[2k + h] (radix-2 decimation in frequency). inverse,
 // store and post as in line_fft; `valid` is false for padding threads, which compute
-// on a duplicate line but neither store nor call post. The two warps of the pair meet
-// at named barrier `bar` (1 or 2: at most two pairs of warps per CTA, N <= 64) between
-// their loads and their stores.
+// on a duplicate line but neither store nor call post. The pair synchronises between
+// its loads and its stores: __syncwarp for adjacent lanes, else named barrier `bar`
+// (1 or 2: at most two pairs of warps per CTA, N <= 64).
 template <typename T, int N, typename Post>
 __device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool inverse, bool store,
                                           int h, bool valid, int bar, Post&& post) {
   constexpr int M = N / 2;
   auto pair_barrier = [&]() {
-    if (bar == 1)   // warp-uniform; immediate barrier ids
+    if constexpr (kPairLanes) {
+      __syncwarp();
+    } else if (bar == 1) {   // warp-uniform; immediate barrier ids
       asm volatile("bar.sync 1, 64;\n" ::: "memory");
-    else
+    } else {
       asm volatile("bar.sync 2, 64;\n" ::: "memory");
+    }
   };
   if constexpr (std::is_same<T, float>::value) {   // packed FP32 core
     using fft::pk::u64;
     u64 x[M];
-    if (h == 0) {
+    if constexpr (kPairLanes) {   // both halves in one warp: no branch on h
+      fft::static_for<M>([&](auto I) {
+        constexpr int n = decltype(I)::value;
+        constexpr fft::CS w = fft::cs2pi(n, N);     // e^{-2 pi i n / N} = c - i s
+        const float2 a = base[n * stride], b = base[(n + M) * stride];
+        const u64 pa = fft::pk::pack(a.x, a.y), pb = fft::pk::pack(b.x, b.y);
+        if constexpr (n == 0) {
+          x[n] = h ? fft::pk::sub(pa, pb) : fft::pk::add(pa, pb);
+        } else {
+          const u64 t = fft::pk::cmul_const(fft::pk::sub(pa, pb), float(w.c), float(-w.s));
+          x[n] = h ? t : fft::pk::add(pa, pb);
+        }
+      });
+    } else if (h == 0) {
       fft::static_for<M>([&](auto I) {
         constexpr int n = decltype(I)::value;
         const float2 a = base[n * stride], b = base[(n + M) * stride];
@@ -269,10 +291,11 @@ __device__ __forceinline__ void run_lines(cplx_t<T>* plane, int P, bool rows, bo
                                           bool store, Post&& post) {
   if constexpr (line_split(N) == 2) {
     const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
-    const int line0 = (w >> 1) * 32 + lane;
+    const int line0 = kPairLanes ? (int)threadIdx.x >> 1 : (w >> 1) * 32 + lane;
+    const int h = kPairLanes ? (int)threadIdx.x & 1 : w & 1;
     const bool valid = line0 < N;
     const int line = valid ? line0 : N - 1;
-    line_fft2<T, N>(rows ? plane + line * P : plane + line, rows ? 1 : P, inverse, store, w & 1,
+    line_fft2<T, N>(rows ? plane + line * P : plane + line, rows ? 1 : P, inverse, store, h,
                     valid, 1 + (w >> 1), [&](int k, T& re, T& im) { post(line, k, re, im); });
   } else {
     if (threadIdx.x < N) {
@@ -724,16 +747,17 @@ pass_d(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
 }
 
 // ------------------------------------------------------------------ pass D, bulk-copy form
-// The same accumulation with every operand moved by the bulk-copy (TMA) engine. Tiles of
-// kBulkTile consecutive points; for a tile, one producer thread (the last warp) copies, per field and
-// per orbital plane, the tile's contiguous tp points into shared memory:
+// The same accumulation with every operand moved by the bulk-copy (TMA) engine, in tiles
+// of kBulkTile consecutive points. For a tile, one producer thread (the last warp) copies
+// the tile's contiguous points of every field and orbital plane into shared memory,
 //   W: nf fields, u_k: nocc planes, u_k': nkp nocc planes, Y_k and Y_k': as many,
 // counting the bytes on the buffer's `full` mbarrier. The consumer warps (one point per
 // thread) wait for it, compute, store Y with plain coalesced stores and arrive on the
 // buffer's `free` mbarrier, after which the producer refills it with the tile kBulkStages
-// ahead.
-// The bytes in flight therefore sit in shared memory, not in registers. Every wait is
-// bounded: on timeout the kernel records OCCRI_ETIMEOUT in the plan status and leaves.
+// ahead. The bytes in flight therefore sit in shared memory, not in registers; a CTA
+// takes about 100 KB, so two run per SM, or one next to a transform pass of the other
+// stream's wave. Every wait is bounded: on timeout the kernel records OCCRI_ETIMEOUT in
+// the plan status and leaves.
 namespace tma {
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -773,11 +797,11 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
 }
 }  // namespace tma
 
-constexpr int kBulkTile = 128;   // points per tile = consumer threads (four warps)
+constexpr int kBulkTile = 64;    // points per tile = consumer threads (two warps)
 constexpr int kBulkStages = 2;   // tile buffers per CTA (one in use, one filling)
 
 template <typename T, int NOC>
-__global__ void __launch_bounds__(kBulkTile + 32, 1)
+__global__ void __launch_bounds__(kBulkTile + 32, 2)
 pass_d_bulk(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
             cplx_t<T>* __restrict__ Y, PairParams p) {
   using C2 = cplx_t<T>;
@@ -940,21 +964,20 @@ cudaError_t launch_pass_d_noc(const PairParams& p, const cplx_t<T>* S, const cpl
   const size_t sm = bulk_smem(p.nocc, p.nkp, p.diag, sizeof(cplx_t<T>));
   if (sm) {
     static size_t sm_set = 0;
-    static int nsm = 0;
     if (sm > sm_set) {
       cudaFuncSetAttribute(pass_d_bulk<T, NOC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sm);
       sm_set = sm;
     }
-    if (!nsm) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      nsm = std::max(1, nsm);
+    static int cached_diag[2] = {-1, -1}, cached_slots[2] = {1, 1};   // per wave kind
+    const int c = p.diag ? 0 : 1;
+    if (cached_diag[c] < 0) {
+      cached_slots[c] = resident_slots(pass_d_bulk<T, NOC>, kBulkTile + 32, sm);
+      cached_diag[c] = p.diag;
     }
     const long long tiles = (p.ng + kBulkTile - 1) / kBulkTile;
-    pass_d_bulk<T, NOC><<<(unsigned)std::min<long long>(tiles, nsm), kBulkTile + 32, sm, st>>>(
-        S, psi, Y, p);
+    pass_d_bulk<T, NOC><<<(unsigned)std::min<long long>(tiles, cached_slots[c]), kBulkTile + 32,
+                          sm, st>>>(S, psi, Y, p);
     return cudaGetLastError();
   }
   static int slots = 0;
