@@ -204,6 +204,39 @@ int occri_plan_stage_times(occri_plan *plan, double *ms, long long *launches, do
  * serialised by the caller. */
 int occri_orbitals_noalloc(const occri_plan *plan, const void *C_dev, void *psi_dev);
 
+/* ---- Batches of cells: several uneven cells built by one graph launch ----
+ * A batch builds several plans together: cells that may differ in size, k-mesh, basis,
+ * kernel or precision, such as the five cells of a lattice-constant scan. On the first
+ * occri_batch_build (and again whenever the caller's buffers change) the builds of all
+ * cells are captured into one CUDA graph, each cell on its own branch, so that the cells
+ * run concurrently; every call then launches that graph once on the batch's stream. No
+ * counterpart in the paper, whose parallel loops run one cell at a time.
+ * plans: nplans (>= 1) distinct plans, owned by the caller and alive while the batch
+ *   exists; a batch build does not use their own streams, and their stage timing is off
+ *   while the graph is captured.
+ * cuda_stream: the stream the graph is launched on (a cudaStream_t, or NULL for the
+ *   legacy default stream).
+ * On success *out owns the batch (occri_batch_destroy); on failure *out is NULL. */
+typedef struct occri_batch occri_batch;
+int occri_batch_create(occri_batch **out, occri_plan *const *plans, int nplans,
+                       void *cuda_stream);
+
+/* One build of every cell of the batch. Each argument is an array of nplans device
+ * pointers with the meaning and layout of the same argument of occri_k_build (entries of
+ * KC_dev, K_dev and Ex_dev may be NULL; the arrays themselves may be NULL for "all
+ * NULL"). Asynchronous on the batch's stream; the captured graph is reused while the
+ * pointers stay the same. Returns OCCRI_EINVAL for a NULL C entry and OCCRI_ECUDA when the
+ * capture or the launch fails. */
+int occri_batch_build(occri_batch *batch, const void *const *C_dev, void *const *KC_dev,
+                      void *const *K_dev, double *const *Ex_dev);
+
+/* Synchronise the batch's stream and return the first device-side status of any cell
+ * since the previous sync (as occri_plan_sync); *bad_cell and *bad_k (may be NULL)
+ * receive the cell and the k index of an OCCRI_ENOTPD failure, else -1. */
+int occri_batch_sync(occri_batch *batch, int *bad_cell, int *bad_k);
+
+int occri_batch_destroy(occri_batch *batch);
+
 const char *occri_status_string(int status);
 
 #ifdef __cplusplus

@@ -60,6 +60,7 @@ class occri_plan_info_t(ctypes.Structure):
 EXPORTED = ["occri_plan_create", "occri_plan_destroy", "occri_plan_info", "occri_plan_set_stream",
             "occri_plan_sync", "occri_k_build", "occri_k_build_host", "occri_orbitals",
             "occri_vjp", "occri_plan_set_timing", "occri_plan_stage_times", "occri_orbitals_noalloc",
+            "occri_batch_create", "occri_batch_build", "occri_batch_sync", "occri_batch_destroy",
             "occri_status_string"]
 
 STAGES = ["orbitals", "pair_a", "pair_b", "pair_c", "contract", "assemble", "pairs"]
@@ -94,6 +95,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                            ctypes.POINTER(ctypes.c_longlong),
                                            ctypes.POINTER(ctypes.c_double)]
     lib.occri_orbitals_noalloc.argtypes = [vp, vp, vp]
+    lib.occri_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ip, vp]
+    lib.occri_batch_build.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                      ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    lib.occri_batch_sync.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.occri_batch_destroy.argtypes = [vp]
     lib.occri_status_string.argtypes = [ip]
     lib.occri_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -287,6 +293,55 @@ class Plan:
             pass
 
 
+class Batch:
+    """Several plans (cells) built by one CUDA-graph launch (see occri_batch_create)."""
+
+    def __init__(self, plans: Sequence[Plan], stream=None):
+        lib = load_library()
+        self._lib = lib
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[pl._h.value for pl in self.plans])
+        handle = ctypes.c_void_p()
+        _check(lib.occri_batch_create(ctypes.byref(handle), arr, len(self.plans),
+                                      stream if stream is not None else _current_stream()),
+               "occri_batch_create")
+        self._h = handle
+
+    def build(self, Cs, KCs=None, Ks=None, Exs=None, sync: bool = True):
+        """One build of every cell; Cs etc. are lists of device tensors (or None)."""
+        n = len(self.plans)
+        for pl, C in zip(self.plans, Cs):
+            pl._check_c(C)
+
+        def arr(ts):
+            if ts is None:
+                return None
+            return (ctypes.c_void_p * n)(*[None if t is None else t.data_ptr() for t in ts])
+
+        _check(self._lib.occri_batch_build(self._h, arr(Cs), arr(KCs), arr(Ks), arr(Exs)),
+               "occri_batch_build")
+        if sync:
+            self.sync()
+        return KCs, Ks, Exs
+
+    def sync(self):
+        cell, k = ctypes.c_int(-1), ctypes.c_int(-1)
+        st = self._lib.occri_batch_sync(self._h, ctypes.byref(cell), ctypes.byref(k))
+        if st != OCCRI_OK:
+            raise OccriError(st, f"occri_batch_sync (cell {cell.value})", k.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.occri_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def exchange_energy(plan: Plan, C, omega=None):
     """E_x(C[, omega]) as a differentiable torch scalar (backward = occri_vjp).
 
@@ -318,5 +373,6 @@ def exchange_energy(plan: Plan, C, omega=None):
     return _ExchangeEnergy.apply(C, omega)
 
 
-__all__ = ["Plan", "OccriError", "load_library", "exchange_energy", "EXPORTED", "LIB_PATH"] + [
+__all__ = ["Plan", "Batch", "OccriError", "load_library", "exchange_energy", "EXPORTED",
+           "LIB_PATH"] + [
     n for n in globals() if n.startswith("OCCRI_")]

@@ -303,18 +303,20 @@ __device__ __forceinline__ void orbital_shell(const AOParams& p, const ShellDev&
 
 // Scaled coefficients N_mu C^k_{mu i}, formed in FP64 (and split hi/lo for FP32).
 __global__ void scale_c_kernel_d(const double2* __restrict__ C, const double* __restrict__ nrm,
-                                 double2* __restrict__ out, int nao, int nocc, long long n) {
+                                 double2* __restrict__ out, int nao, int nocc, long long n,
+                                 double factor = 1.0) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    const double s = nrm[(e / nocc) % nao];
+    const double s = factor * nrm[(e / nocc) % nao];
     out[e] = make_double2(s * C[e].x, s * C[e].y);
   }
 }
 __global__ void scale_c_kernel_f(const double2* __restrict__ C, const double* __restrict__ nrm,
-                                 float4* __restrict__ out, int nao, int nocc, long long n) {
+                                 float4* __restrict__ out, int nao, int nocc, long long n,
+                                 double factor = 1.0) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    const double s = nrm[(e / nocc) % nao];
+    const double s = factor * nrm[(e / nocc) % nao];
     const double x = s * C[e].x, y = s * C[e].y;
     const float xh = (float)x, yh = (float)y;
     out[e] = make_float4(xh, yh, (float)(x - (double)xh), (float)(y - (double)yh));
@@ -518,17 +520,43 @@ template cudaError_t launch_phase_fields<float>(const Plan&, void*, int, cudaStr
 template cudaError_t launch_phase_fields<double>(const Plan&, void*, int, cudaStream_t);
 
 template <typename T>
-cudaError_t launch_orbitals(const Plan& p, cudaStream_t s) {
+cudaError_t launch_orbitals_to(const Plan& p, const void* cs, void* out, cudaStream_t s) {
   constexpr int NI = kOrbChunk, KB = orbital_kbatch<T>();
-  const AOParams ap = p.ao_params();
+  AOParams ap = p.ao_params();
+  ap.cs = cs;
   dim3 grid((unsigned)((p.nblk + 3) / 4), (p.nk + KB - 1) / KB);
   for (int i0 = 0; i0 < p.nocc; i0 += NI)
-    ao::orbitals_kernel<T, NI, KB><<<grid, 128, 0, s>>>(ap, (cplx_t<T>*)p.psi, i0);
+    ao::orbitals_kernel<T, NI, KB><<<grid, 128, 0, s>>>(ap, (cplx_t<T>*)out, i0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_orbitals(const Plan& p, cudaStream_t s) {
+  return launch_orbitals_to<T>(p, p.cs, p.psi, s);
+}
+
+// Scaled coefficients factor N_mu X^k_{mu i} of any [nk][nao][nocc] c128 array X, in the
+// plan's coefficient format, into `out` (sized like the plan's own coefficients).
+template <>
+cudaError_t launch_scale_to<double>(const Plan& p, const double2* X, void* out, double factor,
+                                    cudaStream_t s) {
+  const long long n = (long long)p.nk * p.nao * p.nocc;
+  ao::scale_c_kernel_d<<<2 * 152, 256, 0, s>>>(X, p.ao_norm, (double2*)out, p.nao, p.nocc, n,
+                                               factor);
+  return cudaGetLastError();
+}
+template <>
+cudaError_t launch_scale_to<float>(const Plan& p, const double2* X, void* out, double factor,
+                                   cudaStream_t s) {
+  const long long n = (long long)p.nk * p.nao * p.nocc;
+  ao::scale_c_kernel_f<<<2 * 152, 256, 0, s>>>(X, p.ao_norm, (float4*)out, p.nao, p.nocc, n,
+                                               factor);
   return cudaGetLastError();
 }
 
 template <typename T, int L>
-static void launch_contract_l(const Plan& p, const AOParams& ap, cudaStream_t s) {
+static void launch_contract_l(const Plan& p, const AOParams& ap, const void* Yf, double2* out,
+                              double scale, cudaStream_t s) {
   constexpr int NI = contract_chunk<T>();
   const int ns = (int)p.shells_by_l[L].size();
   if (ns == 0) return;
@@ -538,22 +566,29 @@ static void launch_contract_l(const Plan& p, const AOParams& ap, cudaStream_t s)
   if (parts > maxparts) parts = maxparts;
   if (parts < 1) parts = 1;
   const long long chunk = (p.nblk + parts - 1) / parts;
-  // Y carries N_g/(4 pi) (see PairParams), hence -Omega 4 pi / (N_k N_g^2)
-  const double scale = -p.omega_cell * 4.0 * 3.14159265358979323846 /
-                       ((double)p.nk * (double)p.ng * (double)p.ng);
   for (int i0 = 0; i0 < p.nocc; i0 += NI)
     ao::contract_kernel<T, L, NI><<<dim3((unsigned)parts, p.nk, ns), 256, 0, s>>>(
-        ap, (const cplx_t<T>*)p.Y, p.kc, p.shell_list_l[L], i0, chunk, scale);
+        ap, (const cplx_t<T>*)Yf, out, p.shell_list_l[L], i0, chunk, scale);
+}
+
+// out[k][mu][i] += scale N_mu sum_r conj(chi~_{mu k}(r)) F_ik(r) for an orbital-shaped field F
+template <typename T>
+cudaError_t launch_contract_field(const Plan& p, const void* F, double2* out, double scale,
+                                  cudaStream_t s) {
+  const AOParams ap = p.ao_params();
+  launch_contract_l<T, 0>(p, ap, F, out, scale, s);
+  launch_contract_l<T, 1>(p, ap, F, out, scale, s);
+  launch_contract_l<T, 2>(p, ap, F, out, scale, s);
+  launch_contract_l<T, 3>(p, ap, F, out, scale, s);
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_contract(const Plan& p, cudaStream_t s) {
-  const AOParams ap = p.ao_params();
-  launch_contract_l<T, 0>(p, ap, s);
-  launch_contract_l<T, 1>(p, ap, s);
-  launch_contract_l<T, 2>(p, ap, s);
-  launch_contract_l<T, 3>(p, ap, s);
-  return cudaGetLastError();
+  // Y carries N_g/(4 pi) (see PairParams), hence -Omega 4 pi / (N_k N_g^2)
+  const double scale = -p.omega_cell * 4.0 * 3.14159265358979323846 /
+                       ((double)p.nk * (double)p.ng * (double)p.ng);
+  return launch_contract_field<T>(p, p.Y, p.kc, scale, s);
 }
 
 template <typename T>
@@ -566,6 +601,12 @@ cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s) {
 
 template cudaError_t launch_orbitals<float>(const Plan&, cudaStream_t);
 template cudaError_t launch_orbitals<double>(const Plan&, cudaStream_t);
+template cudaError_t launch_orbitals_to<float>(const Plan&, const void*, void*, cudaStream_t);
+template cudaError_t launch_orbitals_to<double>(const Plan&, const void*, void*, cudaStream_t);
+template cudaError_t launch_contract_field<float>(const Plan&, const void*, double2*, double,
+                                                  cudaStream_t);
+template cudaError_t launch_contract_field<double>(const Plan&, const void*, double2*, double,
+                                                   cudaStream_t);
 template cudaError_t launch_contract<float>(const Plan&, cudaStream_t);
 template cudaError_t launch_contract<double>(const Plan&, cudaStream_t);
 template cudaError_t launch_widen<float>(const Plan&, void*, cudaStream_t);

@@ -421,6 +421,9 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
     void* sc[2] = {p->scratch, p->scratch2};
     if (cudaEventRecord(p->ev_fork, s) != cudaSuccess) return OCCRI_ECUDA;
     if (cudaStreamWaitEvent(p->aux, p->ev_fork, 0) != cudaSuccess) return OCCRI_ECUDA;
+    // the first wave's accumulation waits on this record (within the same build, which
+    // keeps the chain inside a captured graph when the build is captured)
+    if (cudaEventRecord(p->ev_y, s) != cudaSuccess) return OCCRI_ECUDA;
     double fields = 0.0;
     long long wave = 0;
     for (int k = 0; k < p->nk; ++k)
@@ -518,6 +521,101 @@ int vjp_impl(Plan* p, const double2* C, double gEx, void* gC, double* gomega) {
 }
 
 }  // namespace
+
+// A batch of cells built by one graph launch (see occri_batch_create in occri.h).
+struct occri_batch {
+  std::vector<occri_plan*> plans;
+  cudaStream_t stream = nullptr;           // launch stream (the caller's)
+  cudaStream_t cap = nullptr;              // capture origin
+  std::vector<cudaStream_t> branch;        // one capture branch per cell
+  cudaEvent_t ev_start = nullptr;
+  std::vector<cudaEvent_t> ev_end;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // the buffers the graph was captured with
+  std::vector<const void*> c;
+  std::vector<void*> kc, k;
+  std::vector<double*> ex;
+};
+
+namespace occri_impl {
+
+void batch_release_graph(occri_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+void batch_free(occri_batch* b) {
+  if (!b) return;
+  batch_release_graph(b);
+  for (cudaEvent_t e : b->ev_end)
+    if (e) cudaEventDestroy(e);
+  if (b->ev_start) cudaEventDestroy(b->ev_start);
+  for (cudaStream_t st : b->branch)
+    if (st) cudaStreamDestroy(st);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+// Capture one build of every cell into b->graph: the capture starts on b->cap, forks one
+// branch per cell (each plan's own two-stream pipeline joins back into its branch), and
+// joins all branches on b->cap. Plans run their normal build code with their stream set
+// to the branch and timing off.
+int batch_capture(occri_batch* b) {
+  batch_release_graph(b);
+  const size_t n = b->plans.size();
+  std::vector<cudaStream_t> saved_stream(n);
+  std::vector<int> saved_timing(n);
+  for (size_t i = 0; i < n; ++i) {
+    Plan* p = b->plans[i]->p;
+    saved_stream[i] = p->stream;
+    saved_timing[i] = p->timing_every;
+    p->timing_every = 0;
+  }
+  int st = OCCRI_OK;
+  if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    st = OCCRI_ECUDA;
+  } else {
+    if (cudaEventRecord(b->ev_start, b->cap) != cudaSuccess) st = OCCRI_ECUDA;
+    for (size_t i = 0; i < n && st == OCCRI_OK; ++i) {
+      Plan* p = b->plans[i]->p;
+      if (cudaStreamWaitEvent(b->branch[i], b->ev_start, 0) != cudaSuccess) {
+        st = OCCRI_ECUDA;
+        break;
+      }
+      p->stream = b->branch[i];
+      const double2* C = (const double2*)b->c[i];
+      st = p->precision == OCCRI_FP64 ? build_impl<double>(p, C, b->kc[i], b->k[i], b->ex[i])
+                                      : build_impl<float>(p, C, b->kc[i], b->k[i], b->ex[i]);
+      if (st == OCCRI_OK && (cudaEventRecord(b->ev_end[i], b->branch[i]) != cudaSuccess ||
+                             cudaStreamWaitEvent(b->cap, b->ev_end[i], 0) != cudaSuccess))
+        st = OCCRI_ECUDA;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    if (st == OCCRI_OK && (e != cudaSuccess || !g)) st = OCCRI_ECUDA;
+    if (st == OCCRI_OK) {
+      b->graph = g;
+      if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) st = OCCRI_ECUDA;
+    } else if (g) {
+      cudaGraphDestroy(g);
+    }
+  }
+  for (size_t i = 0; i < n; ++i) {
+    Plan* p = b->plans[i]->p;
+    p->stream = saved_stream[i];
+    p->timing_every = saved_timing[i];
+  }
+  if (st != OCCRI_OK) {
+    cudaGetLastError();
+    batch_release_graph(b);
+  }
+  return st;
+}
+
+}  // namespace occri_impl
 
 extern "C" {
 
@@ -1032,6 +1130,93 @@ int occri_vjp(occri_plan* plan, const void* C_dev, double gEx, void* gC_dev, dou
   const double2* C = (const double2*)C_dev;
   return p->precision == OCCRI_FP64 ? occri_impl::vjp_impl<double>(p, C, gEx, gC_dev, gomega_dev)
                                     : occri_impl::vjp_impl<float>(p, C, gEx, gC_dev, gomega_dev);
+}
+
+int occri_batch_create(occri_batch** out, occri_plan* const* plans, int nplans,
+                       void* cuda_stream) {
+  if (!out) return OCCRI_EINVAL;
+  *out = nullptr;
+  if (!plans || nplans < 1) return OCCRI_EINVAL;
+  for (int i = 0; i < nplans; ++i) {
+    if (!plans[i]) return OCCRI_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return OCCRI_EINVAL;
+  }
+  occri_batch* b = new occri_batch();
+  b->plans.assign(plans, plans + nplans);
+  b->stream = (cudaStream_t)cuda_stream;
+  b->branch.assign(nplans, nullptr);
+  b->ev_end.assign(nplans, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < nplans && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_end[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    occri_impl::batch_free(b);
+    return OCCRI_ECUDA;
+  }
+  *out = b;
+  return OCCRI_OK;
+}
+
+int occri_batch_build(occri_batch* b, const void* const* C_dev, void* const* KC_dev,
+                      void* const* K_dev, double* const* Ex_dev) {
+  if (!b || !C_dev) return OCCRI_EINVAL;
+  const size_t n = b->plans.size();
+  std::vector<const void*> c(n);
+  std::vector<void*> kc(n, nullptr), k(n, nullptr);
+  std::vector<double*> ex(n, nullptr);
+  for (size_t i = 0; i < n; ++i) {
+    if (!C_dev[i]) return OCCRI_EINVAL;
+    c[i] = C_dev[i];
+    if (KC_dev) kc[i] = KC_dev[i];
+    if (K_dev) k[i] = K_dev[i];
+    if (Ex_dev) ex[i] = Ex_dev[i];
+  }
+  if (!b->exec || c != b->c || kc != b->kc || k != b->k || ex != b->ex) {
+    b->c = c;
+    b->kc = kc;
+    b->k = k;
+    b->ex = ex;
+    const int st = occri_impl::batch_capture(b);
+    if (st != OCCRI_OK) {
+      b->c.clear();
+      return st;
+    }
+  }
+  return cudaGraphLaunch(b->exec, b->stream) == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
+}
+
+int occri_batch_sync(occri_batch* b, int* bad_cell, int* bad_k) {
+  if (bad_cell) *bad_cell = -1;
+  if (bad_k) *bad_k = -1;
+  if (!b) return OCCRI_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return OCCRI_ECUDA;
+  int first = OCCRI_OK;
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    Plan* p = b->plans[i]->p;
+    int st[2] = {0, -1};
+    if (cudaMemcpy(st, p->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return OCCRI_ECUDA;
+    if (st[0] != 0) {
+      if (cudaMemset(p->status, 0, sizeof(st)) != cudaSuccess) return OCCRI_ECUDA;
+      if (first == OCCRI_OK) {
+        first = st[0];
+        if (bad_cell) *bad_cell = (int)i;
+        if (bad_k) *bad_k = st[1];
+      }
+    }
+  }
+  return first;
+}
+
+int occri_batch_destroy(occri_batch* b) {
+  if (!b) return OCCRI_EINVAL;
+  cudaStreamSynchronize(b->stream);
+  occri_impl::batch_free(b);
+  return OCCRI_OK;
 }
 
 }  // extern "C"

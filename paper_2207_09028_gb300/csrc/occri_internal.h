@@ -186,6 +186,17 @@ template <typename T>
 cudaError_t launch_orbitals(const Plan& p, cudaStream_t s);
 template <typename T>
 cudaError_t launch_contract(const Plan& p, cudaStream_t s);
+// The same stages on other buffers (the adjoint): orbitals of the scaled coefficients cs
+// into out; scaled coefficients factor N_mu X of X into out; scale N_mu sum_r conj(chi) F
+// added into out.
+template <typename T>
+cudaError_t launch_orbitals_to(const Plan& p, const void* cs, void* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scale_to(const Plan& p, const double2* X, void* out, double factor,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_contract_field(const Plan& p, const void* F, double2* out, double scale,
+                                  cudaStream_t s);
 // F[k][i][.] *= e^{sign i k.r} over the orbital-shaped field F (psi -> periodic parts
 // with sign -1 before the pair passes, accumulated periodic parts -> Y with +1 after).
 template <typename T>

@@ -7,6 +7,11 @@ and occupied count, and runs `--builds` full exchange builds. With a 1x1x1 mesh
 one build issues exactly one wave of each pair-transform pass, which is the unit
 ncu captures; a 2x2x2 mesh adds waves with q = 1/2 on every axis (no tied bins),
 like most waves of a 6x6x6 mesh. --timing prints per-stage CUDA-event times.
+
+    python -m paper_2207_09028_gb300.prof --batch cfg4 --builds 5
+
+times the five cells of the lattice-constant scan built one after the other on one
+stream against the same cells built as one batch (one CUDA-graph launch per build).
 """
 import argparse
 import json
@@ -26,7 +31,10 @@ def main():
     ap.add_argument("--builds", type=int, default=2)
     ap.add_argument("--precision", default="mixed")
     ap.add_argument("--timing", action="store_true")
+    ap.add_argument("--batch", default=None, help="time a multi-cell config as a batch")
     args = ap.parse_args()
+    if args.batch:
+        return batch_timing(args)
     import torch
     import paper_2207_09028_gb300 as occri
     from workloads import small_workload
@@ -43,6 +51,45 @@ def main():
     if args.timing:
         out["stages"] = plan.stage_times()
     print(json.dumps(out))
+
+
+def batch_timing(args):
+    import torch
+    import paper_2207_09028_gb300 as occri
+    from workloads import config
+
+    cells = config(args.batch)
+    plans = [occri.Plan.from_workload(w, precision=args.precision) for w in cells]
+    Cs = [torch.from_numpy(w.C).cuda() for w in cells]
+    Exs = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in cells]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()                                    # warm-up (and graph capture)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.builds):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.builds
+
+    def one_by_one():
+        for pl, C, E in zip(plans, Cs, Exs):
+            pl.k_build(C, None, None, E, sync=False)
+
+    ms_seq = timed(one_by_one)
+    ex_seq = [float(e.cpu()[0]) for e in Exs]
+    batch = occri.Batch(plans)
+    ms_batch = timed(lambda: batch.build(Cs, None, None, Exs, sync=False))
+    batch.sync()
+    ex_batch = [float(e.cpu()[0]) for e in Exs]
+    print(json.dumps({"config": args.batch, "cells": len(cells), "precision": args.precision,
+                      "ms_per_build_one_by_one": ms_seq, "ms_per_build_batch": ms_batch,
+                      "speedup": ms_seq / ms_batch,
+                      "max_abs_dE_x_batch_vs_one_by_one": max(abs(a - b) for a, b in
+                                                              zip(ex_seq, ex_batch))}))
 
 
 if __name__ == "__main__":

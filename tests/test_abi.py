@@ -82,3 +82,20 @@ def test_null_arguments(lib):
     assert lib.occri_k_build(None, None, None, None, None) == occri.OCCRI_EINVAL
     assert lib.occri_vjp(None, None, 1.0, None, None) == occri.OCCRI_EINVAL
     assert lib.occri_plan_sync(None, None) == occri.OCCRI_EINVAL
+
+
+def test_batch_rejects_invalid_arguments_on_the_host(lib):
+    """occri_batch_* check their arguments before any CUDA call."""
+    vp = ctypes.c_void_p
+    out = vp(123)
+    assert lib.occri_batch_create(ctypes.byref(out), None, 1, None) == occri.OCCRI_EINVAL
+    assert out.value is None
+    none_plans = (vp * 2)(None, None)
+    assert lib.occri_batch_create(ctypes.byref(out), none_plans, 2, None) == occri.OCCRI_EINVAL
+    assert lib.occri_batch_create(ctypes.byref(out), none_plans, 0, None) == occri.OCCRI_EINVAL
+    assert lib.occri_batch_create(None, none_plans, 2, None) == occri.OCCRI_EINVAL
+    assert lib.occri_batch_build(None, none_plans, None, None, None) == occri.OCCRI_EINVAL
+    cell, k = ctypes.c_int(0), ctypes.c_int(0)
+    assert lib.occri_batch_sync(None, ctypes.byref(cell), ctypes.byref(k)) == occri.OCCRI_EINVAL
+    assert cell.value == -1 and k.value == -1
+    assert lib.occri_batch_destroy(None) == occri.OCCRI_EINVAL
