@@ -171,6 +171,23 @@ int occri_orbitals(occri_plan *plan, const void *C_dev, void *psi_dev);
 int occri_vjp(occri_plan *plan, const void *C_dev, double gEx, void *gC_dev,
               double *gomega_dev);
 
+/* Adjoint of the whole build for any seed: dL/dE_x, dL/dK_{mu i} and dL/dK (the energy
+ * of Sec. II.A, Eq. occrik and the ACE assembly, differentiated; not in the paper).
+ * gEx      : dL/dE_x.
+ * gKC_dev  : device c128 [nk][nao][nocc], the gradient of L with respect to K_{mu i}(k) in
+ *            PyTorch's convention (2 dL/dKC*), or NULL.
+ * gK_dev   : device c128 [nk][nao][nao], the same for K (any matrix; K is Hermitian, so
+ *            only the Hermitian part of the seed matters), or NULL.
+ * gC_dev   : device c128 [nk][nao][nocc] receives 2 dL/dC* (every C entry free).
+ * The assembly is differentiated in FP64. The rest recomputes, per unordered pair, the
+ * forward potential W and the potential Z of the adjoint density conj(psi_jk') g_ik +
+ * conj(g_jk') psi_ik, g_ik = sum_mu chi_mu dL/dK_{mu i}: two pair round trips per pair.
+ * With gKC_dev = gK_dev = NULL it equals occri_vjp's gC. Requires a preceding
+ * occri_k_build with the same C; the first call allocates two more orbital-sized fields.
+ * Asynchronous on the plan's stream. */
+int occri_vjp_full(occri_plan *plan, const void *C_dev, double gEx, const void *gKC_dev,
+                   const void *gK_dev, void *gC_dev);
+
 /* Sampled stage timing with CUDA events on the plan's stream. every > 0 brackets
  * every `every`-th pair wave (and every orbital, contraction and assembly stage)
  * with events; every = 0 turns timing off and discards pending samples. */

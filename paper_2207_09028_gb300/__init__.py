@@ -60,7 +60,8 @@ class occri_plan_info_t(ctypes.Structure):
 EXPORTED = ["occri_plan_create", "occri_plan_destroy", "occri_plan_info", "occri_plan_set_stream",
             "occri_plan_sync", "occri_k_build", "occri_k_build_host", "occri_orbitals",
             "occri_vjp", "occri_plan_set_timing", "occri_plan_stage_times", "occri_orbitals_noalloc",
-            "occri_batch_create", "occri_batch_build", "occri_batch_sync", "occri_batch_destroy",
+            "occri_vjp_full", "occri_batch_create", "occri_batch_build", "occri_batch_sync",
+            "occri_batch_destroy",
             "occri_status_string"]
 
 STAGES = ["orbitals", "pair_a", "pair_b", "pair_c", "contract", "assemble", "pairs"]
@@ -90,6 +91,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.occri_k_build_host.argtypes = [vp, vp, vp, vp, vp]
     lib.occri_orbitals.argtypes = [vp, vp, vp]
     lib.occri_vjp.argtypes = [vp, vp, ctypes.c_double, vp, vp]
+    lib.occri_vjp_full.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp]
     lib.occri_plan_set_timing.argtypes = [vp, ip]
     lib.occri_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong),
@@ -264,6 +266,16 @@ class Plan:
         _check(self._lib.occri_vjp(self._h, _ptr(C), float(gEx), _ptr(gC), _ptr(gw)), "occri_vjp")
         self.sync()
         return gC, gw
+
+    def vjp_full(self, C, gEx: float = 0.0, gKC=None, gK=None):
+        """occri_vjp_full: 2 dL/dC* for the seeds dL/dE_x, dL/dKC, dL/dK (after a build)."""
+        import torch
+        self.set_stream()
+        gC = torch.empty_like(C)
+        _check(self._lib.occri_vjp_full(self._h, _ptr(C), float(gEx), _ptr(gKC), _ptr(gK),
+                                        _ptr(gC)), "occri_vjp_full")
+        self.sync()
+        return gC
 
     def build(self, C, want_k: bool = True, sync: bool = True):
         """Allocate outputs and run one build: returns (KC, K or None, Ex[1])."""

@@ -328,6 +328,177 @@ __global__ void domega_finish_kernel(const double* __restrict__ acc, double s, d
   if (threadIdx.x == 0 && blockIdx.x == 0) *out = s * acc[0];
 }
 
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zmulc(double2 a, double2 b) {   // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+// Adjoint of the ACE assembly and of E_x, one CTA per k (FP64). With K = KC M^{-1} KC^H,
+// M = herm(C^H KC), E_x = (1/N_k) sum_k Re Tr M and the seeds G = dL/dK (gK, or none),
+// gKC (or none) and gE = dL/dE_x / N_k, in the convention dL = Re <grad, d.>:
+//   grad_KC = G KC M^{-1} + G^H KC M^{-1} - C H + gE C + gKC,
+//   grad_C  = -KC H + gE KC   (the part through the assembly), H = herm(M^{-1} KC^H G KC M^{-1}).
+// T = G KC and U = G^H KC are formed row by row; T + U is parked in gcf until the row of
+// grad_KC has been written.
+__global__ void __launch_bounds__(256)
+ace_adjoint_kernel(const double2* __restrict__ C, const double2* __restrict__ kc,
+                   const double2* __restrict__ mmat, const double2* __restrict__ gK,
+                   const double2* __restrict__ gKC, double gE, double2* __restrict__ gkc,
+                   double2* __restrict__ gcf, int nao, int nocc, double pivot_tol, int* status) {
+  extern __shared__ double2 sm[];
+  double2* A = sm;                     // L, then L^{-1}, then herm(H)
+  double2* Minv = sm + nocc * nocc;
+  double2* Pm = sm + 2 * nocc * nocc;  // KC^H T, then H
+  __shared__ int ok;
+  const int k = blockIdx.x;
+  const double2* Ck = C + (size_t)k * nao * nocc;
+  const double2* KCk = kc + (size_t)k * nao * nocc;
+  const double2* Mk = mmat + (size_t)k * nocc * nocc;
+  double2* gk = gkc + (size_t)k * nao * nocc;
+  double2* fk = gcf + (size_t)k * nao * nocc;
+  for (int e = threadIdx.x; e < nocc * nocc; e += blockDim.x) Pm[e] = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0) {
+    // -M = L L^H (as in the assembly), L^{-1}, then M^{-1} = -L^{-H} L^{-1}
+    ok = 1;
+    double amax = 0.0;
+    for (int j = 0; j < nocc; ++j) amax = fmax(amax, -Mk[j * nocc + j].x);
+    for (int j = 0; j < nocc && ok; ++j) {
+      double d = -Mk[j * nocc + j].x;
+      for (int l = 0; l < j; ++l) d -= A[j * nocc + l].x * A[j * nocc + l].x + A[j * nocc + l].y * A[j * nocc + l].y;
+      if (!(d > pivot_tol * amax) || !isfinite(d)) { ok = 0; break; }
+      const double ljj = sqrt(d);
+      A[j * nocc + j] = make_double2(ljj, 0.0);
+      for (int i = j + 1; i < nocc; ++i) {
+        double ar = -Mk[i * nocc + j].x, ai = -Mk[i * nocc + j].y;
+        for (int l = 0; l < j; ++l) {
+          const double2 x = A[i * nocc + l], y = A[j * nocc + l];
+          ar -= x.x * y.x + x.y * y.y;
+          ai -= x.y * y.x - x.x * y.y;
+        }
+        A[i * nocc + j] = make_double2(ar / ljj, ai / ljj);
+      }
+    }
+    if (ok) {
+      // lower-triangular inverse in place, column by column (entries below the diagonal
+      // of column j use the diagonal entries of later rows, still those of L)
+      for (int j = 0; j < nocc; ++j) {
+        const double inv = 1.0 / A[j * nocc + j].x;
+        for (int i = j + 1; i < nocc; ++i) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int l = j; l < i; ++l) {
+            const double2 a = A[i * nocc + l];   // L_il (row i is still L to the left of i)
+            const double2 b = (l == j) ? make_double2(inv, 0.0) : A[l * nocc + j];   // Linv_lj
+            acc.x += a.x * b.x - a.y * b.y;
+            acc.y += a.x * b.y + a.y * b.x;
+          }
+          const double lii = A[i * nocc + i].x;
+          A[i * nocc + j] = make_double2(-acc.x / lii, -acc.y / lii);
+        }
+      }
+      for (int j = 0; j < nocc; ++j) A[j * nocc + j] = make_double2(1.0 / A[j * nocc + j].x, 0.0);
+      for (int i = 0; i < nocc; ++i)
+        for (int j = 0; j < nocc; ++j) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int l = (i > j ? i : j); l < nocc; ++l) {
+            const double2 t = zmulc(A[l * nocc + i], A[l * nocc + j]);
+            acc.x += t.x;
+            acc.y += t.y;
+          }
+          Minv[i * nocc + j] = make_double2(-acc.x, -acc.y);
+        }
+    } else {
+      record_status(status, OCCRI_ENOTPD, k);
+    }
+  }
+  __syncthreads();
+  if (!ok) return;
+  if (gK) {   // T + U parked in gcf; Pm += KC^H T
+    const double2* Gk = gK + (size_t)k * nao * nao;
+    for (int mu = threadIdx.x; mu < nao; mu += blockDim.x) {
+      for (int j = 0; j < nocc; ++j) {
+        double2 t = make_double2(0.0, 0.0), u = make_double2(0.0, 0.0);
+        for (int nu = 0; nu < nao; ++nu) {
+          const double2 x = KCk[(size_t)nu * nocc + j];
+          const double2 a = zmul(Gk[(size_t)mu * nao + nu], x);
+          const double2 b = zmulc(Gk[(size_t)nu * nao + mu], x);
+          t.x += a.x; t.y += a.y;
+          u.x += b.x; u.y += b.y;
+        }
+        fk[(size_t)mu * nocc + j] = make_double2(t.x + u.x, t.y + u.y);
+        for (int i = 0; i < nocc; ++i) {
+          const double2 v = zmulc(KCk[(size_t)mu * nocc + i], t);
+          atomicAdd(&Pm[i * nocc + j].x, v.x);
+          atomicAdd(&Pm[i * nocc + j].y, v.y);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // H = M^{-1} Pm M^{-1} (through A), then herm(H) into A
+  for (int e = threadIdx.x; e < nocc * nocc; e += blockDim.x) {
+    const int i = e / nocc, j = e - (e / nocc) * nocc;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l < nocc; ++l) {
+      const double2 t = zmul(Pm[i * nocc + l], Minv[l * nocc + j]);
+      acc.x += t.x; acc.y += t.y;
+    }
+    A[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nocc * nocc; e += blockDim.x) {
+    const int i = e / nocc, j = e - (e / nocc) * nocc;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l < nocc; ++l) {
+      const double2 t = zmul(Minv[i * nocc + l], A[l * nocc + j]);
+      acc.x += t.x; acc.y += t.y;
+    }
+    Pm[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nocc * nocc; e += blockDim.x) {
+    const int i = e / nocc, j = e - (e / nocc) * nocc;
+    const double2 a = Pm[i * nocc + j], b = Pm[j * nocc + i];
+    A[e] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  }
+  __syncthreads();
+  for (int mu = threadIdx.x; mu < nao; mu += blockDim.x) {
+    const size_t row = (size_t)mu * nocc;
+    for (int i = 0; i < nocc; ++i) {
+      double2 g = make_double2(gE * Ck[row + i].x, gE * Ck[row + i].y);
+      if (gKC) {
+        g.x += gKC[(size_t)k * nao * nocc + row + i].x;
+        g.y += gKC[(size_t)k * nao * nocc + row + i].y;
+      }
+      for (int l = 0; l < nocc; ++l) {
+        const double2 t = zmul(Ck[row + l], A[l * nocc + i]);
+        g.x -= t.x; g.y -= t.y;
+        if (gK) {
+          const double2 v = zmul(fk[row + l], Minv[l * nocc + i]);
+          g.x += v.x; g.y += v.y;
+        }
+      }
+      gk[row + i] = g;
+    }
+    for (int i = 0; i < nocc; ++i) {
+      double2 f = make_double2(gE * KCk[row + i].x, gE * KCk[row + i].y);
+      for (int l = 0; l < nocc; ++l) {
+        const double2 t = zmul(KCk[row + l], A[l * nocc + i]);
+        f.x -= t.x; f.y -= t.y;
+      }
+      fk[row + i] = f;
+    }
+  }
+}
+
+__global__ void add_kernel(const double2* __restrict__ a, const double2* __restrict__ b,
+                           double2* __restrict__ out, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = make_double2(a[e].x + b[e].x, a[e].y + b[e].y);
+}
+
 void free_plan(Plan* p) {
   if (!p) return;
   void* bufs[] = {p->shells, p->atom_shell0, p->img_d, p->img_hi, p->img_lo, p->img_phase,
@@ -338,6 +509,8 @@ void free_plan(Plan* p) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->scratch2) cudaFree(p->scratch2);
+  for (void* b : {p->gam, p->gpsi, p->cs_g, (void*)p->gkc, (void*)p->gcf, (void*)p->gacc})
+    if (b) cudaFree(b);
   for (cudaEvent_t e : {p->ev_fork, p->ev_join, p->ev_y, p->ev_iso})
     if (e) cudaEventDestroy(e);
   if (p->aux) cudaStreamDestroy(p->aux);
@@ -517,6 +690,64 @@ int vjp_impl(Plan* p, const double2* C, double gEx, void* gC, double* gomega) {
     const double sc = -gEx * p->omega_cell * 4.0 * kPiD / ((double)p->nk * p->nk) / (ngd * ngd);
     domega_finish_kernel<<<1, 32, 0, s>>>(p->dacc, sc, gomega);
   }
+  return cudaGetLastError() == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
+}
+
+// Adjoint of the whole build for the seeds gEx, gKC, gK (see occri_vjp_full).
+template <typename T>
+int vjp_full_impl(Plan* p, const double2* C, double gEx, const double2* gKC, const double2* gK,
+                  double2* gC) {
+  using namespace occri;
+  cudaStream_t s = p->stream;
+  const size_t nkc = (size_t)p->nk * p->nao * p->nocc;
+  const size_t orb = (size_t)p->nk * p->nocc * p->fs * sizeof(cplx_t<T>);
+  const size_t csb = (p->precision == OCCRI_FP64 ? sizeof(double2) : sizeof(float4)) * nkc;
+  if (!p->gam) {   // first call: the adjoint workspaces
+    bool ok = cudaMalloc(&p->gam, orb) == cudaSuccess && cudaMalloc(&p->gpsi, orb) == cudaSuccess &&
+              cudaMalloc(&p->cs_g, csb) == cudaSuccess &&
+              cudaMalloc((void**)&p->gkc, nkc * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc((void**)&p->gcf, nkc * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc((void**)&p->gacc, nkc * sizeof(double2)) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      for (void** b : {&p->gam, &p->gpsi, &p->cs_g, (void**)&p->gkc, (void**)&p->gcf,
+                       (void**)&p->gacc}) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+      }
+      return OCCRI_ENOMEM;
+    }
+  }
+  // (f): the assembly's adjoint
+  const double tol = (p->precision == OCCRI_FP64) ? 1e-10 : 1e-5;
+  const size_t sm = 3 * sizeof(double2) * (size_t)p->nocc * p->nocc;
+  ace_adjoint_kernel<<<p->nk, 256, sm, s>>>(C, p->kc, p->mmat, gK, gKC, gEx / p->nk, p->gkc,
+                                            p->gcf, p->nao, p->nocc, tol, p->status);
+  // the adjoint orbital field g = -sum_mu chi_mu dL/dKC_mu (in units that leave out the
+  // contraction's Omega/(N_k N_g)) and the orbitals of C, both as periodic parts
+  if (launch_scale_to<T>(*p, p->gkc, p->cs_g, -1.0, s) != cudaSuccess) return OCCRI_ECUDA;
+  if (launch_orbitals_to<T>(*p, p->cs_g, p->gam, s) != cudaSuccess) return OCCRI_ECUDA;
+  if (launch_phase_fields<T>(*p, p->gam, -1, s) != cudaSuccess) return OCCRI_ECUDA;
+  if (launch_scale_c<T>(*p, C, s) != cudaSuccess) return OCCRI_ECUDA;
+  if (launch_orbitals<T>(*p, s) != cudaSuccess) return OCCRI_ECUDA;
+  if (launch_phase_fields<T>(*p, p->psi, -1, s) != cudaSuccess) return OCCRI_ECUDA;
+  // (c)+(d): two round trips per unordered pair, dL/dpsi accumulated
+  if (cudaMemsetAsync(p->gpsi, 0, orb, s) != cudaSuccess) return OCCRI_ECUDA;
+  for (int k = 0; k < p->nk; ++k)
+    for (int kp0 = k; kp0 < p->nk;) {
+      const int diag = (kp0 == k) ? 1 : 0;
+      const int nkp = diag ? 1 : std::min(p->nkp_wave, p->nk - kp0);
+      if (launch_vjp_wave<T>(*p, k, kp0, nkp, diag, s) != cudaSuccess) return OCCRI_ECUDA;
+      kp0 += nkp;
+    }
+  // (b): dL/dC_{mu i} = sum_r conj(chi_mu) dL/dpsi_i; the transforms carry N_g/(4 pi)
+  // and g carried N_k N_g/Omega, hence the factor 4 pi Omega/(N_k N_g^2)
+  if (launch_phase_fields<T>(*p, p->gpsi, +1, s) != cudaSuccess) return OCCRI_ECUDA;
+  if (cudaMemsetAsync(p->gacc, 0, nkc * sizeof(double2), s) != cudaSuccess) return OCCRI_ECUDA;
+  const double ngd = (double)p->ng;
+  const double scale = 4.0 * kPiD * p->omega_cell / ((double)p->nk * ngd * ngd);
+  if (launch_contract_field<T>(*p, p->gpsi, p->gacc, scale, s) != cudaSuccess) return OCCRI_ECUDA;
+  add_kernel<<<4 * 152, 256, 0, s>>>(p->gcf, p->gacc, gC, (long long)nkc);
   return cudaGetLastError() == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
 }
 
@@ -1121,6 +1352,20 @@ int occri_orbitals(occri_plan* plan, const void* C_dev, void* psi_dev) {
     if (e == cudaSuccess) e = occri::launch_widen<float>(*p, psi_dev, p->stream);
   }
   return e == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
+}
+
+int occri_vjp_full(occri_plan* plan, const void* C_dev, double gEx, const void* gKC_dev,
+                   const void* gK_dev, void* gC_dev) {
+  if (!plan || !C_dev || !gC_dev) return OCCRI_EINVAL;
+  Plan* p = plan->p;
+  if (!p->have_kc) return OCCRI_EINVAL;
+  const double2* C = (const double2*)C_dev;
+  const double2* gKC = (const double2*)gKC_dev;
+  const double2* gK = (const double2*)gK_dev;
+  double2* gC = (double2*)gC_dev;
+  return p->precision == OCCRI_FP64
+             ? occri_impl::vjp_full_impl<double>(p, C, gEx, gKC, gK, gC)
+             : occri_impl::vjp_full_impl<float>(p, C, gEx, gKC, gK, gC);
 }
 
 int occri_vjp(occri_plan* plan, const void* C_dev, double gEx, void* gC_dev, double* gomega_dev) {

@@ -138,6 +138,13 @@ struct Plan {
   // which both update Y_k, are ordered across the two streams (event ev_y).
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_y = nullptr, ev_iso = nullptr;
+  // adjoint workspaces, allocated by the first occri_vjp_full call
+  void* gam = nullptr;       // [nk][nocc][fs] adjoint orbital field (periodic parts)
+  void* gpsi = nullptr;      // [nk][nocc][fs] accumulated dL/dpsi (periodic parts)
+  void* cs_g = nullptr;      // scaled coefficients of -dL/dKC (like cs)
+  double2* gkc = nullptr;    // [nk][nao][nocc] dL/dKC after the assembly's adjoint
+  double2* gcf = nullptr;    // [nk][nao][nocc] dL/dC through the assembly alone
+  double2* gacc = nullptr;   // [nk][nao][nocc] dL/dC through the orbitals
   double2* kc = nullptr;     // [nk][nao][nocc]
   double2* xi = nullptr;     // [nk][nao][nocc]
   double2* mmat = nullptr;   // [nk][nocc][nocc]
@@ -211,6 +218,10 @@ cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, int diag, c
                              void* S, cudaEvent_t* ev = nullptr, cudaEvent_t ev_y = nullptr);
 template <typename T>
 cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s);
+// One wave of the adjoint build: forward potentials in scratch, adjoint potentials in
+// scratch2, their contributions added to gpsi (uses psi and gam).
+template <typename T>
+cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s);
 
 // fields and pass-C targets of a wave
 __host__ __device__ inline int wave_fields(int nocc, int nkp, int diag) {

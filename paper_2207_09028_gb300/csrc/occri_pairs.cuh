@@ -451,9 +451,12 @@ __device__ __forceinline__ T bin_value(const PairParams& p, const Consts<T>& k,
 // ------------------------------------------------------------------ pass A
 // plane n1 of field (i, j): rho = conj(u_jk') u_ik (= conj(psi_jk') psi_ik e^{-iq.r}, the
 // orbitals being held as their periodic parts u); FFT along n3, then n2.
-template <typename T, int N>
+// With ADJ (the adjoint build): the field is sigma = conj(u_jk') g_ik + conj(g_jk') u_ik,
+// g being the adjoint orbital field, i.e. the change of rho when u moves along g.
+template <typename T, int N, bool ADJ = false>
 __global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
-pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams p) {
+pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams p,
+       const cplx_t<T>* __restrict__ gam = nullptr) {
   using C2 = cplx_t<T>;
   constexpr int P = pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -465,11 +468,24 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
   // plane n1 of the periodic parts: N rows (n3) of N contiguous points (n2)
   const C2* pi = psi + (size_t)(p.k * p.nocc + fi.i) * p.fs + (size_t)n1 * N;
   const C2* pj = psi + (size_t)(kp * p.nocc + fi.j) * p.fs + (size_t)n1 * N;
+  if constexpr (ADJ) {
+    const C2* gi = gam + (size_t)(p.k * p.nocc + fi.i) * p.fs + (size_t)n1 * N;
+    const C2* gj = gam + (size_t)(kp * p.nocc + fi.j) * p.fs + (size_t)n1 * N;
+#pragma unroll 2
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+      const int n3 = e / N, n2 = e - (e / N) * N;
+      const size_t off = (size_t)n3 * N * N + n2;
+      const C2 a = cmulc<T>(__ldg(pj + off), __ldg(gi + off));
+      const C2 b = cmulc<T>(__ldg(gj + off), __ldg(pi + off));
+      pl[n2 * P + n3] = mk<T>(a.x + b.x, a.y + b.y);
+    }
+  } else {
 #pragma unroll 4
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int n3 = e / N, n2 = e - (e / N) * N;
-    const size_t off = (size_t)n3 * N * N + n2;
-    pl[n2 * P + n3] = cmulc<T>(__ldg(pj + off), __ldg(pi + off));
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+      const int n3 = e / N, n2 = e - (e / N) * N;
+      const size_t off = (size_t)n3 * N * N + n2;
+      pl[n2 * P + n3] = cmulc<T>(__ldg(pj + off), __ldg(pi + off));
+    }
   }
   __syncthreads();
 #pragma unroll 1
@@ -996,6 +1012,118 @@ cudaError_t launch_pass_d(const PairParams& p, const cplx_t<T>* S, const cplx_t<
   return launch_pass_d_noc<T, 32>(p, S, psi, Y, st);
 }
 
+// ------------------------------------------------------------------ pass E (adjoint)
+// The adjoint of the Y accumulation and of the pair densities, per grid point (fields'
+// point order, periodic parts). With W the potentials of the wave's fields (scratch SW)
+// and Z the potentials of their adjoint densities sigma (scratch SZ), g the adjoint
+// orbital field and u the orbitals, every unordered pair (k, k', i, j) adds
+//   G_ik  += u_jk' Z_ij + g_jk' W_ij,      G_jk' += u_ik conj(Z_ij) + g_ik conj(W_ij),
+// a field (k, k, i, i) of a diagonal wave only the first. NOC >= nocc.
+template <typename T, int NOC>
+__global__ void __launch_bounds__(256)
+pass_e(const cplx_t<T>* __restrict__ SW, const cplx_t<T>* __restrict__ SZ,
+       const cplx_t<T>* __restrict__ psi, const cplx_t<T>* __restrict__ gam,
+       cplx_t<T>* __restrict__ G, PairParams p) {
+  using C2 = cplx_t<T>;
+  const long long ng = p.ng;
+  const int nocc = p.nocc;
+  auto mac = [](C2& acc, C2 a, C2 b) {   // acc += a * b
+    acc.x += a.x * b.x - a.y * b.y;
+    acc.y += a.x * b.y + a.y * b.x;
+  };
+  auto macc = [](C2& acc, C2 a, C2 b) {   // acc += a * conj(b)
+    acc.x += a.x * b.x + a.y * b.y;
+    acc.y += a.y * b.x - a.x * b.y;
+  };
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < ng;
+       r += (long long)gridDim.x * blockDim.x) {
+    C2 uk[NOC], gk[NOC], acc[NOC];
+#pragma unroll
+    for (int i = 0; i < NOC; ++i) {
+      uk[i] = gk[i] = acc[i] = mk<T>(T(0), T(0));
+      if (i < nocc) {
+        uk[i] = __ldg(psi + (size_t)(p.k * nocc + i) * p.fs + r);
+        gk[i] = __ldg(gam + (size_t)(p.k * nocc + i) * p.fs + r);
+      }
+    }
+    if (p.diag) {
+#pragma unroll
+      for (int j = 0; j < NOC; ++j) {
+        if (j >= nocc) break;
+#pragma unroll
+        for (int i = 0; i <= j; ++i) {
+          const size_t f = (size_t)diag_field(i, j, nocc) * p.fs + r;
+          const C2 w = __ldg(SW + f), z = __ldg(SZ + f);
+          mac(acc[i], uk[j], z);
+          mac(acc[i], gk[j], w);
+          if (i < j) {
+            macc(acc[j], uk[i], z);
+            macc(acc[j], gk[i], w);
+          }
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int kpl = 0; kpl < p.nkp; ++kpl) {
+        const int kp = p.kp0 + kpl;
+        C2 uq[NOC], gq[NOC], accq[NOC];
+#pragma unroll
+        for (int j = 0; j < NOC; ++j) {
+          uq[j] = gq[j] = accq[j] = mk<T>(T(0), T(0));
+          if (j < nocc) {
+            uq[j] = __ldg(psi + (size_t)(kp * nocc + j) * p.fs + r);
+            gq[j] = __ldg(gam + (size_t)(kp * nocc + j) * p.fs + r);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < NOC; ++i) {
+          if (i >= nocc) break;
+#pragma unroll
+          for (int j = 0; j < NOC; ++j) {
+            if (j >= nocc) break;
+            const size_t f = (size_t)((kpl * nocc + i) * nocc + j) * p.fs + r;
+            const C2 w = __ldg(SW + f), z = __ldg(SZ + f);
+            mac(acc[i], uq[j], z);
+            mac(acc[i], gq[j], w);
+            macc(accq[j], uk[i], z);
+            macc(accq[j], gk[i], w);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NOC; ++j) {
+          if (j >= nocc) break;
+          C2* g = G + (size_t)(kp * nocc + j) * p.fs + r;
+          C2 v = *g;
+          v.x += accq[j].x;
+          v.y += accq[j].y;
+          *g = v;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NOC; ++i) {
+      if (i >= nocc) break;
+      C2* g = G + (size_t)(p.k * nocc + i) * p.fs + r;
+      C2 v = *g;
+      v.x += acc[i].x;
+      v.y += acc[i].y;
+      *g = v;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_pass_e(const PairParams& p, const cplx_t<T>* SW, const cplx_t<T>* SZ,
+                          const cplx_t<T>* psi, const cplx_t<T>* gam, cplx_t<T>* G,
+                          cudaStream_t st) {
+  const unsigned nb = (unsigned)std::min<long long>((p.ng + 255) / 256, 152LL * 8);
+  if (p.nocc <= 4) pass_e<T, 4><<<nb, 256, 0, st>>>(SW, SZ, psi, gam, G, p);
+  else if (p.nocc <= 8) pass_e<T, 8><<<nb, 256, 0, st>>>(SW, SZ, psi, gam, G, p);
+  else if (p.nocc <= 16) pass_e<T, 16><<<nb, 256, 0, st>>>(SW, SZ, psi, gam, G, p);
+  else pass_e<T, 32><<<nb, 256, 0, st>>>(SW, SZ, psi, gam, G, p);
+  return cudaGetLastError();
+}
+
 template <int N> constexpr size_t smem_a(size_t csz) { return csz * N * pitch(N); }
 template <int N> constexpr size_t smem_b(size_t csz, size_t tab) {
   return kPassBBuffers * csz * N * pitch(N) + N * tab + csz / 2 * N * N;
@@ -1054,6 +1182,39 @@ cudaError_t run_domega_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>
   pass_a<T, N><<<dim3(N, nf), nt, sa, st>>>(psi, S, p);
   pass_b_domega<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S, p, dacc);
   return cudaGetLastError();
+}
+
+// One wave of the adjoint: the forward potentials W into S0, the potentials Z of the
+// adjoint densities into S1 (the same three transform passes), then pass E.
+template <typename T, int N>
+cudaError_t run_vjp_wave(const PairParams& p, const cplx_t<T>* psi, const cplx_t<T>* gam,
+                         cplx_t<T>* S0, cplx_t<T>* S1, cplx_t<T>* G, cudaStream_t st) {
+  using C2 = cplx_t<T>;
+  const int nt = threads_for(N);
+  const int nf = wave_fields(p.nocc, p.nkp, p.diag);
+  const size_t sa = smem_a<N>(sizeof(C2));
+  const size_t sb = smem_b<N>(sizeof(C2), sizeof(Axis1<T>));
+  const size_t sc = smem_c<N>(sizeof(C2));
+  static bool configured = false;
+  static int slots_b = 1;
+  if (!configured) {
+    cudaFuncSetAttribute(pass_a<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sa);
+    cudaFuncSetAttribute(pass_a<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sa);
+    cudaFuncSetAttribute(pass_b<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    cudaFuncSetAttribute(pass_c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+    slots_b = resident_slots(pass_b<T, N>, nt, sb);
+    configured = true;
+  }
+  pass_a<T, N, false><<<dim3(N, nf), nt, sa, st>>>(psi, S0, p, nullptr);
+  pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S0, p);
+  pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S0, p);
+  pass_a<T, N, true><<<dim3(N, nf), nt, sa, st>>>(psi, S1, p, gam);
+  pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S1, p);
+  pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S1, p);
+  const cudaError_t e = launch_pass_e<T>(p, S0, S1, psi, gam, G, st);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace pairs

@@ -46,6 +46,31 @@ cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag,
   }
 }
 
+template <typename T>
+cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s) {
+  PairParams pp = p.pair_params();
+  pp.k = k;
+  pp.kp0 = kp0;
+  pp.nkp = nkp;
+  pp.diag = diag;
+  const cplx_t<T>* psi = (const cplx_t<T>*)p.psi;
+  const cplx_t<T>* gam = (const cplx_t<T>*)p.gam;
+  cplx_t<T>* S0 = (cplx_t<T>*)p.scratch;
+  cplx_t<T>* S1 = (cplx_t<T>*)p.scratch2;
+  cplx_t<T>* G = (cplx_t<T>*)p.gpsi;
+  switch (p.N[0]) {
+#define OCCRI_VJP_CASE(NN) \
+  case NN:                 \
+    return pairs::run_vjp_wave<T, NN>(pp, psi, gam, S0, S1, G, s);
+    OCCRI_FOR_EACH_N(OCCRI_VJP_CASE)
+#undef OCCRI_VJP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_vjp_wave<float>(const Plan&, int, int, int, int, cudaStream_t);
+template cudaError_t launch_vjp_wave<double>(const Plan&, int, int, int, int, cudaStream_t);
 template cudaError_t launch_pair_wave<float>(const Plan&, int, int, int, int, cudaStream_t, void*,
                                              cudaEvent_t*, cudaEvent_t);
 template cudaError_t launch_pair_wave<double>(const Plan&, int, int, int, int, cudaStream_t, void*,

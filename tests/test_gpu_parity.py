@@ -230,6 +230,73 @@ def test_adjoint_matches_central_differences(torch_cuda, kind, g0_mode):
     assert abs(float(om.grad) - ref) <= 1e-10 * abs(ref)
 
 
+# ------------------------------------------------------------------ full adjoint (any seed)
+
+def _oracle_loss(w, C, G, H):
+    """L(C) = Re sum conj(G) K(C) + Re sum conj(H) KC(C), all from the FP64 oracle."""
+    chi = O.bloch_aos(w.lattice, w.xyz, w.shell_atom, w.shell_l, w.shell_alpha, w.kfrac,
+                      grid=w.grid)
+    psi = O.orbitals_on_grid(chi, C)
+    g0 = O.g0_value(w.kernel, w.omega, w.g0_mode)
+    kc = O.occri_kc(w.lattice, w.grid, w.kfrac, psi, chi, w.kernel, w.omega, g0)
+    k, _, _ = O.ace_assemble(C, kc)
+    return float(np.real(np.sum(np.conj(G) * k)) + np.real(np.sum(np.conj(H) * kc)))
+
+
+@pytest.mark.parametrize("kind,g0_mode,mesh", [("coulomb", 0, (1, 1, 2)), ("erfc", 1, (2, 1, 1))])
+def test_full_adjoint_matches_oracle_central_differences(torch_cuda, kind, g0_mode, mesh):
+    """occri_vjp_full with seeds on K and on K_{mu i}: the directional derivative
+    Re <gC, d> equals central differences of the FP64 oracle's loss."""
+    import paper_2207_09028_gb300 as occri
+    torch = torch_cuda
+    w = small_workload(mesh=mesh, grid=(9, 9, 9), counts=(2, 1), nocc=2, kernel=kind,
+                       omega=0.4, g0_mode=g0_mode, seed=31)
+    rng = np.random.default_rng(5)
+    G = rng.standard_normal((w.nk, w.nao, w.nao)) + 1j * rng.standard_normal((w.nk, w.nao, w.nao))
+    H = rng.standard_normal(w.C.shape) + 1j * rng.standard_normal(w.C.shape)
+    plan = occri.Plan.from_workload(w, precision="fp64")
+    C = torch.from_numpy(w.C).cuda()
+    plan.build(C)
+    gC = plan.vjp_full(C, 0.0, torch.from_numpy(H).cuda(), torch.from_numpy(G).cuda())
+    gC = gC.cpu().numpy()
+    h = 1e-5
+    for trial in range(2):
+        d = rng.standard_normal(w.C.shape) + 1j * rng.standard_normal(w.C.shape)
+        fd = (_oracle_loss(w, w.C + h * d, G, H) - _oracle_loss(w, w.C - h * d, G, H)) / (2 * h)
+        an = float(np.real(np.sum(np.conj(gC) * d)))
+        assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-3), (trial, fd, an)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 2e-5)])
+def test_full_adjoint_with_energy_seed_reduces_to_4KC_over_nk(torch_cuda, precision, tol):
+    """With only dL/dE_x the full adjoint (assembly adjoint, adjoint orbital field, two
+    round trips per pair, contraction) must give (4/N_k) K_{mu i} times the seed."""
+    import paper_2207_09028_gb300 as occri
+    torch = torch_cuda
+    w = small_workload(mesh=(1, 2, 1), grid=(12, 12, 12), counts=(2, 1, 1), nocc=3, seed=44)
+    plan = occri.Plan.from_workload(w, precision=precision)
+    C = torch.from_numpy(w.C).cuda()
+    KC, _, _ = plan.build(C, want_k=False)
+    gC = plan.vjp_full(C, 1.7).cpu().numpy()
+    ref = 1.7 * 4.0 / w.nk * KC.cpu().numpy()
+    assert np.abs(gC - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_full_adjoint_mixed_matches_fp64(torch_cuda):
+    import paper_2207_09028_gb300 as occri
+    torch = torch_cuda
+    w = small_workload(mesh=(1, 1, 2), grid=(12, 12, 12), counts=(2, 1), nocc=3, seed=45)
+    rng = np.random.default_rng(6)
+    G = torch.from_numpy(rng.standard_normal((w.nk, w.nao, w.nao)) + 0j).cuda()
+    out = {}
+    for prec in ("fp64", "mixed"):
+        plan = occri.Plan.from_workload(w, precision=prec)
+        C = torch.from_numpy(w.C).cuda()
+        plan.build(C)
+        out[prec] = plan.vjp_full(C, 0.3, None, G).cpu().numpy()
+    assert np.abs(out["mixed"] - out["fp64"]).max() <= 1e-5 * np.abs(out["fp64"]).max()
+
+
 # ------------------------------------------------------------------ paper scale, sampled
 
 def test_config5_mixed_properties_and_orbital_samples(torch_cuda):
