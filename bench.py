@@ -179,6 +179,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        cfg = dict(cfg, precision="FP64 CPU oracle (numpy), one core")
         samples = []
         for _ in range(args.warmup + args.steps):
             t, desc, wall = oracle_sample_seconds(w)

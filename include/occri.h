@@ -179,14 +179,17 @@ int occri_vjp(occri_plan *plan, const void *C_dev, double gEx, void *gC_dev,
  * gK_dev   : device c128 [nk][nao][nao], the same for K (any matrix; K is Hermitian, so
  *            only the Hermitian part of the seed matters), or NULL.
  * gC_dev   : device c128 [nk][nao][nocc] receives 2 dL/dC* (every C entry free).
+ * gomega_dev: device double receives dL/d omega through the kernel (zero for Coulomb), or
+ *            NULL; it adds, per unordered pair, sum_m (dv_q(m)/d omega) Re(conj(sigma^) rho^)
+ *            with sigma the adjoint density below.
  * The assembly is differentiated in FP64. The rest recomputes, per unordered pair, the
  * forward potential W and the potential Z of the adjoint density conj(psi_jk') g_ik +
  * conj(g_jk') psi_ik, g_ik = sum_mu chi_mu dL/dK_{mu i}: two pair round trips per pair.
- * With gKC_dev = gK_dev = NULL it equals occri_vjp's gC. Requires a preceding
+ * With gKC_dev = gK_dev = NULL it equals occri_vjp's gC and gomega. Requires a preceding
  * occri_k_build with the same C; the first call allocates two more orbital-sized fields.
  * Asynchronous on the plan's stream. */
 int occri_vjp_full(occri_plan *plan, const void *C_dev, double gEx, const void *gKC_dev,
-                   const void *gK_dev, void *gC_dev);
+                   const void *gK_dev, void *gC_dev, double *gomega_dev);
 
 /* Sampled stage timing with CUDA events on the plan's stream. every > 0 brackets
  * every `every`-th pair wave (and every orbital, contraction and assembly stage)

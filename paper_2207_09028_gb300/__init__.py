@@ -91,7 +91,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.occri_k_build_host.argtypes = [vp, vp, vp, vp, vp]
     lib.occri_orbitals.argtypes = [vp, vp, vp]
     lib.occri_vjp.argtypes = [vp, vp, ctypes.c_double, vp, vp]
-    lib.occri_vjp_full.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp]
+    lib.occri_vjp_full.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp, vp]
     lib.occri_plan_set_timing.argtypes = [vp, ip]
     lib.occri_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong),
@@ -267,15 +267,17 @@ class Plan:
         self.sync()
         return gC, gw
 
-    def vjp_full(self, C, gEx: float = 0.0, gKC=None, gK=None):
-        """occri_vjp_full: 2 dL/dC* for the seeds dL/dE_x, dL/dKC, dL/dK (after a build)."""
+    def vjp_full(self, C, gEx: float = 0.0, gKC=None, gK=None, want_omega: bool = False):
+        """occri_vjp_full: 2 dL/dC* (and dL/d omega) for the seeds dL/dE_x, dL/dKC, dL/dK
+        (after a build). Returns gC, or (gC, d omega) with want_omega."""
         import torch
         self.set_stream()
         gC = torch.empty_like(C)
+        gw = torch.zeros(1, dtype=torch.float64, device=C.device) if want_omega else None
         _check(self._lib.occri_vjp_full(self._h, _ptr(C), float(gEx), _ptr(gKC), _ptr(gK),
-                                        _ptr(gC)), "occri_vjp_full")
+                                        _ptr(gC), _ptr(gw)), "occri_vjp_full")
         self.sync()
-        return gC
+        return (gC, float(gw.cpu()[0])) if want_omega else gC
 
     def build(self, C, want_k: bool = True, sync: bool = True):
         """Allocate outputs and run one build: returns (KC, K or None, Ex[1])."""

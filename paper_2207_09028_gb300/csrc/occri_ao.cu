@@ -326,13 +326,13 @@ __global__ void scale_c_kernel_f(const double2* __restrict__ C, const double* __
 // One warp per point block, four blocks per CTA; KB k-points per thread.
 template <typename T, int NI, int KB>
 __global__ void __launch_bounds__(128)
-orbitals_kernel(AOParams p, cplx_t<T>* __restrict__ psi, int i0) {
+orbitals_kernel(AOParams p, cplx_t<T>* __restrict__ psi, int i0, int kbase = 0) {
   const int blk = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (blk >= p.nblk) return;
   bool valid;
   long long q;
   const long long n = block_point(p, blk, threadIdx.x & 31, &valid, &q);
-  const int k0 = blockIdx.y * KB;
+  const int k0 = kbase + blockIdx.y * KB;
   T ar[KB][NI], ai[KB][NI];
 #pragma unroll
   for (int b = 0; b < KB; ++b)
@@ -376,11 +376,12 @@ orbitals_kernel(AOParams p, cplx_t<T>* __restrict__ psi, int i0) {
 template <typename T, int L, int NI>
 __global__ void __launch_bounds__(256)
 contract_kernel(AOParams p, const cplx_t<T>* __restrict__ Y, double2* __restrict__ kc,
-                const int* __restrict__ shell_list, int i0, long long chunk, double scale) {
+                const int* __restrict__ shell_list, int i0, long long chunk, double scale,
+                int kbase) {
   constexpr int NM = 2 * L + 1;
   constexpr int NV = 2 * NM * NI;
   const int s = shell_list[blockIdx.z];
-  const int k = blockIdx.y;
+  const int k = kbase + blockIdx.y;
   const ShellDev sh = p.shells[s];
   const int start = blockIdx.x * (int)chunk;
   const int end = min(p.nblk, start + (int)chunk);
@@ -472,14 +473,14 @@ __global__ void widen_kernel(const cplx_t<T>* __restrict__ in, double2* __restri
 // 2 pi sum_d kint_d n_d / (D_d N), reduced exactly in integers.
 template <typename T>
 __global__ void phase_fields_kernel(cplx_t<T>* __restrict__ F, const int* __restrict__ kint,
-                                    int nk, int nocc, int N, long long fs, int D0, int D1, int D2,
-                                    int sign) {
+                                    int k0, int nk, int nocc, int N, long long fs, int D0, int D1,
+                                    int D2, int sign) {
   const long long ng = (long long)N * N * N;
   const long long Dc = (long long)D0 * D1 * D2;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nk * ng;
        e += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(e / ng);
-    const long long q = e - (long long)k * ng;
+    const int k = k0 + (int)(e / ng);
+    const long long q = e - (long long)(k - k0) * ng;
     const int n3 = (int)(q / ((long long)N * N));
     const int rem = (int)(q - (long long)n3 * N * N);
     const int n1 = rem / N, n2 = rem - (rem / N) * N;
@@ -511,28 +512,31 @@ cudaError_t launch_scale_c<float>(const Plan& p, const double2* C, cudaStream_t 
 }
 
 template <typename T>
-cudaError_t launch_phase_fields(const Plan& p, void* F, int sign, cudaStream_t s) {
-  ao::phase_fields_kernel<T><<<8 * 152, 256, 0, s>>>((cplx_t<T>*)F, p.kint, p.nk, p.nocc, p.N[0],
-                                                      p.fs, p.D[0], p.D[1], p.D[2], sign);
+cudaError_t launch_phase_fields(const Plan& p, void* F, int sign, cudaStream_t s, int k0, int nkk) {
+  if (nkk < 0) nkk = p.nk - k0;
+  ao::phase_fields_kernel<T><<<8 * 152, 256, 0, s>>>((cplx_t<T>*)F, p.kint, k0, nkk, p.nocc,
+                                                      p.N[0], p.fs, p.D[0], p.D[1], p.D[2], sign);
   return cudaGetLastError();
 }
-template cudaError_t launch_phase_fields<float>(const Plan&, void*, int, cudaStream_t);
-template cudaError_t launch_phase_fields<double>(const Plan&, void*, int, cudaStream_t);
+template cudaError_t launch_phase_fields<float>(const Plan&, void*, int, cudaStream_t, int, int);
+template cudaError_t launch_phase_fields<double>(const Plan&, void*, int, cudaStream_t, int, int);
 
 template <typename T>
-cudaError_t launch_orbitals_to(const Plan& p, const void* cs, void* out, cudaStream_t s) {
+cudaError_t launch_orbitals_to(const Plan& p, const void* cs, void* out, cudaStream_t s, int k0,
+                               int nkk) {
   constexpr int NI = kOrbChunk, KB = orbital_kbatch<T>();
+  if (nkk < 0) nkk = p.nk - k0;
   AOParams ap = p.ao_params();
   ap.cs = cs;
-  dim3 grid((unsigned)((p.nblk + 3) / 4), (p.nk + KB - 1) / KB);
+  dim3 grid((unsigned)((p.nblk + 3) / 4), (nkk + KB - 1) / KB);
   for (int i0 = 0; i0 < p.nocc; i0 += NI)
-    ao::orbitals_kernel<T, NI, KB><<<grid, 128, 0, s>>>(ap, (cplx_t<T>*)out, i0);
+    ao::orbitals_kernel<T, NI, KB><<<grid, 128, 0, s>>>(ap, (cplx_t<T>*)out, i0, k0);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_orbitals(const Plan& p, cudaStream_t s) {
-  return launch_orbitals_to<T>(p, p.cs, p.psi, s);
+  return launch_orbitals_to<T>(p, p.cs, p.psi, s, 0, -1);
 }
 
 // Scaled coefficients factor N_mu X^k_{mu i} of any [nk][nao][nocc] c128 array X, in the
@@ -556,39 +560,40 @@ cudaError_t launch_scale_to<float>(const Plan& p, const double2* X, void* out, d
 
 template <typename T, int L>
 static void launch_contract_l(const Plan& p, const AOParams& ap, const void* Yf, double2* out,
-                              double scale, cudaStream_t s) {
+                              double scale, cudaStream_t s, int k0, int nkk) {
   constexpr int NI = contract_chunk<T>();
   const int ns = (int)p.shells_by_l[L].size();
   if (ns == 0) return;
   const long long target = 4LL * 152 * 8;   // CTAs to fill the GPU several times over
-  long long parts = (target + (long long)p.nk * ns - 1) / ((long long)p.nk * ns);
+  long long parts = (target + (long long)nkk * ns - 1) / ((long long)nkk * ns);
   const long long maxparts = (p.nblk + 31) / 32;   // at least 32 point blocks per CTA
   if (parts > maxparts) parts = maxparts;
   if (parts < 1) parts = 1;
   const long long chunk = (p.nblk + parts - 1) / parts;
   for (int i0 = 0; i0 < p.nocc; i0 += NI)
-    ao::contract_kernel<T, L, NI><<<dim3((unsigned)parts, p.nk, ns), 256, 0, s>>>(
-        ap, (const cplx_t<T>*)Yf, out, p.shell_list_l[L], i0, chunk, scale);
+    ao::contract_kernel<T, L, NI><<<dim3((unsigned)parts, nkk, ns), 256, 0, s>>>(
+        ap, (const cplx_t<T>*)Yf, out, p.shell_list_l[L], i0, chunk, scale, k0);
 }
 
 // out[k][mu][i] += scale N_mu sum_r conj(chi~_{mu k}(r)) F_ik(r) for an orbital-shaped field F
 template <typename T>
 cudaError_t launch_contract_field(const Plan& p, const void* F, double2* out, double scale,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int k0, int nkk) {
+  if (nkk < 0) nkk = p.nk - k0;
   const AOParams ap = p.ao_params();
-  launch_contract_l<T, 0>(p, ap, F, out, scale, s);
-  launch_contract_l<T, 1>(p, ap, F, out, scale, s);
-  launch_contract_l<T, 2>(p, ap, F, out, scale, s);
-  launch_contract_l<T, 3>(p, ap, F, out, scale, s);
+  launch_contract_l<T, 0>(p, ap, F, out, scale, s, k0, nkk);
+  launch_contract_l<T, 1>(p, ap, F, out, scale, s, k0, nkk);
+  launch_contract_l<T, 2>(p, ap, F, out, scale, s, k0, nkk);
+  launch_contract_l<T, 3>(p, ap, F, out, scale, s, k0, nkk);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_contract(const Plan& p, cudaStream_t s) {
+cudaError_t launch_contract(const Plan& p, cudaStream_t s, int k0, int nkk) {
   // Y carries N_g/(4 pi) (see PairParams), hence -Omega 4 pi / (N_k N_g^2)
   const double scale = -p.omega_cell * 4.0 * 3.14159265358979323846 /
                        ((double)p.nk * (double)p.ng * (double)p.ng);
-  return launch_contract_field<T>(p, p.Y, p.kc, scale, s);
+  return launch_contract_field<T>(p, p.Y, p.kc, scale, s, k0, nkk);
 }
 
 template <typename T>
@@ -601,14 +606,16 @@ cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s) {
 
 template cudaError_t launch_orbitals<float>(const Plan&, cudaStream_t);
 template cudaError_t launch_orbitals<double>(const Plan&, cudaStream_t);
-template cudaError_t launch_orbitals_to<float>(const Plan&, const void*, void*, cudaStream_t);
-template cudaError_t launch_orbitals_to<double>(const Plan&, const void*, void*, cudaStream_t);
+template cudaError_t launch_orbitals_to<float>(const Plan&, const void*, void*, cudaStream_t, int,
+                                               int);
+template cudaError_t launch_orbitals_to<double>(const Plan&, const void*, void*, cudaStream_t, int,
+                                                int);
 template cudaError_t launch_contract_field<float>(const Plan&, const void*, double2*, double,
-                                                  cudaStream_t);
+                                                  cudaStream_t, int, int);
 template cudaError_t launch_contract_field<double>(const Plan&, const void*, double2*, double,
-                                                   cudaStream_t);
-template cudaError_t launch_contract<float>(const Plan&, cudaStream_t);
-template cudaError_t launch_contract<double>(const Plan&, cudaStream_t);
+                                                   cudaStream_t, int, int);
+template cudaError_t launch_contract<float>(const Plan&, cudaStream_t, int, int);
+template cudaError_t launch_contract<double>(const Plan&, cudaStream_t, int, int);
 template cudaError_t launch_widen<float>(const Plan&, void*, cudaStream_t);
 template cudaError_t launch_widen<double>(const Plan&, void*, cudaStream_t);
 

@@ -547,18 +547,20 @@ cudaEvent_t take_event(Plan* p) {
 // Bracket one stage with a pair of events (no-op when timing is off).
 struct StageTimer {
   Plan* p;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  StageTimer(Plan* pl, bool on) : p(pl) {
+  StageTimer(Plan* pl, bool on, cudaStream_t stream = nullptr)
+      : p(pl), st(stream ? stream : pl->stream) {
     if (on) {
       a = take_event(p);
-      if (a) cudaEventRecord(a, p->stream);
+      if (a) cudaEventRecord(a, st);
     }
   }
   void done(int stage, double units) {
     if (!a) return;
     cudaEvent_t b = take_event(p);
     if (!b) return;
-    cudaEventRecord(b, p->stream);
+    cudaEventRecord(b, st);
     p->ev_pending.push_back(Plan::TimedSpan{a, b, stage, units});
   }
 };
@@ -696,7 +698,7 @@ int vjp_impl(Plan* p, const double2* C, double gEx, void* gC, double* gomega) {
 // Adjoint of the whole build for the seeds gEx, gKC, gK (see occri_vjp_full).
 template <typename T>
 int vjp_full_impl(Plan* p, const double2* C, double gEx, const double2* gKC, const double2* gK,
-                  double2* gC) {
+                  double2* gC, double* gomega) {
   using namespace occri;
   cudaStream_t s = p->stream;
   const size_t nkc = (size_t)p->nk * p->nao * p->nocc;
@@ -731,13 +733,18 @@ int vjp_full_impl(Plan* p, const double2* C, double gEx, const double2* gKC, con
   if (launch_scale_c<T>(*p, C, s) != cudaSuccess) return OCCRI_ECUDA;
   if (launch_orbitals<T>(*p, s) != cudaSuccess) return OCCRI_ECUDA;
   if (launch_phase_fields<T>(*p, p->psi, -1, s) != cudaSuccess) return OCCRI_ECUDA;
-  // (c)+(d): two round trips per unordered pair, dL/dpsi accumulated
+  // (c)+(d): two round trips per unordered pair, dL/dpsi accumulated (and the omega
+  // term of the kernel's derivative, for the erfc and erf kernels)
   if (cudaMemsetAsync(p->gpsi, 0, orb, s) != cudaSuccess) return OCCRI_ECUDA;
+  const bool want_w = gomega && p->kernel.kind != OCCRI_COULOMB;
+  if (gomega && cudaMemsetAsync(p->dacc, 0, 2 * sizeof(double), s) != cudaSuccess)
+    return OCCRI_ECUDA;
   for (int k = 0; k < p->nk; ++k)
     for (int kp0 = k; kp0 < p->nk;) {
       const int diag = (kp0 == k) ? 1 : 0;
       const int nkp = diag ? 1 : std::min(p->nkp_wave, p->nk - kp0);
-      if (launch_vjp_wave<T>(*p, k, kp0, nkp, diag, s) != cudaSuccess) return OCCRI_ECUDA;
+      if (launch_vjp_wave<T>(*p, k, kp0, nkp, diag, want_w ? p->dacc : nullptr, s) != cudaSuccess)
+        return OCCRI_ECUDA;
       kp0 += nkp;
     }
   // (b): dL/dC_{mu i} = sum_r conj(chi_mu) dL/dpsi_i; the transforms carry N_g/(4 pi)
@@ -748,6 +755,8 @@ int vjp_full_impl(Plan* p, const double2* C, double gEx, const double2* gKC, con
   const double scale = 4.0 * kPiD * p->omega_cell / ((double)p->nk * ngd * ngd);
   if (launch_contract_field<T>(*p, p->gpsi, p->gacc, scale, s) != cudaSuccess) return OCCRI_ECUDA;
   add_kernel<<<4 * 152, 256, 0, s>>>(p->gcf, p->gacc, gC, (long long)nkc);
+  // dL/d omega = Re <dL/dKC, dKC/d omega>: the same units as the gradient of C
+  if (gomega) domega_finish_kernel<<<1, 32, 0, s>>>(p->dacc, scale, gomega);
   return cudaGetLastError() == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
 }
 
@@ -1355,7 +1364,7 @@ int occri_orbitals(occri_plan* plan, const void* C_dev, void* psi_dev) {
 }
 
 int occri_vjp_full(occri_plan* plan, const void* C_dev, double gEx, const void* gKC_dev,
-                   const void* gK_dev, void* gC_dev) {
+                   const void* gK_dev, void* gC_dev, double* gomega_dev) {
   if (!plan || !C_dev || !gC_dev) return OCCRI_EINVAL;
   Plan* p = plan->p;
   if (!p->have_kc) return OCCRI_EINVAL;
@@ -1364,8 +1373,8 @@ int occri_vjp_full(occri_plan* plan, const void* C_dev, double gEx, const void* 
   const double2* gK = (const double2*)gK_dev;
   double2* gC = (double2*)gC_dev;
   return p->precision == OCCRI_FP64
-             ? occri_impl::vjp_full_impl<double>(p, C, gEx, gKC, gK, gC)
-             : occri_impl::vjp_full_impl<float>(p, C, gEx, gKC, gK, gC);
+             ? occri_impl::vjp_full_impl<double>(p, C, gEx, gKC, gK, gC, gomega_dev)
+             : occri_impl::vjp_full_impl<float>(p, C, gEx, gKC, gK, gC, gomega_dev);
 }
 
 int occri_vjp(occri_plan* plan, const void* C_dev, double gEx, void* gC_dev, double* gomega_dev) {

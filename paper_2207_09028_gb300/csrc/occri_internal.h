@@ -191,23 +191,26 @@ template <typename T>
 cudaError_t launch_scale_c(const Plan& p, const double2* C, cudaStream_t s);
 template <typename T>
 cudaError_t launch_orbitals(const Plan& p, cudaStream_t s);
+// k-points [k0, k0 + nkk) (nkk < 0: all from k0)
 template <typename T>
-cudaError_t launch_contract(const Plan& p, cudaStream_t s);
+cudaError_t launch_contract(const Plan& p, cudaStream_t s, int k0 = 0, int nkk = -1);
 // The same stages on other buffers (the adjoint): orbitals of the scaled coefficients cs
 // into out; scaled coefficients factor N_mu X of X into out; scale N_mu sum_r conj(chi) F
 // added into out.
 template <typename T>
-cudaError_t launch_orbitals_to(const Plan& p, const void* cs, void* out, cudaStream_t s);
+cudaError_t launch_orbitals_to(const Plan& p, const void* cs, void* out, cudaStream_t s,
+                               int k0 = 0, int nkk = -1);
 template <typename T>
 cudaError_t launch_scale_to(const Plan& p, const double2* X, void* out, double factor,
                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_contract_field(const Plan& p, const void* F, double2* out, double scale,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int k0 = 0, int nkk = -1);
 // F[k][i][.] *= e^{sign i k.r} over the orbital-shaped field F (psi -> periodic parts
 // with sign -1 before the pair passes, accumulated periodic parts -> Y with +1 after).
 template <typename T>
-cudaError_t launch_phase_fields(const Plan& p, void* F, int sign, cudaStream_t s);
+cudaError_t launch_phase_fields(const Plan& p, void* F, int sign, cudaStream_t s, int k0 = 0,
+                                int nkk = -1);
 // Pair-wave launches over unordered pairs: diag = 1 is the wave (k, k) with fields
 // i <= j; diag = 0 covers k' in [kp0, kp0 + nkp), all kp0 > k, with every (i, j).
 // S is the wave's scratch. When ev != nullptr, ev[0..3] are recorded before pass A,
@@ -219,9 +222,11 @@ cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, int diag, c
 template <typename T>
 cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s);
 // One wave of the adjoint build: forward potentials in scratch, adjoint potentials in
-// scratch2, their contributions added to gpsi (uses psi and gam).
+// scratch2, their contributions added to gpsi (uses psi and gam); with dacc != nullptr
+// also the omega term sum (dv/d omega)/(4 pi) Re(conj(sigma^) rho^) added to *dacc.
 template <typename T>
-cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s);
+cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, double* dacc,
+                            cudaStream_t s);
 
 // fields and pass-C targets of a wave
 __host__ __device__ inline int wave_fields(int nocc, int nkp, int diag) {

@@ -1012,6 +1012,72 @@ cudaError_t launch_pass_d(const PairParams& p, const cplx_t<T>* S, const cplx_t<
   return launch_pass_d_noc<T, 32>(p, S, psi, Y, st);
 }
 
+// ------------------------------------------------------------------ omega term of the adjoint
+// Plane m3 of field f, after pass A has transformed both the pair density rho (S0) and
+// its adjoint density sigma (S1) along n3 and n2: both planes are transformed along n1
+// and sum_m (dv/d omega)/(4 pi) Re(conj(sigma^) rho^) is added to *dacc, weight 1/2 for
+// a field (k, k, i, i) of a diagonal wave (the only pair that is its own reverse).
+template <typename T, int N>
+__global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
+pass_b_domega2(const cplx_t<T>* __restrict__ S0, const cplx_t<T>* __restrict__ S1,
+               PairParams p, double* __restrict__ dacc) {
+  using C2 = cplx_t<T>;
+  constexpr int P = pitch(N);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* rho = reinterpret_cast<C2*>(smem_raw);                     // [n1][m2]
+  C2* sig = rho + N * P;
+  Axis1<T>* ax1 = reinterpret_cast<Axis1<T>*>(sig + N * P);     // [m1]
+  T* vtab = reinterpret_cast<T*>(ax1 + N);                       // [m1][m2] dv/(4 pi)
+  __shared__ double red[4];
+  const int m3 = blockIdx.x;
+  const int f = blockIdx.y;
+  const FieldIdx fi = field_idx(f, p.nocc, p.diag);
+  const int kp = p.kp0 + fi.kpl;
+  stage_plane<T, N, P>(rho, S0 + (size_t)f * p.fs + (size_t)m3 * N * N);
+  stage_plane<T, N, P>(sig, S1 + (size_t)f * p.fs + (size_t)m3 * N * N);
+  cp_async_commit();
+  const MetricHL<T> gm(p);
+  int Q[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
+  for (int t = threadIdx.x; t < N; t += blockDim.x)
+    ax1[t] = axis1_entry<T>(gm, axis_int(t, Q[0], p.D[0], N));
+  __syncthreads();
+  {
+    constexpr int SP = line_split(N);
+    const int c = (int)threadIdx.x / SP, h = (int)threadIdx.x % SP;
+    if (c < N) {
+      const ColumnConst<T> cc = column_const<T>(gm, axis_int(c, Q[1], p.D[1], N),
+                                                axis_int(m3, Q[2], p.D[2], N));
+#pragma unroll 1
+      for (int m1 = h; m1 < N; m1 += SP) vtab[m1 * N + c] = bin_value<T, true>(p, gm, ax1[m1], cc);
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  T dsum = T(0);
+#pragma unroll 1
+  for (int job = 0; job < 2; ++job) {   // rho^ (stored), then sigma^ (paired with rho^)
+    run_lines<T, N>(job == 0 ? rho : sig, P, false, false, job == 0,
+                    [&](int line, int k, T& re, T& im) {
+                      if (job == 1) {
+                        const C2 r = rho[k * P + line];
+                        dsum += vtab[k * N + line] * (re * r.x + im * r.y);
+                      }
+                    });
+    __syncthreads();
+  }
+  double part = double(dsum);
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(dacc, (p.diag && fi.i == fi.j) ? 0.5 * t : t);
+  }
+}
+
 // ------------------------------------------------------------------ pass E (adjoint)
 // The adjoint of the Y accumulation and of the pair densities, per grid point (fields'
 // point order, periodic parts). With W the potentials of the wave's fields (scratch SW)
@@ -1188,7 +1254,8 @@ cudaError_t run_domega_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>
 // adjoint densities into S1 (the same three transform passes), then pass E.
 template <typename T, int N>
 cudaError_t run_vjp_wave(const PairParams& p, const cplx_t<T>* psi, const cplx_t<T>* gam,
-                         cplx_t<T>* S0, cplx_t<T>* S1, cplx_t<T>* G, cudaStream_t st) {
+                         cplx_t<T>* S0, cplx_t<T>* S1, cplx_t<T>* G, double* dacc,
+                         cudaStream_t st) {
   using C2 = cplx_t<T>;
   const int nt = threads_for(N);
   const int nf = wave_fields(p.nocc, p.nkp, p.diag);
@@ -1204,13 +1271,18 @@ cudaError_t run_vjp_wave(const PairParams& p, const cplx_t<T>* psi, const cplx_t
                          (int)sa);
     cudaFuncSetAttribute(pass_b<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
     cudaFuncSetAttribute(pass_c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+    cudaFuncSetAttribute(pass_b_domega2<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sb + sizeof(C2) * N * pitch(N)));
     slots_b = resident_slots(pass_b<T, N>, nt, sb);
     configured = true;
   }
   pass_a<T, N, false><<<dim3(N, nf), nt, sa, st>>>(psi, S0, p, nullptr);
+  pass_a<T, N, true><<<dim3(N, nf), nt, sa, st>>>(psi, S1, p, gam);
+  if (dacc)
+    pass_b_domega2<T, N><<<dim3(N, nf), nt, sb + sizeof(C2) * N * pitch(N), st>>>(S0, S1, p,
+                                                                                dacc);
   pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S0, p);
   pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S0, p);
-  pass_a<T, N, true><<<dim3(N, nf), nt, sa, st>>>(psi, S1, p, gam);
   pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S1, p);
   pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S1, p);
   const cudaError_t e = launch_pass_e<T>(p, S0, S1, psi, gam, G, st);

@@ -16,7 +16,8 @@ cudaError_t run_domega_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>
                             double* dacc, cudaStream_t st);
 template <typename T, int N>
 cudaError_t run_vjp_wave(const PairParams& p, const cplx_t<T>* psi, const cplx_t<T>* gam,
-                         cplx_t<T>* S0, cplx_t<T>* S1, cplx_t<T>* G, cudaStream_t st);
+                         cplx_t<T>* S0, cplx_t<T>* S1, cplx_t<T>* G, double* dacc,
+                         cudaStream_t st);
 
 }  // namespace pairs
 }  // namespace occri

@@ -47,7 +47,8 @@ cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag,
 }
 
 template <typename T>
-cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s) {
+cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, double* dacc,
+                            cudaStream_t s) {
   PairParams pp = p.pair_params();
   pp.k = k;
   pp.kp0 = kp0;
@@ -61,7 +62,7 @@ cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, cu
   switch (p.N[0]) {
 #define OCCRI_VJP_CASE(NN) \
   case NN:                 \
-    return pairs::run_vjp_wave<T, NN>(pp, psi, gam, S0, S1, G, s);
+    return pairs::run_vjp_wave<T, NN>(pp, psi, gam, S0, S1, G, dacc, s);
     OCCRI_FOR_EACH_N(OCCRI_VJP_CASE)
 #undef OCCRI_VJP_CASE
     default:
@@ -69,8 +70,10 @@ cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, cu
   }
 }
 
-template cudaError_t launch_vjp_wave<float>(const Plan&, int, int, int, int, cudaStream_t);
-template cudaError_t launch_vjp_wave<double>(const Plan&, int, int, int, int, cudaStream_t);
+template cudaError_t launch_vjp_wave<float>(const Plan&, int, int, int, int, double*,
+                                            cudaStream_t);
+template cudaError_t launch_vjp_wave<double>(const Plan&, int, int, int, int, double*,
+                                             cudaStream_t);
 template cudaError_t launch_pair_wave<float>(const Plan&, int, int, int, int, cudaStream_t, void*,
                                              cudaEvent_t*, cudaEvent_t);
 template cudaError_t launch_pair_wave<double>(const Plan&, int, int, int, int, cudaStream_t, void*,

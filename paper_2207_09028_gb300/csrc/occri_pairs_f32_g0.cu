@@ -26,16 +26,16 @@ template cudaError_t run_wave<float, 25>(const PairParams&, const cplx_t<float>*
 template cudaError_t run_domega_wave<float, 25>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
 template cudaError_t run_wave<float, 27>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t, cudaEvent_t*, cudaEvent_t);
 template cudaError_t run_domega_wave<float, 27>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 8>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 9>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 10>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 12>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 15>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 16>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 18>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 20>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 24>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 25>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 27>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 8>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 9>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 10>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 12>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 15>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 16>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 18>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 20>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 24>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 25>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 27>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
 }  // namespace pairs
 }  // namespace occri

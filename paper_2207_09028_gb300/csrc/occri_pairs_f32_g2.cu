@@ -8,7 +8,7 @@ template cudaError_t run_wave<float, 40>(const PairParams&, const cplx_t<float>*
 template cudaError_t run_domega_wave<float, 40>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
 template cudaError_t run_wave<float, 45>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t, cudaEvent_t*, cudaEvent_t);
 template cudaError_t run_domega_wave<float, 45>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 40>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
-template cudaError_t run_vjp_wave<float, 45>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 40>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_vjp_wave<float, 45>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
 }  // namespace pairs
 }  // namespace occri

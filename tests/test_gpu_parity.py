@@ -282,6 +282,32 @@ def test_full_adjoint_with_energy_seed_reduces_to_4KC_over_nk(torch_cuda, precis
     assert np.abs(gC - ref).max() <= tol * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("kind", ["erfc", "erf"])
+def test_full_adjoint_omega_gradient(torch_cuda, kind):
+    """d L / d omega of the full adjoint: with an E_x seed alone it equals occri_vjp's,
+    and with seeds on K and K_{mu i} it matches central differences of the oracle in omega."""
+    import paper_2207_09028_gb300 as occri
+    torch = torch_cuda
+    g0_mode = 1 if kind == "erfc" else 0
+    w = small_workload(mesh=(1, 1, 2), grid=(9, 9, 9), counts=(2, 1), nocc=2, kernel=kind,
+                       omega=0.4, g0_mode=g0_mode, seed=33)
+    plan = occri.Plan.from_workload(w, precision="fp64")
+    C = torch.from_numpy(w.C).cuda()
+    plan.build(C)
+    _, gw_e = plan.vjp(C, 0.8, want_c=False, want_omega=True)
+    _, gw_full = plan.vjp_full(C, 0.8, want_omega=True)
+    assert abs(gw_full - float(gw_e.cpu()[0])) <= 1e-10 * abs(gw_full)
+    rng = np.random.default_rng(7)
+    G = rng.standard_normal((w.nk, w.nao, w.nao)) + 1j * rng.standard_normal((w.nk, w.nao, w.nao))
+    H = rng.standard_normal(w.C.shape) + 1j * rng.standard_normal(w.C.shape)
+    _, gw = plan.vjp_full(C, 0.0, torch.from_numpy(H).cuda(), torch.from_numpy(G).cuda(),
+                          want_omega=True)
+    h = 1e-5
+    fd = (_oracle_loss(w.with_kernel(kind, 0.4 + h, g0_mode), w.C, G, H) -
+          _oracle_loss(w.with_kernel(kind, 0.4 - h, g0_mode), w.C, G, H)) / (2 * h)
+    assert abs(gw - fd) <= 1e-6 * abs(fd), (gw, fd)
+
+
 def test_full_adjoint_mixed_matches_fp64(torch_cuda):
     import paper_2207_09028_gb300 as occri
     torch = torch_cuda
