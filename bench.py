@@ -145,6 +145,23 @@ def oracle_sample_seconds(w, n_k: int = 2, pts=(256, 1024), seed: int = 0):
     return total, desc, t_pairs + sum(ts)
 
 
+# ---------------------------------------------------------------- ranks
+
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """The slowest rank's time (replicas: every rank runs the whole build on its GPU)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, ms: float) -> float:
+    """Builds per second of the whole job: every rank completes `steps` builds in `ms`."""
+    return world * steps / (ms / 1e3)
+
+
 # ---------------------------------------------------------------- main
 
 def main():
@@ -238,12 +255,9 @@ def main():
     plan.sync()
     stages = plan.stage_times()
     plan.set_timing(0)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = job_throughput(world, args.steps, ms)
     info = plan.info()
 
     # Per-build stage times. Pair-transform passes are timed on every `timing_every`-th
