@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 # ("round_trip", grid edge, fields per wave), from one ncu --set full capture of the same
 # launch shape (an off-diagonal 64-field wave at 60^3 of the 2x2x2-k profiling cell,
 # profiles/pair_passes_wave64_60cube_fp32.md; cold cache, each launch replayed alone).
-TRAFFIC = {}
+TRAFFIC = {("round_trip", 60, 64): 585.3e6}
 
 METRIC = "K-builds/s at 6x6x6 k, 350 AO; mixed vs FP64 GPU at |dE_x|<=1e-6 Ha/cell"
 UNIT = "K-builds/s"

@@ -351,3 +351,24 @@ def test_config5_mixed_properties_and_orbital_samples(torch_cuda):
     assert np.abs(kk - np.conj(np.swapaxes(kk, 1, 2))).max() <= 1e-12 * np.abs(kk).max()
     # K C = KC holds to the size of the anti-Hermitian part of C^H KC, which is FP32 noise here
     assert np.abs(np.einsum("kmv,kvi->kmi", kk, w.C[:4]) - kc).max() <= 1e-6 * np.abs(kc).max()
+
+
+def test_config5_mixed_energy_within_1e6_of_fp64(torch_cuda):
+    """The metric's criterion at full size (6x6x6 k, 350 AO, nocc 8, 60^3): the mixed
+    build's E_x is within 1e-6 Ha per cell of the FP64 build's, and its K_{mu i} within
+    the mixed-precision bar. (The FP64 path itself is held to 1e-10 against the oracle on
+    the smaller cells.)"""
+    import paper_2207_09028_gb300 as occri
+    torch = torch_cuda
+    w = config("cfg5")
+    C = torch.from_numpy(w.C).cuda()
+    out = {}
+    for prec in ("mixed", "fp64"):
+        plan = occri.Plan.from_workload(w, precision=prec)
+        KC, _, Ex = plan.build(C, want_k=False)
+        out[prec] = (KC.cpu().numpy(), float(Ex.cpu()[0]))
+        plan.close()
+        del plan, KC
+        torch.cuda.empty_cache()
+    assert abs(out["mixed"][1] - out["fp64"][1]) <= 1e-6
+    assert np.abs(out["mixed"][0] - out["fp64"][0]).max() <= TOL["mixed"]["k_abs"]
