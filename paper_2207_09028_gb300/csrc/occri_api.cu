@@ -1184,7 +1184,7 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
   p->fs = (ng + 63) / 64 * 64;
   const size_t field_bytes = csz * (size_t)p->fs;
   const size_t per_kp = field_bytes * (size_t)nocc * nocc;
-  const size_t budget = (size_t)96 << 20;
+  const size_t budget = (size_t)kWaveBudgetMB << 20;
   int nkp = (int)std::max<size_t>(1, budget / per_kp);
   nkp = std::min(nkp, p->nk);
   nkp = std::max(1, std::min(nkp, 65535 / (nocc * nocc)));   // grid.y limit of the passes

@@ -228,6 +228,9 @@ template <typename T>
 cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, double* dacc,
                             cudaStream_t s);
 
+// scratch per wave (MB): how many k' one wave takes when nocc^2 fields of a k' fit
+constexpr int kWaveBudgetMB = 96;
+
 // fields and pass-C targets of a wave
 __host__ __device__ inline int wave_fields(int nocc, int nkp, int diag) {
   return diag ? nocc * (nocc + 1) / 2 : nkp * nocc * nocc;

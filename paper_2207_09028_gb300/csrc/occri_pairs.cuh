@@ -185,7 +185,8 @@ __device__ __forceinline__ void line_fft(cplx_t<T>* base, int stride, bool inver
 // store and post as in line_fft; `valid` is false for padding threads, which compute
 // on a duplicate line but neither store nor call post. The pair synchronises between
 // its loads and its stores: __syncwarp for adjacent lanes, else named barrier `bar`
-// (1 or 2: at most two pairs of warps per CTA, N <= 64).
+// (1 or 2: at most two pairs of warps per CTA, N <= 64), or with bar = 0 the whole CTA
+// (every thread of the CTA then calls it).
 template <typename T, int N, typename Post>
 __device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool inverse, bool store,
                                           int h, bool valid, int bar, Post&& post) {
@@ -193,7 +194,9 @@ __device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool inve
   auto pair_barrier = [&]() {
     if constexpr (kPairLanes) {
       __syncwarp();
-    } else if (bar == 1) {   // warp-uniform; immediate barrier ids
+    } else if (bar == 0) {   // warp-uniform; immediate barrier ids
+      __syncthreads();
+    } else if (bar == 1) {
       asm volatile("bar.sync 1, 64;\n" ::: "memory");
     } else {
       asm volatile("bar.sync 2, 64;\n" ::: "memory");
@@ -1012,6 +1015,232 @@ cudaError_t launch_pass_d(const PairParams& p, const cplx_t<T>* S, const cplx_t<
   return launch_pass_d_noc<T, 32>(p, S, psi, Y, st);
 }
 
+// ------------------------------------------------------------------ pass CD (C and D fused)
+// Passes C and D as one kernel, for FP32 waves with nocc <= kCdNoc. A CTA owns the points
+// with every n3, one n1 and CdShape::CW consecutive n2 (row pieces). Per batch of
+// at most kCdFields fields it copies those pieces of the batch's fields into shared
+// memory, transforms every (field, n2) line inversely along m3 in place, and adds the
+// batch's terms
+//   Y_{ik}  += sum_j W_{k'ij} u_{jk'},      Y_{jk'} += sum_i conj(W_{k'ij}) u_{ik}
+// at its points (diagonal waves: fields i <= j, W_ji = conj(W_ij), Y_{k'} = Y_k), so
+// the potentials W never go back to global memory. The orbital planes u_k and u_{k'} of
+// the CTA's points sit in shared memory beside the batch; the sums for Y stay in
+// registers (one point per thread) and are added to Y once per k' (Y_{k'}) and once per
+// wave (Y_k). A batch holds whole rows i of the wave's field list, so a row's terms
+// land in fixed registers.
+constexpr int kCdFields = 32;   // fields per batch
+constexpr int kCdNoc = 8;       // largest nocc of the fused form
+// CTA shape: CW n2 columns (CW x 8 bytes per row piece), NT threads (NT >= N CW, and
+// kCdFields CW lines per transform round with two threads a line), MB CTAs per SM.
+struct CdShape {
+  static constexpr int CW = 4, NT = 256, MB = 2;
+  static constexpr bool DB = false;   // two batch buffers (next batch copied in meanwhile)
+};
+// Plane pitch (points) in shared memory: >= N CW and = CW (mod 16), so that the 8-byte
+// loads of a half warp (16 / CW fields x CW columns at one m3) hit 32 distinct banks.
+constexpr int cd_pitch(int n, int cw) {
+  return n * cw + ((cw - (n * cw) % 16) + 16) % 16;
+}
+constexpr size_t cd_smem(int n, int cw, bool db) {
+  return sizeof(float2) * (size_t)cd_pitch(n, cw) * ((db ? 2 : 1) * kCdFields + 2 * kCdNoc);
+}
+
+// Rows n3 = 0..N-1 of columns [c0, c0 + CW) at row n1 of np planes (plane pl starts at
+// src(pl)) into dst + pl * PP + n3 CW + c; columns >= N are skipped. 16-byte copies
+// for even N (the pieces start at even points), 8-byte ones otherwise.
+template <int N, int CW, int NT, typename Src>
+__device__ __forceinline__ void cd_copy(float2* dst, int np, Src src, int n1, int c0) {
+  constexpr int PP = cd_pitch(N, CW);
+  constexpr int W = (N % 2 == 0) ? 2 : 1;      // points per copy
+  constexpr int RW = CW / W;                   // copies per row piece
+  constexpr int per = N * RW;                  // copies per plane
+  for (int e = threadIdx.x; e < np * per; e += NT) {
+    const int pl = e / per, r = e - (e / per) * per;
+    const int n3 = r / RW, c = (r - (r / RW) * RW) * W;
+    if (c0 + c < N)
+      cp_async<8 * W>(dst + pl * PP + n3 * CW + c,
+                      src(pl) + ((size_t)n3 * N + n1) * N + c0 + c);
+  }
+}
+
+// A batch of the wave's field list: rows [i0, i1) of k' offset kpl, fields [fa, fa + cnt).
+struct CdBatch { int kpl, i0, i1, fa, cnt; };
+__device__ __forceinline__ CdBatch cd_batch(int kpl, int i0, int nocc, int diag) {
+  CdBatch b;
+  b.kpl = kpl;
+  b.i0 = i0;
+  if (diag) {   // whole rows i <= j, at most kCdFields fields (a row has <= kCdNoc)
+    b.fa = diag_field(i0, i0, nocc);
+    b.cnt = 0;
+    b.i1 = i0;
+    while (b.i1 < nocc && b.cnt + (nocc - b.i1) <= kCdFields) b.cnt += nocc - b.i1++;
+  } else {
+    b.i1 = min(nocc, i0 + max(1, kCdFields / nocc));
+    b.fa = kpl * nocc * nocc + i0 * nocc;
+    b.cnt = (b.i1 - b.i0) * nocc;
+  }
+  return b;
+}
+
+template <int N, int CW, int NT, int MB, bool DB>
+__global__ void __launch_bounds__(NT, MB)
+pass_cd(const float2* __restrict__ S, const float2* __restrict__ psi, float2* __restrict__ Y,
+        PairParams p) {
+  static_assert(N * CW <= NT, "one point per thread");
+  constexpr int PP = cd_pitch(N, CW);
+  constexpr int NOC = kCdNoc;
+  constexpr int NBUF = DB ? 2 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* W0 = reinterpret_cast<float2*>(smem_raw);   // NBUF x [field of batch][n3][c], pitch PP
+  float2* Uk = W0 + NBUF * kCdFields * PP;             // [i][n3][c]
+  float2* Uq = Uk + NOC * PP;                          // [j][n3][c]
+  const int c0 = blockIdx.x * CW, n1 = blockIdx.y;
+  const int nocc = p.nocc;
+  const int t = threadIdx.x;
+  const int tc = t % CW;
+  const bool pvalid = t < N * CW && c0 + tc < N;
+  const size_t q = ((size_t)(t / CW) * N + n1) * N + c0 + tc;   // the thread's point
+  const int nkl = p.diag ? 1 : p.nkp;
+  auto copy_w = [&](float2* dst, const CdBatch& b) {
+    cd_copy<N, CW, NT>(dst, b.cnt, [&](int f) { return S + (size_t)(b.fa + f) * p.fs; }, n1, c0);
+  };
+  auto copy_uq = [&](int kpl) {
+    const int kp = p.kp0 + kpl;
+    cd_copy<N, CW, NT>(Uq, nocc, [&](int j) { return psi + (size_t)(kp * nocc + j) * p.fs; }, n1,
+                       c0);
+  };
+  float ar[NOC], ai[NOC], br[NOC], bi[NOC];
+#pragma unroll
+  for (int i = 0; i < NOC; ++i) { ar[i] = ai[i] = br[i] = bi[i] = 0.f; }
+  cd_copy<N, CW, NT>(Uk, nocc, [&](int i) { return psi + (size_t)(p.k * nocc + i) * p.fs; }, n1,
+                     c0);
+  CdBatch cur = cd_batch(0, 0, nocc, p.diag);
+  if (!p.diag) copy_uq(0);
+  copy_w(W0, cur);
+  cp_async_commit();
+  int buf = 0;
+#pragma unroll 1
+  while (true) {
+    const bool more = cur.i1 < nocc || cur.kpl + 1 < nkl;
+    const bool end_kpl = cur.i1 >= nocc;
+    auto next_batch = [&]() {
+      return end_kpl ? cd_batch(cur.kpl + 1, 0, nocc, p.diag)
+                     : cd_batch(cur.kpl, cur.i1, nocc, p.diag);
+    };
+    // with two buffers, the next batch of the same k' is copied in while this one is used
+    const bool pre = DB && !end_kpl;
+    if (pre) copy_w(W0 + (buf ^ 1) * kCdFields * PP, next_batch());
+    cp_async_commit();
+    if (pre) cp_async_wait<1>(); else cp_async_wait<0>();
+    __syncthreads();
+    float2* Wb = W0 + buf * kCdFields * PP;
+    // inverse along m3 of every (field, column) line of the batch, in place
+    {
+      const int lines = cur.cnt * CW;
+      constexpr int SP = line_split(N);
+      constexpr int per_round = NT / SP;
+#pragma unroll 1
+      for (int l0 = 0; l0 < lines; l0 += per_round) {
+        if constexpr (SP == 2) {
+          const int w = t >> 5;
+          const int line0 = l0 + (w >> 1) * 32 + (t & 31);
+          const bool valid = line0 < lines;
+          const int line = valid ? line0 : lines - 1;
+          line_fft2<float, N>(Wb + (line / CW) * PP + line % CW, CW, true, true, w & 1, valid, 0,
+                              [](int, float&, float&) {});
+        } else {
+          const int line = l0 + t;
+          if (line < lines)
+            line_fft<float, N>(Wb + (line / CW) * PP + line % CW, CW, true, true,
+                               [](int, float&, float&) {});
+        }
+      }
+    }
+    __syncthreads();
+    // the batch's terms at this thread's point
+    const int i0 = cur.i0, i1 = cur.i1, fa = cur.fa;
+    if (pvalid) {
+      if (p.diag) {
+#pragma unroll
+        for (int i = 0; i < NOC; ++i) {
+          if (i < i0 || i >= i1) continue;
+          const float2 ui = Uk[i * PP + t];
+#pragma unroll
+          for (int j = i; j < NOC; ++j) {
+            if (j >= nocc) break;
+            const float2 w = Wb[(diag_field(i, j, nocc) - fa) * PP + t];
+            const float2 uj = Uk[j * PP + t];
+            ar[i] += w.x * uj.x - w.y * uj.y;     // W_ij u_j
+            ai[i] += w.x * uj.y + w.y * uj.x;
+            if (i < j) {                          // W_ji u_i = conj(W_ij) u_i
+              ar[j] += w.x * ui.x + w.y * ui.y;
+              ai[j] += w.x * ui.y - w.y * ui.x;
+            }
+          }
+        }
+      } else {
+        float qr[NOC], qi[NOC];
+#pragma unroll
+        for (int j = 0; j < NOC; ++j) {
+          const float2 v = j < nocc ? Uq[j * PP + t] : make_float2(0.f, 0.f);
+          qr[j] = v.x; qi[j] = v.y;
+        }
+#pragma unroll
+        for (int i = 0; i < NOC; ++i) {
+          if (i < i0 || i >= i1) continue;
+          const float2 ui = Uk[i * PP + t];
+          const float2* wrow = Wb + (i - i0) * nocc * PP + t;
+#pragma unroll
+          for (int j = 0; j < NOC; ++j) {
+            if (j >= nocc) break;
+            const float2 w = wrow[j * PP];
+            ar[i] += w.x * qr[j] - w.y * qi[j];     // W u_{jk'}
+            ai[i] += w.x * qi[j] + w.y * qr[j];
+            br[j] += w.x * ui.x + w.y * ui.y;       // conj(W) u_{ik}
+            bi[j] += w.x * ui.y - w.y * ui.x;
+          }
+        }
+      }
+    }
+    // add the k' sums to Y_{k'}: all loads before the first store, so that the planes'
+    // loads are in flight together
+    if (end_kpl && pvalid && !p.diag) {
+      const int kp = p.kp0 + cur.kpl;
+      float2 v[NOC];
+#pragma unroll
+      for (int j = 0; j < NOC; ++j)
+        if (j < nocc) v[j] = Y[(size_t)(kp * nocc + j) * p.fs + q];
+#pragma unroll
+      for (int j = 0; j < NOC; ++j) {
+        if (j >= nocc) break;
+        Y[(size_t)(kp * nocc + j) * p.fs + q] = make_float2(v[j].x + br[j], v[j].y + bi[j]);
+        br[j] = bi[j] = 0.f;
+      }
+    }
+    __syncthreads();   // this batch's buffer (and at a k' change the u_{k'} planes) is free
+    if (!more) break;
+    const CdBatch nxt = next_batch();
+    if (!pre) {
+      if (end_kpl && !p.diag) copy_uq(nxt.kpl);
+      copy_w(W0 + (buf ^ (DB ? 1 : 0)) * kCdFields * PP, nxt);
+    }
+    cp_async_commit();   // the next batch's copies form a group of their own
+    buf ^= DB ? 1 : 0;
+    cur = nxt;
+  }
+  if (pvalid) {
+    float2 v[NOC];
+#pragma unroll
+    for (int i = 0; i < NOC; ++i)
+      if (i < nocc) v[i] = Y[(size_t)(p.k * nocc + i) * p.fs + q];
+#pragma unroll
+    for (int i = 0; i < NOC; ++i) {
+      if (i >= nocc) break;
+      Y[(size_t)(p.k * nocc + i) * p.fs + q] = make_float2(v[i].x + ar[i], v[i].y + ai[i]);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ omega term of the adjoint
 // Plane m3 of field f, after pass A has transformed both the pair density rho (S0) and
 // its adjoint density sigma (S1) along n3 and n2: both planes are transformed along n1
@@ -1212,6 +1441,10 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
     cudaFuncSetAttribute(pass_a<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
     cudaFuncSetAttribute(pass_b<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
     cudaFuncSetAttribute(pass_c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+    if constexpr (std::is_same<T, float>::value)
+      cudaFuncSetAttribute(pass_cd<N, CdShape::CW, CdShape::NT, CdShape::MB, CdShape::DB>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)cd_smem(N, CdShape::CW, CdShape::DB));
     slots_b = resident_slots(pass_b<T, N>, nt, sb);
     configured = true;
   }
@@ -1220,9 +1453,19 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   if (ev) cudaEventRecord(ev[1], st);
   pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S, p);
   if (ev) cudaEventRecord(ev[2], st);
-  pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S, p);
+  // FP32 waves of nocc <= kCdNoc: passes C and D fused (the potentials stay on chip)
+  constexpr bool kFusable = std::is_same<T, float>::value;
+  const bool fused = kFusable && p.nocc <= kCdNoc;
+  if (!fused) pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S, p);
   if (ev_y) cudaStreamWaitEvent(st, ev_y, 0);   // the previous wave's Y updates
-  const cudaError_t e = launch_pass_d<T>(p, S, psi, Y, st);
+  cudaError_t e = cudaSuccess;
+  if constexpr (kFusable) {
+    if (fused)
+      pass_cd<N, CdShape::CW, CdShape::NT, CdShape::MB, CdShape::DB>
+          <<<dim3((N + CdShape::CW - 1) / CdShape::CW, N), CdShape::NT,
+              cd_smem(N, CdShape::CW, CdShape::DB), st>>>((const float2*)S, (const float2*)psi, (float2*)Y, p);
+  }
+  if (!fused) e = launch_pass_d<T>(p, S, psi, Y, st);
   if (ev_y) cudaEventRecord(ev_y, st);
   if (ev) cudaEventRecord(ev[3], st);
   return e != cudaSuccess ? e : cudaGetLastError();
