@@ -28,11 +28,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) of one full wave (pass_a + pass_b + pass_c + pass_d), keyed by
-# ("round_trip", grid edge, fields per wave), from one ncu --set full capture of the same
-# launch shape (an off-diagonal 64-field wave at 60^3 of the 2x2x2-k profiling cell,
+# DRAM bytes (read + write) of one full mixed-precision wave (pass_a + pass_b + pass_cd), keyed
+# by ("round_trip", grid edge, fields per wave, precision), from one ncu --set full capture of
+# the same launch shape (an off-diagonal 64-field wave at 60^3 of the 2x2x2-k profiling cell,
 # profiles/pair_passes_wave64_60cube_fp32.md; cold cache, each launch replayed alone).
-TRAFFIC = {("round_trip", 60, 64): 585.3e6}
+TRAFFIC = {("round_trip", 60, 64, "mixed"): 423.2e6}
 
 METRIC = "K-builds/s at 6x6x6 k, 350 AO; mixed vs FP64 GPU at |dE_x|<=1e-6 Ha/cell"
 UNIT = "K-builds/s"
@@ -287,11 +287,15 @@ def main():
         fields = loop["units"]
         achieved = 32.0 * ng * fields / (loop["ms"] / 1e3) / 1e9
         fpw = int(info["fields_per_wave"])
-        roof = {"kernel": "pair round trip: pass_a + pass_b + pass_c + pass_d over waves of "
+        mixed = int(info.get("precision", 1)) == 1
+        fused = mixed and w.nocc <= 8   # FP32 waves of nocc <= 8 fuse passes C and D
+        passes = "pass_a + pass_b + pass_cd" if fused else "pass_a + pass_b + pass_c + pass_d"
+        roof = {"kernel": f"pair round trip: {passes} over waves of "
                           f"{fpw} fields of {w.grid[0]}^3 (two streams)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
                 "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": TRAFFIC.get(("round_trip", w.grid[0], fpw)),
+                "traffic": TRAFFIC.get(("round_trip", w.grid[0], fpw,
+                                        "mixed" if mixed else "fp64")),
                 "bytes_per_launch": 32.0 * ng * fpw,
                 "ms_per_launch": loop["ms"] * fpw / fields,
                 "pass_ms_share": ({s_: stages[s_]["ms"] / rt_ms for s_ in pair} if rt_ms > 0

@@ -617,7 +617,7 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
         if (launch_pair_wave<T>(*p, k, kp0, nkp, diag, st[w], sc[w], sample ? ev : nullptr,
                                 p->ev_y) != cudaSuccess)
           return OCCRI_ECUDA;
-        launches += 4;
+        launches += pair_wave_launches<T>(p->nocc);
         const double nf = (double)wave_fields(p->nocc, nkp, diag);
         fields += nf;
         if (sample) {   // and keep the other stream waiting until this wave is done

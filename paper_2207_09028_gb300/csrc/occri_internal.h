@@ -1,6 +1,8 @@
 // occri_internal.h -- plan layout and kernel launchers shared by the CUDA sources.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -227,6 +229,13 @@ cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag,
 template <typename T>
 cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, double* dacc,
                             cudaStream_t s);
+
+// Largest nocc whose FP32 waves run the inverse along m3 and the Y accumulation as one
+// fused pass (three launches per wave instead of four).
+constexpr int kFusedCdNoc = 8;
+template <typename T> constexpr int pair_wave_launches(int nocc) {
+  return (std::is_same<T, float>::value && nocc <= kFusedCdNoc) ? 3 : 4;
+}
 
 // scratch per wave (MB): how many k' one wave takes when nocc^2 fields of a k' fit
 constexpr int kWaveBudgetMB = 96;

@@ -121,13 +121,26 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING));
 }
 
+// body(r, c) for every element of an N x N block, in a CTA of threads_for(N) threads:
+// thread t < RT N takes column c = t mod N and rows t / N, t / N + RT, ... (RT = the
+// threads_for(N) / N rows in flight), so the row is an induction variable and the
+// addresses advance by constant steps instead of being re-derived from a flat index.
+template <int N, typename F>
+__device__ __forceinline__ void plane_loop(F&& body) {
+  constexpr int RT = threads_for(N) / N;
+  static_assert(RT >= 1, "a thread per column");
+  const int t = threadIdx.x;
+  if (t < RT * N) {
+    const int c = t % N;
+#pragma unroll 4
+    for (int r = t / N; r < N; r += RT) body(r, c);
+  }
+}
+
 // Copy a contiguous N x N plane into shared memory with row pitch P.
 template <typename T, int N, int P>
 __device__ __forceinline__ void stage_plane(cplx_t<T>* dst, const cplx_t<T>* src) {
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int r = e / N, c = e - (e / N) * N;
-    cp_async<sizeof(cplx_t<T>)>(dst + r * P + c, src + e);
-  }
+  plane_loop<N>([&](int r, int c) { cp_async<sizeof(cplx_t<T>)>(dst + r * P + c, src + r * N + c); });
 }
 
 // ------------------------------------------------------------------ one line transform
@@ -474,21 +487,17 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
   if constexpr (ADJ) {
     const C2* gi = gam + (size_t)(p.k * p.nocc + fi.i) * p.fs + (size_t)n1 * N;
     const C2* gj = gam + (size_t)(kp * p.nocc + fi.j) * p.fs + (size_t)n1 * N;
-#pragma unroll 2
-    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-      const int n3 = e / N, n2 = e - (e / N) * N;
+    plane_loop<N>([&](int n3, int n2) {
       const size_t off = (size_t)n3 * N * N + n2;
       const C2 a = cmulc<T>(__ldg(pj + off), __ldg(gi + off));
       const C2 b = cmulc<T>(__ldg(gj + off), __ldg(pi + off));
       pl[n2 * P + n3] = mk<T>(a.x + b.x, a.y + b.y);
-    }
+    });
   } else {
-#pragma unroll 4
-    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-      const int n3 = e / N, n2 = e - (e / N) * N;
+    plane_loop<N>([&](int n3, int n2) {
       const size_t off = (size_t)n3 * N * N + n2;
       pl[n2 * P + n3] = cmulc<T>(__ldg(pj + off), __ldg(pi + off));
-    }
+    });
   }
   __syncthreads();
 #pragma unroll 1
@@ -497,10 +506,7 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
     __syncthreads();
   }
   C2* out = S + (size_t)f * p.fs;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int m3 = e / N, m2 = e - (e / N) * N;
-    out[((size_t)m3 * N + n1) * N + m2] = pl[m2 * P + m3];
-  }
+  plane_loop<N>([&](int m3, int m2) { out[((size_t)m3 * N + n1) * N + m2] = pl[m2 * P + m3]; });
 }
 
 // ------------------------------------------------------------------ pass B
@@ -597,10 +603,7 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
     }
     if constexpr (!DOMEGA) {
       C2* buf = S + (size_t)f * p.fs + (size_t)m3 * N * N;
-      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int r = e / N, c = e - (e / N) * N;
-        buf[e] = plane[r * P + c];
-      }
+      plane_loop<N>([&](int r, int c) { buf[r * N + c] = plane[r * P + c]; });
       __syncthreads();   // releases this buffer for the copy NB items ahead
     }
     if constexpr (NB == 1) {   // one buffer: the next plane is copied in only now
@@ -657,21 +660,16 @@ pass_c(cplx_t<T>* __restrict__ S, PairParams p) {
   const int n1 = blockIdx.x;
   const int f = blockIdx.y;
   C2* rows = S + (size_t)f * p.fs + (size_t)n1 * N;   // row m3 at rows + m3 N^2
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int m3 = e / N, n2 = e - (e / N) * N;
+  plane_loop<N>([&](int m3, int n2) {
     cp_async<sizeof(C2)>(cur + m3 * P + n2, rows + (size_t)m3 * N * N + n2);
-  }
+  });
   cp_async_commit();
   cp_async_wait<0>();
   __syncthreads();
   // columns (n2 = line): inverse along m3
   run_lines<T, N>(cur, P, false, true, true, [](int, int, T&, T&) {});
   __syncthreads();
-#pragma unroll 4
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int n3 = e / N, n2 = e - (e / N) * N;
-    rows[(size_t)n3 * N * N + n2] = cur[n3 * P + n2];
-  }
+  plane_loop<N>([&](int n3, int n2) { rows[(size_t)n3 * N * N + n2] = cur[n3 * P + n2]; });
 }
 
 // ------------------------------------------------------------------ pass D
@@ -1029,7 +1027,7 @@ cudaError_t launch_pass_d(const PairParams& p, const cplx_t<T>* S, const cplx_t<
 // wave (Y_k). A batch holds whole rows i of the wave's field list, so a row's terms
 // land in fixed registers.
 constexpr int kCdFields = 32;   // fields per batch
-constexpr int kCdNoc = 8;       // largest nocc of the fused form
+constexpr int kCdNoc = kFusedCdNoc;   // largest nocc of the fused form
 // CTA shape: CW n2 columns (CW x 8 bytes per row piece), NT threads (NT >= N CW, and
 // kCdFields CW lines per transform round with two threads a line), MB CTAs per SM.
 struct CdShape {
@@ -1455,7 +1453,7 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   if (ev) cudaEventRecord(ev[2], st);
   // FP32 waves of nocc <= kCdNoc: passes C and D fused (the potentials stay on chip)
   constexpr bool kFusable = std::is_same<T, float>::value;
-  const bool fused = kFusable && p.nocc <= kCdNoc;
+  const bool fused = pair_wave_launches<T>(p.nocc) == 3;
   if (!fused) pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S, p);
   if (ev_y) cudaStreamWaitEvent(st, ev_y, 0);   // the previous wave's Y updates
   cudaError_t e = cudaSuccess;
@@ -1463,7 +1461,8 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
     if (fused)
       pass_cd<N, CdShape::CW, CdShape::NT, CdShape::MB, CdShape::DB>
           <<<dim3((N + CdShape::CW - 1) / CdShape::CW, N), CdShape::NT,
-              cd_smem(N, CdShape::CW, CdShape::DB), st>>>((const float2*)S, (const float2*)psi, (float2*)Y, p);
+              cd_smem(N, CdShape::CW, CdShape::DB), st>>>((const float2*)S, (const float2*)psi,
+                                                           (float2*)Y, p);
   }
   if (!fused) e = launch_pass_d<T>(p, S, psi, Y, st);
   if (ev_y) cudaEventRecord(ev_y, st);
