@@ -62,6 +62,10 @@ constexpr int threads_for(int n) {
 constexpr int min_blocks(int n, int elem_bytes) {
   return elem_bytes > 8 ? (n <= 32 ? 4 : 2) : (n <= 32 ? 8 : 4);
 }
+// pass A (29 KB of shared memory at 60^3, FP32) gains from a fifth CTA per SM
+constexpr int min_blocks_a(int n, int elem_bytes) {
+  return elem_bytes > 8 ? min_blocks(n, elem_bytes) : (n <= 32 ? 8 : 5);
+}
 // f(|G+q|)/(4 pi) of Eq. recipcoul for |G+q|^2 = g2 > 0.
 template <typename T>
 __device__ __forceinline__ T kernel_f(T g2, int kind, T inv4w2) {
@@ -147,9 +151,9 @@ __device__ __forceinline__ void stage_plane(cplx_t<T>* dst, const cplx_t<T>* src
 // DFT (e^{-2 pi i m n / N}) of the N elements at base[m * stride], in place, with the
 // whole line in registers. The unnormalised inverse (e^{+2 pi i m n / N}) is the same
 // transform with output k stored at index (N - k) mod N. post(k, re, im) sees output
-// index k (after that reversal) before the store (store is skipped when !store). Each
-// kernel calls this once, inside a runtime loop, so the unrolled transform exists
-// once in the instruction stream.
+// index k (after that reversal) before the store (store is skipped when !store). Every
+// call site has its own unrolled copy with a compile-time stride, so no address is
+// computed at run time from a stride.
 template <typename T, int N, typename Post>
 __device__ __forceinline__ void line_fft(cplx_t<T>* base, int stride, bool inverse, bool store,
                                          Post&& post) {
@@ -470,7 +474,7 @@ __device__ __forceinline__ T bin_value(const PairParams& p, const Consts<T>& k,
 // With ADJ (the adjoint build): the field is sigma = conj(u_jk') g_ik + conj(g_jk') u_ik,
 // g being the adjoint orbital field, i.e. the change of rho when u moves along g.
 template <typename T, int N, bool ADJ = false>
-__global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
+__global__ void __launch_bounds__(threads_for(N), min_blocks_a(N, sizeof(cplx_t<T>)))
 pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams p,
        const cplx_t<T>* __restrict__ gam = nullptr) {
   using C2 = cplx_t<T>;
@@ -500,13 +504,14 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
     });
   }
   __syncthreads();
-#pragma unroll 1
-  for (int job = 0; job < 2; ++job) {   // rows (along n3), then columns (along n2)
-    run_lines<T, N>(pl, P, job == 0, false, true, [](int, int, T&, T&) {});
-    __syncthreads();
-  }
+  // columns (line n3, along n2), then rows (line m2, along n3); the rows' outputs go
+  // straight to S[f][m3][n1][m2], a warp's lanes on consecutive m2
+  run_lines<T, N>(pl, P, false, false, true, [](int, int, T&, T&) {});
+  __syncthreads();
   C2* out = S + (size_t)f * p.fs;
-  plane_loop<N>([&](int m3, int m2) { out[((size_t)m3 * N + n1) * N + m2] = pl[m2 * P + m3]; });
+  run_lines<T, N>(pl, P, true, false, false, [&](int line, int k, T& re, T& im) {
+    out[((size_t)k * N + n1) * N + line] = mk<T>(re, im);
+  });
 }
 
 // ------------------------------------------------------------------ pass B
@@ -594,16 +599,14 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
     });
     __syncthreads();
     if constexpr (!DOMEGA) {
-      // inverse along m1 (columns), then along m2 (rows)
-#pragma unroll 1
-      for (int job = 1; job < 3; ++job) {
-        run_lines<T, N>(plane, P, job == 2, true, true, [](int, int, T&, T&) {});
-        __syncthreads();
-      }
-    }
-    if constexpr (!DOMEGA) {
+      // inverse along m2 (rows), then along m1 (columns); the columns' outputs go straight
+      // to S[f][m3][n1][n2], a warp's lanes on consecutive n2
+      run_lines<T, N>(plane, P, true, true, true, [](int, int, T&, T&) {});
+      __syncthreads();
       C2* buf = S + (size_t)f * p.fs + (size_t)m3 * N * N;
-      plane_loop<N>([&](int r, int c) { buf[r * N + c] = plane[r * P + c]; });
+      run_lines<T, N>(plane, P, false, true, false, [&](int line, int k, T& re, T& im) {
+        buf[(size_t)k * N + line] = mk<T>(re, im);
+      });
       __syncthreads();   // releases this buffer for the copy NB items ahead
     }
     if constexpr (NB == 1) {   // one buffer: the next plane is copied in only now
@@ -1045,20 +1048,24 @@ constexpr size_t cd_smem(int n, int cw, bool db) {
 
 // Rows n3 = 0..N-1 of columns [c0, c0 + CW) at row n1 of np planes (plane pl starts at
 // src(pl)) into dst + pl * PP + n3 CW + c; columns >= N are skipped. 16-byte copies
-// for even N (the pieces start at even points), 8-byte ones otherwise.
+// for even N (the pieces start at even points), 8-byte ones otherwise. Each thread keeps
+// one (n3, c) and steps through the planes, NT / (copies per plane) at a time.
 template <int N, int CW, int NT, typename Src>
 __device__ __forceinline__ void cd_copy(float2* dst, int np, Src src, int n1, int c0) {
   constexpr int PP = cd_pitch(N, CW);
   constexpr int W = (N % 2 == 0) ? 2 : 1;      // points per copy
   constexpr int RW = CW / W;                   // copies per row piece
   constexpr int per = N * RW;                  // copies per plane
-  for (int e = threadIdx.x; e < np * per; e += NT) {
-    const int pl = e / per, r = e - (e / per) * per;
-    const int n3 = r / RW, c = (r - (r / RW) * RW) * W;
-    if (c0 + c < N)
-      cp_async<8 * W>(dst + pl * PP + n3 * CW + c,
-                      src(pl) + ((size_t)n3 * N + n1) * N + c0 + c);
-  }
+  constexpr int PT = NT / per;                 // planes in flight per step
+  static_assert(PT >= 1, "a copy per thread and plane");
+  const int t = threadIdx.x;
+  if (t >= PT * per) return;
+  const int r = t % per;
+  const int n3 = r / RW, c = (r % RW) * W;
+  if (c0 + c >= N) return;
+  float2* d = dst + n3 * CW + c;
+  const size_t off = ((size_t)n3 * N + n1) * N + c0 + c;
+  for (int pl = t / per; pl < np; pl += PT) cp_async<8 * W>(d + pl * PP, src(pl) + off);
 }
 
 // A batch of the wave's field list: rows [i0, i1) of k' offset kpl, fields [fa, fa + cnt).
