@@ -51,6 +51,7 @@ PairParams Plan::pair_params() const {
   q.nk = nk; q.nocc = nocc; q.ng = ng; q.fs = fs; q.N1 = N[0];
   q.status = status;
   q.k = 0; q.kp0 = 0; q.nkp = 1; q.diag = 0;
+  q.vt_off = (long long)fields_cap * fs * (precision == OCCRI_FP64 ? 16 : 8);
   for (int d = 0; d < 3; ++d) q.D[d] = D[d];
   q.kint = kint;
   // reciprocal vectors b_i (rows): B = 2 pi (A^{-1})^T
@@ -1195,8 +1196,10 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     unsigned char* b = nullptr;
     chk(dalloc(&b, orb * csz, &tot)); p->psi = b; b = nullptr;
     chk(dalloc(&b, orb * csz, &tot)); p->Y = b; b = nullptr;
-    chk(dalloc(&b, (size_t)p->fields_cap * field_bytes, &tot)); p->scratch = b; b = nullptr;
-    chk(dalloc(&b, (size_t)p->fields_cap * field_bytes, &tot)); p->scratch2 = b;
+    // behind each scratch buffer, the kernel tables v/(4 pi) of one wave (one per k')
+    const size_t sbytes = (size_t)p->fields_cap * field_bytes + (size_t)nkp * ng * (csz / 2);
+    chk(dalloc(&b, sbytes, &tot)); p->scratch = b; b = nullptr;
+    chk(dalloc(&b, sbytes, &tot)); p->scratch2 = b;
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
   for (cudaEvent_t* ev : {&p->ev_fork, &p->ev_join, &p->ev_y, &p->ev_iso})

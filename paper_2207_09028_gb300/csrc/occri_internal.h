@@ -73,6 +73,7 @@ struct PairParams {
                              // fields): ng rounded up to 64, every field 512-byte aligned
   int k, kp0, nkp;
   int diag;                  // 1: the wave is (k, k) and holds the fields i <= j only
+  long long vt_off;          // bytes from a scratch buffer's start to its kernel tables
   int* status;               // plan status word (first device error, k), for bounded waits
   int D[3];
   const int* kint;           // [nk][3]
@@ -133,7 +134,8 @@ struct Plan {
   // long, so each starts 512-byte aligned (whole-tile bulk copies).
   void* psi = nullptr;       // [nk][nocc][fs] cplx_t<T>
   void* Y = nullptr;         // [nk][nocc][fs] cplx_t<T>
-  void* scratch = nullptr;   // [fields_cap][fs] cplx_t<T>, waves on the plan's stream
+  void* scratch = nullptr;   // [fields_cap][fs] cplx_t<T>, waves on the plan's stream, then
+                             // the wave's kernel tables [nkp_wave][m3][m1][m2] T
   void* scratch2 = nullptr;  // the same for the waves on the second stream
   // Consecutive waves alternate between the plan's stream and `aux`, each with its own
   // scratch, so one wave's passes overlap the next one's; only the accumulation passes,
@@ -231,10 +233,11 @@ cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, do
                             cudaStream_t s);
 
 // Largest nocc whose FP32 waves run the inverse along m3 and the Y accumulation as one
-// fused pass (three launches per wave instead of four).
+// fused pass. A wave launches the kernel-table fill and passes A and B, then the fused
+// pass or passes C and D.
 constexpr int kFusedCdNoc = 8;
 template <typename T> constexpr int pair_wave_launches(int nocc) {
-  return (std::is_same<T, float>::value && nocc <= kFusedCdNoc) ? 3 : 4;
+  return (std::is_same<T, float>::value && nocc <= kFusedCdNoc) ? 4 : 5;
 }
 
 // scratch per wave (MB): how many k' one wave takes when nocc^2 fields of a k' fit

@@ -110,14 +110,17 @@ __device__ __forceinline__ void record_timeout(int* status) {
 
 // ------------------------------------------------------------------ async plane staging
 // cp.async copies global -> shared without staging through registers, so a whole
-// plane is in flight per CTA. Element size 8 B (FP32 complex) or 16 B (FP64 complex).
+// plane is in flight per CTA. 4, 8 or 16 bytes, both addresses aligned to the size.
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   if constexpr (BYTES == 16)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-  else
+  else if constexpr (BYTES == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int PENDING>
@@ -468,6 +471,46 @@ __device__ __forceinline__ T bin_value(const PairParams& p, const Consts<T>& k,
   return (c.nv == 1 && !t1) ? s : s / T(c.nv * (t1 ? 2 : 1));
 }
 
+// v/(4 pi) (DERIV: its omega-derivative) on the bins (m1, m2) of plane m3 for the wave's
+// k' = kp0 + kpl: out[m1 N + m2], rows m1 = r0, r0 + rs, ... of every column. ax1 is an
+// N-entry scratch table in shared memory; every thread of the CTA calls this (one
+// __syncthreads inside, between the axis-1 table and its use).
+template <typename T, int N, bool DERIV>
+__device__ __forceinline__ void fill_vtab(const PairParams& p, const MetricHL<T>& gm, int m3,
+                                          int kpl, Axis1<T>* ax1, T* out, int r0, int rs) {
+  const int kp = p.kp0 + kpl;
+  int Q[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
+  for (int t = threadIdx.x; t < N; t += blockDim.x)
+    ax1[t] = axis1_entry<T>(gm, axis_int(t, Q[0], p.D[0], N));
+  __syncthreads();
+  // one rolled loop per column (split between the line's threads)
+  constexpr int SP = line_split(N);
+  const int c = (int)threadIdx.x / SP, h = (int)threadIdx.x % SP;
+  if (c < N) {
+    const ColumnConst<T> cc = column_const<T>(gm, axis_int(c, Q[1], p.D[1], N),
+                                              axis_int(m3, Q[2], p.D[2], N));
+#pragma unroll 1
+    for (int m1 = r0 + h * rs; m1 < N; m1 += SP * rs)
+      out[m1 * N + c] = bin_value<T, DERIV>(p, gm, ax1[m1], cc);
+  }
+}
+
+// The wave's kernel tables vt[kpl][m3][m1][m2] = v/(4 pi), once per wave, for pass B to
+// copy plane by plane (instead of every pass-B CTA forming the planes it meets). CTA
+// (m3, kpl, z) fills rows m1 = z (mod kVtabSplit) of plane m3.
+constexpr int kVtabSplit = 4;
+template <typename T, int N>
+__global__ void __launch_bounds__(threads_for(N))
+vtab_kernel(T* __restrict__ vt, PairParams p) {
+  __shared__ Axis1<T> ax1[N];
+  const int m3 = blockIdx.x, kpl = blockIdx.y;
+  const MetricHL<T> gm(p);
+  fill_vtab<T, N, false>(p, gm, m3, kpl, ax1, vt + ((size_t)kpl * N + m3) * N * N,
+                         (int)blockIdx.z, kVtabSplit);
+}
+
 // ------------------------------------------------------------------ pass A
 // plane n1 of field (i, j): rho = conj(u_jk') u_ik (= conj(psi_jk') psi_ik e^{-iq.r}, the
 // orbitals being held as their periodic parts u); FFT along n3, then n2.
@@ -515,26 +558,34 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
 }
 
 // ------------------------------------------------------------------ pass B
-// Plane buffers per pass-B CTA: 2 copies the next item in while the current one is
-// transformed; 1 leaves room for a fourth CTA per SM, whose warps cover the copies.
-constexpr int kPassBBuffers = 1;
 // Items (m3, field), m3-major; CTA b takes the contiguous chunk [b c, (b + 1) c) of
 // them (c = ceil(items / grid), the grid being the SMs' resident CTA slots), so there is
 // no partly filled last round of CTAs. Per item: FFT along n1, multiply by v/(4 pi),
-// inverse along m1, inverse along m2. Consecutive items share m3 and (mostly) q, so the
-// kernel values of a plane are formed only when (m3, k') changes; the next item's plane
-// is copied in while the current one is transformed (two plane buffers).
-// With DOMEGA: the forward part only, accumulating sum_m (dv/d omega)/(4 pi) |rho^(m)|^2.
+// inverse along m2, inverse along m1. Consecutive items share m3 and (mostly) q, so a
+// plane of kernel values is copied in (from the wave's tables, vt) only when (m3, k')
+// changes, in the same cp.async group as the item's plane. One plane buffer per CTA: a
+// fourth CTA per SM hides the copies better than a second buffer did.
+// With DOMEGA: the forward part only, accumulating sum_m (dv/d omega)/(4 pi) |rho^(m)|^2,
+// with the derivative's kernel values formed in the CTA.
+template <typename T, int N>
+__device__ __forceinline__ void copy_table(T* dst, const T* src) {
+  // even N: N^2 values are a whole number of 16-byte pieces, and every plane of the
+  // tables and of the shared-memory layout starts 16-byte aligned
+  constexpr int BYTES = (N % 2 == 0) ? 16 : (int)sizeof(T);
+  constexpr int PER = BYTES / (int)sizeof(T);
+  for (int e = threadIdx.x; e < N * N / PER; e += blockDim.x)
+    cp_async<BYTES>(dst + e * PER, src + e * PER);
+}
+
 template <typename T, int N, bool DOMEGA>
 __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const PairParams& p,
-                                            double* dacc) {
+                                            const T* __restrict__ vt, double* dacc) {
   using C2 = cplx_t<T>;
   constexpr int P = pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2* planes = reinterpret_cast<C2*>(smem_raw);                      // 2 x [n1][m2]
-  constexpr int NB = kPassBBuffers;
-  Axis1<T>* ax1 = reinterpret_cast<Axis1<T>*>(planes + NB * N * P);  // [m1]
-  T* vtab = reinterpret_cast<T*>(ax1 + N);                           // [m1][m2] v or dv
+  C2* plane = reinterpret_cast<C2*>(smem_raw);                 // [n1][m2]
+  T* vtab = reinterpret_cast<T*>(plane + N * P);               // [m1][m2] v or dv
+  Axis1<T>* ax1 = reinterpret_cast<Axis1<T>*>(vtab + N * N);   // [m1] (DOMEGA)
   __shared__ double red[4];
   const int nf = wave_fields(p.nocc, p.nkp, p.diag);
   const int items = N * nf;
@@ -542,47 +593,35 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
   const int i0 = min(items, (int)blockIdx.x * per);
   const int i1 = min(items, i0 + per);
   const MetricHL<T> gm(p);
-  auto plane_src = [&](int it) {
-    const int m3 = it / nf, f = it - (it / nf) * nf;
-    return S + (size_t)f * p.fs + (size_t)m3 * N * N;
-  };
-  if (i0 < i1) stage_plane<T, N, P>(planes, plane_src(i0));
-  cp_async_commit();
   int m3_tab = -1, kpl_tab = -1;
+  // the item's plane and, where (m3, k') changes, its plane of kernel values
+  auto stage = [&](int it) {
+    const int m3 = it / nf, f = it - (it / nf) * nf;
+    stage_plane<T, N, P>(plane, S + (size_t)f * p.fs + (size_t)m3 * N * N);
+    if constexpr (!DOMEGA) {
+      const int kpl = field_idx(f, p.nocc, p.diag).kpl;
+      if (m3 != m3_tab || kpl != kpl_tab) {   // uniform over the CTA
+        m3_tab = m3;
+        kpl_tab = kpl;
+        copy_table<T, N>(vtab, vt + ((size_t)kpl * N + m3) * N * N);
+      }
+    }
+  };
+  if (i0 < i1) stage(i0);
+  cp_async_commit();
   T dsum = T(0);
 #pragma unroll 1
   for (int it = i0; it < i1; ++it) {
-    C2* plane = planes + ((it - i0) % NB) * N * P;
     const int m3 = it / nf, f = it - (it / nf) * nf;
     const FieldIdx fi = field_idx(f, p.nocc, p.diag);
-    if constexpr (NB == 2) {
-      if (it + 1 < i1)   // the other buffer was released by the barrier ending item it - 1
-        stage_plane<T, N, P>(planes + ((it + 1 - i0) & 1) * N * P, plane_src(it + 1));
-      cp_async_commit();
-    }
-    if (fi.kpl != kpl_tab || m3 != m3_tab) {   // uniform over the CTA
-      kpl_tab = fi.kpl;
-      m3_tab = m3;
-      const int kp = p.kp0 + fi.kpl;
-      int Q[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
-      for (int t = threadIdx.x; t < N; t += blockDim.x)
-        ax1[t] = axis1_entry<T>(gm, axis_int(t, Q[0], p.D[0], N));
-      __syncthreads();
-      // kernel values, one rolled loop per column (split between the line's threads)
-      constexpr int SP = line_split(N);
-      const int c = (int)threadIdx.x / SP, h = (int)threadIdx.x % SP;
-      if (c < N) {
-        const ColumnConst<T> cc = column_const<T>(gm, axis_int(c, Q[1], p.D[1], N),
-                                                  axis_int(m3, Q[2], p.D[2], N));
-#pragma unroll 1
-        for (int m1 = h; m1 < N; m1 += SP)
-          vtab[m1 * N + c] = bin_value<T, DOMEGA>(p, gm, ax1[m1], cc);
+    if constexpr (DOMEGA) {
+      if (fi.kpl != kpl_tab || m3 != m3_tab) {   // uniform over the CTA
+        kpl_tab = fi.kpl;
+        m3_tab = m3;
+        fill_vtab<T, N, true>(p, gm, m3, fi.kpl, ax1, vtab, 0, 1);
       }
     }
-    // this item's plane has landed (with two buffers the next one may be in flight)
-    if constexpr (NB == 2) cp_async_wait<1>(); else cp_async_wait<0>();
+    cp_async_wait<0>();   // this item's plane (and table) have landed
     __syncthreads();
     // an unordered pair stands for itself and its reverse, except (k, k, i, i)
     const T wgt = (p.diag && fi.i == fi.j) ? T(1) : T(2);
@@ -607,12 +646,10 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
       run_lines<T, N>(plane, P, false, true, false, [&](int line, int k, T& re, T& im) {
         buf[(size_t)k * N + line] = mk<T>(re, im);
       });
-      __syncthreads();   // releases this buffer for the copy NB items ahead
+      __syncthreads();   // releases the buffers for the next item's copies
     }
-    if constexpr (NB == 1) {   // one buffer: the next plane is copied in only now
-      if (it + 1 < i1) stage_plane<T, N, P>(planes, plane_src(it + 1));
-      cp_async_commit();
-    }
+    if (it + 1 < i1) stage(it + 1);
+    cp_async_commit();
   }
   if constexpr (DOMEGA) {
     double part = double(dsum);
@@ -629,14 +666,14 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
 
 template <typename T, int N>
 __global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
-pass_b(cplx_t<T>* __restrict__ S, PairParams p) {
-  pass_b_body<T, N, false>(S, p, nullptr);
+pass_b(cplx_t<T>* __restrict__ S, PairParams p, const T* __restrict__ vt) {
+  pass_b_body<T, N, false>(S, p, vt, nullptr);
 }
 
 template <typename T, int N>
 __global__ void __launch_bounds__(threads_for(N), min_blocks(N, sizeof(cplx_t<T>)))
 pass_b_domega(cplx_t<T>* __restrict__ S, PairParams p, double* dacc) {
-  pass_b_body<T, N, true>(S, p, dacc);
+  pass_b_body<T, N, true>(S, p, nullptr, dacc);
 }
 
 // Resident CTA slots of a kernel on this device (SMs x CTAs per SM), at least 1.
@@ -1266,27 +1303,11 @@ pass_b_domega2(const cplx_t<T>* __restrict__ S0, const cplx_t<T>* __restrict__ S
   const int m3 = blockIdx.x;
   const int f = blockIdx.y;
   const FieldIdx fi = field_idx(f, p.nocc, p.diag);
-  const int kp = p.kp0 + fi.kpl;
   stage_plane<T, N, P>(rho, S0 + (size_t)f * p.fs + (size_t)m3 * N * N);
   stage_plane<T, N, P>(sig, S1 + (size_t)f * p.fs + (size_t)m3 * N * N);
   cp_async_commit();
   const MetricHL<T> gm(p);
-  int Q[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
-  for (int t = threadIdx.x; t < N; t += blockDim.x)
-    ax1[t] = axis1_entry<T>(gm, axis_int(t, Q[0], p.D[0], N));
-  __syncthreads();
-  {
-    constexpr int SP = line_split(N);
-    const int c = (int)threadIdx.x / SP, h = (int)threadIdx.x % SP;
-    if (c < N) {
-      const ColumnConst<T> cc = column_const<T>(gm, axis_int(c, Q[1], p.D[1], N),
-                                                axis_int(m3, Q[2], p.D[2], N));
-#pragma unroll 1
-      for (int m1 = h; m1 < N; m1 += SP) vtab[m1 * N + c] = bin_value<T, true>(p, gm, ax1[m1], cc);
-    }
-  }
+  fill_vtab<T, N, true>(p, gm, m3, fi.kpl, ax1, vtab, 0, 1);
   cp_async_wait<0>();
   __syncthreads();
   T dsum = T(0);
@@ -1426,7 +1447,7 @@ cudaError_t launch_pass_e(const PairParams& p, const cplx_t<T>* SW, const cplx_t
 
 template <int N> constexpr size_t smem_a(size_t csz) { return csz * N * pitch(N); }
 template <int N> constexpr size_t smem_b(size_t csz, size_t tab) {
-  return kPassBBuffers * csz * N * pitch(N) + N * tab + csz / 2 * N * N;
+  return csz * N * pitch(N) + N * tab + csz / 2 * N * N;
 }
 
 template <int N> constexpr size_t smem_c(size_t csz) { return csz * N * pitch(N); }
@@ -1456,11 +1477,13 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   if (ev) cudaEventRecord(ev[0], st);
   pass_a<T, N><<<dim3(N, nf), nt, sa, st>>>(psi, S, p);
   if (ev) cudaEventRecord(ev[1], st);
-  pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S, p);
+  T* vt = reinterpret_cast<T*>(reinterpret_cast<char*>(S) + p.vt_off);
+  vtab_kernel<T, N><<<dim3(N, p.diag ? 1 : p.nkp, kVtabSplit), nt, 0, st>>>(vt, p);
+  pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S, p, vt);
   if (ev) cudaEventRecord(ev[2], st);
   // FP32 waves of nocc <= kCdNoc: passes C and D fused (the potentials stay on chip)
   constexpr bool kFusable = std::is_same<T, float>::value;
-  const bool fused = pair_wave_launches<T>(p.nocc) == 3;
+  const bool fused = pair_wave_launches<T>(p.nocc) == 4;
   if (!fused) pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S, p);
   if (ev_y) cudaStreamWaitEvent(st, ev_y, 0);   // the previous wave's Y updates
   cudaError_t e = cudaSuccess;
@@ -1530,9 +1553,11 @@ cudaError_t run_vjp_wave(const PairParams& p, const cplx_t<T>* psi, const cplx_t
   if (dacc)
     pass_b_domega2<T, N><<<dim3(N, nf), nt, sb + sizeof(C2) * N * pitch(N), st>>>(S0, S1, p,
                                                                                 dacc);
-  pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S0, p);
+  T* vt = reinterpret_cast<T*>(reinterpret_cast<char*>(S0) + p.vt_off);
+  vtab_kernel<T, N><<<dim3(N, p.diag ? 1 : p.nkp, kVtabSplit), nt, 0, st>>>(vt, p);
+  pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S0, p, vt);
   pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S0, p);
-  pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S1, p);
+  pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S1, p, vt);
   pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S1, p);
   const cudaError_t e = launch_pass_e<T>(p, S0, S1, psi, gam, G, st);
   return e != cudaSuccess ? e : cudaGetLastError();
