@@ -28,11 +28,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) of one full mixed-precision wave (pass_a + pass_b + pass_cd), keyed
-# by ("round_trip", grid edge, fields per wave, precision), from one ncu --set full capture of
-# the same launch shape (an off-diagonal 64-field wave at 60^3 of the 2x2x2-k profiling cell,
-# profiles/pair_passes_wave64_60cube_fp32.md; cold cache, each launch replayed alone).
-TRAFFIC = {("round_trip", 60, 64, "mixed"): 423.2e6}
+# DRAM bytes (read + write) of one full mixed-precision wave (vtab_kernel + pass_a + pass_b +
+# pass_cd), keyed by ("round_trip", grid edge, fields per wave, precision), from one ncu --set
+# full capture of the same launch shape (an off-diagonal 64-field wave at 60^3 of the 2x2x2-k
+# profiling cell, profiles/pair_passes_wave64_60cube_fp32.md; cold cache, each launch replayed
+# alone).
+TRAFFIC = {("round_trip", 60, 64, "mixed"): 425.0e6}
 
 METRIC = "K-builds/s at 6x6x6 k, 350 AO; mixed vs FP64 GPU at |dE_x|<=1e-6 Ha/cell"
 UNIT = "K-builds/s"
@@ -289,7 +290,8 @@ def main():
         fpw = int(info["fields_per_wave"])
         mixed = int(info.get("precision", 1)) == 1
         fused = mixed and w.nocc <= 8   # FP32 waves of nocc <= 8 fuse passes C and D
-        passes = "pass_a + pass_b + pass_cd" if fused else "pass_a + pass_b + pass_c + pass_d"
+        passes = ("vtab_kernel + pass_a + pass_b + pass_cd" if fused
+                  else "vtab_kernel + pass_a + pass_b + pass_c + pass_d")
         roof = {"kernel": f"pair round trip: {passes} over waves of "
                           f"{fpw} fields of {w.grid[0]}^3 (two streams)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
