@@ -1072,15 +1072,14 @@ constexpr int kCdNoc = kFusedCdNoc;   // largest nocc of the fused form
 // kCdFields CW lines per transform round with two threads a line), MB CTAs per SM.
 struct CdShape {
   static constexpr int CW = 4, NT = 256, MB = 2;
-  static constexpr bool DB = false;   // two batch buffers (next batch copied in meanwhile)
 };
 // Plane pitch (points) in shared memory: >= N CW and = CW (mod 16), so that the 8-byte
 // loads of a half warp (16 / CW fields x CW columns at one m3) hit 32 distinct banks.
 constexpr int cd_pitch(int n, int cw) {
   return n * cw + ((cw - (n * cw) % 16) + 16) % 16;
 }
-constexpr size_t cd_smem(int n, int cw, bool db) {
-  return sizeof(float2) * (size_t)cd_pitch(n, cw) * ((db ? 2 : 1) * kCdFields + 2 * kCdNoc);
+constexpr size_t cd_smem(int n, int cw) {
+  return sizeof(float2) * (size_t)cd_pitch(n, cw) * (kCdFields + 2 * kCdNoc);
 }
 
 // Rows n3 = 0..N-1 of columns [c0, c0 + CW) at row n1 of np planes (plane pl starts at
@@ -1124,17 +1123,16 @@ __device__ __forceinline__ CdBatch cd_batch(int kpl, int i0, int nocc, int diag)
   return b;
 }
 
-template <int N, int CW, int NT, int MB, bool DB>
+template <int N, int CW, int NT, int MB>
 __global__ void __launch_bounds__(NT, MB)
 pass_cd(const float2* __restrict__ S, const float2* __restrict__ psi, float2* __restrict__ Y,
         PairParams p) {
   static_assert(N * CW <= NT, "one point per thread");
   constexpr int PP = cd_pitch(N, CW);
   constexpr int NOC = kCdNoc;
-  constexpr int NBUF = DB ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* W0 = reinterpret_cast<float2*>(smem_raw);   // NBUF x [field of batch][n3][c], pitch PP
-  float2* Uk = W0 + NBUF * kCdFields * PP;             // [i][n3][c]
+  float2* Wb = reinterpret_cast<float2*>(smem_raw);   // [field of batch][n3][c], pitch PP
+  float2* Uk = Wb + kCdFields * PP;                    // [i][n3][c]
   float2* Uq = Uk + NOC * PP;                          // [j][n3][c]
   const int c0 = blockIdx.x * CW, n1 = blockIdx.y;
   const int nocc = p.nocc;
@@ -1158,24 +1156,14 @@ pass_cd(const float2* __restrict__ S, const float2* __restrict__ psi, float2* __
                      c0);
   CdBatch cur = cd_batch(0, 0, nocc, p.diag);
   if (!p.diag) copy_uq(0);
-  copy_w(W0, cur);
+  copy_w(Wb, cur);
   cp_async_commit();
-  int buf = 0;
 #pragma unroll 1
   while (true) {
     const bool more = cur.i1 < nocc || cur.kpl + 1 < nkl;
     const bool end_kpl = cur.i1 >= nocc;
-    auto next_batch = [&]() {
-      return end_kpl ? cd_batch(cur.kpl + 1, 0, nocc, p.diag)
-                     : cd_batch(cur.kpl, cur.i1, nocc, p.diag);
-    };
-    // with two buffers, the next batch of the same k' is copied in while this one is used
-    const bool pre = DB && !end_kpl;
-    if (pre) copy_w(W0 + (buf ^ 1) * kCdFields * PP, next_batch());
-    cp_async_commit();
-    if (pre) cp_async_wait<1>(); else cp_async_wait<0>();
+    cp_async_wait<0>();   // this batch (and at its k' change the u_k' planes) has landed
     __syncthreads();
-    float2* Wb = W0 + buf * kCdFields * PP;
     // inverse along m3 of every (field, column) line of the batch, in place
     {
       const int lines = cur.cnt * CW;
@@ -1261,13 +1249,11 @@ pass_cd(const float2* __restrict__ S, const float2* __restrict__ psi, float2* __
     }
     __syncthreads();   // this batch's buffer (and at a k' change the u_{k'} planes) is free
     if (!more) break;
-    const CdBatch nxt = next_batch();
-    if (!pre) {
-      if (end_kpl && !p.diag) copy_uq(nxt.kpl);
-      copy_w(W0 + (buf ^ (DB ? 1 : 0)) * kCdFields * PP, nxt);
-    }
-    cp_async_commit();   // the next batch's copies form a group of their own
-    buf ^= DB ? 1 : 0;
+    const CdBatch nxt = end_kpl ? cd_batch(cur.kpl + 1, 0, nocc, p.diag)
+                                : cd_batch(cur.kpl, cur.i1, nocc, p.diag);
+    if (end_kpl && !p.diag) copy_uq(nxt.kpl);
+    copy_w(Wb, nxt);
+    cp_async_commit();
     cur = nxt;
   }
   if (pvalid) {
@@ -1468,9 +1454,9 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
     cudaFuncSetAttribute(pass_b<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
     cudaFuncSetAttribute(pass_c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
     if constexpr (std::is_same<T, float>::value)
-      cudaFuncSetAttribute(pass_cd<N, CdShape::CW, CdShape::NT, CdShape::MB, CdShape::DB>,
+      cudaFuncSetAttribute(pass_cd<N, CdShape::CW, CdShape::NT, CdShape::MB>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)cd_smem(N, CdShape::CW, CdShape::DB));
+                           (int)cd_smem(N, CdShape::CW));
     slots_b = resident_slots(pass_b<T, N>, nt, sb);
     configured = true;
   }
@@ -1482,16 +1468,15 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S, p, vt);
   if (ev) cudaEventRecord(ev[2], st);
   // FP32 waves of nocc <= kCdNoc: passes C and D fused (the potentials stay on chip)
-  constexpr bool kFusable = std::is_same<T, float>::value;
   const bool fused = pair_wave_launches<T>(p.nocc) == 4;
   if (!fused) pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S, p);
   if (ev_y) cudaStreamWaitEvent(st, ev_y, 0);   // the previous wave's Y updates
   cudaError_t e = cudaSuccess;
-  if constexpr (kFusable) {
+  if constexpr (std::is_same<T, float>::value) {
     if (fused)
-      pass_cd<N, CdShape::CW, CdShape::NT, CdShape::MB, CdShape::DB>
+      pass_cd<N, CdShape::CW, CdShape::NT, CdShape::MB>
           <<<dim3((N + CdShape::CW - 1) / CdShape::CW, N), CdShape::NT,
-              cd_smem(N, CdShape::CW, CdShape::DB), st>>>((const float2*)S, (const float2*)psi,
+              cd_smem(N, CdShape::CW), st>>>((const float2*)S, (const float2*)psi,
                                                            (float2*)Y, p);
   }
   if (!fused) e = launch_pass_d<T>(p, S, psi, Y, st);
