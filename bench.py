@@ -274,7 +274,8 @@ def main():
     # Roofline of the dominant work, the pair round trip (steps c, d). Its unit is one
     # transformed field; each of the two 3-D transforms reads and writes the field once,
     # so the streaming model is 2 x 2 x 8 B x N_g = 32 N_g bytes per field in FP32 (c64).
-    # A round trip runs as four launches (pass_a..pass_d) over a wave of fields; waves
+    # A round trip runs as four launches over a wave of fields (kernel tables, pass_a,
+    # pass_b and the fused pass_cd; FP64 or nocc > 8: pass_c and pass_d instead); waves
     # alternate between two streams, so the achieved rate is taken over the wall time of
     # the whole wave loop (CUDA events on the plan's stream around the loop, every timed
     # build). The per-pass split comes from every `timing_every`-th wave, run alone.

@@ -112,8 +112,10 @@ typedef struct {
 enum {
   OCCRI_STAGE_ORBITALS = 0,  /* (a)+(b) */
   OCCRI_STAGE_PAIR_A = 1,    /* (c)+(d) pass A: pair density, FFT along n3 and n2 */
-  OCCRI_STAGE_PAIR_B = 2,    /* (d) pass B: FFT along n1, kernel, inverse along m1, m2 */
-  OCCRI_STAGE_PAIR_C = 3,    /* (d) pass C: inverse along m3; pass D: accumulate Y */
+  OCCRI_STAGE_PAIR_B = 2,    /* (d) kernel tables; pass B: FFT along n1, kernel, inverse
+                                along m2, m1 */
+  OCCRI_STAGE_PAIR_C = 3,    /* (d) inverse along m3 and the Y accumulation (one fused pass
+                                for FP32 waves of nocc <= 8, else passes C and D) */
   OCCRI_STAGE_CONTRACT = 4,  /* (e) */
   OCCRI_STAGE_ASSEMBLE = 5,  /* (f) */
   OCCRI_STAGE_PAIRS = 6,     /* (c)+(d): the whole loop over pair waves, wall time */
