@@ -148,6 +148,59 @@ def oracle_sample_seconds(w, n_k: int = 2, pts=(256, 1024), seed: int = 0):
 
 # ---------------------------------------------------------------- ranks
 
+def pair_waves(nk: int, nocc: int, fields_per_wave: int) -> int:
+    """Waves of one build: (k, k) once per k, then blocks of up to nkp k' > k."""
+    nkp = max(1, fields_per_wave // (nocc * nocc))
+    return nk + sum((nk - 1 - k + nkp - 1) // nkp for k in range(nk))
+
+
+def stage_ms_per_build(stages: dict, waves: int, steps: int) -> dict:
+    """Per-build stage times. Pair-transform passes are timed on every `timing_every`-th
+    wave only, so their sampled sums are scaled by (waves per build / sampled waves)."""
+    out = {}
+    for name, st in stages.items():
+        if name.startswith("pair_"):
+            out[name] = st["ms"] * waves / max(1, st["launches"])
+        else:
+            out[name] = st["ms"] / steps
+    return out
+
+
+def roofline(stages: dict, info: dict, edge: int, ng: int, nocc: int, hbm: float,
+             peak_kind: str):
+    """Roofline of the dominant work, the pair round trip (steps c, d).
+
+    Its unit is one transformed field; each of the two 3-D transforms reads and writes the
+    field once, so the streaming model is 2 x 2 x 8 B x N_g = 32 N_g bytes per field in
+    FP32 (c64). A round trip runs as four launches over a wave of fields (kernel tables,
+    pass_a, pass_b and the fused pass_cd; FP64 or nocc > 8: pass_c and pass_d instead);
+    waves alternate between two streams, so the achieved rate is taken over the wall time
+    of the whole wave loop (the `pairs` stage: CUDA events on the plan's stream around the
+    loop, every timed build). The per-pass split comes from the sampled waves, run alone.
+    """
+    loop = stages.get("pairs", {})
+    if not loop.get("launches") or loop.get("ms", 0) <= 0:
+        return None
+    pair = [s_ for s_ in ("pair_a", "pair_b", "pair_c") if s_ in stages]
+    rt_ms = sum(stages[s_]["ms"] for s_ in pair)
+    fields = loop["units"]
+    achieved = 32.0 * ng * fields / (loop["ms"] / 1e3) / 1e9
+    fpw = int(info["fields_per_wave"])
+    mixed = int(info.get("precision", 1)) == 1
+    fused = mixed and nocc <= 8   # FP32 waves of nocc <= 8 fuse passes C and D
+    passes = ("vtab_kernel + pass_a + pass_b + pass_cd" if fused
+              else "vtab_kernel + pass_a + pass_b + pass_c + pass_d")
+    return {"kernel": f"pair round trip: {passes} over waves of {fpw} fields of {edge}^3 "
+                      "(two streams)",
+            "bound": "hbm", "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
+            "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": TRAFFIC.get(("round_trip", edge, fpw, "mixed" if mixed else "fp64")),
+            "bytes_per_launch": 32.0 * ng * fpw,
+            "ms_per_launch": loop["ms"] * fpw / fields,
+            "pass_ms_share": ({s_: stages[s_]["ms"] / rt_ms for s_ in pair} if rt_ms > 0
+                              else None)}
+
+
 def max_over_ranks(ms: float, dist=None, device=None) -> float:
     """The slowest rank's time (replicas: every rank runs the whole build on its GPU)."""
     if dist is None:
@@ -261,49 +314,10 @@ def main():
     value = job_throughput(world, args.steps, ms)
     info = plan.info()
 
-    # Per-build stage times. Pair-transform passes are timed on every `timing_every`-th
-    # wave, so their sampled sums are scaled by (waves per build / sampled waves).
-    nkp = max(1, int(info["fields_per_wave"]) // (w.nocc * w.nocc))
-    waves = w.nk + sum((w.nk - 1 - k + nkp - 1) // nkp for k in range(w.nk))
-    stage_ms = {}
-    for name, st in stages.items():
-        if name.startswith("pair_"):
-            stage_ms[name] = st["ms"] * waves * args.steps / max(1, st["launches"]) / args.steps
-        else:
-            stage_ms[name] = st["ms"] / args.steps
-    # Roofline of the dominant work, the pair round trip (steps c, d). Its unit is one
-    # transformed field; each of the two 3-D transforms reads and writes the field once,
-    # so the streaming model is 2 x 2 x 8 B x N_g = 32 N_g bytes per field in FP32 (c64).
-    # A round trip runs as four launches over a wave of fields (kernel tables, pass_a,
-    # pass_b and the fused pass_cd; FP64 or nocc > 8: pass_c and pass_d instead); waves
-    # alternate between two streams, so the achieved rate is taken over the wall time of
-    # the whole wave loop (CUDA events on the plan's stream around the loop, every timed
-    # build). The per-pass split comes from every `timing_every`-th wave, run alone.
+    waves = pair_waves(w.nk, w.nocc, int(info["fields_per_wave"]))
+    stage_share = stage_ms_per_build(stages, waves, args.steps)
     hbm, peak_kind = _peaks()
-    ng = w.ng
-    roof = None
-    pair = [s_ for s_ in ("pair_a", "pair_b", "pair_c") if s_ in stages]
-    rt_ms = sum(stages[s_]["ms"] for s_ in pair)
-    loop = stages.get("pairs", {})
-    if loop.get("launches") and loop.get("ms", 0) > 0:
-        fields = loop["units"]
-        achieved = 32.0 * ng * fields / (loop["ms"] / 1e3) / 1e9
-        fpw = int(info["fields_per_wave"])
-        mixed = int(info.get("precision", 1)) == 1
-        fused = mixed and w.nocc <= 8   # FP32 waves of nocc <= 8 fuse passes C and D
-        passes = ("vtab_kernel + pass_a + pass_b + pass_cd" if fused
-                  else "vtab_kernel + pass_a + pass_b + pass_c + pass_d")
-        roof = {"kernel": f"pair round trip: {passes} over waves of "
-                          f"{fpw} fields of {w.grid[0]}^3 (two streams)",
-                "bound": "hbm", "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
-                "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": TRAFFIC.get(("round_trip", w.grid[0], fpw,
-                                        "mixed" if mixed else "fp64")),
-                "bytes_per_launch": 32.0 * ng * fpw,
-                "ms_per_launch": loop["ms"] * fpw / fields,
-                "pass_ms_share": ({s_: stages[s_]["ms"] / rt_ms for s_ in pair} if rt_ms > 0
-                                  else None)}
-    stage_share = stage_ms
+    roof = roofline(stages, info, w.grid[0], w.ng, w.nocc, hbm, peak_kind)
 
     out = {"impl": "occri", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
