@@ -69,3 +69,10 @@ def test_roofline_of_unfused_waves_has_no_borrowed_traffic(bench):
     assert "pass_c + pass_d" in wide["kernel"] and wide["traffic"] is None
     assert bench.roofline({"pairs": {"ms": 0.0, "launches": 0, "units": 0}},
                           {"fields_per_wave": 64}, 60, ng, 8, 6000.0, "measured") is None
+
+
+def test_l2_note_follows_the_field_sizes(bench):
+    big = bench.l2_note(216, 8, 60 ** 3)         # 216 x 8 x 216,000 x 8 B = 2.99 GB
+    assert big.startswith("no flush") and "3 GB" in big
+    small = bench.l2_note(1, 4, 24 ** 3)
+    assert small.startswith("fields fit L2")
