@@ -322,9 +322,11 @@ def apply_coulomb_operator(f: np.ndarray, v: np.ndarray, qfrac, dft: bool = Fals
     ph = grid_phase(grid, qfrac)
     rho = f * np.conj(ph)
     if dft:
+        # three 1-D DFT-matrix products, one axis at a time (the separable definition)
         f1, f2, f3 = dft_matrices(grid)
-        rhohat = np.einsum("ai,bj,ck,ijk->abc", f1, f2, f3, rho) / ng
-        u = np.einsum("ai,bj,ck,ijk->abc", np.conj(f1), np.conj(f2), np.conj(f3), v * rhohat)
+        rhohat = np.einsum("ai,bj,ck,ijk->abc", f1, f2, f3, rho, optimize=True) / ng
+        u = np.einsum("ai,bj,ck,ijk->abc", np.conj(f1), np.conj(f2), np.conj(f3), v * rhohat,
+                      optimize=True)
     else:
         rhohat = np.fft.fftn(rho) / ng
         u = ng * np.fft.ifftn(v * rhohat)
