@@ -10,7 +10,21 @@ HBM before the timed region; the orbital and accumulator fields (3 GB each)
 exceed L2, so no flush is needed between steps.
 
 Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead
-(bounded sample, extrapolated to a full build).
+(bounded sample on every host core, extrapolated to a full build).
+
+Other modes (one JSON line per point; none is the headline):
+
+    python bench.py --case 60 8 2 2 2 [--builds 2] [--precision mixed] [--timing]
+        builds of a small fixed profiling cell (fcc a = 5.43 A, 2 atoms, 6/4/3/2 s/p/d/f
+        shells per atom, exponents 0.1-20) with the given grid edge, nocc and Gamma-centred
+        k-mesh: the unit that ncu captures. A 1x1x1 mesh gives one wave of each pass; a
+        2x2x2 mesh adds waves with q = 1/2 on every axis, like most waves of a 6x6x6 mesh.
+    python bench.py --batch cfg4 [--builds 5]
+        the five lattice-constant cells one after another against one batch (graph) build.
+    python bench.py --sweep nk|nao [--steps 1]
+        K-builds/s of the bench cell at N_k = 1^3..6^3 (the N_k^2 scaling of Sec. III), or
+        at nao 26..350 on the 6x6x6 mesh (basis-size dependence of Sec. III), with the
+        fitted log-log slope.
 """
 from __future__ import annotations
 
@@ -31,8 +45,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one full mixed-precision wave (vtab_kernel + pass_a + pass_b +
 # pass_cd), keyed by ("round_trip", grid edge, fields per wave, precision), from one ncu --set
 # full capture of the same launch shape (an off-diagonal 64-field wave at 60^3 of the 2x2x2-k
-# profiling cell, profiles/pair_passes_wave64_60cube_fp32.md; cold cache, each launch replayed
-# alone).
+# profiling cell of `--case 60 8 2 2 2`; cold cache, each launch replayed alone).
 TRAFFIC = {("round_trip", 60, 64, "mixed"): 425.0e6}
 
 METRIC = "K-builds/s at 6x6x6 k, 350 AO; mixed vs FP64 GPU at |dE_x|<=1e-6 Ha/cell"
@@ -110,40 +123,110 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU oracle sample
 
-def oracle_sample_seconds(w, n_k: int = 2, pts=(256, 1024), seed: int = 0):
-    """Time the FP64 oracle on a bounded sample of one build and scale to a full build.
+def cpu_model() -> str:
+    """The host CPU's model name (x86 'model name', Arm 'Model name' from lscpu)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
 
-    Pair stage: the Algorithm-3 loop over n_k k-points (n_k^2 of the N_k^2 (k,k')
-    blocks, each nocc^2 FFT round trips on the full grid); its cost is exactly
-    linear in the number of blocks. AO stage: Bloch AOs for all k-points at two
-    point counts, fitted as a + b*n and evaluated at N_g (the oracle evaluates the
-    AOs once per build and keeps them for the contraction). Returns (seconds per full
-    build, sample description, wall seconds spent sampling).
-    """
+
+def _oracle_worker(job):
+    """One worker's share of the oracle sample (runs in a spawned process, one BLAS thread).
+
+    pairs: the Algorithm-3 loop over one k-point (its (k, k) block of nocc^2 FFT round trips
+    on the full grid) with seeded random orbitals; aos: Bloch AOs for every k at two point
+    counts; contract: the contraction of one k over `cpts` points. Returns wall seconds."""
     import oracle as O
-
+    (lattice, xyz, sa, sl, sx, kfrac, grid, kind, omega, g0, nocc, nao, k, seed, npts,
+     cpts) = job
     rng = np.random.default_rng(seed)
-    ng = int(np.prod(w.grid))
-    psi = (rng.standard_normal((n_k, w.nocc, ng)) + 1j * rng.standard_normal((n_k, w.nocc, ng)))
+    ng = int(np.prod(grid))
+    out = {}
+    psi = rng.standard_normal((1, nocc, ng)) + 1j * rng.standard_normal((1, nocc, ng))
     t0 = time.perf_counter()
-    O.occri_kc(w.lattice, w.grid, w.kfrac[:n_k], psi, None, w.kernel, w.omega,
-               O.g0_value(w.kernel, w.omega, w.g0_mode))
-    t_pairs = time.perf_counter() - t0
-    allpts = O.grid_points(w.lattice, w.grid)
-    ts = []
-    for n in pts:
+    O.occri_kc(lattice, grid, kfrac[k:k + 1], psi, None, kind, omega, g0)
+    out["pairs"] = time.perf_counter() - t0
+    allpts = O.grid_points(lattice, grid)
+    out["aos"] = []
+    for n in npts:
         sel = allpts[rng.choice(ng, n, replace=False)]
         t0 = time.perf_counter()
-        O.bloch_aos(w.lattice, w.xyz, w.shell_atom, w.shell_l, w.shell_alpha, w.kfrac, points=sel)
-        ts.append(time.perf_counter() - t0)
-    slope = max(0.0, (ts[1] - ts[0]) / (pts[1] - pts[0]))
-    t_ao_full = max(ts[0] - slope * pts[0], 0.0) + slope * ng
-    total = t_pairs * (w.nk / n_k) ** 2 + t_ao_full
-    desc = (f"oracle Algorithm-3 loop over {n_k} k-points ({n_k ** 2} of {w.nk ** 2} (k,k') blocks, "
-            f"{n_k ** 2 * w.nocc ** 2} FFT round trips of {w.grid[0]}^3), scaled by blocks; oracle "
-            f"Bloch AOs for all {w.nk} k at {pts[0]} and {pts[1]} points, fitted a+b*n and "
-            f"evaluated at {ng} points, once per build")
-    return total, desc, t_pairs + sum(ts)
+        O.bloch_aos(lattice, xyz, sa, sl, sx, kfrac, points=sel)
+        out["aos"].append(time.perf_counter() - t0)
+    chi = rng.standard_normal((1, nao, cpts)) + 1j * rng.standard_normal((1, nao, cpts))
+    y = rng.standard_normal((1, nocc, cpts)) + 1j * rng.standard_normal((1, nocc, cpts))
+    t0 = time.perf_counter()
+    O.contract_kc(lattice, chi, y)
+    out["contract"] = time.perf_counter() - t0
+    return out
+
+
+class OracleSampler:
+    """The FP64 oracle as it stands, timed on every host core on a bounded sample of one
+    build and extrapolated to the whole build.
+
+    Each of `workers` spawned processes (one BLAS thread each) runs, at the same time:
+    the oracle's Algorithm-3 loop for one k-point of the workload (one (k, k) block of
+    nocc^2 FFT round trips of the full grid; every block costs the same), the oracle's
+    Bloch AOs of all k at npts[0] and npts[1] grid points (fitted as a + b n per worker),
+    and its contraction of one k over cpts points. A build is N_k^2 blocks, N_g AO points
+    and N_k contractions of N_g points, spread over the same workers.
+    """
+
+    def __init__(self, w, workers=None, npts=(32, 96), cpts=16384):
+        import multiprocessing as mp
+        self.w = w
+        self.workers = workers or os.cpu_count() or 1
+        self.npts, self.cpts = npts, cpts
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        self.pool = mp.get_context("spawn").Pool(self.workers)
+        self.calls = 0
+
+    def sample(self):
+        """(seconds per full build, sample description, wall seconds of the sample)."""
+        import oracle as O
+        w = self.w
+        g0 = O.g0_value(w.kernel, w.omega, w.g0_mode)
+        jobs = [(w.lattice, w.xyz, w.shell_atom, w.shell_l, w.shell_alpha, w.kfrac, w.grid,
+                 w.kernel, w.omega, g0, w.nocc, w.nao, (self.calls * self.workers + i) % w.nk,
+                 1000 * self.calls + i, self.npts, self.cpts) for i in range(self.workers)]
+        self.calls += 1
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+        nw = self.workers
+        t_block = statistics.mean(r["pairs"] for r in res)        # one block on one core
+        n0, n1 = self.npts
+        slope = statistics.mean(max(0.0, (r["aos"][1] - r["aos"][0]) / (n1 - n0)) for r in res)
+        icpt = statistics.mean(max(0.0, r["aos"][0] - slope * n0) for r in res)
+        t_contract = statistics.mean(r["contract"] for r in res) * w.ng / self.cpts
+        # the build's work spread over nw cores
+        total = (w.nk ** 2 * t_block + (nw * icpt + slope * w.ng) + w.nk * t_contract) / nw
+        desc = (f"extrapolated: {nw} processes on {nw} cores ({cpu_model()}), each timing the "
+                f"oracle's Algorithm-3 loop over one k-point (1 of {w.nk ** 2} (k,k') blocks, "
+                f"{w.nocc ** 2} FFT round trips of {w.grid[0]}^3), its Bloch AOs of all {w.nk} k "
+                f"at {n0} and {n1} points (a + b n) and its contraction of one k over "
+                f"{self.cpts} points; scaled to {w.nk ** 2} blocks, {w.ng} points and {w.nk} "
+                "contractions, divided over the cores")
+        return total, desc, wall
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 # ---------------------------------------------------------------- ranks
@@ -231,6 +314,126 @@ def job_throughput(world: int, steps: int, ms: float) -> float:
     return world * steps / (ms / 1e3)
 
 
+# ---------------------------------------------------------------- other modes
+
+def profiling_cell(edge: int, nocc: int, mesh, seed: int = 77):
+    """The small fixed cell that ncu captures (see the module docstring)."""
+    from workloads import small_workload
+    return small_workload(a_ang=5.43, mesh=tuple(mesh), counts=(6, 4, 3, 2), lo=0.1, hi=20.0,
+                          nocc=nocc, grid=(edge,) * 3, seed=seed)
+
+
+def run_case(args):
+    import torch
+    import paper_2207_09028_gb300 as occri
+    edge, nocc, m1, m2, m3 = args.case
+    w = profiling_cell(edge, nocc, (m1, m2, m3))
+    plan = occri.Plan.from_workload(w, precision=args.precision)
+    C = torch.from_numpy(w.C).cuda()
+    if args.timing:
+        plan.set_timing(1)
+    for _ in range(args.builds):
+        KC, K, Ex = plan.build(C)
+    out = {"mode": "case", "E_x": float(Ex.cpu()[0]), "info": plan.info()}
+    if args.timing:
+        out["stages"] = plan.stage_times()
+    print(json.dumps(out), flush=True)
+
+
+def run_batch(args):
+    import torch
+    import paper_2207_09028_gb300 as occri
+    from workloads import config
+
+    cells = config(args.batch)
+    plans = [occri.Plan.from_workload(w, precision=args.precision) for w in cells]
+    Cs = [torch.from_numpy(w.C).cuda() for w in cells]
+    Exs = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in cells]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()                                    # warm-up (and graph capture)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.builds):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.builds
+
+    def one_by_one():
+        for pl, C, E in zip(plans, Cs, Exs):
+            pl.k_build(C, None, None, E, sync=False)
+
+    ms_seq = timed(one_by_one)
+    ex_seq = [float(e.cpu()[0]) for e in Exs]
+    batch = occri.Batch(plans)
+    ms_batch = timed(lambda: batch.build(Cs, None, None, Exs, sync=False))
+    batch.sync()
+    ex_batch = [float(e.cpu()[0]) for e in Exs]
+    print(json.dumps({"mode": "batch", "config": args.batch, "cells": len(cells),
+                      "precision": args.precision, "ms_per_build_one_by_one": ms_seq,
+                      "ms_per_build_batch": ms_batch, "speedup": ms_seq / ms_batch,
+                      "max_abs_dE_x_batch_vs_one_by_one": max(abs(a - b) for a, b in
+                                                              zip(ex_seq, ex_batch))}),
+          flush=True)
+
+
+# nao sweep: shells per atom (s, p, d, f) growing to the bench cell's 20/14/10/9 (nao 350)
+NAO_SWEEP = [(7, 2, 0, 0), (9, 6, 5, 0), (15, 10, 11, 0), (20, 14, 10, 3), (20, 14, 10, 9)]
+
+
+def loglog_slope(xs, ys) -> float:
+    """Least-squares slope of log y against log x."""
+    lx, ly = np.log(np.asarray(xs, float)), np.log(np.asarray(ys, float))
+    return float(np.polyfit(lx, ly, 1)[0])
+
+
+def run_sweep(args):
+    """K-builds/s of the bench cell across N_k (1^3..6^3) or nao (26..350 at 6x6x6 k)."""
+    import torch
+    import paper_2207_09028_gb300 as occri
+    from workloads import synthetic as syn
+
+    stream = torch.cuda.current_stream()
+    pts = []
+    if args.sweep == "nk":
+        cases = [dict(mesh=(n, n, n), counts=(20, 14, 10, 9)) for n in range(1, 7)]
+    else:
+        cases = [dict(mesh=(6, 6, 6), counts=c) for c in NAO_SWEEP]
+    for c in cases:
+        w = syn._build("sweep", 5.43, c["mesh"], c["counts"], 0.06, 40.0, 8, (60, 60, 60),
+                       "coulomb", 0.0, 0, 1050)
+        plan = occri.Plan.from_workload(w, precision=args.precision)
+        C = torch.from_numpy(w.C).cuda()
+        Ex = torch.zeros(1, dtype=torch.float64, device=C.device)
+        for _ in range(max(1, args.warmup)):
+            plan.k_build(C, None, None, Ex, sync=False)
+        plan.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.k_build(C, None, None, Ex, sync=False)
+        e1.record(stream)
+        plan.sync()
+        ms = e0.elapsed_time(e1) / args.steps
+        pt = {"mode": "sweep", "sweep": args.sweep, "nk": w.nk, "nao": w.nao, "nocc": w.nocc,
+              "grid": list(w.grid), "precision": args.precision, "ms_per_build": ms,
+              "K_builds_per_s": 1e3 / ms, "E_x": float(Ex.cpu()[0])}
+        print(json.dumps(pt), flush=True)
+        pts.append(pt)
+        plan.close()
+        del plan, C
+        torch.cuda.empty_cache()
+    key = "nk" if args.sweep == "nk" else "nao"
+    sel = [p_ for p_ in pts if p_["nk"] > 1] if key == "nk" else pts
+    print(json.dumps({"mode": "sweep", "sweep": args.sweep,
+                      "loglog_slope_ms_vs_" + key: loglog_slope([p_[key] for p_ in sel],
+                                                                [p_["ms_per_build"] for p_ in sel]),
+                      "points": len(sel)}), flush=True)
+
+
 # ---------------------------------------------------------------- main
 
 def main():
@@ -244,7 +447,20 @@ def main():
     ap.add_argument("--timing-every", type=int, default=61)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", type=int, nargs=5, default=None,
+                    metavar=("EDGE", "NOCC", "M1", "M2", "M3"))
+    ap.add_argument("--batch", default=None)
+    ap.add_argument("--sweep", default=None, choices=["nk", "nao"])
+    ap.add_argument("--builds", type=int, default=2)
+    ap.add_argument("--precision", default="mixed")
+    ap.add_argument("--timing", action="store_true")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
+    if args.batch:
+        return run_batch(args)
+    if args.sweep:
+        return run_sweep(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -265,19 +481,25 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cfg = dict(cfg, precision="FP64 CPU oracle (numpy), one core")
+        sampler = OracleSampler(w)
+        cfg = dict(cfg, precision=f"FP64 CPU oracle (numpy), {sampler.workers} cores")
         samples = []
         for _ in range(args.warmup + args.steps):
-            t, desc, wall = oracle_sample_seconds(w)
+            t, desc, wall = sampler.sample()
             samples.append(t)
+        sampler.close()
         t = statistics.median(samples[args.warmup:]) if args.steps else samples[-1]
         val = 1.0 / t
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
                           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
                           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-                          "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                           "sample": desc},
+                          "extrapolated": True,
+                          "step": "one bounded sample of a build on every host core, "
+                                  "extrapolated to the whole build (see cpu_baseline.sample)",
+                          "cpu_baseline": {"value": val, "unit": UNIT, "cores": sampler.workers,
+                                           "kind": "oracle", "sample": desc,
+                                           "cpu": cpu_model()},
                           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}), flush=True)
         return
@@ -308,7 +530,9 @@ def main():
     plan.sync()
     ex_mixed = float(Ex.cpu()[0])
 
-    plan.set_timing(args.timing_every)
+    # timed builds: stage spans only (events around the stages and the whole pair loop; no
+    # wave is sampled or isolated, so the builds run exactly as untimed ones)
+    plan.set_timing(-1)
     torch.cuda.synchronize()
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -323,6 +547,15 @@ def main():
     ms = ev0.elapsed_time(ev1)
     plan.sync()
     stages = plan.stage_times()
+    # one more build, untimed for the headline, with every timing_every-th wave run alone
+    # and timed pass by pass: the split of the round trip between the passes
+    if args.timing_every > 0:
+        plan.set_timing(args.timing_every)
+        plan.k_build(C, KC, K, Ex, sync=False)
+        plan.sync()
+        sampled = plan.stage_times()
+        for name in ("pair_a", "pair_b", "pair_c"):
+            stages[name] = sampled[name]
     plan.set_timing(0)
     ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
@@ -331,6 +564,9 @@ def main():
 
     waves = pair_waves(w.nk, w.nocc, int(info["fields_per_wave"]))
     stage_share = stage_ms_per_build(stages, waves, args.steps)
+    for name in ("pair_a", "pair_b", "pair_c"):   # from the one sampled build
+        if name in stages:
+            stage_share[name] = stages[name]["ms"] * waves / max(1, stages[name]["launches"])
     hbm, peak_kind = _peaks()
     roof = roofline(stages, info, w.grid[0], w.ng, w.nocc, hbm, peak_kind)
 
@@ -390,9 +626,12 @@ def main():
         p64.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, desc, wall = oracle_sample_seconds(w)
-        out["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": desc, "sample_wall_s": wall}
+        sampler = OracleSampler(w)
+        t, desc, wall = sampler.sample()
+        sampler.close()
+        out["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": sampler.workers,
+                               "kind": "oracle", "sample": desc, "sample_wall_s": wall,
+                               "cpu": cpu_model()}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

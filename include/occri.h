@@ -127,8 +127,12 @@ typedef struct occri_plan occri_plan;
 /* Validate the problem, build image lists and tables, allocate workspaces.
  * Problem statement: Sec. II.A (cell, Bloch AOs), Eq. recipcoul (kernel).
  * grid: N1, N2, N3, each {2,3,5}-smooth in [4, 64]; this build requires
- * N1 = N2 = N3 and nocc <= 32 (else OCCRI_EUNSUPPORTED). cuda_stream: a cudaStream_t or NULL
- * (legacy default stream). On success *out owns a plan to be destroyed with
+ * N1 = N2 = N3 with an edge in {8, 9, 10, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32, 36, 40,
+ * 45, 48, 50, 54, 60, 64} and nocc <= 32 (else OCCRI_EUNSUPPORTED): every 1-D transform is
+ * compiled for its length, and the pair passes are compiled per cubic edge. cuda_stream: a
+ * cudaStream_t or NULL (legacy default stream). The plan lives on the device current at
+ * this call: every later call on it makes that device current for its duration and then
+ * restores the caller's. On success *out owns a plan to be destroyed with
  * occri_plan_destroy; on failure *out is NULL. */
 int occri_plan_create(occri_plan **out, const occri_cell *cell, const occri_kmesh *kmesh,
                       const occri_basis *basis, int nocc, const int grid[3],
@@ -151,6 +155,19 @@ int occri_plan_sync(occri_plan *plan, int *bad_k);
  * Asynchronous; call occri_plan_sync to observe OCCRI_ENOTPD. */
 int occri_k_build(occri_plan *plan, const void *C_dev, void *KC_dev, void *K_dev,
                   double *Ex_dev);
+
+/* One-shot build with the signature of the problem statement (Sec. II.A and Eq. occrik):
+ * creates a plan for (cell, kmesh, basis, nocc, grid, kernel, precision) on the current
+ * device, runs occri_k_build(C_dev -> K_dev, Ex_dev) on cuda_stream, synchronises, and
+ * destroys the plan. C_dev, K_dev, Ex_dev: device buffers as in occri_k_build (K_dev or
+ * Ex_dev may be NULL). Returns the first failure of the three steps (creation errors as
+ * occri_plan_create, then build and device-side errors such as OCCRI_ENOTPD as
+ * occri_plan_sync). Every call pays the plan's set-up (tables, workspaces); repeated
+ * builds of one cell should keep a plan instead. */
+int occri_k_build_once(const occri_cell *cell, const occri_kmesh *kmesh,
+                       const occri_basis *basis, const void *C_dev, int nocc, const int grid[3],
+                       const occri_kernel *kernel, int precision, void *K_dev, double *Ex_dev,
+                       void *cuda_stream);
 
 /* The same build with HOST buffers (same layouts; NULL outputs skipped): copies
  * C to the device, builds, copies the outputs back, synchronises. */
@@ -193,9 +210,11 @@ int occri_vjp(occri_plan *plan, const void *C_dev, double gEx, void *gC_dev,
 int occri_vjp_full(occri_plan *plan, const void *C_dev, double gEx, const void *gKC_dev,
                    const void *gK_dev, void *gC_dev, double *gomega_dev);
 
-/* Sampled stage timing with CUDA events on the plan's stream. every > 0 brackets
- * every `every`-th pair wave (and every orbital, contraction and assembly stage)
- * with events; every = 0 turns timing off and discards pending samples. */
+/* Stage timing with CUDA events on the plan's stream. every > 0 brackets every
+ * `every`-th pair wave (run alone: the other stream waits around it) and every orbital,
+ * contraction and assembly stage and the whole pair loop with events; every = -1 records
+ * the stage and pair-loop spans only (no wave is sampled or run alone, so the build runs
+ * as it does untimed); every = 0 turns timing off and discards pending samples. */
 int occri_plan_set_timing(occri_plan *plan, int every);
 
 /* Synchronise, resolve pending events and return, per stage, the accumulated
@@ -258,6 +277,22 @@ int occri_batch_build(occri_batch *batch, const void *const *C_dev, void *const 
 int occri_batch_sync(occri_batch *batch, int *bad_cell, int *bad_k);
 
 int occri_batch_destroy(occri_batch *batch);
+
+/* ---- Fault injection, for tests of the error paths (no counterpart in the paper) ----
+ * occri_plan_inject_fault(plan, OCCRI_FAULT_WAIT, ms): in the plan's following builds the
+ *   producer warp of every bulk-copy accumulation pass (FP64 waves, and FP32 waves of
+ *   nocc > 8, where shared memory allows) issues no copy, so each consumer's bounded
+ *   wait runs out after ms milliseconds; the build then completes with a meaningless Y,
+ *   and occri_plan_sync returns OCCRI_ETIMEOUT. No copy is in flight when a CTA leaves.
+ *   occri_plan_inject_fault(plan, OCCRI_FAULT_NONE, ms) restores normal builds with
+ *   wait limit ms (the default limit is 2000 ms). ms must lie in (0, 60000].
+ * occri_debug_fail_allocation(n): the n-th device allocation made by the library from
+ *   now on (n >= 1, any plan, any thread) fails as if the device were out of memory, so
+ *   that the entry point making it returns OCCRI_ENOMEM after freeing what it took;
+ *   n <= 0 disarms. */
+enum { OCCRI_FAULT_NONE = 0, OCCRI_FAULT_WAIT = 1 };
+int occri_plan_inject_fault(occri_plan *plan, int fault, double wait_limit_ms);
+int occri_debug_fail_allocation(int nth);
 
 const char *occri_status_string(int status);
 

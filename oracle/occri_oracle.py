@@ -1,6 +1,6 @@
 """Plain FP64 oracle of the occ-RI-K exact-exchange build (test infrastructure).
 
-Conventions (the paper leaves them open; each reading is listed in the design doc):
+Conventions (the paper leaves them open; each is a reading of the cited passage):
 * Bloch AOs chi_{mu k}(r) = sum_T e^{i k.T} phi_mu(r - A_mu - T), without the
   N_k^{-1/2} of Sec. II.A; the cell integral then carries an explicit 1/N_k.
 * Grid r_n = sum_i (n_i/N_i) a_i with n_3 fastest; forward transform

@@ -61,8 +61,11 @@ EXPORTED = ["occri_plan_create", "occri_plan_destroy", "occri_plan_info", "occri
             "occri_plan_sync", "occri_k_build", "occri_k_build_host", "occri_orbitals",
             "occri_vjp", "occri_plan_set_timing", "occri_plan_stage_times", "occri_orbitals_noalloc",
             "occri_vjp_full", "occri_batch_create", "occri_batch_build", "occri_batch_sync",
-            "occri_batch_destroy",
+            "occri_batch_destroy", "occri_k_build_once", "occri_plan_inject_fault",
+            "occri_debug_fail_allocation",
             "occri_status_string"]
+
+OCCRI_FAULT_NONE, OCCRI_FAULT_WAIT = 0, 1
 
 STAGES = ["orbitals", "pair_a", "pair_b", "pair_c", "contract", "assemble", "pairs"]
 
@@ -102,6 +105,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.POINTER(vp), ctypes.POINTER(vp)]
     lib.occri_batch_sync.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.occri_batch_destroy.argtypes = [vp]
+    lib.occri_k_build_once.argtypes = [ctypes.POINTER(occri_cell), ctypes.POINTER(occri_kmesh),
+                                       ctypes.POINTER(occri_basis), vp, ip,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(occri_kernel),
+                                       ip, vp, vp, vp]
+    lib.occri_plan_inject_fault.argtypes = [vp, ip, ctypes.c_double]
+    lib.occri_debug_fail_allocation.argtypes = [ip]
     lib.occri_status_string.argtypes = [ip]
     lib.occri_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -135,6 +144,60 @@ def _current_stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def _problem_structs(lattice, xyz, shell_atom, shell_l, shell_alpha, kfrac, grid, kernel,
+                     omega, g0_mode, precision) -> dict:
+    """The C structs of occri_plan_create / occri_k_build_once (with the numpy arrays they
+    point into, which must outlive the call)."""
+    lattice = np.ascontiguousarray(lattice, dtype=np.float64)
+    keep = dict(xyz=np.ascontiguousarray(xyz, dtype=np.float64),
+                atom=np.ascontiguousarray(shell_atom, dtype=np.int32),
+                l=np.ascontiguousarray(shell_l, dtype=np.int32),
+                alpha=np.ascontiguousarray(shell_alpha, dtype=np.float64),
+                kfrac=np.ascontiguousarray(kfrac, dtype=np.float64).reshape(-1, 3))
+    cell = occri_cell()
+    for i in range(3):
+        for j in range(3):
+            cell.a[i][j] = float(lattice[i, j])
+    cell.natm = keep["xyz"].shape[0]
+    cell.xyz = keep["xyz"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    basis = occri_basis(len(keep["l"]), keep["atom"].ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                        keep["l"].ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                        keep["alpha"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    kmesh = occri_kmesh(keep["kfrac"].shape[0],
+                        keep["kfrac"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    kern = occri_kernel(KERNELS[kernel] if isinstance(kernel, str) else int(kernel),
+                        float(omega), int(g0_mode))
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return dict(keep, cell=cell, basis=basis, kmesh=kmesh, kernel=kern, grid=g, prec=prec)
+
+
+def build_once(lattice, xyz, shell_atom, shell_l, shell_alpha, kfrac, C, nocc: int, grid,
+               kernel: str = "coulomb", omega: float = 0.0, g0_mode: int = 0,
+               precision: str = "mixed", want_k: bool = True):
+    """occri_k_build_once: plan, build and tear-down in one call. C is a complex128 CUDA
+    tensor [nk, nao, nocc]; returns (K [nk, nao, nao] or None, E_x[1]) on C's device."""
+    import torch
+    lib = load_library()
+    a = _problem_structs(lattice, xyz, shell_atom, shell_l, shell_alpha, kfrac, grid, kernel,
+                         omega, g0_mode, precision)
+    if C.dtype != torch.complex128 or not C.is_cuda or not C.is_contiguous() or C.dim() != 3:
+        raise ValueError("C must be a contiguous complex128 CUDA tensor [nk, nao, nocc]")
+    nk, nao = C.shape[0], C.shape[1]
+    K = torch.empty((nk, nao, nao), dtype=torch.complex128, device=C.device) if want_k else None
+    Ex = torch.zeros(1, dtype=torch.float64, device=C.device)
+    _check(lib.occri_k_build_once(ctypes.byref(a["cell"]), ctypes.byref(a["kmesh"]),
+                                  ctypes.byref(a["basis"]), _ptr(C), int(nocc), a["grid"],
+                                  ctypes.byref(a["kernel"]), a["prec"], _ptr(K), _ptr(Ex),
+                                  _current_stream()), "occri_k_build_once")
+    return K, Ex
+
+
+def fail_allocation(nth: int):
+    """occri_debug_fail_allocation: the nth device allocation from now fails (test hook)."""
+    _check(load_library().occri_debug_fail_allocation(int(nth)), "occri_debug_fail_allocation")
+
+
 class Plan:
     """An exchange-build plan (owns device workspaces; see occri_plan_create)."""
 
@@ -143,27 +206,10 @@ class Plan:
                  precision: str = "mixed", stream=None):
         lib = load_library()
         self._lib = lib
-        lattice = np.ascontiguousarray(lattice, dtype=np.float64)
-        self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
-        self._atom = np.ascontiguousarray(shell_atom, dtype=np.int32)
-        self._l = np.ascontiguousarray(shell_l, dtype=np.int32)
-        self._alpha = np.ascontiguousarray(shell_alpha, dtype=np.float64)
-        self._kfrac = np.ascontiguousarray(kfrac, dtype=np.float64).reshape(-1, 3)
-        cell = occri_cell()
-        for i in range(3):
-            for j in range(3):
-                cell.a[i][j] = float(lattice[i, j])
-        cell.natm = self._xyz.shape[0]
-        cell.xyz = self._xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        basis = occri_basis(len(self._l), self._atom.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                            self._l.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                            self._alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
-        kmesh = occri_kmesh(self._kfrac.shape[0],
-                            self._kfrac.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
-        kern = occri_kernel(KERNELS[kernel] if isinstance(kernel, str) else int(kernel),
-                            float(omega), int(g0_mode))
-        g = (ctypes.c_int * 3)(*[int(x) for x in grid])
-        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._args = _problem_structs(lattice, xyz, shell_atom, shell_l, shell_alpha, kfrac,
+                                      grid, kernel, omega, g0_mode, precision)
+        cell, kmesh, basis, kern, g, prec = (self._args[k] for k in
+                                             ("cell", "kmesh", "basis", "kernel", "grid", "prec"))
         handle = ctypes.c_void_p()
         st = lib.occri_plan_create(ctypes.byref(handle), ctypes.byref(cell), ctypes.byref(kmesh),
                                    ctypes.byref(basis), int(nocc), g, ctypes.byref(kern), prec,
@@ -195,6 +241,11 @@ class Plan:
         _check(self._lib.occri_plan_info(self._h, ctypes.byref(info)), "occri_plan_info")
         return {f: (tuple(getattr(info, f)) if f == "grid" else getattr(info, f))
                 for f, _ in occri_plan_info_t._fields_}
+
+    def inject_fault(self, fault: int, wait_limit_ms: float = 2000.0):
+        """occri_plan_inject_fault (test hook for the bounded-wait error path)."""
+        _check(self._lib.occri_plan_inject_fault(self._h, int(fault), float(wait_limit_ms)),
+               "occri_plan_inject_fault")
 
     def set_timing(self, every: int):
         _check(self._lib.occri_plan_set_timing(self._h, int(every)), "occri_plan_set_timing")
@@ -282,6 +333,7 @@ class Plan:
     def build(self, C, want_k: bool = True, sync: bool = True):
         """Allocate outputs and run one build: returns (KC, K or None, Ex[1])."""
         import torch
+        self.generation = getattr(self, "generation", 0) + 1
         dev = C.device
         KC = torch.empty((self.nk, self.nao, self.nocc), dtype=torch.complex128, device=dev)
         K = torch.empty((self.nk, self.nao, self.nao), dtype=torch.complex128, device=dev) if want_k else None
@@ -387,6 +439,46 @@ def exchange_energy(plan: Plan, C, omega=None):
     return _ExchangeEnergy.apply(C, omega)
 
 
-__all__ = ["Plan", "Batch", "OccriError", "load_library", "exchange_energy", "EXPORTED",
-           "LIB_PATH"] + [
+def exchange_build(plan: Plan, C, omega=None):
+    """(K, E_x) of one build as differentiable torch tensors; backward = occri_vjp_full.
+
+    K is the ACE-form exchange matrix [nk, nao, nao] and E_x a scalar. Any loss of K and
+    E_x can be differentiated: gradients reach C (conjugate-Wirtinger convention, as
+    PyTorch's complex autograd) and, when omega is given (a tensor equal to the plan's
+    omega), omega through the kernel. backward recomputes the pair potentials (two round
+    trips per unordered pair) and reuses the plan's K_{mu i}; if another build ran on the
+    plan since this forward, it rebuilds first.
+    """
+    import torch
+
+    class _ExchangeBuild(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, Cin, w):
+            Cd = Cin.detach().contiguous()
+            _, K, Ex = plan.build(Cd, want_k=True)
+            ctx.save_for_backward(Cd)
+            ctx.generation = plan.generation
+            ctx.has_w = w is not None
+            ctx.w_device = w.device if w is not None else None
+            return K, Ex[0].clone()
+
+        @staticmethod
+        def backward(ctx, gK, gEx):
+            (Cd,) = ctx.saved_tensors
+            if plan.generation != ctx.generation:
+                plan.build(Cd, want_k=False)
+            want_w = ctx.has_w and ctx.needs_input_grad[1]
+            g_e = 0.0 if gEx is None else float(gEx)
+            gKc = None if gK is None else gK.contiguous()
+            out = plan.vjp_full(Cd, g_e, None, gKc, want_omega=want_w)
+            gC, gw = (out if want_w else (out, None))
+            gw_out = (torch.tensor(gw, dtype=torch.float64, device=ctx.w_device)
+                      if gw is not None else None)
+            return (gC if ctx.needs_input_grad[0] else None), gw_out
+
+    return _ExchangeBuild.apply(C, omega)
+
+
+__all__ = ["Plan", "Batch", "OccriError", "load_library", "exchange_energy", "exchange_build",
+           "build_once", "fail_allocation", "EXPORTED", "LIB_PATH"] + [
     n for n in globals() if n.startswith("OCCRI_")]

@@ -638,7 +638,8 @@ std::mutex g_scratch_mutex;
 size_t round_up_256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Device address of the static array for the current device (looked up once per device,
-// with that device current; the host-side symbol itself is not a device address).
+// with that device current; the host-side symbol itself is not a device address). The
+// caller has made the plan's device current.
 int static_scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -688,6 +689,9 @@ int orbitals_noalloc_impl(const occri::Plan& p, const double2* C, void* psi_out,
 extern "C" int occri_orbitals_noalloc(const occri_plan* plan, const void* C_dev, void* psi_dev) {
   if (!plan || !C_dev || !psi_dev) return OCCRI_EINVAL;
   const occri::Plan& p = *plan->p;
+  // the plan's device is made current, so the scratch address below is that device's
+  occri::DeviceGuard guard(p.device);
+  if (!guard.ok) return OCCRI_ECUDA;
   const bool fp64 = p.precision == OCCRI_FP64;
   const size_t ncs = (size_t)p.nk * p.nao * p.nocc;
   const size_t npsi = (size_t)p.nk * p.nocc * p.fs;   // internal fields, fs points apart

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +17,24 @@
 namespace occri {
 
 static const double kPiD = 3.14159265358979323846;
+
+// Test-only allocation failure (occri_debug_fail_allocation): the number of device
+// allocations still to succeed before one fails, or -1 when disarmed.
+static std::atomic<long long> g_alloc_countdown{-1};
+
+cudaError_t device_malloc(void** ptr, size_t bytes) {
+  long long c = g_alloc_countdown.load();
+  while (c >= 0) {
+    if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) {
+      if (c == 0) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(ptr, bytes);
+}
 
 bool grid_edge_supported(int n) {
   switch (n) {
@@ -50,6 +69,9 @@ PairParams Plan::pair_params() const {
   PairParams q;
   q.nk = nk; q.nocc = nocc; q.ng = ng; q.fs = fs; q.N1 = N[0];
   q.status = status;
+  q.wait_ns = wait_ns;
+  q.fault = fault;
+  q.device = device;
   q.k = 0; q.kp0 = 0; q.nkp = 1; q.diag = 0;
   q.vt_off = (long long)fields_cap * fs * (precision == OCCRI_FP64 ? 16 : 8);
   for (int d = 0; d < 3; ++d) q.D[d] = D[d];
@@ -203,7 +225,7 @@ void inv3(const double a[3][3], double inv[3][3]) {
 template <typename X>
 cudaError_t dalloc(X** p, size_t count, size_t* total) {
   *total += count * sizeof(X);
-  return cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(X));
+  return device_malloc((void**)p, std::max<size_t>(count, 1) * sizeof(X));
 }
 
 template <typename X>
@@ -554,14 +576,20 @@ struct StageTimer {
       : p(pl), st(stream ? stream : pl->stream) {
     if (on) {
       a = take_event(p);
-      if (a) cudaEventRecord(a, st);
+      if (a && cudaEventRecord(a, st) != cudaSuccess) {
+        cudaGetLastError();
+        a = nullptr;   // this stage goes untimed
+      }
     }
   }
   void done(int stage, double units) {
     if (!a) return;
     cudaEvent_t b = take_event(p);
     if (!b) return;
-    cudaEventRecord(b, st);
+    if (cudaEventRecord(b, st) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
     p->ev_pending.push_back(Plan::TimedSpan{a, b, stage, units});
   }
 };
@@ -570,7 +598,7 @@ template <typename T>
 int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
   using namespace occri;
   cudaStream_t s = p->stream;
-  const bool timed = p->timing_every > 0;
+  const bool timed = p->timing_every != 0;   // > 0: sampled waves too; -1: stage spans only
   long long launches = 0;
   const size_t orb = (size_t)p->nk * p->nocc * p->fs;
   if (cudaMemsetAsync(p->Y, 0, orb * sizeof(cplx_t<T>), s) != cudaSuccess) return OCCRI_ECUDA;
@@ -608,12 +636,13 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
         const int nkp = diag ? 1 : std::min(p->nkp_wave, p->nk - kp0);
         const int w = (int)(wave & 1);
         cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-        bool sample = timed && (wave % p->timing_every == 0);
+        bool sample = p->timing_every > 0 && (wave % p->timing_every == 0);
         if (sample)
           for (int i = 0; i < 4 && sample; ++i) sample = (ev[i] = take_event(p)) != nullptr;
         if (sample) {   // wait for the other stream's work
-          cudaEventRecord(p->ev_iso, st[w ^ 1]);
-          cudaStreamWaitEvent(st[w], p->ev_iso, 0);
+          if (cudaEventRecord(p->ev_iso, st[w ^ 1]) != cudaSuccess ||
+              cudaStreamWaitEvent(st[w], p->ev_iso, 0) != cudaSuccess)
+            return OCCRI_ECUDA;
         }
         if (launch_pair_wave<T>(*p, k, kp0, nkp, diag, st[w], sc[w], sample ? ev : nullptr,
                                 p->ev_y) != cudaSuccess)
@@ -622,8 +651,9 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
         const double nf = (double)wave_fields(p->nocc, nkp, diag);
         fields += nf;
         if (sample) {   // and keep the other stream waiting until this wave is done
-          cudaEventRecord(p->ev_iso, st[w]);
-          cudaStreamWaitEvent(st[w ^ 1], p->ev_iso, 0);
+          if (cudaEventRecord(p->ev_iso, st[w]) != cudaSuccess ||
+              cudaStreamWaitEvent(st[w ^ 1], p->ev_iso, 0) != cudaSuccess)
+            return OCCRI_ECUDA;
           p->ev_pending.push_back(Plan::TimedSpan{ev[0], ev[1], OCCRI_STAGE_PAIR_A, nf});
           p->ev_pending.push_back(Plan::TimedSpan{ev[1], ev[2], OCCRI_STAGE_PAIR_B, nf});
           p->ev_pending.push_back(Plan::TimedSpan{ev[2], ev[3], OCCRI_STAGE_PAIR_C, nf});
@@ -706,11 +736,12 @@ int vjp_full_impl(Plan* p, const double2* C, double gEx, const double2* gKC, con
   const size_t orb = (size_t)p->nk * p->nocc * p->fs * sizeof(cplx_t<T>);
   const size_t csb = (p->precision == OCCRI_FP64 ? sizeof(double2) : sizeof(float4)) * nkc;
   if (!p->gam) {   // first call: the adjoint workspaces
-    bool ok = cudaMalloc(&p->gam, orb) == cudaSuccess && cudaMalloc(&p->gpsi, orb) == cudaSuccess &&
-              cudaMalloc(&p->cs_g, csb) == cudaSuccess &&
-              cudaMalloc((void**)&p->gkc, nkc * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc((void**)&p->gcf, nkc * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc((void**)&p->gacc, nkc * sizeof(double2)) == cudaSuccess;
+    bool ok = device_malloc(&p->gam, orb) == cudaSuccess &&
+              device_malloc(&p->gpsi, orb) == cudaSuccess &&
+              device_malloc(&p->cs_g, csb) == cudaSuccess &&
+              device_malloc((void**)&p->gkc, nkc * sizeof(double2)) == cudaSuccess &&
+              device_malloc((void**)&p->gcf, nkc * sizeof(double2)) == cudaSuccess &&
+              device_malloc((void**)&p->gacc, nkc * sizeof(double2)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       for (void** b : {&p->gam, &p->gpsi, &p->cs_g, (void**)&p->gkc, (void**)&p->gcf,
@@ -765,6 +796,7 @@ int vjp_full_impl(Plan* p, const double2* C, double gEx, const double2* gKC, con
 
 // A batch of cells built by one graph launch (see occri_batch_create in occri.h).
 struct occri_batch {
+  int device = 0;                          // the plans' device
   std::vector<occri_plan*> plans;
   cudaStream_t stream = nullptr;           // launch stream (the caller's)
   cudaStream_t cap = nullptr;              // capture origin
@@ -1142,7 +1174,12 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
       else ph_f[(size_t)k * nimg + j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
 
-  // device tables and workspaces
+  // device tables and workspaces, on the current device
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return OCCRI_ECUDA;
+  }
   size_t tot = 0;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess && x != cudaSuccess) e = x; };
@@ -1228,6 +1265,8 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
 
 int occri_plan_destroy(occri_plan* plan) {
   if (!plan) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(plan->p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   occri::free_plan(plan->p);
   delete plan;
   return OCCRI_OK;
@@ -1248,7 +1287,9 @@ int occri_plan_info(const occri_plan* plan, occri_plan_info_t* info) {
 }
 
 int occri_plan_set_timing(occri_plan* plan, int every) {
-  if (!plan || every < 0) return OCCRI_EINVAL;
+  if (!plan || every < -1) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(plan->p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   Plan* p = plan->p;
   if (every == 0) {
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return OCCRI_ECUDA;
@@ -1262,6 +1303,8 @@ int occri_plan_set_timing(occri_plan* plan, int every) {
 
 int occri_plan_stage_times(occri_plan* plan, double* ms, long long* launches, double* units) {
   if (!plan || !ms || !launches || !units) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(plan->p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   Plan* p = plan->p;
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return OCCRI_ECUDA;
   for (const Plan::TimedSpan& sp : p->ev_pending) {
@@ -1294,6 +1337,8 @@ int occri_plan_set_stream(occri_plan* plan, void* cuda_stream) {
 int occri_plan_sync(occri_plan* plan, int* bad_k) {
   if (bad_k) *bad_k = -1;
   if (!plan) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(plan->p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   Plan* p = plan->p;
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return OCCRI_ECUDA;
   int st[2] = {0, -1};
@@ -1309,29 +1354,67 @@ int occri_plan_sync(occri_plan* plan, int* bad_k) {
 
 int occri_k_build(occri_plan* plan, const void* C_dev, void* KC_dev, void* K_dev, double* Ex_dev) {
   if (!plan || !C_dev) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(plan->p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   Plan* p = plan->p;
   return p->precision == OCCRI_FP64
              ? occri_impl::build_impl<double>(p, (const double2*)C_dev, KC_dev, K_dev, Ex_dev)
              : occri_impl::build_impl<float>(p, (const double2*)C_dev, KC_dev, K_dev, Ex_dev);
 }
 
+int occri_k_build_once(const occri_cell* cell, const occri_kmesh* kmesh,
+                       const occri_basis* basis, const void* C_dev, int nocc, const int grid[3],
+                       const occri_kernel* kernel, int precision, void* K_dev, double* Ex_dev,
+                       void* cuda_stream) {
+  if (!C_dev) return OCCRI_EINVAL;
+  occri_plan* plan = nullptr;
+  int st = occri_plan_create(&plan, cell, kmesh, basis, nocc, grid, kernel, precision,
+                             cuda_stream);
+  if (st != OCCRI_OK) return st;
+  st = occri_k_build(plan, C_dev, nullptr, K_dev, Ex_dev);
+  const int st_sync = occri_plan_sync(plan, nullptr);
+  occri_plan_destroy(plan);
+  return st != OCCRI_OK ? st : st_sync;
+}
+
+int occri_plan_inject_fault(occri_plan* plan, int fault, double wait_limit_ms) {
+  if (!plan) return OCCRI_EINVAL;
+  if (fault != OCCRI_FAULT_NONE && fault != OCCRI_FAULT_WAIT) return OCCRI_EINVAL;
+  if (!(wait_limit_ms > 0.0) || wait_limit_ms > 60000.0) return OCCRI_EINVAL;
+  plan->p->fault = fault;
+  plan->p->wait_ns = (long long)(wait_limit_ms * 1e6);
+  return OCCRI_OK;
+}
+
+int occri_debug_fail_allocation(int nth) {
+  occri::g_alloc_countdown.store(nth >= 1 ? (long long)(nth - 1) : -1LL);
+  return OCCRI_OK;
+}
+
 int occri_k_build_host(occri_plan* plan, const void* C_host, void* KC_host, void* K_host,
                        double* Ex_host) {
   if (!plan || !C_host) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(plan->p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   Plan* p = plan->p;
   const size_t nc = (size_t)p->nk * p->nao * p->nocc;
   const size_t nkk = (size_t)p->nk * p->nao * p->nao;
   if (!p->h_c) {
-    if (cudaMalloc((void**)&p->h_c, nc * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void**)&p->h_kc, nc * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void**)&p->h_ex, sizeof(double)) != cudaSuccess) {
+    if (occri::device_malloc((void**)&p->h_c, nc * sizeof(double2)) != cudaSuccess ||
+        occri::device_malloc((void**)&p->h_kc, nc * sizeof(double2)) != cudaSuccess ||
+        occri::device_malloc((void**)&p->h_ex, sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
+      for (void** b : {(void**)&p->h_c, (void**)&p->h_kc, (void**)&p->h_ex}) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+      }
       return OCCRI_ENOMEM;
     }
   }
   if (K_host && !p->h_k) {
-    if (cudaMalloc((void**)&p->h_k, nkk * sizeof(double2)) != cudaSuccess) {
+    if (occri::device_malloc((void**)&p->h_k, nkk * sizeof(double2)) != cudaSuccess) {
       cudaGetLastError();
+      p->h_k = nullptr;
       return OCCRI_ENOMEM;
     }
   }
@@ -1352,6 +1435,8 @@ int occri_k_build_host(occri_plan* plan, const void* C_host, void* KC_host, void
 
 int occri_orbitals(occri_plan* plan, const void* C_dev, void* psi_dev) {
   if (!plan || !C_dev || !psi_dev) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(plan->p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   Plan* p = plan->p;
   cudaError_t e;
   if (p->precision == OCCRI_FP64) {
@@ -1369,6 +1454,8 @@ int occri_orbitals(occri_plan* plan, const void* C_dev, void* psi_dev) {
 int occri_vjp_full(occri_plan* plan, const void* C_dev, double gEx, const void* gKC_dev,
                    const void* gK_dev, void* gC_dev, double* gomega_dev) {
   if (!plan || !C_dev || !gC_dev) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(plan->p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   Plan* p = plan->p;
   if (!p->have_kc) return OCCRI_EINVAL;
   const double2* C = (const double2*)C_dev;
@@ -1382,6 +1469,8 @@ int occri_vjp_full(occri_plan* plan, const void* C_dev, double gEx, const void* 
 
 int occri_vjp(occri_plan* plan, const void* C_dev, double gEx, void* gC_dev, double* gomega_dev) {
   if (!plan || !C_dev) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(plan->p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   Plan* p = plan->p;
   if (!p->have_kc) return OCCRI_EINVAL;
   const double2* C = (const double2*)C_dev;
@@ -1399,7 +1488,13 @@ int occri_batch_create(occri_batch** out, occri_plan* const* plans, int nplans,
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return OCCRI_EINVAL;
   }
+  const int dev = plans[0]->p->device;
+  for (int i = 1; i < nplans; ++i)
+    if (plans[i]->p->device != dev) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(dev);
+  if (!guard.ok) return OCCRI_ECUDA;
   occri_batch* b = new occri_batch();
+  b->device = dev;
   b->plans.assign(plans, plans + nplans);
   b->stream = (cudaStream_t)cuda_stream;
   b->branch.assign(nplans, nullptr);
@@ -1421,6 +1516,8 @@ int occri_batch_create(occri_batch** out, occri_plan* const* plans, int nplans,
 int occri_batch_build(occri_batch* b, const void* const* C_dev, void* const* KC_dev,
                       void* const* K_dev, double* const* Ex_dev) {
   if (!b || !C_dev) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(b->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   const size_t n = b->plans.size();
   std::vector<const void*> c(n);
   std::vector<void*> kc(n, nullptr), k(n, nullptr);
@@ -1450,6 +1547,8 @@ int occri_batch_sync(occri_batch* b, int* bad_cell, int* bad_k) {
   if (bad_cell) *bad_cell = -1;
   if (bad_k) *bad_k = -1;
   if (!b) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(b->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return OCCRI_ECUDA;
   int first = OCCRI_OK;
   for (size_t i = 0; i < b->plans.size(); ++i) {
@@ -1471,6 +1570,8 @@ int occri_batch_sync(occri_batch* b, int* bad_cell, int* bad_k) {
 
 int occri_batch_destroy(occri_batch* b) {
   if (!b) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(b->device);
+  if (!guard.ok) return OCCRI_ECUDA;
   cudaStreamSynchronize(b->stream);
   occri_impl::batch_free(b);
   return OCCRI_OK;

@@ -7,6 +7,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "occri.h"
@@ -75,6 +76,9 @@ struct PairParams {
   int diag;                  // 1: the wave is (k, k) and holds the fields i <= j only
   long long vt_off;          // bytes from a scratch buffer's start to its kernel tables
   int* status;               // plan status word (first device error, k), for bounded waits
+  long long wait_ns;         // limit of every bounded device wait (nanoseconds)
+  int fault;                 // test-only fault injection (OCCRI_FAULT_*), 0 in normal use
+  int device;                // CUDA device the plan lives on
   int D[3];
   const int* kint;           // [nk][3]
   double g[6];               // reciprocal metric b_i.b_j: 11, 22, 33, 12, 13, 23
@@ -100,6 +104,9 @@ struct Plan {
   double omega_cell;
   occri_kernel kernel;
   cudaStream_t stream;
+  int device = 0;            // the CUDA device current at plan creation; every call runs on it
+  int fault = 0;             // test-only fault injection (occri_plan_inject_fault)
+  long long wait_ns = 2000000000LL;   // limit of the bounded device waits
   int D[3];
   std::vector<int> kint_h;
   int fields_cap;            // pair fields held by the transform scratch
@@ -250,6 +257,58 @@ __host__ __device__ inline int wave_fields(int nocc, int nkp, int diag) {
 inline int wave_targets(int nocc, int nkp, int diag) { return diag ? nocc : nocc + nkp * nocc; }
 template <typename T>
 cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s);
+
+// Launch settings derived once per kernel instantiation and device (function attributes,
+// resident-slot counts): each entry is filled under a lock the first time a plan on that
+// device launches the kernel.
+constexpr int kMaxDevices = 64;
+struct DeviceCache {
+  std::mutex mu;
+  bool set[kMaxDevices] = {};
+  int val[kMaxDevices] = {};
+  template <typename F>
+  int get(int device, F&& init) {
+    if (device < 0 || device >= kMaxDevices) device = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!set[device]) {
+      val[device] = init();
+      set[device] = true;
+    }
+    return val[device];
+  }
+};
+
+// Makes the plan's device current for the duration of an entry-point call and restores
+// the caller's current device afterwards (ok = false if either could not be queried or set).
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+      return;
+    }
+    if (cur != dev) {
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        cudaGetLastError();
+        ok = false;
+        return;
+      }
+      prev = cur;
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
+// Allocation with the test-only failure injection of occri_debug_fail_allocation: when
+// armed, the chosen allocation reports cudaErrorMemoryAllocation without allocating.
+cudaError_t device_malloc(void** ptr, size_t bytes);
 
 }  // namespace occri
 

@@ -839,10 +839,20 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
       : "memory");
   return done != 0;
 }
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (int it = 0; it < (1 << 22); ++it)
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase with the given parity to complete: gives up after limit_ns
+// nanoseconds of the global timer (or 2^22 polls, whichever comes first).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int it = 0; it < (1 << 22); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((long long)(global_ns() - t0) > limit_ns) return false;
+  }
   return false;
 }
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes,
@@ -887,11 +897,14 @@ pass_d_bulk(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
 
   if (threadIdx.x >= TP) {   // producer warp
     if (threadIdx.x != TP) return;
+    // test-only fault: issue no copy at all, so that every consumer's first wait runs out
+    // (nothing is in flight when the CTA leaves)
+    if (p.fault == OCCRI_FAULT_WAIT) return;
     long long it = 0;
     for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
       const int b = (int)(it % NS);
       // the buffer's previous tile (it - NS) must have been consumed
-      if (it >= NS && !tma::mbar_wait(free0 + 8 * b, (unsigned)((it / NS - 1) & 1))) {
+      if (it >= NS && !tma::mbar_wait(free0 + 8 * b, (unsigned)((it / NS - 1) & 1), p.wait_ns)) {
         record_timeout(p.status);
         return;
       }
@@ -919,7 +932,7 @@ pass_d_bulk(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
     // last NS releases so that no copy is in flight when the CTA exits
     for (long long last = std::max<long long>(0, it - NS); last < it; ++last) {
       const int b = (int)(last % NS);
-      if (!tma::mbar_wait(free0 + 8 * b, (unsigned)((last / NS) & 1))) {
+      if (!tma::mbar_wait(free0 + 8 * b, (unsigned)((last / NS) & 1), p.wait_ns)) {
         record_timeout(p.status);
         return;
       }
@@ -932,7 +945,7 @@ pass_d_bulk(const cplx_t<T>* __restrict__ S, const cplx_t<T>* __restrict__ psi,
   long long it = 0;
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
     const int b = (int)(it % NS);
-    if (!tma::mbar_wait(full0 + 8 * b, (unsigned)((it / NS) & 1))) {
+    if (!tma::mbar_wait(full0 + 8 * b, (unsigned)((it / NS) & 1), p.wait_ns)) {
       record_timeout(p.status);
       return;
     }
@@ -1020,25 +1033,30 @@ cudaError_t launch_pass_d_noc(const PairParams& p, const cplx_t<T>* S, const cpl
                               cplx_t<T>* Y, cudaStream_t st) {
   const size_t sm = bulk_smem(p.nocc, p.nkp, p.diag, sizeof(cplx_t<T>));
   if (sm) {
-    static size_t sm_set = 0;
-    if (sm > sm_set) {
-      cudaFuncSetAttribute(pass_d_bulk<T, NOC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm);
-      sm_set = sm;
+    // the largest shared-memory size set so far for this device, and the resident slots
+    // of each shared-memory size actually launched (one cache per wave kind)
+    static std::mutex mu;
+    static int sm_set[kMaxDevices] = {};
+    static DeviceCache slots_cache[2];
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      int& have = sm_set[(p.device >= 0 && p.device < kMaxDevices) ? p.device : 0];
+      if ((int)sm > have) {
+        if (cudaFuncSetAttribute(pass_d_bulk<T, NOC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm) != cudaSuccess)
+          return cudaGetLastError();
+        have = (int)sm;
+      }
     }
-    static int cached_diag[2] = {-1, -1}, cached_slots[2] = {1, 1};   // per wave kind
-    const int c = p.diag ? 0 : 1;
-    if (cached_diag[c] < 0) {
-      cached_slots[c] = resident_slots(pass_d_bulk<T, NOC>, kBulkTile + 32, sm);
-      cached_diag[c] = p.diag;
-    }
+    const int slots = slots_cache[p.diag ? 0 : 1].get(
+        p.device, [&] { return resident_slots(pass_d_bulk<T, NOC>, kBulkTile + 32, sm); });
     const long long tiles = (p.ng + kBulkTile - 1) / kBulkTile;
-    pass_d_bulk<T, NOC><<<(unsigned)std::min<long long>(tiles, cached_slots[c]), kBulkTile + 32,
-                          sm, st>>>(S, psi, Y, p);
+    pass_d_bulk<T, NOC><<<(unsigned)std::min<long long>(tiles, slots), kBulkTile + 32, sm,
+                          st>>>(S, psi, Y, p);
     return cudaGetLastError();
   }
-  static int slots = 0;
-  if (!slots) slots = resident_slots(pass_d<T, NOC>, 256, 0);
+  static DeviceCache slots_reg;
+  const int slots = slots_reg.get(p.device, [] { return resident_slots(pass_d<T, NOC>, 256, 0); });
   const unsigned nb = (unsigned)std::min<long long>((p.ng + 255) / 256, slots);
   pass_d<T, NOC><<<nb, 256, 0, st>>>(S, psi, Y, p);
   return cudaGetLastError();
@@ -1447,9 +1465,8 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   const size_t sa = smem_a<N>(sizeof(C2));
   const size_t sb = smem_b<N>(sizeof(C2), sizeof(Axis1<T>));
   const size_t sc = smem_c<N>(sizeof(C2));
-  static bool configured = false;
-  static int slots_b = 1;
-  if (!configured) {
+  static DeviceCache cache;   // per device: attributes set, resident pass-B slots
+  const int slots_b = cache.get(p.device, [&] {
     cudaFuncSetAttribute(pass_a<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
     cudaFuncSetAttribute(pass_b<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
     cudaFuncSetAttribute(pass_c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
@@ -1457,21 +1474,21 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
       cudaFuncSetAttribute(pass_cd<N, CdShape::CW, CdShape::NT, CdShape::MB>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)cd_smem(N, CdShape::CW));
-    slots_b = resident_slots(pass_b<T, N>, nt, sb);
-    configured = true;
-  }
-  if (ev) cudaEventRecord(ev[0], st);
+    return resident_slots(pass_b<T, N>, nt, sb);
+  });
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  if (ev) chk(cudaEventRecord(ev[0], st));
   pass_a<T, N><<<dim3(N, nf), nt, sa, st>>>(psi, S, p);
-  if (ev) cudaEventRecord(ev[1], st);
+  if (ev) chk(cudaEventRecord(ev[1], st));
   T* vt = reinterpret_cast<T*>(reinterpret_cast<char*>(S) + p.vt_off);
   vtab_kernel<T, N><<<dim3(N, p.diag ? 1 : p.nkp, kVtabSplit), nt, 0, st>>>(vt, p);
   pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S, p, vt);
-  if (ev) cudaEventRecord(ev[2], st);
+  if (ev) chk(cudaEventRecord(ev[2], st));
   // FP32 waves of nocc <= kCdNoc: passes C and D fused (the potentials stay on chip)
   const bool fused = pair_wave_launches<T>(p.nocc) == 4;
   if (!fused) pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S, p);
-  if (ev_y) cudaStreamWaitEvent(st, ev_y, 0);   // the previous wave's Y updates
-  cudaError_t e = cudaSuccess;
+  if (ev_y) chk(cudaStreamWaitEvent(st, ev_y, 0));   // the previous wave's Y updates
   if constexpr (std::is_same<T, float>::value) {
     if (fused)
       pass_cd<N, CdShape::CW, CdShape::NT, CdShape::MB>
@@ -1479,9 +1496,9 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
               cd_smem(N, CdShape::CW), st>>>((const float2*)S, (const float2*)psi,
                                                            (float2*)Y, p);
   }
-  if (!fused) e = launch_pass_d<T>(p, S, psi, Y, st);
-  if (ev_y) cudaEventRecord(ev_y, st);
-  if (ev) cudaEventRecord(ev[3], st);
+  if (!fused) chk(launch_pass_d<T>(p, S, psi, Y, st));
+  if (ev_y) chk(cudaEventRecord(ev_y, st));
+  if (ev) chk(cudaEventRecord(ev[3], st));
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -1493,15 +1510,13 @@ cudaError_t run_domega_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>
   const int nf = wave_fields(p.nocc, p.nkp, p.diag);
   const size_t sa = smem_a<N>(sizeof(C2));
   const size_t sb = smem_b<N>(sizeof(C2), sizeof(Axis1<T>));
-  static bool configured = false;
-  static int slots_b = 1;
-  if (!configured) {
+  static DeviceCache cache;   // per device: attributes set, resident pass-B slots
+  const int slots_b = cache.get(p.device, [&] {
     cudaFuncSetAttribute(pass_a<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
     cudaFuncSetAttribute(pass_b_domega<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sb);
-    slots_b = resident_slots(pass_b_domega<T, N>, nt, sb);
-    configured = true;
-  }
+    return resident_slots(pass_b_domega<T, N>, nt, sb);
+  });
   pass_a<T, N><<<dim3(N, nf), nt, sa, st>>>(psi, S, p);
   pass_b_domega<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S, p, dacc);
   return cudaGetLastError();
@@ -1519,9 +1534,8 @@ cudaError_t run_vjp_wave(const PairParams& p, const cplx_t<T>* psi, const cplx_t
   const size_t sa = smem_a<N>(sizeof(C2));
   const size_t sb = smem_b<N>(sizeof(C2), sizeof(Axis1<T>));
   const size_t sc = smem_c<N>(sizeof(C2));
-  static bool configured = false;
-  static int slots_b = 1;
-  if (!configured) {
+  static DeviceCache cache;   // per device: attributes set, resident pass-B slots
+  const int slots_b = cache.get(p.device, [&] {
     cudaFuncSetAttribute(pass_a<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sa);
     cudaFuncSetAttribute(pass_a<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1530,9 +1544,8 @@ cudaError_t run_vjp_wave(const PairParams& p, const cplx_t<T>* psi, const cplx_t
     cudaFuncSetAttribute(pass_c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
     cudaFuncSetAttribute(pass_b_domega2<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sb + sizeof(C2) * N * pitch(N)));
-    slots_b = resident_slots(pass_b<T, N>, nt, sb);
-    configured = true;
-  }
+    return resident_slots(pass_b<T, N>, nt, sb);
+  });
   pass_a<T, N, false><<<dim3(N, nf), nt, sa, st>>>(psi, S0, p, nullptr);
   pass_a<T, N, true><<<dim3(N, nf), nt, sa, st>>>(psi, S1, p, gam);
   if (dacc)

@@ -7,6 +7,7 @@ cases) or from tests/golden/*.npz written by tests/golden/make_golden.py.
 """
 import math
 import os
+import warnings
 
 import numpy as np
 import pytest
@@ -18,10 +19,14 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 TOL = {"fp64": dict(k_rel=1e-10, e_rel=1e-10), "mixed": dict(k_abs=1e-5, e_abs=1e-6)}
-# The mixed-precision bar |dE_x| <= 1e-6 Ha per cell is set for the 6x6x6-k, 350-AO cell,
-# whose |E_x| is about 2.5 Ha. FP32 rounding error is relative, so cells with a larger
-# |E_x| (many occupied orbitals in a small basis) get the same relative bar.
+# The mixed-precision bar |dE_x| <= 1e-6 Ha per cell is met absolutely by every config cell
+# and every live case whose |E_x| is within 4 Ha (the bench cell's is 2.47 Ha). Two live
+# cases exist only to exercise the register blocks for nocc 12 and 20: 12 and 20 occupied
+# orbitals in a 28-AO basis in a 3 A cell, |E_x| = 8.6 and 22.7 Ha. FP32 rounding error is
+# relative, so those two are held to the same relative bar (1e-6 Ha per 2.5 Ha of |E_x|),
+# and the error they reach is reported as a warning in the test summary.
 E_X_BAR_SCALE = 2.5
+E_X_ABS_LIMIT = 4.0
 
 
 @pytest.fixture(scope="module")
@@ -63,8 +68,13 @@ def _assert_close(got, ref, precision, what="", strict_e=False):
         assert abs(got["ex"] - ref["ex"]) <= t["e_rel"] * abs(ref["ex"]), what
     else:
         assert np.abs(got["k"] - ref["k"]).max() <= t["k_abs"], (what, np.abs(got["k"] - ref["k"]).max())
-        tol_e = t["e_abs"] * (1.0 if strict_e else max(1.0, abs(ref["ex"]) / E_X_BAR_SCALE))
-        assert abs(got["ex"] - ref["ex"]) <= tol_e, (what, got["ex"], ref["ex"])
+        de = abs(got["ex"] - ref["ex"])
+        if strict_e or abs(ref["ex"]) <= E_X_ABS_LIMIT:
+            assert de <= t["e_abs"], (what, got["ex"], ref["ex"])
+        else:
+            warnings.warn(f"mixed |dE_x| = {de:.2e} Ha at |E_x| = {abs(ref['ex']):.2f} Ha "
+                          f"({what}): relative bar {t['e_abs'] / E_X_BAR_SCALE:.1e}")
+            assert de <= t["e_abs"] * abs(ref["ex"]) / E_X_BAR_SCALE, (what, got["ex"], ref["ex"])
 
 
 # ------------------------------------------------------------------ steps (a)+(b)
@@ -172,12 +182,14 @@ def test_config_matches_golden(torch_cuda, name, precision):
 
 
 @pytest.mark.parametrize("name", ["cfg3_erfc", "cfg3_erf"])
-def test_config3_mixed_matches_golden(torch_cuda, name):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config3_matches_golden(torch_cuda, name, precision):
     w = config(name)
     g = _golden(name)
     k_ref, _, ex_ref = O.ace_assemble(w.C, g["kc"])
-    got = _gpu(torch_cuda, w, "mixed")
-    _assert_close(got, dict(k=k_ref, kc=g["kc"], ex=float(g["ex"])), "mixed", name, strict_e=True)
+    got = _gpu(torch_cuda, w, precision)
+    _assert_close(got, dict(k=k_ref, kc=g["kc"], ex=float(g["ex"])), precision, name,
+                  strict_e=True)
 
 
 @pytest.mark.parametrize("cell", range(5))
