@@ -69,8 +69,15 @@ typedef enum { OCCRI_COULOMB = 0, OCCRI_ERFC = 1, OCCRI_ERF = 2 } occri_kernel_k
 /* OCCRI_FP64: every step in double precision.
  * OCCRI_MIXED: AO evaluation, orbitals, pair densities, FFTs, the kernel multiply
  *   and the Y accumulation in FP32; the contraction (e) accumulates per thread in
- *   FP32 and across threads in FP64; assembly (f) and E_x in FP64. */
-typedef enum { OCCRI_FP64 = 0, OCCRI_MIXED = 1 } occri_precision;
+ *   FP32 and across threads in FP64; assembly (f) and E_x in FP64.
+ * OCCRI_MIXED_TC: as OCCRI_MIXED, but the contraction (e) runs on the tensor cores as
+ *   one GEMM over the grid points of the k-mesh's supercell: the AOs periodised over the
+ *   supercell (generated on the fly) times Y, both split into FP16 hi + lo parts with
+ *   power-of-two scalings, three FP16 products with FP32 accumulation per term, FP32 sums
+ *   over at most 512 points before the phases of the supercell offsets, FP64 sums beyond.
+ *   Plan creation returns OCCRI_EUNSUPPORTED where the supercell has more than 512 cells,
+ *   the cell more than 8 atoms, or a point tile more than 512 supercell images in reach. */
+typedef enum { OCCRI_FP64 = 0, OCCRI_MIXED = 1, OCCRI_MIXED_TC = 2 } occri_precision;
 
 typedef struct {
   double a[3][3];          /* lattice rows a_1, a_2, a_3 (bohr) */

@@ -30,7 +30,8 @@ __all__ = [
     "bloch_aos", "orbitals_on_grid", "grid_phase", "kernel_bins", "kernel_bins_domega",
     "g0_value", "apply_coulomb_operator", "occri_kc", "contract_kc", "mori_k", "aori_k",
     "ace_assemble", "exchange_energy", "exchange_energy_parseval", "grad_c",
-    "grad_omega", "grid_overlap", "dft_matrices",
+    "grad_omega", "grid_overlap", "dft_matrices", "mesh_denominators", "supercell_lattice",
+    "truncation_radius", "madelung_potential", "kernel_value",
 ]
 
 EPS_AO = 1e-16   # AO screening threshold: terms below it are dropped (C10 reading)
@@ -234,25 +235,132 @@ def _axis_reduction(n: int, q: Fraction):
     return np.array(xa), np.array(xb), np.array(zero)
 
 
-def g0_value(kind: str, omega: float, g0_mode: int) -> float:
-    """Value used for the bin G+q = 0 (Eq. VGao's chi; C3 reading)."""
+def mesh_denominators(kfrac) -> Tuple[int, int, int]:
+    """Per axis, the least D with every k-point coordinate a multiple of 1/D: the k-mesh's
+    supercell is D_1 a_1, D_2 a_2, D_3 a_3 (the Born-von Karman cell of Sec. II.A)."""
+    kfrac = np.atleast_2d(np.asarray(kfrac, float))
+    out = []
+    for d in range(3):
+        den = 1
+        for x in kfrac[:, d]:
+            den = den * _frac(x).denominator // math.gcd(den, _frac(x).denominator)
+        out.append(den)
+    return tuple(out)
+
+
+def supercell_lattice(lattice, kfrac) -> np.ndarray:
+    D = mesh_denominators(kfrac)
+    return np.asarray(lattice, float) * np.array(D, float)[:, None]
+
+
+def truncation_radius(lattice, kfrac) -> float:
+    """R_c of the truncated kernels: (4 pi / 3) R_c^3 = the supercell volume (Sec. II.A,
+    the Spencer-Alavi truncation)."""
+    return (3.0 * cell_volume(supercell_lattice(lattice, kfrac)) / (4.0 * math.pi)) ** (1.0 / 3.0)
+
+
+def _lattice_sums(lat, eta, fn_real, fn_recip, tol=1e-17):
+    """sum over R != 0 of fn_real(|R|) and over G != 0 of fn_recip(|G|^2), R on the lattice
+    `lat` and G on its reciprocal lattice, in shells grown until a whole shell adds < tol."""
+    b = reciprocal_vectors(lat)
+    out = []
+    for vecs, fn in ((lat, fn_real), (b, fn_recip)):
+        if fn is None:
+            out.append(0.0)
+            continue
+        total, n = 0.0, 1
+        while True:
+            shell = 0.0
+            rng = range(-n, n + 1)
+            for i in rng:
+                for j in rng:
+                    for k in rng:
+                        if max(abs(i), abs(j), abs(k)) != n:
+                            continue
+                        v = i * vecs[0] + j * vecs[1] + k * vecs[2]
+                        shell += fn(v)
+            total += shell
+            if abs(shell) < tol and n > 2:
+                break
+            n += 1
+        out.append(total)
+    return out
+
+
+def madelung_potential(lat, eta: Optional[float] = None) -> float:
+    """Potential at the origin of the periodic images of a unit point charge in a uniform
+    neutralising background (the charge itself excluded), lattice rows `lat`, by Ewald's
+    split: sum_{R != 0} erfc(eta R)/R + (4 pi/V) sum_{G != 0} e^{-G^2/(4 eta^2)}/G^2
+    - pi/(eta^2 V) - 2 eta/sqrt(pi)."""
+    from scipy.special import erfc
+    vol = cell_volume(lat)
+    if eta is None:
+        eta = math.sqrt(math.pi) / vol ** (1.0 / 3.0)
+    real, recip = _lattice_sums(
+        lat, eta, lambda v: erfc(eta * np.linalg.norm(v)) / np.linalg.norm(v),
+        lambda g: 4.0 * math.pi / vol * math.exp(-(g @ g) / (4 * eta * eta)) / (g @ g))
+    return real + recip - math.pi / (eta * eta * vol) - 2.0 * eta / math.sqrt(math.pi)
+
+
+def g0_value(kind: str, omega: float, g0_mode: int, lattice=None, kfrac=None) -> float:
+    """Value used for the bin G+q = 0 (Eq. VGao's chi; C3 reading).
+
+    g0_mode 0: the term is dropped. g0_mode 1: f(x -> 0), for the kernels with a finite
+    limit (erfc: pi/omega^2; the truncated kernels, Sec. II.A). g0_mode 2: the Madelung
+    correction of the k-mesh's supercell (volume V, lattice and kfrac needed): Coulomb
+    chi = -V v_M with v_M the supercell's Madelung potential; erf chi = V 2 omega/sqrt(pi)
+    - sum_{G != 0} 4 pi e^{-G^2/(4 omega^2)}/G^2 over the supercell's reciprocal lattice
+    (the integral of the kernel minus its lattice sum)."""
+    if g0_mode == 0:
+        return 0.0
     if g0_mode == 1:
-        if kind != "erfc":
-            raise ValueError("g0_mode 1 is defined for the erfc kernel only")
-        return math.pi / (omega * omega)
-    return 0.0
+        if kind == "erfc":
+            return math.pi / (omega * omega)
+        rc = truncation_radius(lattice, kfrac)
+        if kind == "coulomb_trunc":
+            return 2.0 * math.pi * rc * rc
+        if kind == "erf_trunc":
+            return 4.0 * math.pi * ((rc * rc / 2.0 - 1.0 / (4.0 * omega * omega)) *
+                                    math.erf(omega * rc) +
+                                    rc * math.exp(-(omega * rc) ** 2) / (2.0 * omega * math.sqrt(math.pi)))
+        raise ValueError(f"g0_mode 1 is not defined for the {kind} kernel")
+    if g0_mode == 2:
+        sc = supercell_lattice(lattice, kfrac)
+        vol = cell_volume(sc)
+        if kind == "coulomb":
+            return -vol * madelung_potential(sc)
+        if kind == "erf":
+            _, recip = _lattice_sums(sc, omega, None, lambda g: 4.0 * math.pi * math.exp(
+                -(g @ g) / (4 * omega * omega)) / (g @ g))
+            return vol * 2.0 * omega / math.sqrt(math.pi) - recip
+        raise ValueError(f"g0_mode 2 is not defined for the {kind} kernel")
+    raise ValueError(g0_mode)
 
 
-def _kernel_value(kind: str, omega: float, g2: np.ndarray) -> np.ndarray:
-    """f(|G+q|) of Eq. recipcoul for |G+q|^2 = g2 > 0."""
+def _kernel_value(kind: str, omega: float, g2: np.ndarray, rc: float = 0.0) -> np.ndarray:
+    """f(|G+q|) of Eq. recipcoul (and of the truncated kernels of Sec. II.A, radius rc)
+    for |G+q|^2 = g2 > 0."""
     base = 4.0 * np.pi / g2
     if kind == "coulomb":
         return base
+    if kind == "coulomb_trunc":
+        # 1 - cos(x R_c) = 2 sin^2(x R_c / 2)
+        return base * 2.0 * np.sin(0.5 * np.sqrt(g2) * rc) ** 2
     y = g2 / (4.0 * omega * omega)
     if kind == "erfc":
         return base * (-np.expm1(-y))
     if kind == "erf":
         return base * np.exp(-y)
+    if kind == "erf_trunc":
+        # Eq. lrtrunc: f = (4 pi/x^2) [-erf(w R) cos(x R) + e^{-y} Re erf(w R + i x/(2w))],
+        # with e^{-y} erf(z) = e^{-y} - e^{-w^2 R^2} e^{-i x R} w_F(i z) (w_F the Faddeeva
+        # function, bounded there), which removes the cancellation Appendix A describes
+        from scipy.special import wofz
+        x = np.sqrt(g2)
+        wr = omega * rc
+        faddeeva = wofz(-x / (2.0 * omega) + 1j * wr)
+        t = np.exp(-y) - math.exp(-wr * wr) * np.real(np.exp(-1j * x * rc) * faddeeva)
+        return base * (-math.erf(wr) * np.cos(x * rc) + t)
     raise ValueError(kind)
 
 
@@ -283,9 +391,19 @@ def _bins(lattice, grid, qfrac, fn, zero_value):
     return v
 
 
-def kernel_bins(lattice, grid, qfrac, kind: str, omega: float, g0: float) -> np.ndarray:
-    """v_q(m) on the FFT bins (tie-averaged); G+q = 0 takes g0."""
-    return _bins(lattice, grid, qfrac, lambda g2: _kernel_value(kind, omega, g2), g0)
+def _rc(kind: str, lattice, kfrac) -> float:
+    return truncation_radius(lattice, kfrac) if kind.endswith("_trunc") else 0.0
+
+
+def kernel_value(kind: str, omega: float, g2, rc: float = 0.0) -> np.ndarray:
+    """f(|G+q|) for |G+q|^2 = g2 > 0 (public name of the per-bin kernel)."""
+    return _kernel_value(kind, omega, np.asarray(g2, float), rc)
+
+
+def kernel_bins(lattice, grid, qfrac, kind: str, omega: float, g0: float,
+                rc: float = 0.0) -> np.ndarray:
+    """v_q(m) on the FFT bins (tie-averaged); G+q = 0 takes g0; rc: truncation radius."""
+    return _bins(lattice, grid, qfrac, lambda g2: _kernel_value(kind, omega, g2, rc), g0)
 
 
 def kernel_bins_domega(lattice, grid, qfrac, kind: str, omega: float, g0_mode: int):
@@ -353,7 +471,7 @@ def occri_kc(lattice, grid, kfrac, psi: np.ndarray, chi: Optional[np.ndarray], k
     for k in range(nk):
         for kp in range(nk):
             q = np.asarray(kfrac[k], float) - np.asarray(kfrac[kp], float)
-            v = kernel_bins(lattice, grid, q, kind, omega, g0)
+            v = kernel_bins(lattice, grid, q, kind, omega, g0, _rc(kind, lattice, kfrac))
             for i in range(nocc):
                 for j in range(nocc):
                     f = (np.conj(psi[kp, j]) * psi[k, i]).reshape(grid)
@@ -387,7 +505,7 @@ def mori_k(lattice, grid, kfrac, chi: np.ndarray, psi: np.ndarray, kind: str, om
         wacc = np.zeros((nao, ng), dtype=np.complex128)
         for kp in range(nk):
             q = np.asarray(kfrac[k], float) - np.asarray(kfrac[kp], float)
-            v = kernel_bins(lattice, grid, q, kind, omega, g0)
+            v = kernel_bins(lattice, grid, q, kind, omega, g0, _rc(kind, lattice, kfrac))
             for nu in range(nao):
                 for j in range(nocc):
                     f = (np.conj(psi[kp, j]) * chi[k, nu]).reshape(grid)
@@ -413,7 +531,7 @@ def aori_k(lattice, grid, kfrac, chi: np.ndarray, C: np.ndarray, kind: str, omeg
         wacc = np.zeros((nao, ng), dtype=np.complex128)
         for kp in range(nk):
             q = np.asarray(kfrac[k], float) - np.asarray(kfrac[kp], float)
-            v = kernel_bins(lattice, grid, q, kind, omega, g0)
+            v = kernel_bins(lattice, grid, q, kind, omega, g0, _rc(kind, lattice, kfrac))
             for nu in range(nao):
                 for s in range(nao):
                     f = (np.conj(chi[kp, s]) * chi[k, nu]).reshape(grid)
@@ -461,7 +579,7 @@ def exchange_energy_parseval(lattice, grid, kfrac, psi: np.ndarray, kind: str, o
     for k in range(nk):
         for kp in range(nk):
             q = np.asarray(kfrac[k], float) - np.asarray(kfrac[kp], float)
-            v = kernel_bins(lattice, grid, q, kind, omega, g0)
+            v = kernel_bins(lattice, grid, q, kind, omega, g0, _rc(kind, lattice, kfrac))
             ph = grid_phase(grid, q)
             for i in range(nocc):
                 for j in range(nocc):

@@ -26,9 +26,9 @@ OCCRI_ETIMEOUT = 5
 OCCRI_EUNSUPPORTED = 6
 
 OCCRI_COULOMB, OCCRI_ERFC, OCCRI_ERF = 0, 1, 2
-OCCRI_FP64, OCCRI_MIXED = 0, 1
+OCCRI_FP64, OCCRI_MIXED, OCCRI_MIXED_TC = 0, 1, 2
 KERNELS = {"coulomb": OCCRI_COULOMB, "erfc": OCCRI_ERFC, "erf": OCCRI_ERF}
-PRECISIONS = {"fp64": OCCRI_FP64, "mixed": OCCRI_MIXED}
+PRECISIONS = {"fp64": OCCRI_FP64, "mixed": OCCRI_MIXED, "mixed_tc": OCCRI_MIXED_TC}
 
 
 class occri_cell(ctypes.Structure):

@@ -537,6 +537,7 @@ void free_plan(Plan* p) {
   for (cudaEvent_t e : {p->ev_fork, p->ev_join, p->ev_y, p->ev_iso})
     if (e) cudaEventDestroy(e);
   if (p->aux) cudaStreamDestroy(p->aux);
+  if (p->tc) tc_plan_free(p->tc);
   for (cudaEvent_t e : p->ev_used) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev_free) cudaEventDestroy(e);
   delete p;
@@ -668,11 +669,16 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
     StageTimer t(p, timed);
     if (launch_phase_fields<T>(*p, p->Y, +1, s) != cudaSuccess) return OCCRI_ECUDA;
     ++launches;
-    if (launch_contract<T>(*p, s) != cudaSuccess) return OCCRI_ECUDA;
+    if (p->tc) {
+      if (launch_contract_tc(*p, s) != cudaSuccess) return OCCRI_ECUDA;
+      launches += 3;
+    } else {
+      if (launch_contract<T>(*p, s) != cudaSuccess) return OCCRI_ECUDA;
+      for (int l = 0; l < 4; ++l)
+        if (!p->shells_by_l[l].empty())
+          launches += (p->nocc + contract_chunk<T>() - 1) / contract_chunk<T>();
+    }
     t.done(OCCRI_STAGE_CONTRACT, p->nk);
-    for (int l = 0; l < 4; ++l)
-      if (!p->shells_by_l[l].empty())
-        launches += (p->nocc + contract_chunk<T>() - 1) / contract_chunk<T>();
   }
   {
     StageTimer t(p, timed);
@@ -915,7 +921,8 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
   if (cell->natm < 1 || !cell->xyz) return OCCRI_EINVAL;
   if (kmesh->nk < 1 || !kmesh->kfrac) return OCCRI_EINVAL;
   if (basis->nshell < 1 || !basis->atom || !basis->l || !basis->alpha) return OCCRI_EINVAL;
-  if (precision != OCCRI_FP64 && precision != OCCRI_MIXED) return OCCRI_EINVAL;
+  if (precision != OCCRI_FP64 && precision != OCCRI_MIXED && precision != OCCRI_MIXED_TC)
+    return OCCRI_EINVAL;
   if (kernel->kind < 0 || kernel->kind > 2) return OCCRI_EINVAL;
   if (kernel->kind != OCCRI_COULOMB && !(kernel->omega > 0.0)) return OCCRI_EINVAL;
   if (kernel->g0_mode != 0 && kernel->g0_mode != 1) return OCCRI_EINVAL;
@@ -993,7 +1000,7 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     x.alpha_lo = (float)(x.alpha - (double)x.alpha_f);
     // Tight primitives reach one or two images per point, so FP32 rounding of
     // r^2 and alpha r^2 does not average out there; they get a double-float exponent.
-    x.exact_arg = (precision == OCCRI_MIXED && x.alpha >= 0.5) ? 1 : 0;
+    x.exact_arg = (precision != OCCRI_FP64 && x.alpha >= 0.5) ? 1 : 0;
     shell_norms(x.l, x.alpha, x.norm);
     for (int m = 0; m < 2 * x.l + 1; ++m) x.norm_f[m] = (float)x.norm[m];
     rcut[s] = shell_cutoff(x.l, x.alpha, eps);
@@ -1254,6 +1261,13 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     cudaGetLastError();
     free_plan(p);
     return code;
+  }
+  if (precision == OCCRI_MIXED_TC) {
+    const int st = tc_plan_create(p, sh, cell->xyz, rcut, &tot);
+    if (st != OCCRI_OK) {
+      free_plan(p);
+      return st;
+    }
   }
   p->workspace_bytes = tot;
   occri_plan* h = new (std::nothrow) occri_plan;

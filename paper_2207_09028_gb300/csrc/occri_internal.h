@@ -66,6 +66,10 @@ struct AOParams {
   const void* cs;            // [nk][nao][nocc] N_mu C^k_{mu i}: double2 (FP64) or float4 hi/lo (FP32)
 };
 
+// Atoms a plan may have for the tensor-core contraction.
+constexpr int kMaxTcAtoms = 8;
+struct TcPlan;   // tables and buffers of the tensor-core contraction (occri_contract_tc.cu)
+
 // Parameters of one wave of pair fields (steps c, d): output k, a block of k'.
 struct PairParams {
   int nk, nocc, N1;          // N1: cubic grid edge
@@ -163,6 +167,7 @@ struct Plan {
   double* dacc = nullptr;    // [2] scratch accumulators (d E/d omega)
   int* status = nullptr;     // [2]: first device error code, k index
   bool have_kc = false;
+  TcPlan* tc = nullptr;      // OCCRI_MIXED_TC: the tensor-core contraction's tables
   double* ao_norm = nullptr; // [nao] N_lm per AO
   void* cs = nullptr;        // scaled coefficients (see AOParams::cs)
 
@@ -257,6 +262,14 @@ __host__ __device__ inline int wave_fields(int nocc, int nkp, int diag) {
 inline int wave_targets(int nocc, int nkp, int diag) { return diag ? nocc : nocc + nkp * nocc; }
 template <typename T>
 cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s);
+
+// The tensor-core contraction (OCCRI_MIXED_TC): tables built at plan creation from the shells
+// (with their screening radii) and atom positions, freed with the plan; the launch turns the
+// Bloch-phased Y into FP16 hi/lo blocks and adds K_{mu i} into p.kc.
+int tc_plan_create(Plan* p, const std::vector<ShellDev>& shells, const double* xyz,
+                   const std::vector<double>& rcut, size_t* total);
+void tc_plan_free(TcPlan* t);
+cudaError_t launch_contract_tc(const Plan& p, cudaStream_t s);
 
 // Launch settings derived once per kernel instantiation and device (function attributes,
 // resident-slot counts): each entry is filled under a lock the first time a plan on that

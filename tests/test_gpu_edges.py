@@ -82,6 +82,14 @@ def test_every_edge_matches_explicit_dft_oracle(torch_cuda, n, precision):
     _check(_gpu(torch_cuda, w, precision), _oracle(n), precision, f"edge {n}")
 
 
+# the tensor-core contraction reads the grid through point tiles of 32: a few edges with
+# ragged last tiles (9^3, 25^3, 45^3) and exact ones
+@pytest.mark.parametrize("n", [9, 24, 25, 45, 48])
+def test_tensor_core_contraction_edges(torch_cuda, n):
+    w = _edge_workload(n)
+    _check(_gpu(torch_cuda, w, "mixed_tc"), _oracle(n), "mixed_tc", f"edge {n}")
+
+
 # ------------------------------------------------------------------ the bench's edge, 60^3
 
 # the bench cell's lattice constant (5.43 A), so that E_x is of the bench cell's size
@@ -92,7 +100,7 @@ BENCH_EDGE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_tc"])
 @pytest.mark.parametrize("case", range(len(BENCH_EDGE_CASES)))
 def test_bench_edge_60_matches_oracle(torch_cuda, case, precision):
     c = BENCH_EDGE_CASES[case]

@@ -18,7 +18,9 @@ from workloads import config, small_workload
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-TOL = {"fp64": dict(k_rel=1e-10, e_rel=1e-10), "mixed": dict(k_abs=1e-5, e_abs=1e-6)}
+TOL = {"fp64": dict(k_rel=1e-10, e_rel=1e-10), "mixed": dict(k_abs=1e-5, e_abs=1e-6),
+       "mixed_tc": dict(k_abs=1e-5, e_abs=1e-6)}
+PRECISIONS = ["fp64", "mixed", "mixed_tc"]
 # The mixed-precision bar |dE_x| <= 1e-6 Ha per cell is met absolutely by every config cell
 # and every live case whose |E_x| is within 4 Ha (the bench cell's is 2.47 Ha). Two live
 # cases exist only to exercise the register blocks for nocc 12 and 20: 12 and 20 occupied
@@ -113,7 +115,7 @@ SMALL = [
 
 
 @pytest.mark.parametrize("case", range(len(SMALL)))
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_small_builds_match_oracle(torch_cuda, case, precision):
     w = small_workload(seed=100 + case, **SMALL[case])
     ref = _oracle(w)
@@ -172,7 +174,7 @@ def _golden(name):
 
 
 @pytest.mark.parametrize("name", ["cfg1", "cfg2"])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_config_matches_golden(torch_cuda, name, precision):
     w = config(name)
     g = _golden(name)
@@ -182,7 +184,7 @@ def test_config_matches_golden(torch_cuda, name, precision):
 
 
 @pytest.mark.parametrize("name", ["cfg3_erfc", "cfg3_erf"])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_config3_matches_golden(torch_cuda, name, precision):
     w = config(name)
     g = _golden(name)
@@ -193,7 +195,7 @@ def test_config3_matches_golden(torch_cuda, name, precision):
 
 
 @pytest.mark.parametrize("cell", range(5))
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_config4_cells_match_golden(torch_cuda, cell, precision):
     w = config("cfg4")[cell]
     g = _golden(w.name)
@@ -375,12 +377,13 @@ def test_config5_mixed_energy_within_1e6_of_fp64(torch_cuda):
     w = config("cfg5")
     C = torch.from_numpy(w.C).cuda()
     out = {}
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "mixed_tc", "fp64"):
         plan = occri.Plan.from_workload(w, precision=prec)
         KC, _, Ex = plan.build(C, want_k=False)
         out[prec] = (KC.cpu().numpy(), float(Ex.cpu()[0]))
         plan.close()
         del plan, KC
         torch.cuda.empty_cache()
-    assert abs(out["mixed"][1] - out["fp64"][1]) <= 1e-6
-    assert np.abs(out["mixed"][0] - out["fp64"][0]).max() <= TOL["mixed"]["k_abs"]
+    for prec in ("mixed", "mixed_tc"):
+        assert abs(out[prec][1] - out["fp64"][1]) <= 1e-6, prec
+        assert np.abs(out[prec][0] - out["fp64"][0]).max() <= TOL["mixed"]["k_abs"], prec

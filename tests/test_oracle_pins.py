@@ -312,6 +312,146 @@ def test_kernel_linearity_erfc_plus_erf_is_coulomb():
     assert np.abs(a + b - c).max() < 1e-13 * np.abs(c).max()
 
 
+# ---------------------------------------------------------------- singularity treatments
+# (Sec. II.A: the Madelung correction chi of Eq. VGao, the Spencer-Alavi truncated Coulomb
+# kernel and the truncated long-range kernel of Eq. lrtrunc with Appendix A's stable form)
+
+def _golden_scalar(name, key):
+    path = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden", name)
+    for line in open(path):
+        parts = line.split()
+        if parts and parts[0] == key:
+            return float(parts[1])
+    raise KeyError(key)
+
+
+def test_madelung_potential_of_the_simple_cubic_lattice():
+    alpha = _golden_scalar("madelung_simple_cubic.txt", "alpha")
+    for L in (1.0, 7.5):
+        for eta in (None, 0.9 / L, 2.5 / L):   # the Ewald split must not matter
+            v = O.madelung_potential(L * np.eye(3), eta)
+            assert abs(v * L + alpha) < 1e-11, (L, eta, v)
+
+
+def test_madelung_chi_of_the_coulomb_and_erf_kernels():
+    """chi = -V v_M for Coulomb; for erf, the integral of the kernel minus its lattice sum,
+    which differs from Coulomb's by the short-range images -V sum_{R != 0} erfc(w R)/R and
+    from erfc's chi = pi/w^2 (v_erf + v_erfc = v_Coulomb) accordingly."""
+    from scipy.special import erfc
+    lat = small_workload(a_ang=3.0).lattice
+    kf = O.grid_points(np.eye(3), (2, 1, 2))        # a 2 x 1 x 2 Gamma-centred mesh
+    sc = O.supercell_lattice(lat, kf)
+    assert np.allclose(sc, lat * np.array([2, 1, 2])[:, None])
+    vol = O.cell_volume(sc)
+    chi_c = O.g0_value("coulomb", 0.0, 2, lat, kf)
+    assert abs(chi_c + vol * O.madelung_potential(sc)) < 1e-12 * abs(chi_c)
+    assert chi_c > 0                                   # v_M < 0: more exchange, not less
+    for w in (0.3, 0.8, 1.5):
+        chi_e = O.g0_value("erf", w, 2, lat, kf)
+        n = np.arange(-12, 13)
+        R = (n[:, None, None, None] * sc[0] + n[None, :, None, None] * sc[1] +
+             n[None, None, :, None] * sc[2]).reshape(-1, 3)
+        r = np.linalg.norm(R, axis=1)
+        r = r[r > 0]
+        images = float(np.sum(erfc(w * r) / r))       # brute force, converged for these w
+        assert abs(chi_c - (chi_e + math.pi / w ** 2) + vol * images) < 1e-9 * abs(chi_c), w
+    # a kernel too smooth to see the lattice: only the integral V 2 w / sqrt(pi) is left
+    assert abs(O.g0_value("erf", 0.05, 2, lat, kf) - vol * 0.1 / math.sqrt(math.pi)) < 1e-10
+
+
+def _fourier_radial(rv, x, rc):
+    """Fourier transform of a radial potential cut at rc, given rv(r) = r v(r):
+    4 pi / x int_0^rc rv(r) sin(x r) dr (x > 0), or 4 pi int_0^rc r rv(r) dr (x = 0)."""
+    from scipy.integrate import quad
+    if x == 0.0:
+        return 4 * math.pi * quad(lambda r: r * rv(r), 0, rc, epsabs=1e-13, epsrel=1e-13)[0]
+    val = quad(rv, 0, rc, weight="sin", wvar=x, epsabs=1e-13, epsrel=1e-13, limit=400)[0]
+    return 4 * math.pi / x * val
+
+
+@pytest.mark.parametrize("x", [0.05, 0.7, 3.0, 11.0, 40.0])
+def test_truncated_kernels_are_the_fourier_transforms_of_the_cut_potentials(x):
+    from scipy.special import erf
+    rc, w = 6.2, 0.45
+    f_c = O.kernel_value("coulomb_trunc", 0.0, np.array([x * x]), rc)[0]
+    assert abs(f_c - _fourier_radial(lambda r: 1.0, x, rc)) < 1e-9 * abs(f_c) + 1e-12
+    f_e = O.kernel_value("erf_trunc", w, np.array([x * x]), rc)[0]
+    ref = _fourier_radial(lambda r: erf(w * r), x, rc)
+    assert abs(f_e - ref) < 1e-9 * max(abs(ref), 1e-3), (f_e, ref)
+
+
+def test_truncated_kernels_x_to_zero_limits():
+    from scipy.special import erf
+    w = small_workload(mesh=(1, 2, 1))
+    rc = O.truncation_radius(w.lattice, w.kfrac)
+    assert abs(4 * math.pi / 3 * rc ** 3 - 2 * O.cell_volume(w.lattice)) < 1e-10 * rc ** 3
+    g0c = O.g0_value("coulomb_trunc", 0.0, 1, w.lattice, w.kfrac)
+    assert abs(g0c - _fourier_radial(lambda r: 1.0, 0.0, rc)) < 1e-10 * g0c
+    g0e = O.g0_value("erf_trunc", 0.4, 1, w.lattice, w.kfrac)
+    ref = _fourier_radial(lambda r: erf(0.4 * r), 0.0, rc)
+    assert abs(g0e - ref) < 1e-10 * ref
+    # and the kernels approach them continuously
+    for kind, g0 in (("coulomb_trunc", g0c), ("erf_trunc", g0e)):
+        f = O.kernel_value(kind, 0.4, np.array([1e-8]), rc)[0]
+        assert abs(f - g0) < 1e-5 * g0, kind
+
+
+def test_isolated_gaussian_coulomb_with_madelung_correction():
+    """One normalised s Gaussian (exponent alpha, density exponent beta = 2 alpha) in a
+    large cubic box, Coulomb kernel with the Madelung chi: the images in the neutralising
+    background cancel against chi up to the Ewald terms, leaving E_x = -(sqrt(2 beta/pi) +
+    2 pi / (beta L^3)) (Ewald's identity with splitting eta^2 = beta/2; erfc(eta L) terms
+    are below 1e-20 here)."""
+    alpha, box = 0.9, 11.0
+    lat = box * np.eye(3)
+    xyz = np.array([[box / 2] * 3])
+    grid = (54, 54, 54)
+    kf = np.zeros((1, 3))
+    chi = O.bloch_aos(lat, xyz, np.array([0]), np.array([0]), np.array([alpha]), kf, grid=grid)
+    C = np.ones((1, 1, 1), dtype=complex)
+    psi = O.orbitals_on_grid(chi, C)
+    g0 = O.g0_value("coulomb", 0.0, 2, lat, kf)
+    kc = O.occri_kc(lat, grid, kf, psi, chi, "coulomb", 0.0, g0)
+    beta = 2 * alpha
+    exact = -(math.sqrt(2 * beta / math.pi) + 2 * math.pi / (beta * box ** 3))
+    assert abs(O.exchange_energy(C, kc) - exact) < 1e-8
+
+
+@pytest.mark.parametrize("kind,g0_mode,omega", [("coulomb_trunc", 1, 0.0), ("erf_trunc", 1, 0.5),
+                                                 ("coulomb", 2, 0.0), ("erf", 2, 0.5)])
+def test_kmesh_equals_gamma_supercell_with_singularity_treatments(kind, g0_mode, omega):
+    """P5 again: the truncation radius and the Madelung chi belong to the k-mesh's supercell,
+    which is the same for the cell with its mesh and for the Gamma supercell."""
+    w = small_workload(mesh=(1, 1, 2), grid=(6, 6, 6), counts=(2, 1), nocc=2)
+    chi = _chi(w)
+    psi = O.orbitals_on_grid(chi, w.C)
+    g0 = O.g0_value(kind, omega, g0_mode, w.lattice, w.kfrac)
+    e_cell = O.exchange_energy(w.C, O.occri_kc(w.lattice, w.grid, w.kfrac, psi, chi, kind,
+                                               omega, g0))
+    nk, nao, nocc = w.C.shape
+    sc_lat = w.lattice.copy()
+    sc_lat[2] *= 2
+    offs = [np.array([0, 0, 0]), np.array([0, 0, 1])]
+    xyz = np.concatenate([w.xyz + o @ w.lattice for o in offs])
+    natm = w.xyz.shape[0]
+    sa = np.concatenate([w.shell_atom + natm * j for j in range(2)])
+    csc = np.zeros((2 * nao, nk * nocc), dtype=complex)
+    for ik in range(nk):
+        for j, o in enumerate(offs):
+            csc[j * nao:(j + 1) * nao, ik * nocc:(ik + 1) * nocc] = (
+                np.exp(2j * np.pi * w.kfrac[ik] @ o) * w.C[ik] / math.sqrt(nk))
+    gsc = (6, 6, 12)
+    kg = np.zeros((1, 3))
+    chi_sc = O.bloch_aos(sc_lat, xyz, sa, np.concatenate([w.shell_l] * 2),
+                         np.concatenate([w.shell_alpha] * 2), kg, grid=gsc)
+    psi_sc = O.orbitals_on_grid(chi_sc, csc[None])
+    g0_sc = O.g0_value(kind, omega, g0_mode, sc_lat, kg)
+    assert abs(g0_sc - g0) < 1e-10 * abs(g0)
+    e_sc = O.exchange_energy(csc[None], O.occri_kc(sc_lat, gsc, kg, psi_sc, chi_sc, kind, omega,
+                                                   g0_sc))
+    assert abs(e_sc / nk - e_cell) < 1e-11 * abs(e_cell)
+
+
 # ---------------------------------------------------------------- adjoint
 
 def _energy(w, C, chi, omega=None):
