@@ -61,6 +61,18 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _tensor_peak():
+    """Dense bf16 TFLOP/s: the burst figure of MEASURED_PEAKS.json (the contraction is timed
+    as one stage of a build), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured bf16 burst"
+    return 1900.0, "fallback"
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -299,6 +311,44 @@ def roofline(stages: dict, info: dict, edge: int, ng: int, nocc: int, hbm: float
                               else None)}
 
 
+def pair_field_flops(ng: int) -> float:
+    """Nominal arithmetic of one pair field: two 3-D transforms at the radix-2 count
+    5 N_g log2 N_g each, plus pair formation (a complex product), the kernel multiply (real
+    times complex) and the two accumulations (two complex multiply-adds): 24 N_g."""
+    return (10.0 * np.log2(ng) + 24.0) * ng
+
+
+def alu_roofline(fields: float, ng: int, ms: float, peak_tflops: float, kind: str):
+    """Roofline of a pair loop bound by arithmetic (the FP64 path): nominal flops of the
+    build's fields over its time, against the measured FMA rate of that precision."""
+    if not peak_tflops or ms <= 0:
+        return None
+    achieved = pair_field_flops(ng) * fields / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "peak_kind": f"measured {kind} FMA loop",
+            "flops_per_field": pair_field_flops(ng)}
+
+
+# one stage of the tensor-core contraction: three FP16 MMAs (hi.hi, hi.lo, lo.hi) of
+# M = 128 AO rows, N = 256 real columns, K = 32 grid points
+TC_FLOPS_PER_STAGE = 3 * 2.0 * 128 * 256 * 32
+
+
+def tensor_roofline(info: dict, contract_ms: float, peak_tflops: float, peak_kind: str):
+    """Roofline of the tensor-core contraction: the MMA flops of its stages over the
+    contraction stage's time, against the measured dense bf16 rate (FP16 runs at the same
+    rate on these tensor cores)."""
+    st = int(info.get("tc_stages", 0))
+    if not info.get("contraction_tc") or st <= 0 or contract_ms <= 0:
+        return None
+    achieved = TC_FLOPS_PER_STAGE * st / (contract_ms / 1e3) / 1e12
+    return {"kernel": "contract_tc_kernel (tcgen05.mma kind::f16, FP16 hi/lo x3, FP32 accumulate)",
+            "bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "peak_kind": peak_kind, "stages": st,
+            "flops_per_stage": TC_FLOPS_PER_STAGE,
+            "useful_frac": achieved / 3.0 / peak_tflops}
+
+
 def max_over_ranks(ms: float, dist=None, device=None) -> float:
     """The slowest rank's time (replicas: every rank runs the whole build on its GPU)."""
     if dist is None:
@@ -453,6 +503,8 @@ def main():
     ap.add_argument("--sweep", default=None, choices=["nk", "nao"])
     ap.add_argument("--builds", type=int, default=2)
     ap.add_argument("--precision", default="mixed")
+    ap.add_argument("--bench-precision", default="mixed_tc",
+                    help="precision of the headline builds (mixed_tc: tensor-core contraction)")
     ap.add_argument("--timing", action="store_true")
     args = ap.parse_args()
     if args.case:
@@ -474,7 +526,10 @@ def main():
                         f"Gamma-centred), nao {w.nao}, nocc {w.nocc}, grid {w.grid[0]}^3, "
                         f"{w.kernel} kernel"),
            "nk": w.nk, "nao": w.nao, "nocc": w.nocc, "grid": list(w.grid), "kernel": w.kernel,
-           "precision": "mixed: FP32 AO/orbitals/FFTs/Y, FP64 contraction sum, assembly, E_x",
+           "precision": ("mixed_tc: FP32 AO/orbitals/FFTs/Y; contraction on the tensor cores "
+                         "(FP16 hi/lo x3, FP32 accumulate, FP64 sums); FP64 assembly, E_x"
+                         if args.bench_precision == "mixed_tc" else
+                         "mixed: FP32 AO/orbitals/FFTs/Y, FP64 contraction sum, assembly, E_x"),
            "l2": l2_note(w.nk, w.nocc, w.ng),
            "parallelism": f"replicas x{world}"}
 
@@ -520,7 +575,7 @@ def main():
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    plan = occri.Plan.from_workload(w, precision="mixed")
+    plan = occri.Plan.from_workload(w, precision=args.bench_precision)
     C = torch.from_numpy(w.C).to(dev)
     KC = torch.empty((w.nk, w.nao, w.nocc), dtype=torch.complex128, device=dev)
     K = torch.empty((w.nk, w.nao, w.nao), dtype=torch.complex128, device=dev)
@@ -569,13 +624,16 @@ def main():
             stage_share[name] = stages[name]["ms"] * waves / max(1, stages[name]["launches"])
     hbm, peak_kind = _peaks()
     roof = roofline(stages, info, w.grid[0], w.ng, w.nocc, hbm, peak_kind)
+    tpeak, tpeak_kind = _tensor_peak()
+    contraction_roof = tensor_roofline(info, stage_share.get("contract", 0.0), tpeak, tpeak_kind)
 
     out = {"impl": "occri", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic", "config": cfg, "roofline": roof,
            "gpu_launches": int(info["launches_per_build"]) * args.steps,
-           "stage_ms_per_build": stage_share, "E_x_mixed": ex_mixed}
+           "stage_ms_per_build": stage_share, "E_x_mixed": ex_mixed,
+           "roofline_contraction": contraction_roof}
     clocks = clk.summary()
     out["clocks"] = clocks
 
@@ -619,10 +677,15 @@ def main():
         p64.sync()
         ms64 = e0.elapsed_time(e1) / args.fp64_steps
         ex64 = float(Ex64.cpu()[0])
+        peaks = {k: occri.measure_fma_peak(k) for k in ("fp64", "fp32", "fp32x2")}
+        fields = stages.get("pairs", {}).get("units", 0.0) / max(1, args.steps)
         out["fp64_gpu"] = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
                            "steps": args.fp64_steps, "E_x": ex64,
                            "mixed_speedup": ms64 / ms_per_step,
-                           "abs_dE_x_mixed_vs_fp64": abs(ex_mixed - ex64)}
+                           "abs_dE_x_mixed_vs_fp64": abs(ex_mixed - ex64),
+                           "roofline_whole_build": alu_roofline(fields, w.ng, ms64,
+                                                                peaks["fp64"], "fp64")}
+        out["alu_peaks_tflops"] = peaks
         p64.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

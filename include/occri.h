@@ -64,7 +64,14 @@ typedef enum {
   OCCRI_EUNSUPPORTED = 6   /* valid input outside what this build implements */
 } occri_status;
 
-typedef enum { OCCRI_COULOMB = 0, OCCRI_ERFC = 1, OCCRI_ERF = 2 } occri_kernel_kind;
+/* Kernels v(r) of the exchange operator (Eq. recipcoul, and the truncation of Sec. II.A):
+ * OCCRI_COULOMB 1/r, OCCRI_ERFC erfc(omega r)/r, OCCRI_ERF erf(omega r)/r, and
+ * OCCRI_COULOMB_TRUNC 1/r cut at R_c (Spencer-Alavi), (4 pi/3) R_c^3 = the volume of the
+ * k-mesh's supercell D_1 a_1 x D_2 a_2 x D_3 a_3 (D_d: the k denominators, see occri_kmesh),
+ * whose transform is (4 pi/x^2)(1 - cos(x R_c)). */
+typedef enum {
+  OCCRI_COULOMB = 0, OCCRI_ERFC = 1, OCCRI_ERF = 2, OCCRI_COULOMB_TRUNC = 3
+} occri_kernel_kind;
 
 /* OCCRI_FP64: every step in double precision.
  * OCCRI_MIXED: AO evaluation, orbitals, pair densities, FFTs, the kernel multiply
@@ -75,8 +82,9 @@ typedef enum { OCCRI_COULOMB = 0, OCCRI_ERFC = 1, OCCRI_ERF = 2 } occri_kernel_k
  *   supercell (generated on the fly) times Y, both split into FP16 hi + lo parts with
  *   power-of-two scalings, three FP16 products with FP32 accumulation per term, FP32 sums
  *   over at most 512 points before the phases of the supercell offsets, FP64 sums beyond.
- *   Plan creation returns OCCRI_EUNSUPPORTED where the supercell has more than 512 cells,
- *   the cell more than 8 atoms, or a point tile more than 512 supercell images in reach. */
+ *   Where the supercell has more than 512 cells, the cell more than 8 atoms, or a tile of 32
+ *   grid points more than 128 supercell images in reach (small supercells), the plan keeps
+ *   the CUDA-core contraction of OCCRI_MIXED; occri_plan_info reports which one it uses. */
 typedef enum { OCCRI_FP64 = 0, OCCRI_MIXED = 1, OCCRI_MIXED_TC = 2 } occri_precision;
 
 typedef struct {
@@ -102,7 +110,15 @@ typedef struct {
 typedef struct {
   int kind;                /* occri_kernel_kind (Eq. recipcoul) */
   double omega;            /* range-separation parameter (bohr^-1), > 0 for erfc / erf */
-  int g0_mode;             /* 0: drop the G+q = 0 term; 1: use f(x->0) = pi/omega^2 (erfc only) */
+  int g0_mode;             /* the G+q = 0 term (Eq. VGao's chi):
+                              0: dropped;
+                              1: f(x -> 0): pi/omega^2 (erfc), 2 pi R_c^2 (truncated Coulomb);
+                              2: the Madelung correction of the supercell of volume V
+                                 (Coulomb: chi = -V v_M, v_M the Ewald potential at a unit
+                                 point charge from its images in a neutralising background;
+                                 erf: chi = V 2 omega/sqrt(pi) - sum_{G != 0} 4 pi
+                                 e^{-G^2/(4 omega^2)}/G^2 over the supercell's reciprocal
+                                 lattice, the kernel's integral minus its lattice sum) */
 } occri_kernel;
 
 typedef struct {
@@ -113,6 +129,10 @@ typedef struct {
   size_t workspace_bytes;  /* device bytes owned by the plan */
   int fields_per_wave;     /* pair fields transformed per launch group */
   long long launches_per_build;  /* kernels one occri_k_build launches */
+  int contraction_tc;      /* 1: step (e) runs on the tensor cores (OCCRI_MIXED_TC where the
+                              supercell admits it), 0: on the CUDA cores */
+  long long tc_stages;     /* tensor-core contraction: stages per build, each 3 MMAs of
+                              M = 128, N = 256, K = 32 (FP16 hi/lo products), else 0 */
 } occri_plan_info_t;
 
 /* Stages reported by occri_plan_stage_times. */
@@ -300,6 +320,13 @@ int occri_batch_destroy(occri_batch *batch);
 enum { OCCRI_FAULT_NONE = 0, OCCRI_FAULT_WAIT = 1 };
 int occri_plan_inject_fault(occri_plan *plan, int fault, double wait_limit_ms);
 int occri_debug_fail_allocation(int nth);
+
+/* Measured arithmetic peak of the current device (no counterpart in the paper; the
+ * denominator of the roofline fraction of ALU-bound stages): kind 0 = FP64 FMA, 1 = FP32 FMA,
+ * 2 = packed FP32 FMA (fma.rn.f32x2). Eight independent FMA chains per thread on every SM,
+ * the best of three timed runs after one warm-up, CUDA events on the legacy default stream;
+ * *tflops receives 2 x FMAs / time in TFLOP/s. Synchronises the device. */
+int occri_measure_fma_peak(int kind, double *tflops);
 
 const char *occri_status_string(int status);
 

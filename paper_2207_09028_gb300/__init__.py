@@ -27,7 +27,9 @@ OCCRI_EUNSUPPORTED = 6
 
 OCCRI_COULOMB, OCCRI_ERFC, OCCRI_ERF = 0, 1, 2
 OCCRI_FP64, OCCRI_MIXED, OCCRI_MIXED_TC = 0, 1, 2
-KERNELS = {"coulomb": OCCRI_COULOMB, "erfc": OCCRI_ERFC, "erf": OCCRI_ERF}
+OCCRI_COULOMB_TRUNC = 3
+KERNELS = {"coulomb": OCCRI_COULOMB, "erfc": OCCRI_ERFC, "erf": OCCRI_ERF,
+           "coulomb_trunc": OCCRI_COULOMB_TRUNC}
 PRECISIONS = {"fp64": OCCRI_FP64, "mixed": OCCRI_MIXED, "mixed_tc": OCCRI_MIXED_TC}
 
 
@@ -54,7 +56,8 @@ class occri_plan_info_t(ctypes.Structure):
                 ("natm", ctypes.c_int), ("nshell", ctypes.c_int), ("grid", ctypes.c_int * 3),
                 ("ng", ctypes.c_longlong), ("precision", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_size_t), ("fields_per_wave", ctypes.c_int),
-                ("launches_per_build", ctypes.c_longlong)]
+                ("launches_per_build", ctypes.c_longlong), ("contraction_tc", ctypes.c_int),
+                ("tc_stages", ctypes.c_longlong)]
 
 
 EXPORTED = ["occri_plan_create", "occri_plan_destroy", "occri_plan_info", "occri_plan_set_stream",
@@ -62,7 +65,7 @@ EXPORTED = ["occri_plan_create", "occri_plan_destroy", "occri_plan_info", "occri
             "occri_vjp", "occri_plan_set_timing", "occri_plan_stage_times", "occri_orbitals_noalloc",
             "occri_vjp_full", "occri_batch_create", "occri_batch_build", "occri_batch_sync",
             "occri_batch_destroy", "occri_k_build_once", "occri_plan_inject_fault",
-            "occri_debug_fail_allocation",
+            "occri_debug_fail_allocation", "occri_measure_fma_peak",
             "occri_status_string"]
 
 OCCRI_FAULT_NONE, OCCRI_FAULT_WAIT = 0, 1
@@ -111,6 +114,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                        ip, vp, vp, vp]
     lib.occri_plan_inject_fault.argtypes = [vp, ip, ctypes.c_double]
     lib.occri_debug_fail_allocation.argtypes = [ip]
+    lib.occri_measure_fma_peak.argtypes = [ip, dp]
     lib.occri_status_string.argtypes = [ip]
     lib.occri_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -193,6 +197,18 @@ def build_once(lattice, xyz, shell_atom, shell_l, shell_alpha, kfrac, C, nocc: i
     return K, Ex
 
 
+FMA_KINDS = {"fp64": 0, "fp32": 1, "fp32x2": 2}
+
+
+def measure_fma_peak(kind: str) -> float:
+    """occri_measure_fma_peak: the device's measured FMA rate (TFLOP/s) for fp64, fp32 or
+    packed fp32x2."""
+    out = ctypes.c_double(0.0)
+    _check(load_library().occri_measure_fma_peak(FMA_KINDS[kind], ctypes.byref(out)),
+           "occri_measure_fma_peak")
+    return out.value
+
+
 def fail_allocation(nth: int):
     """occri_debug_fail_allocation: the nth device allocation from now fails (test hook)."""
     _check(load_library().occri_debug_fail_allocation(int(nth)), "occri_debug_fail_allocation")
@@ -224,6 +240,7 @@ class Plan:
         self.precision = info.precision
         self.workspace_bytes = info.workspace_bytes
         self.fields_per_wave = info.fields_per_wave
+        self.contraction_tc = bool(info.contraction_tc)
         self.kernel_kind = kern.kind
 
     @classmethod

@@ -99,10 +99,11 @@ PairParams Plan::pair_params() const {
   q.g[3] = dot(0, 1); q.g[4] = dot(0, 2); q.g[5] = dot(1, 2);
   q.kind = kernel.kind;
   q.omega = kernel.omega;
-  q.inv4w2 = (kernel.kind == OCCRI_COULOMB) ? 0.0 : 1.0 / (4.0 * kernel.omega * kernel.omega);
-  // g0 = pi/omega^2 and d g0/d omega = -2 pi/omega^3, both in units of 4 pi
-  q.g0 = (kernel.g0_mode == 1) ? 0.25 / (kernel.omega * kernel.omega) : 0.0;
-  q.dg0 = (kernel.g0_mode == 1) ? -0.5 / (kernel.omega * kernel.omega * kernel.omega) : 0.0;
+  const bool has_w = kernel.kind == OCCRI_ERFC || kernel.kind == OCCRI_ERF;
+  q.inv4w2 = has_w ? 1.0 / (4.0 * kernel.omega * kernel.omega) : 0.0;
+  q.g0 = g0_4pi;
+  q.dg0 = dg0_4pi;
+  q.rc = rc;
   for (int i = 0; i < 6; ++i) {
     q.gh[i] = (float)q.g[i];
     q.gl[i] = (float)(q.g[i] - (double)q.gh[i]);
@@ -220,6 +221,77 @@ void inv3(const double a[3][3], double inv[3][3]) {
   inv[2][0] = (a[1][0] * a[2][1] - a[1][1] * a[2][0]) / det;
   inv[2][1] = (a[0][1] * a[2][0] - a[0][0] * a[2][1]) / det;
   inv[2][2] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) / det;
+}
+
+// Sums over the lattice with rows L (or, with recip, over its reciprocal lattice) of
+// fn(vector) for every nonzero vector, shell by shell (|i|,|j|,|k| <= n with max = n) until a
+// whole shell adds less than 1e-17 (from the third shell on).
+template <typename F>
+double lattice_shell_sum(const double L[3][3], bool recip, F fn) {
+  double v[3][3];
+  if (recip) {
+    double inv[3][3];
+    inv3(L, inv);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) v[i][j] = 2.0 * kPiD * inv[j][i];
+  } else {
+    std::memcpy(v, L, sizeof(v));
+  }
+  double total = 0.0;
+  for (int n = 1; n < 200; ++n) {
+    double shell = 0.0;
+    for (int i = -n; i <= n; ++i)
+      for (int j = -n; j <= n; ++j)
+        for (int k = -n; k <= n; ++k) {
+          if (std::max(std::abs(i), std::max(std::abs(j), std::abs(k))) != n) continue;
+          const double x[3] = {i * v[0][0] + j * v[1][0] + k * v[2][0],
+                               i * v[0][1] + j * v[1][1] + k * v[2][1],
+                               i * v[0][2] + j * v[1][2] + k * v[2][2]};
+          shell += fn(x);
+        }
+    total += shell;
+    if (n > 2 && std::fabs(shell) < 1e-17) break;
+  }
+  return total;
+}
+
+double volume3(const double L[3][3]) {
+  return std::fabs(L[0][0] * (L[1][1] * L[2][2] - L[1][2] * L[2][1]) -
+                   L[0][1] * (L[1][0] * L[2][2] - L[1][2] * L[2][0]) +
+                   L[0][2] * (L[1][0] * L[2][1] - L[1][1] * L[2][0]));
+}
+
+// Ewald potential at a unit point charge from its periodic images in a uniform neutralising
+// background (the lattice's Madelung potential; negative), splitting parameter eta from the
+// cell volume.
+double madelung_potential(const double L[3][3]) {
+  const double vol = volume3(L);
+  const double eta = std::sqrt(kPiD) / std::cbrt(vol);
+  const double real = lattice_shell_sum(L, false, [&](const double* x) {
+    const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    return std::erfc(eta * r) / r;
+  });
+  const double recip = lattice_shell_sum(L, true, [&](const double* g) {
+    const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    return 4.0 * kPiD / vol * std::exp(-g2 / (4.0 * eta * eta)) / g2;
+  });
+  return real + recip - kPiD / (eta * eta * vol) - 2.0 * eta / std::sqrt(kPiD);
+}
+
+// chi of the erf kernel: V 2 w/sqrt(pi) - sum_{G != 0} 4 pi e^{-G^2/(4 w^2)}/G^2 over the
+// supercell's reciprocal lattice, and its omega-derivative in *dchi.
+double erf_lattice_chi(const double L[3][3], double w, double* dchi) {
+  const double vol = volume3(L);
+  const double s = lattice_shell_sum(L, true, [&](const double* g) {
+    const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    return 4.0 * kPiD * std::exp(-g2 / (4.0 * w * w)) / g2;
+  });
+  const double ds = lattice_shell_sum(L, true, [&](const double* g) {
+    const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    return 2.0 * kPiD * std::exp(-g2 / (4.0 * w * w)) / (w * w * w);
+  });
+  *dchi = 2.0 * vol / std::sqrt(kPiD) - ds;
+  return vol * 2.0 * w / std::sqrt(kPiD) - s;
 }
 
 template <typename X>
@@ -711,7 +783,7 @@ int vjp_impl(Plan* p, const double2* C, double gEx, void* gC, double* gomega) {
   if (gC) scale_copy_kernel<<<4 * 152, 256, 0, s>>>(p->kc, (double2*)gC, nkc, gEx * 4.0 / p->nk);
   if (gomega) {
     if (cudaMemsetAsync(p->dacc, 0, 2 * sizeof(double), s) != cudaSuccess) return OCCRI_ECUDA;
-    if (p->kernel.kind != OCCRI_COULOMB) {
+    if (p->kernel.kind == OCCRI_ERFC || p->kernel.kind == OCCRI_ERF) {
       // periodic parts of the orbitals of C (the plan's copy may have been replaced by
       // an occri_orbitals call since the build)
       if (launch_scale_c<T>(*p, C, s) != cudaSuccess) return OCCRI_ECUDA;
@@ -774,7 +846,7 @@ int vjp_full_impl(Plan* p, const double2* C, double gEx, const double2* gKC, con
   // (c)+(d): two round trips per unordered pair, dL/dpsi accumulated (and the omega
   // term of the kernel's derivative, for the erfc and erf kernels)
   if (cudaMemsetAsync(p->gpsi, 0, orb, s) != cudaSuccess) return OCCRI_ECUDA;
-  const bool want_w = gomega && p->kernel.kind != OCCRI_COULOMB;
+  const bool want_w = gomega && (p->kernel.kind == OCCRI_ERFC || p->kernel.kind == OCCRI_ERF);
   if (gomega && cudaMemsetAsync(p->dacc, 0, 2 * sizeof(double), s) != cudaSuccess)
     return OCCRI_ECUDA;
   for (int k = 0; k < p->nk; ++k)
@@ -923,10 +995,14 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
   if (basis->nshell < 1 || !basis->atom || !basis->l || !basis->alpha) return OCCRI_EINVAL;
   if (precision != OCCRI_FP64 && precision != OCCRI_MIXED && precision != OCCRI_MIXED_TC)
     return OCCRI_EINVAL;
-  if (kernel->kind < 0 || kernel->kind > 2) return OCCRI_EINVAL;
-  if (kernel->kind != OCCRI_COULOMB && !(kernel->omega > 0.0)) return OCCRI_EINVAL;
-  if (kernel->g0_mode != 0 && kernel->g0_mode != 1) return OCCRI_EINVAL;
-  if (kernel->g0_mode == 1 && kernel->kind != OCCRI_ERFC) return OCCRI_EINVAL;
+  if (kernel->kind < 0 || kernel->kind > 3) return OCCRI_EINVAL;
+  if ((kernel->kind == OCCRI_ERFC || kernel->kind == OCCRI_ERF) && !(kernel->omega > 0.0))
+    return OCCRI_EINVAL;
+  if (kernel->g0_mode < 0 || kernel->g0_mode > 2) return OCCRI_EINVAL;
+  if (kernel->g0_mode == 1 && kernel->kind != OCCRI_ERFC && kernel->kind != OCCRI_COULOMB_TRUNC)
+    return OCCRI_EINVAL;
+  if (kernel->g0_mode == 2 && kernel->kind != OCCRI_COULOMB && kernel->kind != OCCRI_ERF)
+    return OCCRI_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (grid[d] < 4 || grid[d] > 64 || !smooth235(grid[d])) return OCCRI_EINVAL;
   int nao = 0;
@@ -982,6 +1058,30 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     }
   }
   const int Dc = p->D[0] * p->D[1] * p->D[2];
+
+  // the G+q = 0 value (Eq. VGao's chi) and the truncation radius, from the k-mesh's
+  // supercell D_1 a_1 x D_2 a_2 x D_3 a_3
+  {
+    double sc[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) sc[i][j] = lat[i][j] * p->D[i];
+    const double vsc = std::fabs(det) * Dc;
+    p->rc = std::cbrt(3.0 * vsc / (4.0 * kPiD));
+    const double w = kernel->omega;
+    double g0 = 0.0, dg0 = 0.0;
+    if (kernel->g0_mode == 1 && kernel->kind == OCCRI_ERFC) {
+      g0 = kPiD / (w * w);
+      dg0 = -2.0 * kPiD / (w * w * w);
+    } else if (kernel->g0_mode == 1 && kernel->kind == OCCRI_COULOMB_TRUNC) {
+      g0 = 2.0 * kPiD * p->rc * p->rc;
+    } else if (kernel->g0_mode == 2 && kernel->kind == OCCRI_COULOMB) {
+      g0 = -vsc * madelung_potential(sc);
+    } else if (kernel->g0_mode == 2 && kernel->kind == OCCRI_ERF) {
+      g0 = erf_lattice_chi(sc, w, &dg0);
+    }
+    p->g0_4pi = g0 / (4.0 * kPiD);
+    p->dg0_4pi = dg0 / (4.0 * kPiD);
+  }
 
   // shells, cutoffs, AO offsets
   const double eps = (precision == OCCRI_FP64) ? 1e-16 : 1e-11;
@@ -1297,6 +1397,8 @@ int occri_plan_info(const occri_plan* plan, occri_plan_info_t* info) {
   info->workspace_bytes = p->workspace_bytes;
   info->fields_per_wave = p->fields_cap;
   info->launches_per_build = p->launches_per_build;
+  info->contraction_tc = p->tc ? 1 : 0;
+  info->tc_stages = tc_plan_stages(p->tc);
   return OCCRI_OK;
 }
 

@@ -8,22 +8,27 @@
 //   K_{mu i}(k) = scale sum_l e^{-ik.L_l} P_l[mu, (k,i)],   P_l = sum_r Phi_mu(r - L_l) Y_ik(r).
 // P_l is a real-by-complex GEMM: rows mu (128 AOs per tile, sorted by screening radius so that
 // tight AOs share tiles), columns the (Re, Im) of 128 (k, i) pairs (N = 256), reduction over the
-// cell's grid points, 32 per stage. Its A operand Phi (real, generated on the fly from the
-// Gaussians, never stored) and its B operand (Y converted once per build to FP16 hi/lo pairs
-// in the tensor cores' shared-memory layout) are split hi + lo, and three FP16 MMAs
-// (hi.hi + hi.lo + lo.hi) with FP32 accumulation give FP32-level products. The sum over l
-// with the phases e^{-ik.L_l} is applied to each P_l in tensor memory by the epilogue warps
-// (acc -> running sum), and the running sums go to K_{mu i} by FP64 atomics. Stages where no
-// AO of the tile reaches the points (r - L_l) are skipped: tight AOs are sparse here.
+// cell's grid points. A stage is one tile of 32 grid points r at one offset l: A = Phi at the
+// points r - L_l, B = Y at the points r. Both operands are split hi + lo in FP16 (power-of-two
+// scalings per row and column), and three FP16 MMAs (hi.hi + hi.lo + lo.hi) with FP32
+// accumulation give FP32-level products. Stages where no AO of the tile reaches r - L_l are
+// skipped: tight AOs are sparse here.
 //
-// Warp roles (one CTA per SM, persistent over a host-made list of work chunks):
-//   warp 0      TMEM allocation; lane 0 issues the MMAs and commits them to mbarriers
-//   warp 1      lane 0 copies each stage's B block (32 KB) with the bulk-copy engine
-//   warps 2-9   generate the A tile of each stage (FP16 hi/lo) into shared memory
-//   warps 10-13 epilogue: P_l from tensor memory, phases, running sums, FP64 atomics
+// Kernels of one contraction:
+//   colmax_kernel, convert_y_kernel  Y -> FP16 hi/lo B blocks (tensor-core layout), once
+//   gen_blocks_kernel               the A blocks of a slab of stages (Phi generated from the
+//                                   Gaussians; each block serves every column tile)
+//   contract_tc_kernel              the GEMM over the slab's stages: one producer thread copies
+//                                   each stage's A and B blocks with the bulk-copy engine, one
+//                                   thread issues the MMAs into one of two tensor-memory
+//                                   accumulators, and 16 epilogue warps take every stage's
+//                                   product out at once (times the phases e^{-ik.L_l}) into
+//                                   FP32 running sums held in registers, which go to K_{mu i}
+//                                   by FP64 atomics. Each product leaves tensor memory after
+//                                   one stage because the tensor cores' FP32 accumulation was
+//                                   measured to bias long sums by ~1e-6 relative.
 // Every mbarrier wait is bounded by the plan's wait limit; on timeout the kernel records
-// OCCRI_ETIMEOUT and the CTA leaves (each role stops issuing; no copy is left in flight
-// unless its own wait failed).
+// OCCRI_ETIMEOUT, each role stops issuing and no copy is left in flight.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -45,23 +50,25 @@ constexpr int kNC = 128;            // complex (k, i) columns per tile
 constexpr int kN = 2 * kNC;         // real columns (Re, Im)
 constexpr int kKP = 32;             // grid points per stage (MMA K, two slices of 16)
 constexpr int kStages = 4;
-constexpr int kChunkTiles = 16;     // point tiles per work chunk (its B blocks stay in L2)
-constexpr int kFlushChunks = 8;     // chunks summed in FP32 before the FP64 atomics
-constexpr int kMaxImg = 512;        // supercell images of one stage, all atoms
-constexpr int kAWarps = 8, kEWarps = 4;
-constexpr int kThreads = 32 * (2 + kAWarps + kEWarps);
+constexpr int kFlushTiles = 16;     // point tiles summed in FP32 before the FP64 atomics
+constexpr int kSlabBlocks = 1 << 18;     // A blocks generated at a time (4 GiB)
+constexpr int kMaxImg = 128;        // supercell images of one stage, all atoms
+constexpr int kEWarps = 16;         // epilogue: four per lane quarter, 32 complex columns each
+constexpr int kEThreads = 32 * kEWarps;
+constexpr int kThreads = 64 + kEThreads;     // + MMA warp and bulk-copy warp
+constexpr int kGenThreads = 256;             // threads of the block-generation kernel
 constexpr int kASlice = kM * 16 * 2;          // bytes of one K slice of A (hi or lo)
 constexpr int kBSlice = kN * 16 * 2;          // bytes of one K slice of B
 constexpr int kABytes = 2 * kASlice;          // A hi (or lo) of a stage
 constexpr int kBBytes = 2 * kBSlice;          // B hi (or lo) of a stage
+constexpr int kABlock = 2 * kABytes;          // one generated A block (hi then lo): 16 KB
 constexpr int kBBlock = 2 * kBBytes;          // one converted Y block (hi then lo): 32 KB
-constexpr int kStageBytes = 2 * kABytes + kBBlock;
+constexpr int kStageBytes = kABlock + kBBlock;
 constexpr uint32_t kIdesc = tc::idesc_f16_f32(kM, kN);
 // Descriptor strides of the no-swizzle K-major layout used below: inside one 16-wide K slice,
 // an 8-row group holds its two 8-column core matrices at +0 and +128 bytes and groups follow
 // every 256 bytes.
 constexpr uint32_t kLBO = 128, kSBO = 256;
-constexpr float kScaleTarget = 8192.f;        // operands scaled to |x| < 2^13 (FP16 max 65504)
 
 // byte offset of element (row, k) inside one operand of a stage (slices of 16 along K)
 __host__ __device__ constexpr int op_off(int row, int k, int slice_bytes) {
@@ -71,37 +78,45 @@ __host__ __device__ constexpr int op_off(int row, int k, int slice_bytes) {
 
 struct TcShell {        // the rows of one shell inside a tile
   float alpha, alpha_lo, rcut2;
-  int atom, l, row0, m0, nm;
+  int atom, l, row0, m0, nm, exact;   // exact: Gaussian argument in double-float
 };
 
+constexpr int kMaxTiles = 4;             // AO tiles of a plan (nao <= 512)
+constexpr int kMaxEntries = 192;         // shell entries of all tiles
+
+// A stage of the GEMM: x = A slot in the slab | l << 22; y = point tile | column tile << 16
+// | flags << 24 | AO tile << 26 (kFirstSum: the running sums start here; kToGlobal: they go
+// to K_{mu i} after this stage).
+enum { kFirstSum = 1, kToGlobal = 2 };
+
 struct TcParams {
-  int nk, nao, nocc, natm, N, ncol, n_ct, ntile_r, nl, nwords;
+  int nk, nao, nocc, natm, N, ncol, n_ct, ntile_r, nl, ntile, nentries;
   int D[3], w[3];
   long long ng;
   const unsigned char* yh;       // converted Y blocks [ct][rt][32 KB]
-  const TcShell* shells;
-  const int* tile_shell0;        // shells of tile t: [tile_shell0[t], tile_shell0[t+1])
+  unsigned char* ablk;           // generated A blocks of the current slab [slot][16 KB]
+  const uint2* blocks;           // the slab's A blocks: (rt | l << 16, tile)
+  int nblocks;
+  const TcShell* shells;         // entries of all tiles, tile by tile
+  const int* tile_shell0;        // entries of tile t: [tile_shell0[t], tile_shell0[t+1])
   const float* rowscale;         // [tile*128 + row]
   const double* rowf;            // N_mu / rowscale, 0 on pad rows
   const int* perm;               // tile row -> AO (or -1)
   const float* reach;            // [tile][natm] largest screening radius of the tile's shells
   const float4* rtiles;          // [ntile_r] centre (x, y, z) and radius of the point tile
-  const unsigned* active;        // [tile][ntile_r][nwords] bit l: the tile reaches r - L_l
-  const int4* chunks;            // (tile, ct, offset into chunk_rt, count | flags << 8)
-  const int* chunk_rt;           // point tiles of each chunk
-  const int* cta_chunk0;         // chunks of CTA b: [cta_chunk0[b], cta_chunk0[b+1])
-  const int* kint;               // [nk][3]
+  const float2* phase;           // [ct][nl][128] e^{-ik.L_l} of the tile's columns (0 past ncol)
+  const uint2* stages;           // the slab's stages, CTA by CTA
+  const long long* cta_stage0;   // stages of CTA b: [cta_stage0[b], cta_stage0[b+1])
   const unsigned* colmax;        // [ncol] max over r of |Re Y| + |Im Y| (float bits)
   double2* kc;
   double scale;
   float lat[9], sc[9], scinv[9]; // rows a_d; supercell rows D_d a_d; cart -> supercell frac
-  int aint[kMaxTcAtoms][3];
-  float arem_hi[kMaxTcAtoms][3], arem_lo[kMaxTcAtoms][3], axyz[kMaxTcAtoms][3];
+  float sclo[9];                 // supercell rows, the remainder sc - (double) sc_f
+  const float* pts;              // [ng][6] grid point r_q: x, y, z (hi), x, y, z (lo)
+  const float* tbase;            // [natm][nl][6] L_l + A_a (hi, lo)
   int* status;
   long long wait_ns;
 };
-
-enum { kFirstSum = 1 << 8, kToGlobal = 1 << 9 };
 
 __device__ __forceinline__ void fail(int* status) {
   if (status && atomicCAS(status, 0, (int)OCCRI_ETIMEOUT) == 0) status[1] = -1;
@@ -132,144 +147,130 @@ __device__ __forceinline__ void solid_h(float x, float y, float z, float (&P)[2 
   }
 }
 
-struct Img { int atom, s0, s1, s2; };
+// One supercell image of one atom for a block: T = L_l + S + A_atom (cartesian, hi + lo).
+struct Img { float th[3], tl[3]; };
 
-struct __align__(16) Smem {
-  unsigned long long full_a[kStages], full_b[kStages], empty[kStages], acc_full, acc_empty, done;
-  uint32_t tmem_slot;
-  int a_ok[2], e_ok;
-  int nimg[2];
-  int img_off[2][kMaxTcAtoms + 1];
-  Img img[2][kMaxImg];
-  float2 phase[kNC];
-  double colinv[kNC];
+// The tables of one A block: its grid points and the supercell images in reach.
+struct StageTab {
+  int ok;                          // 0: the images did not fit
+  int img_off[kMaxTcAtoms + 1];    // images of atom a: [img_off[a], img_off[a+1])
+  float pts[kKP][6];               // the block's grid points r (x, y, z hi; x, y, z lo)
+  Img img[kMaxImg];
 };
 
-// ---- the iteration every role walks identically: chunks -> l groups -> stages
-struct Walk {
-  const unsigned* active;
-  const int* chunk_rt;
-  int ntile_r, nwords, c0, c1;
-  __device__ __forceinline__ const unsigned* act(int tile, int rt) const {
-    return active + ((size_t)tile * ntile_r + rt) * nwords;
-  }
-  __device__ __forceinline__ bool on(int tile, int rt, int l) const {
-    return (act(tile, rt)[l >> 5] >> (l & 31)) & 1u;
-  }
-  // union over the chunk's point tiles of the active l bits, word w
-  __device__ __forceinline__ unsigned lmask(const int4& ch, int w) const {
-    unsigned m = 0;
-    const int n = ch.w & 255;
-    for (int j = 0; j < n; ++j) m |= act(ch.x, chunk_rt[ch.z + j])[w];
-    return m;
-  }
-};
+// FP16 hi/lo split of two values, packed as two 32-bit words (x0 in the low half)
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const float2 back = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x0 - back.x, x1 - back.y);
+  memcpy(&hi, &h, 4);
+  memcpy(&lo, &l, 4);
+}
 
-// A tile of one stage: rows of the tile's shells at points q0 .. q0+31 shifted by -L_l.
-__device__ __forceinline__ void gen_a(const TcParams& p, const Smem& sm, int ib, int tile,
-                                      int rt, const int l3[3], unsigned char* a_hi,
-                                      unsigned char* a_lo, int t) {
-  const int s0 = p.tile_shell0[tile], s1 = p.tile_shell0[tile + 1];
-  const int items = (s1 - s0) * 4;
-  const int N = p.N;
-  const float invN = 1.f / (float)N;
-  for (int it = t; it < items; it += 32 * kAWarps) {
-    const int e = s0 + (it >> 2), g = it & 3;
-    const TcShell sh = p.shells[e];
-    float v[7][8];
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// The rows of one shell entry (angular momentum L) at 4 points of the block.
+template <int L>
+__device__ __forceinline__ void gen_item(const StageTab& tb, const TcShell& sh, int g,
+                                         const float* rowscale, unsigned char* a_hi,
+                                         unsigned char* a_lo) {
+  constexpr int NM = 2 * L + 1;
+  float v[NM][4];
 #pragma unroll
-    for (int m = 0; m < 7; ++m)
+  for (int m = 0; m < NM; ++m)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[m][j] = 0.f;
-    int n[8][3];
-    bool ok[8];
+    for (int j = 0; j < 4; ++j) v[m][j] = 0.f;
+  const int i0 = tb.img_off[sh.atom], i1 = tb.img_off[sh.atom + 1];
+  for (int im = i0; im < i1; ++im) {
+    const Img T = tb.img[im];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const long long q = (long long)rt * kKP + g * 8 + j;
-      ok[j] = q < p.ng;
-      const int qq = ok[j] ? (int)q : 0;
-      n[j][1] = qq % N;                 // n2 (fields' order q = (n3 N + n1) N + n2)
-      const int tq = qq / N;
-      n[j][0] = tq % N;                 // n1
-      n[j][2] = tq / N;                 // n3
-    }
-    const int a = sh.atom;
-    const int i0 = sm.img_off[ib][a], i1 = sm.img_off[ib][a + 1];
-    for (int im = i0; im < i1; ++im) {
-      const Img S = sm.img[ib][im];
-      const int sd[3] = {S.s0, S.s1, S.s2};
-      int base[3];
+    for (int j = 0; j < 4; ++j) {
+      const float* r = tb.pts[g * 4 + j];
+      float c[3], cl[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) base[d] = N * (l3[d] + sd[d] * p.D[d]) + p.aint[a][d];
+      for (int d = 0; d < 3; ++d) {
+        // r - T as an unevaluated hi + lo sum: exact difference of the hi parts near the atom
+        float se, ee;
+        two_sum_f(r[d], -T.th[d], se, ee);
+        c[d] = se;
+        cl[d] = ee + (r[3 + d] - T.tl[d]);
+      }
+      const float x = c[0] + cl[0], y = c[1] + cl[1], z = c[2] + cl[2];
+      float r2, ex;
+      if (sh.exact) {
+        // r^2 and alpha r^2 as hi + lo pairs (FMA two-products), e^{-a} = e^{-ah} (1 - al)
+        float ph[3], pl[3];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float gf[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-          gf[d] = (((float)(n[j][d] - base[d]) - p.arem_hi[a][d]) - p.arem_lo[a][d]) * invN;
-        const float x = gf[0] * p.lat[0] + gf[1] * p.lat[3] + gf[2] * p.lat[6];
-        const float y = gf[0] * p.lat[1] + gf[1] * p.lat[4] + gf[2] * p.lat[7];
-        const float z = gf[0] * p.lat[2] + gf[1] * p.lat[5] + gf[2] * p.lat[8];
-        const float r2 = x * x + y * y + z * z;
-        if (!ok[j] || r2 > sh.rcut2) continue;
-        const float ex = expf(-(sh.alpha * r2 + sh.alpha_lo * r2));
-        switch (sh.l) {
-          case 0: v[0][j] += ex; break;
-          case 1: {
-            float P[3]; solid_h<1>(x, y, z, P);
-#pragma unroll
-            for (int m = 0; m < 3; ++m) v[m][j] += P[m] * ex;
-          } break;
-          case 2: {
-            float P[5]; solid_h<2>(x, y, z, P);
-#pragma unroll
-            for (int m = 0; m < 5; ++m) v[m][j] += P[m] * ex;
-          } break;
-          default: {
-            float P[7]; solid_h<3>(x, y, z, P);
-#pragma unroll
-            for (int m = 0; m < 7; ++m) v[m][j] += P[m] * ex;
-          } break;
+        for (int d = 0; d < 3; ++d) {
+          ph[d] = c[d] * c[d];
+          pl[d] = fmaf(c[d], c[d], -ph[d]) + 2.f * c[d] * cl[d];
         }
+        float s1, e1, s2, e2;
+        two_sum_f(ph[0], ph[1], s1, e1);
+        two_sum_f(s1, ph[2], s2, e2);
+        const float rl = (e1 + e2) + (pl[0] + pl[1] + pl[2]);
+        r2 = s2;
+        const float ah = sh.alpha * s2;
+        const float al = fmaf(sh.alpha, s2, -ah) + sh.alpha * rl + sh.alpha_lo * s2;
+        ex = expf(-ah) * (1.f - al);
+      } else {
+        r2 = x * x + y * y + z * z;
+        ex = expf(-(sh.alpha * r2 + sh.alpha_lo * r2));
       }
-    }
-    // rows row0 .. row0 + nm - 1 hold m = m0 .. m0 + nm - 1
-    for (int r = 0; r < sh.nm; ++r) {
-      const int row = sh.row0 + r;
-      const float s = p.rowscale[tile * kM + row];
-      __align__(16) __half hi[8], lo[8];
+      // points past the grid carry a NaN coordinate and fail the test, like those out of reach
+      if (!(r2 <= sh.rcut2)) ex = 0.f;
+      float P[NM];
+      solid_h<L>(x, y, z, P);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float x = 0.f;
-#pragma unroll
-        for (int m = 0; m < 7; ++m)
-          if (m == sh.m0 + r) x = v[m][j];
-        x *= s;
-        hi[j] = __float2half_rn(x);
-        lo[j] = __float2half_rn(x - __half2float(hi[j]));
-      }
-      const int off = op_off(row, g * 8, kASlice);
-      *reinterpret_cast<uint4*>(a_hi + off) = *reinterpret_cast<const uint4*>(hi);
-      *reinterpret_cast<uint4*>(a_lo + off) = *reinterpret_cast<const uint4*>(lo);
+      for (int m = 0; m < NM; ++m) v[m][j] += (ex != 0.f) ? P[m] * ex : 0.f;
     }
+  }
+  // rows row0 .. row0 + nm - 1 hold m = m0 .. m0 + nm - 1
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    if (m < sh.m0 || m >= sh.m0 + sh.nm) continue;
+    const int row = sh.row0 + (m - sh.m0);
+    const float sc = rowscale[row];
+    uint2 hi, lo;
+    split2(v[m][0] * sc, v[m][1] * sc, hi.x, lo.x);
+    split2(v[m][2] * sc, v[m][3] * sc, hi.y, lo.y);
+    const int off = op_off(row, g * 4, kASlice);
+    *reinterpret_cast<uint2*>(a_hi + off) = hi;
+    *reinterpret_cast<uint2*>(a_lo + off) = lo;
   }
 }
 
-// Images S of the supercell lattice (per atom) within reach of the point tile shifted by -L_l.
-__device__ __forceinline__ bool find_images(const TcParams& p, Smem& sm, int ib, int tile,
-                                            int rt, const int l3[3], int lane) {
+// The block's table of grid points (hi/lo; NaN past the grid) and, per atom, the images
+// T = L_l + A + S of the supercell lattice within reach of the point tile (hi + lo, from the
+// plan's table of L_l + A and error-free products S_d x (supercell row d)). One warp.
+// tb.ok = 0 if the images do not fit the table.
+__device__ __forceinline__ void block_tables(const TcParams& p, StageTab& tb, int tile, int rt,
+                                             int l, int lane) {
   const float4 c = p.rtiles[rt];
-  const float lx = l3[0] * p.lat[0] + l3[1] * p.lat[3] + l3[2] * p.lat[6];
-  const float ly = l3[0] * p.lat[1] + l3[1] * p.lat[4] + l3[2] * p.lat[7];
-  const float lz = l3[0] * p.lat[2] + l3[1] * p.lat[5] + l3[2] * p.lat[8];
+  {
+    const long long q = (long long)rt * kKP + lane;
+    float* o = tb.pts[lane];
+    if (q < p.ng) {
+      const float2* src = reinterpret_cast<const float2*>(p.pts + 6 * (size_t)q);
+      const float2 a0 = src[0], a1 = src[1], a2 = src[2];
+      o[0] = a0.x; o[1] = a0.y; o[2] = a1.x; o[3] = a1.y; o[4] = a2.x; o[5] = a2.y;
+    } else {
+#pragma unroll
+      for (int d = 0; d < 6; ++d) o[d] = __int_as_float(0x7fc00000);
+    }
+  }
   const int W0 = 2 * p.w[0] + 1, W1 = 2 * p.w[1] + 1, W2 = 2 * p.w[2] + 1;
   const int ncand = W0 * W1 * W2;
   int count = 0;
   bool ok = true;
   for (int a = 0; a < p.natm; ++a) {
-    if (lane == 0) sm.img_off[ib][a] = count;
-    const float vx = c.x - lx - p.axyz[a][0], vy = c.y - ly - p.axyz[a][1],
-                vz = c.z - lz - p.axyz[a][2];
+    if (lane == 0) tb.img_off[a] = count;
+    const float* base = p.tbase + ((size_t)a * p.nl + l) * 6;
+    const float vx = c.x - base[0], vy = c.y - base[1], vz = c.z - base[2];
     int s0[3];
     const float u[3] = {vx * p.scinv[0] + vy * p.scinv[3] + vz * p.scinv[6],
                         vx * p.scinv[1] + vy * p.scinv[4] + vz * p.scinv[7],
@@ -280,31 +281,121 @@ __device__ __forceinline__ bool find_images(const TcParams& p, Smem& sm, int ib,
     for (int cb = 0; cb < ncand; cb += 32) {
       const int ci = cb + lane;
       bool in = false;
-      int s[3] = {0, 0, 0};
+      int sv[3] = {0, 0, 0};
       if (ci < ncand) {
-        s[0] = s0[0] + ci / (W1 * W2) - p.w[0];
-        s[1] = s0[1] + (ci / W2) % W1 - p.w[1];
-        s[2] = s0[2] + ci % W2 - p.w[2];
-        const float dx = vx - (s[0] * p.sc[0] + s[1] * p.sc[3] + s[2] * p.sc[6]);
-        const float dy = vy - (s[0] * p.sc[1] + s[1] * p.sc[4] + s[2] * p.sc[7]);
-        const float dz = vz - (s[0] * p.sc[2] + s[1] * p.sc[5] + s[2] * p.sc[8]);
+        sv[0] = s0[0] + ci / (W1 * W2) - p.w[0];
+        sv[1] = s0[1] + (ci / W2) % W1 - p.w[1];
+        sv[2] = s0[2] + ci % W2 - p.w[2];
+        const float dx = vx - (sv[0] * p.sc[0] + sv[1] * p.sc[3] + sv[2] * p.sc[6]);
+        const float dy = vy - (sv[0] * p.sc[1] + sv[1] * p.sc[4] + sv[2] * p.sc[7]);
+        const float dz = vz - (sv[0] * p.sc[2] + sv[1] * p.sc[5] + sv[2] * p.sc[8]);
         in = dx * dx + dy * dy + dz * dz <= lim * lim;
       }
       const unsigned bal = __ballot_sync(0xffffffffu, in);
       const int pos = count + __popc(bal & ((1u << lane) - 1u));
       if (in) {
-        if (pos < kMaxImg) sm.img[ib][pos] = Img{a, s[0], s[1], s[2]};
-        else ok = false;
+        if (pos < kMaxImg) {
+          Img& T = tb.img[pos];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            float th = base[d], tl = base[3 + d];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+              const float sf = (float)sv[e];
+              const float pr = sf * p.sc[3 * e + d];
+              const float pe = fmaf(sf, p.sc[3 * e + d], -pr);   // exact product remainder
+              float ss, se;
+              two_sum_f(th, pr, ss, se);
+              th = ss;
+              tl += se + pe + sf * p.sclo[3 * e + d];
+            }
+            float hh, ll;
+            two_sum_f(th, tl, hh, ll);
+            T.th[d] = hh;
+            T.tl[d] = ll;
+          }
+        } else {
+          ok = false;
+        }
       }
       count += __popc(bal);
     }
   }
   if (count > kMaxImg) count = kMaxImg;
+  ok = __all_sync(0xffffffffu, ok);
   if (lane == 0) {
-    sm.img_off[ib][p.natm] = count;
-    sm.nimg[ib] = count;
+    tb.img_off[p.natm] = count;
+    tb.ok = ok ? 1 : 0;
   }
-  return __all_sync(0xffffffffu, ok);
+}
+
+// The A blocks of the slab: block b (tile, rt, l) holds Phi of the tile's 128 AO rows at the
+// 32 points r - L_l of point tile rt, FP16 hi then lo, in the tensor cores' layout. One CTA
+// per block at a time; warp 0 builds the tables, every thread generates (shell entry, four
+// points) items into shared memory, and the block is stored with 16-byte coalesced stores.
+__global__ void __launch_bounds__(kGenThreads) gen_blocks_kernel(TcParams p) {
+  __shared__ __align__(16) unsigned char a[kABlock];
+  __shared__ StageTab tb;
+  __shared__ TcShell shells[kMaxEntries];
+  __shared__ int tile_shell0[kMaxTiles + 1];
+  __shared__ float rowscale[kMaxTiles * kM];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  for (int e = t; e < p.nentries; e += kGenThreads) shells[e] = p.shells[e];
+  for (int e = t; e <= p.ntile; e += kGenThreads) tile_shell0[e] = p.tile_shell0[e];
+  for (int e = t; e < p.ntile * kM; e += kGenThreads) rowscale[e] = p.rowscale[e];
+  for (int b = blockIdx.x; b < p.nblocks; b += gridDim.x) {
+    const uint2 e = p.blocks[b];
+    const int rt = (int)(e.x & 0xffffu), l = (int)(e.x >> 16), tile = (int)e.y;
+    __syncthreads();   // the previous block is stored (and the tables are free)
+    for (int o = t; o < kABlock / 16; o += kGenThreads)
+      reinterpret_cast<uint4*>(a)[o] = make_uint4(0, 0, 0, 0);
+    if (warp == 0) block_tables(p, tb, tile, rt, l, lane);
+    __syncthreads();
+    if (!tb.ok) {
+      if (t == 0) fail(p.status);
+      continue;
+    }
+    const int s0 = tile_shell0[tile], s1 = tile_shell0[tile + 1];
+    const int items = (s1 - s0) * 8;
+    for (int it = t; it < items; it += kGenThreads) {
+      const TcShell& sh = shells[s0 + (it >> 3)];
+      const int g = it & 7;
+      const float* rs = rowscale + tile * kM;
+      switch (sh.l) {
+        case 0: gen_item<0>(tb, sh, g, rs, a, a + kABytes); break;
+        case 1: gen_item<1>(tb, sh, g, rs, a, a + kABytes); break;
+        case 2: gen_item<2>(tb, sh, g, rs, a, a + kABytes); break;
+        default: gen_item<3>(tb, sh, g, rs, a, a + kABytes); break;
+      }
+    }
+    __syncthreads();
+    uint4* dst = reinterpret_cast<uint4*>(p.ablk + (size_t)b * kABlock);
+    for (int o = t; o < kABlock / 16; o += kGenThreads) dst[o] = reinterpret_cast<const uint4*>(a)[o];
+  }
+}
+
+struct __align__(16) Smem {
+  unsigned long long full[kStages], empty[kStages], acc_full[2], acc_empty[2], done;
+  uint32_t tmem_slot;
+};
+
+static_assert(kStages * kStageBytes + sizeof(Smem) <= 227 * 1024, "shared memory of one CTA");
+
+__device__ __forceinline__ int st_ablk(uint2 e) { return (int)(e.x & 0x3fffffu); }
+__device__ __forceinline__ int st_l(uint2 e) { return (int)(e.x >> 22); }
+__device__ __forceinline__ int st_rt(uint2 e) { return (int)(e.y & 0xffffu); }
+__device__ __forceinline__ int st_ct(uint2 e) { return (int)((e.y >> 16) & 0xffu); }
+__device__ __forceinline__ int st_flags(uint2 e) { return (int)((e.y >> 24) & 3u); }
+
+// One lane of the warp waits (bounded) for the mbarrier phase, the warp follows its verdict,
+// and the other lanes then observe the completed phase themselves (acquire).
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long long limit_ns,
+                                          int lane) {
+  int ok = 1;
+  if (lane == 0) ok = tc::mbar_wait(bar, parity, limit_ns) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (ok && lane != 0) tc::mbar_try_wait(bar, parity);
+  return ok != 0;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
@@ -312,87 +403,62 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
   unsigned char* stage0 = smraw;   // kStages x (A hi | A lo | B hi | B lo)
   Smem& sm = *reinterpret_cast<Smem*>(smraw + kStages * kStageBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const Walk walk{p.active, p.chunk_rt, p.ntile_r, p.nwords, p.cta_chunk0[blockIdx.x],
-                  p.cta_chunk0[blockIdx.x + 1]};
+  const long long s_begin = p.cta_stage0[blockIdx.x];
+  const long long nst = p.cta_stage0[blockIdx.x + 1] - s_begin;
+  const uint2* stages = p.stages + s_begin;
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      tc::mbar_init(tc::smem_u32(&sm.full_a[s]), 32 * kAWarps);
-      tc::mbar_init(tc::smem_u32(&sm.full_b[s]), 1);
+      tc::mbar_init(tc::smem_u32(&sm.full[s]), 1);
       tc::mbar_init(tc::smem_u32(&sm.empty[s]), 1);
     }
-    tc::mbar_init(tc::smem_u32(&sm.acc_full), 1);
-    tc::mbar_init(tc::smem_u32(&sm.acc_empty), 32 * kEWarps);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(tc::smem_u32(&sm.acc_full[b]), 1);
+      tc::mbar_init(tc::smem_u32(&sm.acc_empty[b]), kEThreads);
+    }
     tc::mbar_init(tc::smem_u32(&sm.done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  // pad rows of A are never written by the generators: zero every stage's A once
-  for (int e = tid; e < kStages * 2 * kABytes / 16; e += kThreads) {
-    const int s = e / (2 * kABytes / 16), o = e % (2 * kABytes / 16);
-    reinterpret_cast<uint4*>(stage0 + (size_t)s * kStageBytes)[o] = make_uint4(0, 0, 0, 0);
-  }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(&sm.tmem_slot), 512);
-  tc::fence_proxy_async_smem();
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tmem = sm.tmem_slot;
-  const uint32_t t_acc = tmem, t_sum = tmem + kN;   // columns [0, 256) and [256, 512)
+  const uint32_t tmem = sm.tmem_slot;   // accumulators: columns [0, 256) and [256, 512)
 
   if (warp == 0) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      long long sidx = 0, group = 0;
       bool good = true;
-      for (int ci = walk.c0; ci < walk.c1 && good; ++ci) {
-        const int4 ch = p.chunks[ci];
-        const int nrt = ch.w & 255;
-        for (int w = 0; w < p.nwords && good; ++w) {
-          unsigned lm = walk.lmask(ch, w);
-          while (lm && good) {
-            const int l = w * 32 + __ffs(lm) - 1;
-            lm &= lm - 1;
-            // the epilogue has read the previous group's P_l
-            if (group > 0 &&
-                !tc::mbar_wait(tc::smem_u32(&sm.acc_empty), (unsigned)((group - 1) & 1),
-                               p.wait_ns)) {
-              good = false;
-              break;
-            }
-            bool first = true;
-            for (int j = 0; j < nrt; ++j) {
-              const int rt = p.chunk_rt[ch.z + j];
-              if (!walk.on(ch.x, rt, l)) continue;
-              const int s = (int)(sidx % kStages);
-              const long long u = sidx / kStages;
-              if (!tc::mbar_wait(tc::smem_u32(&sm.full_a[s]), (unsigned)(u & 1), p.wait_ns) ||
-                  !tc::mbar_wait(tc::smem_u32(&sm.full_b[s]), (unsigned)(u & 1), p.wait_ns)) {
-                good = false;
-                break;
-              }
-              tc::tc_fence_after();
-              unsigned char* st = stage0 + (size_t)s * kStageBytes;
-              const uint32_t a_hi = tc::smem_u32(st), a_lo = a_hi + kABytes;
-              const uint32_t b_hi = a_hi + 2 * kABytes, b_lo = b_hi + kBBytes;
-#pragma unroll
-              for (int k = 0; k < 2; ++k) {
-                const uint64_t ah = tc::smem_desc(a_hi + k * kASlice, kLBO, kSBO);
-                const uint64_t al = tc::smem_desc(a_lo + k * kASlice, kLBO, kSBO);
-                const uint64_t bh = tc::smem_desc(b_hi + k * kBSlice, kLBO, kSBO);
-                const uint64_t bl = tc::smem_desc(b_lo + k * kBSlice, kLBO, kSBO);
-                tc::mma_f16(t_acc, ah, bh, kIdesc, (first && k == 0) ? 0u : 1u);
-                tc::mma_f16(t_acc, ah, bl, kIdesc, 1u);
-                tc::mma_f16(t_acc, al, bh, kIdesc, 1u);
-              }
-              first = false;
-              tc::mma_commit(tc::smem_u32(&sm.empty[s]));
-              ++sidx;
-            }
-            if (!good) break;
-            tc::mma_commit(tc::smem_u32(&sm.acc_full));   // P_l complete
-            ++group;
-          }
+      for (long long sidx = 0; sidx < nst && good; ++sidx) {
+        const int s = (int)(sidx % kStages);
+        const long long u = sidx / kStages;
+        const int ab = (int)(sidx & 1);
+        // the epilogue has taken the product of stage sidx - 2 out of this accumulator
+        if (sidx >= 2 && !tc::mbar_wait(tc::smem_u32(&sm.acc_empty[ab]),
+                                        (unsigned)(((sidx >> 1) - 1) & 1), p.wait_ns)) {
+          good = false;
+          break;
         }
+        if (!tc::mbar_wait(tc::smem_u32(&sm.full[s]), (unsigned)(u & 1), p.wait_ns)) {
+          good = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t a_hi = tc::smem_u32(stage0 + (size_t)s * kStageBytes);
+        const uint32_t a_lo = a_hi + kABytes, b_hi = a_hi + kABlock, b_lo = b_hi + kBBytes;
+        const uint32_t t_acc = tmem + (uint32_t)(ab * kN);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const uint64_t ah = tc::smem_desc(a_hi + k * kASlice, kLBO, kSBO);
+          const uint64_t al = tc::smem_desc(a_lo + k * kASlice, kLBO, kSBO);
+          const uint64_t bh = tc::smem_desc(b_hi + k * kBSlice, kLBO, kSBO);
+          const uint64_t bl = tc::smem_desc(b_lo + k * kBSlice, kLBO, kSBO);
+          tc::mma_f16(t_acc, ah, bh, kIdesc, k == 0 ? 0u : 1u);
+          tc::mma_f16(t_acc, ah, bl, kIdesc, 1u);
+          tc::mma_f16(t_acc, al, bh, kIdesc, 1u);
+        }
+        tc::mma_commit(tc::smem_u32(&sm.empty[s]));
+        tc::mma_commit(tc::smem_u32(&sm.acc_full[ab]));
       }
       if (!good) fail(p.status);
       // every MMA issued has completed before the tensor memory is released
@@ -401,207 +467,100 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
     }
     __syncwarp();
   } else if (warp == 1) {
-    // ------------------------------------------------------------ B producer
+    // ------------------------------------------------------------ bulk copies of A and B
     if (lane == 0) {
-      long long sidx = 0;
       bool good = true;
-      for (int ci = walk.c0; ci < walk.c1 && good; ++ci) {
-        const int4 ch = p.chunks[ci];
-        const int nrt = ch.w & 255;
-        for (int w = 0; w < p.nwords && good; ++w) {
-          unsigned lm = walk.lmask(ch, w);
-          while (lm && good) {
-            const int l = w * 32 + __ffs(lm) - 1;
-            lm &= lm - 1;
-            for (int j = 0; j < nrt; ++j) {
-              const int rt = p.chunk_rt[ch.z + j];
-              if (!walk.on(ch.x, rt, l)) continue;
-              const int s = (int)(sidx % kStages);
-              const long long u = sidx / kStages;
-              if (u > 0 && !tc::mbar_wait(tc::smem_u32(&sm.empty[s]), (unsigned)((u - 1) & 1),
-                                          p.wait_ns)) {
-                good = false;
-                break;
-              }
-              const uint32_t fb = tc::smem_u32(&sm.full_b[s]);
-              tc::mbar_expect_tx(fb, kBBlock);
-              const unsigned char* src = p.yh + ((size_t)ch.y * p.ntile_r + rt) * kBBlock;
-              unsigned char* dst = stage0 + (size_t)s * kStageBytes + 2 * kABytes;
-              tc::bulk_g2s(tc::smem_u32(dst), src, kBBlock, fb);
-              ++sidx;
-            }
-          }
+      long long sidx = 0;
+      for (; sidx < nst; ++sidx) {
+        const int s = (int)(sidx % kStages);
+        const long long u = sidx / kStages;
+        if (u > 0 && !tc::mbar_wait(tc::smem_u32(&sm.empty[s]), (unsigned)((u - 1) & 1),
+                                    p.wait_ns)) {
+          good = false;
+          break;
         }
+        const uint2 e = stages[sidx];
+        const uint32_t fb = tc::smem_u32(&sm.full[s]);
+        tc::mbar_expect_tx(fb, kStageBytes);
+        const uint32_t dst = tc::smem_u32(stage0 + (size_t)s * kStageBytes);
+        tc::bulk_g2s(dst, p.ablk + (size_t)st_ablk(e) * kABlock, kABlock, fb);
+        tc::bulk_g2s(dst + kABlock, p.yh + ((size_t)st_ct(e) * p.ntile_r + st_rt(e)) * kBBlock,
+                     kBBlock, fb);
       }
       // no copy may be in flight when the CTA leaves: wait for the last ones issued
       for (long long last = std::max<long long>(0, sidx - kStages); last < sidx; ++last) {
         const int s = (int)(last % kStages);
-        if (!tc::mbar_wait(tc::smem_u32(&sm.full_b[s]), (unsigned)((last / kStages) & 1),
+        if (!tc::mbar_wait(tc::smem_u32(&sm.full[s]), (unsigned)((last / kStages) & 1),
                            p.wait_ns))
           good = false;
       }
       if (!good) fail(p.status);
     }
     __syncwarp();
-  } else if (warp < 2 + kAWarps) {
-    // ------------------------------------------------------------ A generators
-    const int t = tid - 64;
-    long long sidx = 0;
-    bool good = true;
-    for (int ci = walk.c0; ci < walk.c1 && good; ++ci) {
-      const int4 ch = p.chunks[ci];
-      const int nrt = ch.w & 255;
-      for (int w = 0; w < p.nwords && good; ++w) {
-        unsigned lm = walk.lmask(ch, w);
-        while (lm && good) {
-          const int l = w * 32 + __ffs(lm) - 1;
-          lm &= lm - 1;
-          const int l3[3] = {l / (p.D[1] * p.D[2]), (l / p.D[2]) % p.D[1], l % p.D[2]};
-          for (int j = 0; j < nrt; ++j) {
-            const int rt = p.chunk_rt[ch.z + j];
-            if (!walk.on(ch.x, rt, l)) continue;
-            const int s = (int)(sidx % kStages);
-            const long long u = sidx / kStages;
-            const int ib = (int)(sidx & 1);
-            if (warp == 2) {
-              const bool fits = find_images(p, sm, ib, ch.x, rt, l3, lane);
-              // one thread waits for the stage buffer; every generator then follows its verdict
-              bool freed = true;
-              if (lane == 0 && u > 0)
-                freed = tc::mbar_wait(tc::smem_u32(&sm.empty[s]), (unsigned)((u - 1) & 1),
-                                      p.wait_ns);
-              if (lane == 0) sm.a_ok[ib] = (freed && fits) ? 1 : 0;
-            }
-            tc::named_sync(1, 32 * kAWarps);
-            if (!sm.a_ok[ib]) {
-              good = false;
-              break;
-            }
-            // acquire: the phase is complete already, so this returns at once
-            if (u > 0) tc::mbar_try_wait(tc::smem_u32(&sm.empty[s]), (unsigned)((u - 1) & 1));
-            unsigned char* st = stage0 + (size_t)s * kStageBytes;
-            gen_a(p, sm, ib, ch.x, rt, l3, st, st + kABytes, t);
-            tc::fence_proxy_async_smem();
-            tc::mbar_arrive(tc::smem_u32(&sm.full_a[s]));
-            ++sidx;
-          }
-        }
-      }
-    }
-    if (!good && t == 0) fail(p.status);
   } else {
     // ------------------------------------------------------------ epilogue
-    const int et = tid - 32 * (2 + kAWarps);          // 0..127
-    const int quarter = warp & 3;                      // TMEM lanes 32 quarter ..
+    const int ew = warp - 2;                    // 0 .. 15
+    const int quarter = warp & 3;               // TMEM lanes 32 quarter ..
+    const int cs = ew >> 2;                     // complex columns [32 cs, 32 cs + 32)
     const int row = 32 * quarter + lane;
     const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
-    long long group = 0;
-    bool good = true;
-    for (int ci = walk.c0; ci < walk.c1 && good; ++ci) {
-      const int4 ch = p.chunks[ci];
-      const int tile = ch.x, ct = ch.y;
-      const int flags = ch.w;
-      // per-column reciprocal scales of this chunk's columns
-      {
-        const int c = ct * kNC + et;
-        double inv = 0.0;
-        if (c < p.ncol) {
-          const float mx = __uint_as_float(p.colmax[c]);
-          int e2 = 0;
-          if (mx > 0.f) frexpf(mx, &e2);
-          inv = ldexp(1.0, e2 - 13);
-        }
-        tc::named_sync(2, 32 * kEWarps);   // previous chunk's readers of colinv are done
-        sm.colinv[et] = inv;
-      }
-      bool first_group = true;
-      // how many l groups this chunk has (the last one may end in FP64 atomics)
-      int ngroups = 0;
-      for (int w = 0; w < p.nwords; ++w) ngroups += __popc(walk.lmask(ch, w));
-      int gi = 0;
-      for (int w = 0; w < p.nwords && good; ++w) {
-        unsigned lm = walk.lmask(ch, w);
-        while (lm && good) {
-          const int l = w * 32 + __ffs(lm) - 1;
-          lm &= lm - 1;
-          // phases e^{-ik.L_l} of the chunk's columns
-          {
-            const int c = ct * kNC + et;
-            float2 ph = make_float2(0.f, 0.f);
-            if (c < p.ncol) {
-              const int k = c / p.nocc;
-              const int l3[3] = {l / (p.D[1] * p.D[2]), (l / p.D[2]) % p.D[1], l % p.D[2]};
-              const int Dc = p.D[0] * p.D[1] * p.D[2];
-              long long num = 0;
-              for (int d = 0; d < 3; ++d)
-                num += (long long)p.kint[3 * k + d] * l3[d] * (Dc / p.D[d]);
-              const float2 v = dev::cis_frac<float>(num, Dc, -1);
-              ph = v;
-            }
-            tc::named_sync(2, 32 * kEWarps);
-            sm.phase[et] = ph;
-            if (et == 0)
-              sm.e_ok = tc::mbar_wait(tc::smem_u32(&sm.acc_full), (unsigned)(group & 1),
-                                      p.wait_ns) ? 1 : 0;
-            tc::named_sync(2, 32 * kEWarps);
-          }
-          if (!sm.e_ok) {
-            good = false;
-            break;
-          }
-          tc::mbar_try_wait(tc::smem_u32(&sm.acc_full), (unsigned)(group & 1));   // acquire
-          tc::tc_fence_after();
-          const bool init = first_group && (flags & kFirstSum);
-          const bool last = (gi == ngroups - 1);
-          const bool to_global = last && (flags & kToGlobal);
-          const int mu = p.perm[tile * kM + row];
-          const double rf = (mu >= 0) ? p.rowf[tile * kM + row] * p.scale : 0.0;
-#pragma unroll 1
-          for (int q = 0; q < kN / 16; ++q) {
-            uint32_t va[16], vs[16];
-            tc::tmem_ld16(t_acc + lane_off + q * 16, va);
-            if (!init) tc::tmem_ld16(t_sum + lane_off + q * 16, vs);
-            tc::tmem_wait_ld();
+    float sr[32], si[32];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float2 ph = sm.phase[q * 8 + j];
-              const float ar = __uint_as_float(va[2 * j]), ai = __uint_as_float(va[2 * j + 1]);
-              float sr = ph.x * ar - ph.y * ai, si = ph.x * ai + ph.y * ar;
-              if (!init) {
-                sr += __uint_as_float(vs[2 * j]);
-                si += __uint_as_float(vs[2 * j + 1]);
-              }
-              vs[2 * j] = __float_as_uint(sr);
-              vs[2 * j + 1] = __float_as_uint(si);
-            }
-            if (to_global) {
-              if (mu >= 0) {
-#pragma unroll 1
-                for (int j = 0; j < 8; ++j) {
-                  const int cl = q * 8 + j, c = ct * kNC + cl;
-                  if (c >= p.ncol) break;
-                  const int k = c / p.nocc, i = c - k * p.nocc;
-                  const double f = rf * sm.colinv[cl];
-                  double* dst = reinterpret_cast<double*>(
-                      p.kc + ((size_t)k * p.nao + mu) * p.nocc + i);
-                  atomicAdd(dst, f * (double)__uint_as_float(vs[2 * j]));
-                  atomicAdd(dst + 1, f * (double)__uint_as_float(vs[2 * j + 1]));
-                }
-              }
-            } else {
-              tc::tmem_st16(t_sum + lane_off + q * 16, vs);
-            }
+    for (int j = 0; j < 32; ++j) { sr[j] = 0.f; si[j] = 0.f; }
+    bool good = true;
+    for (long long sidx = 0; sidx < nst; ++sidx) {
+      const uint2 e = stages[sidx];
+      const int ab = (int)(sidx & 1);
+      const int flags = st_flags(e), ct = st_ct(e), l = st_l(e);
+      if (!warp_wait(tc::smem_u32(&sm.acc_full[ab]), (unsigned)((sidx >> 1) & 1), p.wait_ns,
+                     lane)) {
+        good = false;
+        break;
+      }
+      tc::tc_fence_after();
+      if (flags & kFirstSum) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) { sr[j] = 0.f; si[j] = 0.f; }
+      }
+      const float2* ph = p.phase + ((size_t)ct * p.nl + l) * kNC + 32 * cs;
+      const uint32_t ta = tmem + (uint32_t)(ab * kN) + lane_off + (uint32_t)(64 * cs);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {             // 16 real columns = 8 complex per load
+        uint32_t va[16];
+        tc::tmem_ld16(ta + 16 * q, va);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float2 w = __ldg(ph + 8 * q + j);
+          const float ar = __uint_as_float(va[2 * j]), ai = __uint_as_float(va[2 * j + 1]);
+          sr[8 * q + j] += w.x * ar - w.y * ai;
+          si[8 * q + j] += w.x * ai + w.y * ar;
+        }
+      }
+      tc::tc_fence_before();
+      tc::mbar_arrive(tc::smem_u32(&sm.acc_empty[ab]));
+      if (flags & kToGlobal) {
+        const int tl = (int)((e.y >> 26) & 3u);
+        const int mu = p.perm[tl * kM + row];
+        if (mu >= 0) {
+          const double rf = p.rowf[tl * kM + row] * p.scale;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int c = ct * kNC + 32 * cs + j;
+            if (c >= p.ncol) continue;
+            const float mx = __uint_as_float(p.colmax[c]);
+            int e2 = 0;
+            if (mx > 0.f) frexpf(mx, &e2);
+            const double f = rf * ldexp(1.0, e2 - 13);
+            const int k = c / p.nocc, i = c - k * p.nocc;
+            double* dst = reinterpret_cast<double*>(p.kc + ((size_t)k * p.nao + mu) * p.nocc + i);
+            atomicAdd(dst, f * (double)sr[j]);
+            atomicAdd(dst + 1, f * (double)si[j]);
           }
-          tc::tmem_wait_st();
-          tc::tc_fence_before();
-          tc::mbar_arrive(tc::smem_u32(&sm.acc_empty));
-          ++group;
-          ++gi;
-          first_group = false;
         }
       }
     }
-    if (!good && et == 0) fail(p.status);
+    if (!good && lane == 0) fail(p.status);
   }
 
   tc::tc_fence_before();
@@ -647,7 +606,7 @@ __global__ void convert_y_kernel(const float2* __restrict__ Y, const unsigned* _
     const int rt = (int)(r % ntile_r);
     const int ct = (int)(r / ntile_r);
     const int c = ct * kNC + cl;
-    __align__(16) __half rh[8], rl[8], ih[8], il[8];
+    uint4 rh, rl, ih, il;
     float s = 0.f;
     if (c < ncol) {
       const float mx = __uint_as_float(colmax[c]);
@@ -655,23 +614,25 @@ __global__ void convert_y_kernel(const float2* __restrict__ Y, const unsigned* _
       if (mx > 0.f) frexpf(mx, &e2);
       s = ldexpf(1.f, 13 - e2);
     }
+    float xr[8], xi[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const long long q = (long long)rt * kKP + g * 8 + j;
       float2 v = make_float2(0.f, 0.f);
       if (c < ncol && q < ng) v = Y[(size_t)c * fs + q];
-      const float xr = v.x * s, xi = v.y * s;
-      rh[j] = __float2half_rn(xr);
-      rl[j] = __float2half_rn(xr - __half2float(rh[j]));
-      ih[j] = __float2half_rn(xi);
-      il[j] = __float2half_rn(xi - __half2float(ih[j]));
+      xr[j] = v.x * s;
+      xi[j] = v.y * s;
     }
+    split2(xr[0], xr[1], rh.x, rl.x); split2(xr[2], xr[3], rh.y, rl.y);
+    split2(xr[4], xr[5], rh.z, rl.z); split2(xr[6], xr[7], rh.w, rl.w);
+    split2(xi[0], xi[1], ih.x, il.x); split2(xi[2], xi[3], ih.y, il.y);
+    split2(xi[4], xi[5], ih.z, il.z); split2(xi[6], xi[7], ih.w, il.w);
     unsigned char* blk = yh + ((size_t)ct * ntile_r + rt) * kBBlock;
     const int o_re = op_off(2 * cl, g * 8, kBSlice), o_im = op_off(2 * cl + 1, g * 8, kBSlice);
-    *reinterpret_cast<uint4*>(blk + o_re) = *reinterpret_cast<const uint4*>(rh);
-    *reinterpret_cast<uint4*>(blk + o_im) = *reinterpret_cast<const uint4*>(ih);
-    *reinterpret_cast<uint4*>(blk + kBBytes + o_re) = *reinterpret_cast<const uint4*>(rl);
-    *reinterpret_cast<uint4*>(blk + kBBytes + o_im) = *reinterpret_cast<const uint4*>(il);
+    *reinterpret_cast<uint4*>(blk + o_re) = rh;
+    *reinterpret_cast<uint4*>(blk + o_im) = ih;
+    *reinterpret_cast<uint4*>(blk + kBBytes + o_re) = rl;
+    *reinterpret_cast<uint4*>(blk + kBBytes + o_im) = il;
   }
 }
 
@@ -713,14 +674,25 @@ cudaError_t put(X** d, const std::vector<X>& v, size_t* tot) {
 
 }  // namespace
 
+// One slab: a run of A blocks generated together, and the CTAs of its stages.
+struct TcSlab {
+  long long block0 = 0, stage0 = 0;
+  int nblocks = 0, cta0 = 0, ncta = 0;
+};
+
 struct TcPlan {
   tcc::TcParams prm;
-  int ncta = 0;
+  long long stages = 0;
   size_t smem = 0;
+  std::vector<TcSlab> slabs;
   std::vector<void*> bufs;
   unsigned char* yh = nullptr;
+  unsigned char* ablk = nullptr;
+  uint2* blocks = nullptr;
   unsigned* colmax = nullptr;
 };
+
+long long tc_plan_stages(const TcPlan* t) { return t ? t->stages : 0; }
 
 void tc_plan_free(TcPlan* t) {
   if (!t) return;
@@ -732,9 +704,10 @@ void tc_plan_free(TcPlan* t) {
 int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
                    const std::vector<double>& rcut, size_t* total) {
   using namespace tcc;
-  if (p->natm > kMaxTcAtoms) return OCCRI_EUNSUPPORTED;
+  // outside these limits the plan keeps the CUDA-core contraction
+  if (p->natm > kMaxTcAtoms) return OCCRI_OK;
   const int NL = p->D[0] * p->D[1] * p->D[2];
-  if (NL > 32 * 16) return OCCRI_EUNSUPPORTED;
+  if (NL > 32 * 16) return OCCRI_OK;
   const int N = p->N[0];
   const long long ng = p->ng;
   TcPlan* t = new TcPlan();
@@ -745,7 +718,7 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
   q.n_ct = (q.ncol + kNC - 1) / kNC;
   q.ntile_r = (int)((ng + kKP - 1) / kKP);
   q.nl = NL;
-  q.nwords = (NL + 31) / 32;
+  const int nwords = (NL + 31) / 32;
   for (int d = 0; d < 3; ++d) q.D[d] = p->D[d];
   double sc[3][3], scinv[3][3];
   for (int i = 0; i < 3; ++i)
@@ -753,24 +726,32 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
       sc[i][j] = p->lat[i][j] * p->D[i];
       q.lat[3 * i + j] = (float)p->lat[i][j];
       q.sc[3 * i + j] = (float)sc[i][j];
+      q.sclo[3 * i + j] = (float)(sc[i][j] - (double)q.sc[3 * i + j]);
     }
   inv3x3(sc, scinv);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) q.scinv[3 * i + j] = (float)scinv[i][j];
-  double linv[3][3];
-  inv3x3(p->lat, linv);
-  for (int a = 0; a < p->natm; ++a) {
-    for (int d = 0; d < 3; ++d) {
-      const double f = xyz[3 * a] * linv[0][d] + xyz[3 * a + 1] * linv[1][d] + xyz[3 * a + 2] * linv[2][d];
-      const double fn = f * N;
-      const double ai = std::nearbyint(fn);
-      const double rem = fn - ai;
-      q.aint[a][d] = (int)ai;
-      q.arem_hi[a][d] = (float)rem;
-      q.arem_lo[a][d] = (float)(rem - (double)(float)rem);
-      q.axyz[a][d] = (float)xyz[3 * a + d];
-    }
+  // grid points r_q (fields' order q = (n3 N + n1) N + n2) and L_l + A_a, as hi/lo floats
+  std::vector<float> pts((size_t)ng * 6), tbase((size_t)p->natm * NL * 6);
+  auto split = [](double x, float* hi, float* lo) {
+    *hi = (float)x;
+    *lo = (float)(x - (double)*hi);
+  };
+  for (long long qq = 0; qq < ng; ++qq) {
+    const int n2 = (int)(qq % N), tq = (int)(qq / N), n1 = tq % N, n3 = tq / N;
+    const double f[3] = {(double)n1 / N, (double)n2 / N, (double)n3 / N};
+    for (int d = 0; d < 3; ++d)
+      split(f[0] * p->lat[0][d] + f[1] * p->lat[1][d] + f[2] * p->lat[2][d], &pts[6 * qq + d],
+            &pts[6 * qq + 3 + d]);
   }
+  for (int a = 0; a < p->natm; ++a)
+    for (int l = 0; l < NL; ++l) {
+      const int l3[3] = {l / (p->D[1] * p->D[2]), (l / p->D[2]) % p->D[1], l % p->D[2]};
+      float* o = &tbase[((size_t)a * NL + l) * 6];
+      for (int d = 0; d < 3; ++d)
+        split(l3[0] * p->lat[0][d] + l3[1] * p->lat[1][d] + l3[2] * p->lat[2][d] + xyz[3 * a + d],
+              &o[d], &o[3 + d]);
+    }
 
   // AO rows sorted by screening radius (descending), shells kept whole
   std::vector<int> order(p->nshell);
@@ -797,7 +778,7 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
       const int take = std::min(nm - m, kM - r0);
       TcShell e;
       e.alpha = s.alpha_f; e.alpha_lo = s.alpha_lo; e.rcut2 = s.rcut2_f;
-      e.atom = s.atom; e.l = s.l; e.row0 = r0; e.m0 = m; e.nm = take;
+      e.atom = s.atom; e.l = s.l; e.row0 = r0; e.m0 = m; e.nm = take; e.exact = s.exact_arg;
       shells.push_back(e);
       for (int j = 0; j < take; ++j) {
         const int gr = tile * kM + r0 + j;
@@ -815,11 +796,11 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
 
   // point tiles: centre and radius
   std::vector<float4> rtiles(q.ntile_r);
-  std::vector<double> pts;
+  std::vector<double> tpts;
   for (int rt = 0; rt < q.ntile_r; ++rt) {
     double c[3] = {0, 0, 0};
     int cnt = 0;
-    pts.clear();
+    tpts.clear();
     for (int j = 0; j < kKP; ++j) {
       const long long qq = (long long)rt * kKP + j;
       if (qq >= ng) break;
@@ -828,14 +809,14 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
       double x[3];
       for (int d = 0; d < 3; ++d)
         x[d] = f[0] * p->lat[0][d] + f[1] * p->lat[1][d] + f[2] * p->lat[2][d];
-      for (int d = 0; d < 3; ++d) { c[d] += x[d]; pts.push_back(x[d]); }
+      for (int d = 0; d < 3; ++d) { c[d] += x[d]; tpts.push_back(x[d]); }
       ++cnt;
     }
     for (int d = 0; d < 3; ++d) c[d] /= std::max(cnt, 1);
     double rad = 0;
     for (int j = 0; j < cnt; ++j) {
       double e2 = 0;
-      for (int d = 0; d < 3; ++d) e2 += (pts[3 * j + d] - c[d]) * (pts[3 * j + d] - c[d]);
+      for (int d = 0; d < 3; ++d) e2 += (tpts[3 * j + d] - c[d]) * (tpts[3 * j + d] - c[d]);
       rad = std::max(rad, std::sqrt(e2));
     }
     rtiles[rt] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)(rad + 1e-6));
@@ -853,7 +834,7 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
     // lies within floor(r |b_d| + 1/2) of s0 along axis d
     q.w[d] = (int)std::floor((rmax + rad_max + 0.02) * bn + 0.5);
   }
-  std::vector<unsigned> active((size_t)ntile * q.ntile_r * q.nwords, 0u);
+  std::vector<unsigned> active((size_t)ntile * q.ntile_r * nwords, 0u);
   std::vector<long long> cost_tile_rt((size_t)ntile * q.ntile_r, 0);
   int max_img = 0;
   {
@@ -898,7 +879,7 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
           for (int a = 0; a < p->natm && !on; ++a)
             on = dmin[a] <= reach[(size_t)tl * p->natm + a] + c.w;
           if (on) {
-            active[((size_t)tl * q.ntile_r + rt) * q.nwords + (l >> 5)] |= 1u << (l & 31);
+            active[((size_t)tl * q.ntile_r + rt) * nwords + (l >> 5)] |= 1u << (l & 31);
             ++cost_tile_rt[(size_t)tl * q.ntile_r + rt];
           }
         }
@@ -906,8 +887,10 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
     }
   }
   if (max_img > kMaxImg) {
+    // a supercell this small puts too many images in reach of a point tile: the plan keeps
+    // the CUDA-core contraction (small cells, where it is cheap anyway)
     delete t;
-    return OCCRI_EUNSUPPORTED;
+    return OCCRI_OK;
   }
   // row scales: powers of two that keep |A| < 2^13, allowing for overlapping images
   for (size_t gr = 0; gr < rowscale.size(); ++gr) {
@@ -919,78 +902,130 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
     rowf[gr] = rowf[gr] / (double)rowscale[gr];
   }
 
-  // work chunks: per (tile, column tile), the active point tiles in runs of kChunkTiles;
-  // CTAs take contiguous runs of chunks of about equal cost
-  struct Chunk { int tile, ct, off, n; long long cost; };
-  std::vector<Chunk> chunks;
-  std::vector<int> chunk_rt;
-  for (int tl = 0; tl < ntile; ++tl)
-    for (int ct = 0; ct < q.n_ct; ++ct) {
-      Chunk cur{tl, ct, (int)chunk_rt.size(), 0, 0};
-      std::vector<unsigned> uni(q.nwords, 0u);
-      auto close = [&]() {
-        if (cur.n == 0) return;
-        long long groups = 0;
-        for (unsigned u : uni) groups += __builtin_popcount(u);
-        cur.cost += groups * 2;      // epilogue of each P_l, in stage units
-        chunks.push_back(cur);
-        cur = Chunk{tl, ct, (int)chunk_rt.size(), 0, 0};
-        std::fill(uni.begin(), uni.end(), 0u);
-      };
-      for (int rt = 0; rt < q.ntile_r; ++rt) {
-        const long long c = cost_tile_rt[(size_t)tl * q.ntile_r + rt];
-        if (c == 0) continue;
-        chunk_rt.push_back(rt);
-        ++cur.n;
-        cur.cost += c;
-        for (int w = 0; w < q.nwords; ++w)
-          uni[w] |= active[((size_t)tl * q.ntile_r + rt) * q.nwords + w];
-        if (cur.n == kChunkTiles) close();
-      }
-      close();
-    }
+  // The A blocks are the (tile, point tile, l) at which the tile reaches r - L_l; they are
+  // generated slab by slab (at most kSlabBlocks, one tile and a range of point tiles per
+  // slab) into one buffer. A slab's stages are its blocks times the column tiles: per column
+  // tile, runs of kFlushTiles point tiles share FP32 running sums, which then go to K_{mu i}.
+  // CTAs take contiguous runs of stages of equal count.
+  if (ntile > kMaxTiles || (int)shells.size() > kMaxEntries || q.ntile_r > 65536 ||
+      q.n_ct > 255) {
+    delete t;
+    return OCCRI_OK;
+  }
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
-  long long total_cost = 0;
-  for (const Chunk& c : chunks) total_cost += c.cost;
-  const int ncta = std::max(1, std::min<int>(nsm > 0 ? nsm : 1, (int)chunks.size()));
-  std::vector<int> cta_chunk0(ncta + 1, (int)chunks.size());
-  {
-    long long acc = 0;
-    int b = 0;
-    cta_chunk0[0] = 0;
-    for (size_t i = 0; i < chunks.size(); ++i) {
-      while (b + 1 < ncta && acc >= (long long)((double)total_cost * (b + 1) / ncta)) {
-        cta_chunk0[++b] = (int)i;
+  nsm = std::max(nsm, 1);
+  std::vector<uint2> blocks;
+  std::vector<uint2> stages;
+  std::vector<long long> cta_stage0;
+  long long total_st = 0;
+  size_t max_slab = 0;
+  for (int tl = 0; tl < ntile; ++tl) {
+    int rt = 0;
+    while (rt < q.ntile_r) {
+      // one slab: point tiles [rt0, rt1) of tile tl
+      TcSlab slab;
+      slab.block0 = (long long)blocks.size();
+      const int rt0 = rt;
+      std::vector<int> slot_of;   // per (point tile - rt0, l): slot or -1
+      std::vector<int> tiles_rt;
+      while (rt < q.ntile_r) {
+        const long long c = cost_tile_rt[(size_t)tl * q.ntile_r + rt];
+        if ((long long)blocks.size() - slab.block0 + c > kSlabBlocks && rt > rt0) break;
+        ++rt;
       }
-      acc += chunks[i].cost;
+      const int rt1 = rt;
+      for (int r = rt0; r < rt1; ++r) {
+        const unsigned* act = &active[((size_t)tl * q.ntile_r + r) * nwords];
+        for (int l = 0; l < NL; ++l)
+          if ((act[l >> 5] >> (l & 31)) & 1u)
+            blocks.push_back(make_uint2((unsigned)r | ((unsigned)l << 16), (unsigned)tl));
+      }
+      slab.nblocks = (int)((long long)blocks.size() - slab.block0);
+      if (slab.nblocks == 0) continue;
+      max_slab = std::max(max_slab, (size_t)slab.nblocks);
+      // stages: column tile by column tile, runs of kFlushTiles active point tiles
+      std::vector<uint2> st;
+      for (int ct = 0; ct < q.n_ct; ++ct) {
+        int slot = 0, in_run = 0;
+        size_t run_first = st.size();
+        for (int r = rt0; r < rt1; ++r) {
+          const unsigned* act = &active[((size_t)tl * q.ntile_r + r) * nwords];
+          bool any = false;
+          for (int l = 0; l < NL; ++l)
+            if ((act[l >> 5] >> (l & 31)) & 1u) {
+              st.push_back(make_uint2((unsigned)slot | ((unsigned)l << 22),
+                                      (unsigned)r | ((unsigned)ct << 16) | ((unsigned)tl << 26)));
+              ++slot;
+              any = true;
+            }
+          if (!any) continue;
+          if (++in_run == kFlushTiles || r + 1 == rt1) {
+            st[run_first].y |= (unsigned)kFirstSum << 24;
+            st.back().y |= (unsigned)kToGlobal << 24;
+            run_first = st.size();
+            in_run = 0;
+          }
+        }
+        if (st.size() > run_first) {   // a run left open by point tiles without activity
+          st[run_first].y |= (unsigned)kFirstSum << 24;
+          st.back().y |= (unsigned)kToGlobal << 24;
+        }
+      }
+      // CTAs: contiguous ranges of runs, cut at run ends, about equal stage counts
+      slab.stage0 = (long long)stages.size();
+      slab.cta0 = (int)cta_stage0.size();
+      const int ncta = std::max(1, std::min<int>(nsm, (int)(st.size() / 64 + 1)));
+      long long cut = 0;
+      int b = 0;
+      cta_stage0.push_back(slab.stage0);
+      for (size_t i = 0; i < st.size(); ++i) {
+        const bool run_end = (st[i].y >> 24) & kToGlobal;
+        if (run_end && b + 1 < ncta &&
+            (long long)(i + 1) >= (long long)((double)st.size() * (b + 1) / ncta)) {
+          cta_stage0.push_back(slab.stage0 + (long long)i + 1);
+          ++b;
+        }
+        (void)cut;
+      }
+      slab.ncta = b + 1;
+      stages.insert(stages.end(), st.begin(), st.end());
+      total_st += (long long)st.size();
+      t->slabs.push_back(slab);
     }
-    while (b + 1 < ncta) cta_chunk0[++b] = (int)chunks.size();
-    cta_chunk0[ncta] = (int)chunks.size();
   }
-  std::vector<int4> ch4(chunks.size());
-  for (int b = 0; b < ncta; ++b) {
-    int since = 0;
-    for (int i = cta_chunk0[b]; i < cta_chunk0[b + 1]; ++i) {
-      const Chunk& c = chunks[i];
-      const bool first = (i == cta_chunk0[b]) || since == 0 ||
-                         chunks[i - 1].tile != c.tile || chunks[i - 1].ct != c.ct;
-      if (first) since = 0;
-      ++since;
-      const bool last = (i + 1 == cta_chunk0[b + 1]) || chunks[i + 1].tile != c.tile ||
-                        chunks[i + 1].ct != c.ct || since == kFlushChunks;
-      if (last) since = 0;
-      ch4[i] = make_int4(c.tile, c.ct, c.off, c.n | (first ? kFirstSum : 0) | (last ? kToGlobal : 0));
-    }
+  cta_stage0.push_back((long long)stages.size());
+  // per (column tile, l): the phases e^{-ik.L_l} of the tile's 128 columns
+  std::vector<float2> phase((size_t)q.n_ct * NL * kNC, make_float2(0.f, 0.f));
+  {
+    const int Dc = NL;
+    for (int ct = 0; ct < q.n_ct; ++ct)
+      for (int l = 0; l < NL; ++l) {
+        const int l3[3] = {l / (p->D[1] * p->D[2]), (l / p->D[2]) % p->D[1], l % p->D[2]};
+        for (int j = 0; j < kNC; ++j) {
+          const int c = ct * kNC + j;
+          if (c >= q.ncol) break;
+          const int k = c / p->nocc;
+          long long num = 0;
+          for (int d = 0; d < 3; ++d)
+            num += (long long)p->kint_h[3 * k + d] * l3[d] * (Dc / p->D[d]);
+          num %= Dc;
+          const double ang = -2.0 * 3.14159265358979323846 * (double)num / (double)Dc;
+          phase[((size_t)ct * NL + l) * kNC + j] =
+              make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+      }
   }
-  t->ncta = ncta;
 
   // device copies
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess && x != cudaSuccess) e = x; };
   TcShell* d_sh = nullptr; int* d_ts = nullptr; float* d_rs = nullptr; double* d_rf = nullptr;
-  int* d_perm = nullptr; float* d_reach = nullptr; float4* d_rt = nullptr; unsigned* d_act = nullptr;
-  int4* d_ch = nullptr; int* d_crt = nullptr; int* d_c0 = nullptr;
+  int* d_perm = nullptr; float* d_reach = nullptr; float4* d_rt = nullptr;
+  uint2* d_st = nullptr; long long* d_s0 = nullptr; uint2* d_bl = nullptr;
+  float* d_pts = nullptr; float* d_tb = nullptr; float2* d_ph = nullptr;
+  chk(put(&d_pts, pts, total)); t->bufs.push_back(d_pts);
+  chk(put(&d_tb, tbase, total)); t->bufs.push_back(d_tb);
   chk(put(&d_sh, shells, total)); t->bufs.push_back(d_sh);
   chk(put(&d_ts, tile_shell0, total)); t->bufs.push_back(d_ts);
   chk(put(&d_rs, rowscale, total)); t->bufs.push_back(d_rs);
@@ -998,15 +1033,19 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
   chk(put(&d_perm, perm, total)); t->bufs.push_back(d_perm);
   chk(put(&d_reach, reach, total)); t->bufs.push_back(d_reach);
   chk(put(&d_rt, rtiles, total)); t->bufs.push_back(d_rt);
-  chk(put(&d_act, active, total)); t->bufs.push_back(d_act);
-  chk(put(&d_ch, ch4, total)); t->bufs.push_back(d_ch);
-  chk(put(&d_crt, chunk_rt, total)); t->bufs.push_back(d_crt);
-  chk(put(&d_c0, cta_chunk0, total)); t->bufs.push_back(d_c0);
+  chk(put(&d_st, stages, total)); t->bufs.push_back(d_st);
+  chk(put(&d_s0, cta_stage0, total)); t->bufs.push_back(d_s0);
+  chk(put(&d_bl, blocks, total)); t->bufs.push_back(d_bl);
+  chk(put(&d_ph, phase, total)); t->bufs.push_back(d_ph);
   {
     void* b = nullptr;
     const size_t yb = (size_t)q.n_ct * q.ntile_r * kBBlock;
     *total += yb;
     chk(device_malloc(&b, yb)); t->bufs.push_back(b); t->yh = (unsigned char*)b;
+    b = nullptr;
+    const size_t ab = std::max<size_t>(1, max_slab) * kABlock;
+    *total += ab;
+    chk(device_malloc(&b, ab)); t->bufs.push_back(b); t->ablk = (unsigned char*)b;
     b = nullptr;
     *total += (size_t)q.ncol * 4;
     chk(device_malloc(&b, (size_t)q.ncol * 4)); t->bufs.push_back(b); t->colmax = (unsigned*)b;
@@ -1016,9 +1055,13 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
     tc_plan_free(t);
     return e == cudaErrorMemoryAllocation ? OCCRI_ENOMEM : OCCRI_ECUDA;
   }
-  q.yh = t->yh; q.shells = d_sh; q.tile_shell0 = d_ts; q.rowscale = d_rs; q.rowf = d_rf;
-  q.perm = d_perm; q.reach = d_reach; q.rtiles = d_rt; q.active = d_act; q.chunks = d_ch;
-  q.chunk_rt = d_crt; q.cta_chunk0 = d_c0; q.kint = p->kint; q.colmax = t->colmax;
+  q.yh = t->yh; q.ablk = t->ablk; q.shells = d_sh; q.tile_shell0 = d_ts; q.rowscale = d_rs;
+  q.rowf = d_rf; q.perm = d_perm; q.reach = d_reach; q.rtiles = d_rt; q.stages = d_st;
+  q.cta_stage0 = d_s0; q.colmax = t->colmax; q.pts = d_pts; q.tbase = d_tb; q.phase = d_ph;
+  q.ntile = ntile;
+  q.nentries = (int)shells.size();
+  t->blocks = d_bl;
+  t->stages = total_st;
   t->smem = (size_t)kStages * kStageBytes + sizeof(Smem);
   p->tc = t;
   return OCCRI_OK;
@@ -1043,7 +1086,14 @@ cudaError_t launch_contract_tc(const Plan& p, cudaStream_t s) {
                          (int)t->smem);
     return 1;
   });
-  contract_tc_kernel<<<t->ncta, kThreads, t->smem, s>>>(q);
+  for (const TcSlab& sl : t->slabs) {
+    TcParams qs = q;
+    qs.blocks = t->blocks + sl.block0;
+    qs.nblocks = sl.nblocks;
+    qs.cta_stage0 = q.cta_stage0 + sl.cta0;
+    gen_blocks_kernel<<<std::min(sl.nblocks, 152 * 8), kGenThreads, 0, s>>>(qs);
+    contract_tc_kernel<<<sl.ncta, kThreads, t->smem, s>>>(qs);
+  }
   return cudaGetLastError();
 }
 

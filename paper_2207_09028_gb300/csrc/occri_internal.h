@@ -91,6 +91,7 @@ struct PairParams {
   double omega;
   double g0;                 // value at G+q = 0, in units of 4 pi
   double dg0;                // d g0 / d omega, in units of 4 pi
+  double rc;                 // truncation radius of OCCRI_COULOMB_TRUNC
   // FP32 copies (hi/lo for the metric) made on the host, so FP32 kernels never
   // convert from double on the device (FP64 issue is 1/64 rate)
   float gh[6], gl[6];
@@ -108,6 +109,8 @@ struct Plan {
   double omega_cell;
   occri_kernel kernel;
   cudaStream_t stream;
+  double g0_4pi = 0.0, dg0_4pi = 0.0;   // the G+q = 0 value and its omega-derivative / (4 pi)
+  double rc = 0.0;                       // truncation radius (OCCRI_COULOMB_TRUNC)
   int device = 0;            // the CUDA device current at plan creation; every call runs on it
   int fault = 0;             // test-only fault injection (occri_plan_inject_fault)
   long long wait_ns = 2000000000LL;   // limit of the bounded device waits
@@ -269,6 +272,7 @@ cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s);
 int tc_plan_create(Plan* p, const std::vector<ShellDev>& shells, const double* xyz,
                    const std::vector<double>& rcut, size_t* total);
 void tc_plan_free(TcPlan* t);
+long long tc_plan_stages(const TcPlan* t);   // stages of one contraction (0 without a plan)
 cudaError_t launch_contract_tc(const Plan& p, cudaStream_t s);
 
 // Launch settings derived once per kernel instantiation and device (function attributes,

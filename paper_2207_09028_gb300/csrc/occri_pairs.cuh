@@ -66,9 +66,18 @@ constexpr int min_blocks(int n, int elem_bytes) {
 constexpr int min_blocks_a(int n, int elem_bytes) {
   return elem_bytes > 8 ? min_blocks(n, elem_bytes) : (n <= 32 ? 8 : 5);
 }
-// f(|G+q|)/(4 pi) of Eq. recipcoul for |G+q|^2 = g2 > 0.
+// f(|G+q|)/(4 pi) of Eq. recipcoul for |G+q|^2 = g2 = g2h + g2l > 0 (a hi + lo pair).
+// The truncated Coulomb kernel (1 - cos(x R_c))/x^2 = 2 sin^2(x R_c/2)/x^2 is evaluated in
+// FP64 from the pair in both precisions: x R_c reaches several hundred radians, where the
+// FP32 argument alone would be off by 1e-5.
 template <typename T>
-__device__ __forceinline__ T kernel_f(T g2, int kind, T inv4w2) {
+__device__ __forceinline__ T kernel_f(T g2h, T g2l, int kind, T inv4w2, double rc) {
+  if (kind == OCCRI_COULOMB_TRUNC) {
+    const double g2 = (double)g2h + (double)g2l;
+    const double s = sin(0.5 * sqrt(g2) * rc);
+    return T(2.0 * s * s / g2);
+  }
+  const T g2 = g2h + g2l;
   const T base = T(1) / g2;
   if (kind == OCCRI_COULOMB) return base;
   const T y = g2 * inv4w2;
@@ -79,7 +88,7 @@ __device__ __forceinline__ T kernel_f(T g2, int kind, T inv4w2) {
 // (d f/d omega)/(4 pi) = -/+ e^{-x^2/(4 omega^2)} / (2 omega^3) (erfc / erf).
 template <typename T>
 __device__ __forceinline__ T kernel_df(T g2, int kind, T inv4w2, T omega) {
-  if (kind == OCCRI_COULOMB) return T(0);
+  if (kind != OCCRI_ERFC && kind != OCCRI_ERF) return T(0);
   const T e = exp_t(-g2 * inv4w2) * T(0.5) / (omega * omega * omega);
   return kind == OCCRI_ERFC ? -e : e;
 }
@@ -456,16 +465,17 @@ template <typename T, bool DERIV>
 __device__ __forceinline__ T bin_value(const PairParams& p, const Consts<T>& k,
                                        const Axis1<T>& a, const ColumnConst<T>& c) {
   if ((a.flags & 2) && c.zero) return DERIV ? k.dg0 : k.g0;
-  auto f = [&](T g2) {
-    return DERIV ? kernel_df<T>(g2, p.kind, k.inv4w2, k.omega) : kernel_f<T>(g2, p.kind, k.inv4w2);
+  auto f = [&](T g2h, T g2l) {
+    return DERIV ? kernel_df<T>(g2h + g2l, p.kind, k.inv4w2, k.omega)
+                 : kernel_f<T>(g2h, g2l, p.kind, k.inv4w2, p.rc);
   };
   const bool t1 = (a.flags & 1) != 0;
   T s = T(0);
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     if (u < c.nv) {
-      s += f((a.ah + a.x * c.bh[u] + c.ch[u]) + (a.al + a.x * c.bl[u] + c.cl[u]));
-      if (t1) s += f((a.bh + a.xb * c.bh[u] + c.ch[u]) + (a.bl + a.xb * c.bl[u] + c.cl[u]));
+      s += f(a.ah + a.x * c.bh[u] + c.ch[u], a.al + a.x * c.bl[u] + c.cl[u]);
+      if (t1) s += f(a.bh + a.xb * c.bh[u] + c.ch[u], a.bl + a.xb * c.bl[u] + c.cl[u]);
     }
   }
   return (c.nv == 1 && !t1) ? s : s / T(c.nv * (t1 ? 2 : 1));

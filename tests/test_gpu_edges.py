@@ -58,7 +58,8 @@ def _gpu(torch, w, precision):
     plan = occri.Plan.from_workload(w, precision=precision)
     C = torch.from_numpy(w.C).cuda()
     KC, K, Ex = plan.build(C)
-    out = dict(kc=KC.cpu().numpy(), k=K.cpu().numpy(), ex=float(Ex.cpu()[0]))
+    out = dict(kc=KC.cpu().numpy(), k=K.cpu().numpy(), ex=float(Ex.cpu()[0]),
+               tc=plan.contraction_tc)
     plan.close()
     return out
 
@@ -82,12 +83,15 @@ def test_every_edge_matches_explicit_dft_oracle(torch_cuda, n, precision):
     _check(_gpu(torch_cuda, w, precision), _oracle(n), precision, f"edge {n}")
 
 
-# the tensor-core contraction reads the grid through point tiles of 32: a few edges with
-# ragged last tiles (9^3, 25^3, 45^3) and exact ones
+# the tensor-core contraction reads the grid through tiles of 32 points: a few edges with
+# ragged last tiles (9^3, 25^3, 45^3) and exact ones, on the bench cell's lattice constant
+# (a supercell large enough for the tensor-core path, which the plan must report)
 @pytest.mark.parametrize("n", [9, 24, 25, 45, 48])
 def test_tensor_core_contraction_edges(torch_cuda, n):
-    w = _edge_workload(n)
-    _check(_gpu(torch_cuda, w, "mixed_tc"), _oracle(n), "mixed_tc", f"edge {n}")
+    w = _edge_workload(n, a_ang=5.43)
+    got = _gpu(torch_cuda, w, "mixed_tc")
+    assert got["tc"]
+    _check(got, _oracle(n, a_ang=5.43), "mixed_tc", f"edge {n}")
 
 
 # ------------------------------------------------------------------ the bench's edge, 60^3
@@ -110,4 +114,7 @@ def test_bench_edge_60_matches_oracle(torch_cuda, case, precision):
     if case == 0:   # the two oracle transforms agree with each other first
         ref_fft = _oracle(*key, dft=False)
         assert np.abs(ref_fft["kc"] - ref["kc"]).max() <= 1e-12 * np.abs(ref["kc"]).max()
-    _check(_gpu(torch_cuda, w, precision), ref, precision, f"60^3 case {c}")
+    got = _gpu(torch_cuda, w, precision)
+    if precision == "mixed_tc" and c["mesh"] != (1, 1, 1):
+        assert got["tc"]
+    _check(got, ref, precision, f"60^3 case {c}")

@@ -45,7 +45,7 @@ def _oracle(w):
     chi = O.bloch_aos(w.lattice, w.xyz, w.shell_atom, w.shell_l, w.shell_alpha, w.kfrac,
                       grid=w.grid)
     psi = O.orbitals_on_grid(chi, w.C)
-    g0 = O.g0_value(w.kernel, w.omega, w.g0_mode)
+    g0 = O.g0_value(w.kernel, w.omega, w.g0_mode, w.lattice, w.kfrac)
     kc = O.occri_kc(w.lattice, w.grid, w.kfrac, psi, chi, w.kernel, w.omega, g0)
     k, m, ex = O.ace_assemble(w.C, kc)
     return dict(chi=chi, psi=psi, kc=kc, k=k, ex=ex)
@@ -121,6 +121,44 @@ def test_small_builds_match_oracle(torch_cuda, case, precision):
     ref = _oracle(w)
     got = _gpu(torch_cuda, w, precision)
     _assert_close(got, ref, precision, str(SMALL[case]))
+
+
+# the singularity treatments of Sec. II.A: Madelung-corrected Coulomb and erf (g0_mode 2) and
+# the truncated Coulomb kernel with its x -> 0 value (g0_mode 1)
+SINGULAR = [
+    dict(mesh=(1, 2, 1), grid=(12, 12, 12), counts=(2, 1), nocc=2, kernel="coulomb", g0_mode=2),
+    dict(mesh=(2, 1, 1), grid=(10, 10, 10), counts=(2, 1), nocc=2, kernel="erf", omega=0.5,
+         g0_mode=2),
+    dict(mesh=(1, 1, 2), grid=(12, 12, 12), counts=(2, 1, 1), nocc=3, kernel="coulomb_trunc",
+         g0_mode=1),
+    dict(mesh=(1, 1, 1), grid=(16, 16, 16), counts=(2, 1), nocc=2, kernel="coulomb_trunc",
+         g0_mode=1),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SINGULAR)))
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_singularity_treatments_match_oracle(torch_cuda, case, precision):
+    w = small_workload(seed=300 + case, **SINGULAR[case])
+    ref = _oracle(w)
+    got = _gpu(torch_cuda, w, precision)
+    _assert_close(got, ref, precision, str(SINGULAR[case]))
+
+
+def test_madelung_erf_omega_gradient_matches_oracle_differences(torch_cuda):
+    """With the Madelung chi of the erf kernel, d E_x / d omega includes d chi / d omega."""
+    import paper_2207_09028_gb300 as occri
+    torch = torch_cuda
+    w = small_workload(mesh=(2, 1, 1), grid=(10, 10, 10), counts=(2, 1), nocc=2, kernel="erf",
+                       omega=0.5, g0_mode=2, seed=310)
+    plan = occri.Plan.from_workload(w, precision="fp64")
+    C = torch.from_numpy(w.C).cuda()
+    plan.build(C, want_k=False)
+    _, gw = plan.vjp(C, 1.0, want_c=False, want_omega=True)
+    h = 1e-5
+    e = [_oracle(w.with_kernel("erf", 0.5 + s * h, 2))["ex"] for s in (1, -1)]
+    fd = (e[0] - e[1]) / (2 * h)
+    assert abs(float(gw.cpu()[0]) - fd) <= 1e-6 * abs(fd), (float(gw.cpu()[0]), fd)
 
 
 def test_shifted_mesh_and_odd_k(torch_cuda):
@@ -379,6 +417,7 @@ def test_config5_mixed_energy_within_1e6_of_fp64(torch_cuda):
     out = {}
     for prec in ("mixed", "mixed_tc", "fp64"):
         plan = occri.Plan.from_workload(w, precision=prec)
+        assert plan.contraction_tc == (prec == "mixed_tc")
         KC, _, Ex = plan.build(C, want_k=False)
         out[prec] = (KC.cpu().numpy(), float(Ex.cpu()[0]))
         plan.close()
