@@ -31,7 +31,7 @@ __all__ = [
     "g0_value", "apply_coulomb_operator", "occri_kc", "contract_kc", "mori_k", "aori_k",
     "ace_assemble", "exchange_energy", "exchange_energy_parseval", "grad_c",
     "grad_omega", "grid_overlap", "dft_matrices", "mesh_denominators", "supercell_lattice",
-    "truncation_radius", "madelung_potential", "kernel_value",
+    "truncation_radius", "madelung_potential", "kernel_value", "assemble_paper",
 ]
 
 EPS_AO = 1e-16   # AO screening threshold: terms below it are dropped (C10 reading)
@@ -456,24 +456,30 @@ def apply_coulomb_operator(f: np.ndarray, v: np.ndarray, qfrac, dft: bool = Fals
 # ----------------------------------------------------------------------------
 
 def occri_kc(lattice, grid, kfrac, psi: np.ndarray, chi: Optional[np.ndarray], kind: str,
-             omega: float, g0: float, dft: bool = False, return_y: bool = False):
+             omega: float, g0: float, dft: bool = False, return_y: bool = False,
+             nsum: Optional[int] = None):
     """AO-occupied block K_{mu i}(k) of Eq. occrik by Algorithm 3.
 
     psi: (nk, nocc, N_g). For every (k, i) and every (k', j): form the pair
     density, apply the kernel-fused transform round trip, accumulate
     Y_{ik} += psi_{jk'} W (Eq. occrikinterm); then contract with conj(chi).
     If chi is None, only Y is returned.
+
+    nsum (conduction-band extension, Sec. II.D): the orbitals j summed over are the
+    first nsum of psi (the occupied ones), while outputs are formed for every orbital
+    of psi, so K_{mu p} for p beyond nsum is the exchange operator built from the
+    occupied orbitals applied to the extra (conduction) orbital p.
     """
     grid = tuple(int(g) for g in grid)
     nk, nocc, ng = psi.shape
-    omega_cell = cell_volume(lattice)
+    nj = nocc if nsum is None else int(nsum)
     y = np.zeros_like(psi)
     for k in range(nk):
         for kp in range(nk):
             q = np.asarray(kfrac[k], float) - np.asarray(kfrac[kp], float)
             v = kernel_bins(lattice, grid, q, kind, omega, g0, _rc(kind, lattice, kfrac))
             for i in range(nocc):
-                for j in range(nocc):
+                for j in range(nj):
                     f = (np.conj(psi[kp, j]) * psi[k, i]).reshape(grid)
                     w = apply_coulomb_operator(f, v, q, dft=dft).reshape(-1)
                     y[k, i] += psi[kp, j] * w
@@ -563,6 +569,28 @@ def ace_assemble(C: np.ndarray, kc: np.ndarray):
         kmat[k] = -xi @ np.conj(xi.T)
         ex += float(np.real(np.trace(m)))
     return kmat, mmat, ex / nk
+
+
+def assemble_paper(ovl: np.ndarray, C: np.ndarray, kc: np.ndarray) -> np.ndarray:
+    """K ~ PKP + PKQ + QKP (Eq. occrikop) in the AO basis, from the AO-occupied block.
+
+    With the occupied projector P = C C^H S (S = ovl, the AO overlap of each k, C
+    S-orthonormal), <mu|K|j> = KC, and M = C^H KC (Hermitised):
+      <mu|PKP|nu> = (S C M C^H S),   <mu|PKQ|nu> = (S C KC^H) - (S C M C^H S),
+      <mu|QKP|nu> = (KC C^H S) - (S C M C^H S),
+    which sum to K = KC C^H S + S C KC^H - S C M C^H S per k. C may also hold chosen
+    conduction bands after the occupied ones (with kc their K_{mu p}, Sec. II.D); P is
+    then the projector on all of them.
+    """
+    nk, nao, ncol = C.shape
+    kmat = np.zeros((nk, nao, nao), dtype=np.complex128)
+    for k in range(nk):
+        m = np.conj(C[k].T) @ kc[k]
+        m = 0.5 * (m + np.conj(m.T))
+        sc = ovl[k] @ C[k]
+        kmat[k] = (kc[k] @ np.conj(sc.T) + sc @ np.conj(kc[k].T)
+                   - sc @ m @ np.conj(sc.T))
+    return kmat
 
 
 def exchange_energy(C: np.ndarray, kc: np.ndarray) -> float:

@@ -215,6 +215,96 @@ def test_ace_reproduces_conventional_on_occupied_space(mesh, kind):
         assert np.abs(d @ w.C[k]).max() < 1e-12 * scale
 
 
+def _virtual_complement(ovl_k, c_k):
+    """An S-orthonormal basis V of the AO-space complement of span(c_k): V^H S V = 1,
+    c_k^H S V = 0 (complete QR in the Cholesky frame of S)."""
+    low = np.linalg.cholesky(ovl_k)
+    ut = np.conj(low.T) @ c_k
+    q, _ = np.linalg.qr(ut, mode="complete")
+    return np.linalg.solve(np.conj(low.T), q[:, c_k.shape[1]:])
+
+
+def _overlap(w):
+    return analytic_overlap(w.lattice, w.xyz, w.shell_atom, w.shell_l, w.shell_alpha, w.kfrac)
+
+
+@pytest.mark.parametrize("mesh,kind", [((1, 1, 1), "coulomb"), ((1, 2, 1), "erfc")])
+def test_conduction_band_columns_apply_the_occupied_exchange(mesh, kind):
+    """Sec. II.D (conduction bands): with the inner sum restricted to the occupied orbitals,
+    every column p of K_{mu p} (occupied or conduction) equals the full exchange operator of
+    the occupied density (brute-force AO-RI-K, Algorithm 1) applied to orbital p, and the
+    occupied columns equal the plain occ-RI-K build."""
+    nocc, nr = 3, 2
+    omega = 0.5 if kind == "erfc" else 0.0
+    w = small_workload(mesh=mesh, grid=(8, 8, 8), nocc=nocc + nr, kernel=kind, omega=omega,
+                       g0_mode=1 if kind == "erfc" else 0)
+    chi = _chi(w)
+    psi = O.orbitals_on_grid(chi, w.C)
+    kc_ext = O.occri_kc(w.lattice, w.grid, w.kfrac, psi, chi, w.kernel, w.omega, _g0(w),
+                        nsum=nocc)
+    c_occ = np.ascontiguousarray(w.C[:, :, :nocc])
+    k_full = O.aori_k(w.lattice, w.grid, w.kfrac, chi, c_occ, w.kernel, w.omega, _g0(w))
+    kc_occ = _kc(w, chi=chi, C=c_occ)
+    scale = np.abs(k_full).max()
+    for k in range(w.nk):
+        assert np.abs(k_full[k] @ w.C[k] - kc_ext[k]).max() < 1e-12 * scale
+    assert np.abs(kc_ext[:, :, :nocc] - kc_occ).max() < 1e-12 * scale
+    # the restriction matters: summing over the conduction orbitals too changes them
+    kc_all = _kc(w, chi=chi)
+    assert np.abs(kc_all[:, :, nocc:] - kc_ext[:, :, nocc:]).max() > 1e-3 * scale
+
+
+@pytest.mark.parametrize("mesh,kind", [((1, 1, 1), "coulomb"), ((1, 2, 1), "erfc")])
+def test_paper_form_assembly_drops_only_the_virtual_block(mesh, kind):
+    """Eq. occrikop: K ~ PKP + PKQ + QKP. With V an S-orthonormal basis of the virtual space,
+    K_full - K = S V (V^H K_full V) V^H S exactly (the QKQ block and nothing else), K C = KC,
+    C^H K C = C^H KC, and K is Hermitian. K_full is the brute-force AO-RI-K build."""
+    omega = 0.5 if kind == "erfc" else 0.0
+    w = small_workload(mesh=mesh, grid=(8, 8, 8), nocc=3, kernel=kind, omega=omega,
+                       g0_mode=1 if kind == "erfc" else 0)
+    chi = _chi(w)
+    ovl = _overlap(w)
+    kc = _kc(w, chi=chi)
+    k_full = O.aori_k(w.lattice, w.grid, w.kfrac, chi, w.C, w.kernel, w.omega, _g0(w))
+    k_pap = O.assemble_paper(ovl, w.C, kc)
+    scale = np.abs(k_full).max()
+    for k in range(w.nk):
+        v = _virtual_complement(ovl[k], w.C[k])
+        sv = ovl[k] @ v
+        qkq = sv @ (np.conj(v.T) @ k_full[k] @ v) @ np.conj(sv.T)
+        assert np.abs(k_full[k] - k_pap[k] - qkq).max() < 1e-11 * scale
+        assert np.abs(qkq).max() > 1e-3 * scale
+        assert np.abs(k_pap[k] @ w.C[k] - kc[k]).max() < 1e-12 * scale
+        assert np.abs(k_pap[k] - np.conj(k_pap[k].T)).max() < 1e-13 * scale
+        assert np.abs(np.conj(v.T) @ k_pap[k] @ v).max() < 1e-12 * scale
+
+
+def test_paper_form_with_conduction_bands_keeps_their_blocks():
+    """Sec. II.D: with the chosen conduction bands R appended to C (and their K_{mu p} from
+    the occupied density), the assembly keeps every block touching P or R and drops only
+    the rest-rest block: K_full - K = S V (V^H K_full V) V^H S with V spanning the
+    complement of occupied + R. (The printed six-term sum counts RKR three times; the
+    reading taken is K ~ K - S~KS~, S~ the projector on the remaining bands.)"""
+    nocc, nr = 3, 2
+    w = small_workload(mesh=(1, 2, 1), grid=(8, 8, 8), nocc=nocc + nr)
+    chi = _chi(w)
+    ovl = _overlap(w)
+    psi = O.orbitals_on_grid(chi, w.C)
+    kc_ext = O.occri_kc(w.lattice, w.grid, w.kfrac, psi, chi, w.kernel, w.omega, _g0(w),
+                        nsum=nocc)
+    c_occ = np.ascontiguousarray(w.C[:, :, :nocc])
+    k_full = O.aori_k(w.lattice, w.grid, w.kfrac, chi, c_occ, w.kernel, w.omega, _g0(w))
+    k_pap = O.assemble_paper(ovl, w.C, kc_ext)
+    scale = np.abs(k_full).max()
+    for k in range(w.nk):
+        v = _virtual_complement(ovl[k], w.C[k])
+        sv = ovl[k] @ v
+        rest = sv @ (np.conj(v.T) @ k_full[k] @ v) @ np.conj(sv.T)
+        assert np.abs(k_full[k] - k_pap[k] - rest).max() < 1e-11 * scale
+        r = w.C[k][:, nocc:]
+        assert np.abs(np.conj(r.T) @ (k_pap[k] - k_full[k]) @ r).max() < 1e-12 * scale
+
+
 def test_energy_identities_occri_mori_aori():
     """P2/P3/P4: E_x by trace = by Parseval = by MO-RI-K = by AO-RI-K, and E_x < 0."""
     w = small_workload(mesh=(1, 1, 2), grid=(8, 8, 8), counts=(2, 1), nocc=2)
