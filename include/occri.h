@@ -131,8 +131,10 @@ typedef struct {
   long long launches_per_build;  /* kernels one occri_k_build launches */
   int contraction_tc;      /* 1: step (e) runs on the tensor cores (OCCRI_MIXED_TC where the
                               supercell admits it), 0: on the CUDA cores */
-  long long tc_stages;     /* tensor-core contraction: stages per build, each 3 MMAs of
-                              M = 128, N = 256, K = 32 (FP16 hi/lo products), else 0 */
+  long long tc_stages;     /* tensor-core contraction: stages per build, else 0 */
+  double tc_flops_per_stage;  /* MMA flops one stage issues: 3 products (FP16 hi/lo) of
+                                 M = 128 AO rows, N = 192 (Re, Im of 96 (k, i) columns),
+                                 K = 32 grid points, i.e. 3 x 2 M N K */
 } occri_plan_info_t;
 
 /* Stages reported by occri_plan_stage_times. */
@@ -182,6 +184,78 @@ int occri_plan_sync(occri_plan *plan, int *bad_k);
  * Asynchronous; call occri_plan_sync to observe OCCRI_ENOTPD. */
 int occri_k_build(occri_plan *plan, const void *C_dev, void *KC_dev, void *K_dev,
                   double *Ex_dev);
+
+/* Launch configuration of the pair loop (Algorithm 3's loops over (k, k') and orbital
+ * pairs, scheduled as waves of fields). None of it changes what is computed; the choice of
+ * wave width and of fused or separate passes C and D changes the order of the FP32/FP64
+ * accumulations, i.e. the rounding. */
+typedef struct {
+  int k_per_wave;       /* k' per wave (1 .. the plan's scratch capacity) */
+  int streams;          /* 2: consecutive waves alternate between two streams; 1: one stream */
+  int pass_b_div;       /* pass-B CTAs = resident CTA slots / pass_b_div (1 or 2) */
+  int split_cd;         /* 1: separate passes C and D where the fused pass CD applies */
+  double us_per_field;  /* autotuner: measured microseconds per pair field of this choice */
+  double us_default;    /* autotuner: the same for the default (widest wave, 2 streams, 1, 0) */
+  int candidates;       /* autotuner: configurations timed; 0: taken from the cache;
+                           occri_plan_tuning: -1 if the autotuner set it, else 0 */
+} occri_tune_t;
+
+enum { OCCRI_TUNE_FORCE = 1 };   /* time again even if the cache holds this shape */
+
+/* Autotuner (not in the paper): times every candidate launch configuration of the pair loop
+ * (k' per wave in powers of two up to the scratch capacity, one or two streams, pass-B CTAs
+ * per resident slot 1 or 1/2, fused or separate passes C and D) on the plan's own buffers,
+ * with CUDA events on the plan's stream, over the same number of pair fields each, and
+ * keeps the fastest. The choice is cached per (device, grid edge, nocc, precision, N_k,
+ * scratch capacity) for the life of the process: later calls, and plans created later with
+ * the same shape, take it from the cache unless flags has OCCRI_TUNE_FORCE.
+ * Synchronises the plan's stream. Leaves the plan's accumulators in an undefined state
+ * (every build overwrites them). chosen (may be NULL) receives the configuration.
+ * OCCRI_EINVAL for a NULL plan or unknown flags. */
+int occri_plan_autotune(occri_plan *plan, int flags, occri_tune_t *chosen);
+
+/* The plan's current launch configuration (us_* fields 0). */
+int occri_plan_tuning(const occri_plan *plan, occri_tune_t *current);
+
+/* Set the launch configuration by hand (k_per_wave >= 1, clamped to the scratch capacity;
+ * streams 1 or 2; pass_b_div 1 or 2; split_cd 0 or 1; other fields ignored), else
+ * OCCRI_EINVAL. Takes effect at the next build. */
+int occri_plan_set_tuning(occri_plan *plan, const occri_tune_t *cfg);
+
+/* The paper's form of the assembly (Sec. II.C, Eq. occrikop): K ~ PKP + PKQ + QKP, where
+ * P = C C^H S projects on the orbitals C (S-orthonormal: C^H S C = 1) and Q = 1 - P; the QKQ
+ * block is dropped. Per k, in FP64:
+ *   K = KC (S C)^H + (S C) KC^H - (S C) M (S C)^H,   M = (C^H KC + KC^H C) / 2.
+ * It agrees with the ACE form of occri_k_build on the occupied space (K C = KC) and keeps the
+ * occupied-virtual blocks exactly.
+ * ncol  : columns of C and KC, 1 <= ncol <= nao: the plan's nocc, or nocc plus chosen
+ *         conduction bands (with KC from occri_k_build_conduction, Sec. II.D; P then projects
+ *         on all ncol orbitals and only the block of the remaining bands is dropped).
+ * S_dev : device c128 [nk][nao][nao], the AO overlap S^k of the Bloch AOs (Hermitian).
+ * C_dev : device c128 [nk][nao][ncol]. KC_dev: device c128 [nk][nao][ncol] = <mu|K|p>.
+ * K_dev : device c128 [nk][nao][nao], written. All buffers are the caller's; read only
+ *         except K_dev. Asynchronous on the plan's stream; the plan keeps a scratch of
+ *         16 (nk ncol^2 + 2 nk nao ncol) bytes, grown on demand (OCCRI_ENOMEM if that fails).
+ * OCCRI_EINVAL for a NULL buffer or ncol outside [1, nao]. */
+int occri_k_assemble_paper(occri_plan *plan, int ncol, const void *S_dev, const void *C_dev,
+                           const void *KC_dev, void *K_dev);
+
+/* Exchange columns of chosen conduction bands (Sec. II.D, conduction-band paragraph):
+ * KCr[k][mu][r] = K_{mu p}(k) = -sum_{k'} sum_{i in occ} (mu_k i_k' | i_k' p_k), p the r-th
+ * conduction band, i.e. the exchange operator of the occupied density applied to band p.
+ * plan_all: a plan whose orbitals are the nocc occupied ones followed by the nr bands
+ *           (its nocc = nocc + nr); plan_r: the same cell, k-mesh, basis, grid, kernel and
+ *           precision with nocc = nr (the bands alone).
+ * The result is KC of plan_all's build (every orbital summed over) minus KC of plan_r's
+ * build (the bands' own terms), so it costs one build of each.
+ * C_all_dev: device c128 [nk][nao][nocc + nr], occupied columns first.
+ * KCr_dev  : device c128 [nk][nao][nr], written.
+ * Both builds run on plan_all's stream; the call synchronises it, allocates and frees a
+ * temporary of 16 nk nao (nocc + 3 nr) bytes (OCCRI_ENOMEM), and returns the first device
+ * error of either build (as occri_plan_sync). OCCRI_EINVAL if the plans differ in anything
+ * but nocc, or plan_r's nocc is not below plan_all's. */
+int occri_k_build_conduction(occri_plan *plan_all, occri_plan *plan_r, const void *C_all_dev,
+                             void *KCr_dev);
 
 /* One-shot build with the signature of the problem statement (Sec. II.A and Eq. occrik):
  * creates a plan for (cell, kmesh, basis, nocc, grid, kernel, precision) on the current

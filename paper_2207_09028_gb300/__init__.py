@@ -51,13 +51,23 @@ class occri_kernel(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("omega", ctypes.c_double), ("g0_mode", ctypes.c_int)]
 
 
+class occri_tune_t(ctypes.Structure):
+    _fields_ = [("k_per_wave", ctypes.c_int), ("streams", ctypes.c_int),
+                ("pass_b_div", ctypes.c_int), ("split_cd", ctypes.c_int),
+                ("us_per_field", ctypes.c_double), ("us_default", ctypes.c_double),
+                ("candidates", ctypes.c_int)]
+
+
+OCCRI_TUNE_FORCE = 1
+
+
 class occri_plan_info_t(ctypes.Structure):
     _fields_ = [("nk", ctypes.c_int), ("nao", ctypes.c_int), ("nocc", ctypes.c_int),
                 ("natm", ctypes.c_int), ("nshell", ctypes.c_int), ("grid", ctypes.c_int * 3),
                 ("ng", ctypes.c_longlong), ("precision", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_size_t), ("fields_per_wave", ctypes.c_int),
                 ("launches_per_build", ctypes.c_longlong), ("contraction_tc", ctypes.c_int),
-                ("tc_stages", ctypes.c_longlong)]
+                ("tc_stages", ctypes.c_longlong), ("tc_flops_per_stage", ctypes.c_double)]
 
 
 EXPORTED = ["occri_plan_create", "occri_plan_destroy", "occri_plan_info", "occri_plan_set_stream",
@@ -66,7 +76,8 @@ EXPORTED = ["occri_plan_create", "occri_plan_destroy", "occri_plan_info", "occri
             "occri_vjp_full", "occri_batch_create", "occri_batch_build", "occri_batch_sync",
             "occri_batch_destroy", "occri_k_build_once", "occri_plan_inject_fault",
             "occri_debug_fail_allocation", "occri_measure_fma_peak",
-            "occri_status_string"]
+            "occri_k_assemble_paper", "occri_k_build_conduction", "occri_plan_autotune",
+            "occri_plan_tuning", "occri_plan_set_tuning", "occri_status_string"]
 
 OCCRI_FAULT_NONE, OCCRI_FAULT_WAIT = 0, 1
 
@@ -115,6 +126,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.occri_plan_inject_fault.argtypes = [vp, ip, ctypes.c_double]
     lib.occri_debug_fail_allocation.argtypes = [ip]
     lib.occri_measure_fma_peak.argtypes = [ip, dp]
+    lib.occri_k_assemble_paper.argtypes = [vp, ip, vp, vp, vp, vp]
+    lib.occri_plan_autotune.argtypes = [vp, ip, ctypes.POINTER(occri_tune_t)]
+    lib.occri_plan_tuning.argtypes = [vp, ctypes.POINTER(occri_tune_t)]
+    lib.occri_plan_set_tuning.argtypes = [vp, ctypes.POINTER(occri_tune_t)]
+    lib.occri_k_build_conduction.argtypes = [vp, vp, vp, vp]
     lib.occri_status_string.argtypes = [ip]
     lib.occri_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -291,6 +307,56 @@ class Plan:
         if sync:
             self.sync()
         return KC, K, Ex
+
+    def autotune(self, force: bool = False) -> dict:
+        """occri_plan_autotune: time the pair loop's launch configurations, keep the fastest."""
+        t = occri_tune_t()
+        self.set_stream()
+        _check(self._lib.occri_plan_autotune(self._h, OCCRI_TUNE_FORCE if force else 0,
+                                             ctypes.byref(t)), "occri_plan_autotune")
+        return {f: getattr(t, f) for f, _ in occri_tune_t._fields_}
+
+    def tuning(self) -> dict:
+        """occri_plan_tuning: the current launch configuration of the pair loop."""
+        t = occri_tune_t()
+        _check(self._lib.occri_plan_tuning(self._h, ctypes.byref(t)), "occri_plan_tuning")
+        return {f: getattr(t, f) for f, _ in occri_tune_t._fields_}
+
+    def force_tuning(self, k_per_wave: int, streams: int, pass_b_div: int, split_cd: int):
+        """occri_plan_set_tuning: set the pair loop's launch configuration by hand."""
+        t = occri_tune_t(k_per_wave=k_per_wave, streams=streams, pass_b_div=pass_b_div,
+                         split_cd=split_cd)
+        _check(self._lib.occri_plan_set_tuning(self._h, ctypes.byref(t)), "occri_plan_set_tuning")
+
+    def assemble_paper(self, S, C, KC, K=None):
+        """occri_k_assemble_paper: K ~ PKP + PKQ + QKP from device tensors S [nk,nao,nao],
+        C and KC [nk,nao,ncol] (complex128); returns K [nk,nao,nao]."""
+        import torch
+        ncol = int(C.shape[2])
+        for t, shape in ((S, (self.nk, self.nao, self.nao)), (C, (self.nk, self.nao, ncol)),
+                         (KC, (self.nk, self.nao, ncol))):
+            if tuple(t.shape) != shape or t.dtype != torch.complex128 or not t.is_contiguous():
+                raise ValueError(f"expected a contiguous complex128 tensor of shape {shape}")
+        if K is None:
+            K = torch.empty((self.nk, self.nao, self.nao), dtype=torch.complex128,
+                            device=C.device)
+        self.set_stream()
+        _check(self._lib.occri_k_assemble_paper(self._h, ncol, _ptr(S), _ptr(C), _ptr(KC),
+                                                _ptr(K)), "occri_k_assemble_paper")
+        return K
+
+    def k_build_conduction(self, plan_r: "Plan", C_all):
+        """occri_k_build_conduction: the exchange columns K_{mu p} of the conduction bands
+        that follow the occupied orbitals in C_all [nk,nao,nocc+nr] (this plan's orbitals),
+        with plan_r the same cell with nocc = nr. Returns KCr [nk,nao,nr] (synchronised)."""
+        import torch
+        self._check_c(C_all)
+        KCr = torch.empty((self.nk, self.nao, plan_r.nocc), dtype=torch.complex128,
+                          device=C_all.device)
+        self.set_stream()
+        _check(self._lib.occri_k_build_conduction(self._h, plan_r._h, _ptr(C_all), _ptr(KCr)),
+               "occri_k_build_conduction")
+        return KCr
 
     def k_build_host(self, C_host: np.ndarray, want_k: bool = True):
         """occri_k_build_host: host (numpy or pinned torch) buffers in and out."""

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -73,6 +74,8 @@ PairParams Plan::pair_params() const {
   q.fault = fault;
   q.device = device;
   q.k = 0; q.kp0 = 0; q.nkp = 1; q.diag = 0;
+  q.b_div = b_div;
+  q.split_cd = split_cd;
   q.vt_off = (long long)fields_cap * fs * (precision == OCCRI_FP64 ? 16 : 8);
   for (int d = 0; d < 3; ++d) q.D[d] = D[d];
   q.kint = kint;
@@ -604,6 +607,7 @@ void free_plan(Plan* p) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->scratch2) cudaFree(p->scratch2);
+  if (p->asm_scratch) cudaFree(p->asm_scratch);
   for (void* b : {p->gam, p->gpsi, p->cs_g, (void*)p->gkc, (void*)p->gcf, (void*)p->gacc})
     if (b) cudaFree(b);
   for (cudaEvent_t e : {p->ev_fork, p->ev_join, p->ev_y, p->ev_iso})
@@ -707,12 +711,12 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
       for (int kp0 = k; kp0 < p->nk; ++wave) {   // unordered pairs: (k, k), then k' > k
         const int diag = (kp0 == k) ? 1 : 0;
         const int nkp = diag ? 1 : std::min(p->nkp_wave, p->nk - kp0);
-        const int w = (int)(wave & 1);
+        const int w = p->nstreams == 2 ? (int)(wave & 1) : 0;
         cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
         bool sample = p->timing_every > 0 && (wave % p->timing_every == 0);
         if (sample)
           for (int i = 0; i < 4 && sample; ++i) sample = (ev[i] = take_event(p)) != nullptr;
-        if (sample) {   // wait for the other stream's work
+        if (sample && p->nstreams == 2) {   // wait for the other stream's work
           if (cudaEventRecord(p->ev_iso, st[w ^ 1]) != cudaSuccess ||
               cudaStreamWaitEvent(st[w], p->ev_iso, 0) != cudaSuccess)
             return OCCRI_ECUDA;
@@ -720,12 +724,12 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
         if (launch_pair_wave<T>(*p, k, kp0, nkp, diag, st[w], sc[w], sample ? ev : nullptr,
                                 p->ev_y) != cudaSuccess)
           return OCCRI_ECUDA;
-        launches += pair_wave_launches<T>(p->nocc);
+        launches += pair_wave_launches<T>(p->nocc, p->split_cd);
         const double nf = (double)wave_fields(p->nocc, nkp, diag);
         fields += nf;
         if (sample) {   // and keep the other stream waiting until this wave is done
-          if (cudaEventRecord(p->ev_iso, st[w]) != cudaSuccess ||
-              cudaStreamWaitEvent(st[w ^ 1], p->ev_iso, 0) != cudaSuccess)
+          if (p->nstreams == 2 && (cudaEventRecord(p->ev_iso, st[w]) != cudaSuccess ||
+                                   cudaStreamWaitEvent(st[w ^ 1], p->ev_iso, 0) != cudaSuccess))
             return OCCRI_ECUDA;
           p->ev_pending.push_back(Plan::TimedSpan{ev[0], ev[1], OCCRI_STAGE_PAIR_A, nf});
           p->ev_pending.push_back(Plan::TimedSpan{ev[1], ev[2], OCCRI_STAGE_PAIR_B, nf});
@@ -743,7 +747,7 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
     ++launches;
     if (p->tc) {
       if (launch_contract_tc(*p, s) != cudaSuccess) return OCCRI_ECUDA;
-      launches += 3;
+      launches += tc_plan_launches(p->tc);
     } else {
       if (launch_contract<T>(*p, s) != cudaSuccess) return OCCRI_ECUDA;
       for (int l = 0; l < 4; ++l)
@@ -964,6 +968,148 @@ int batch_capture(occri_batch* b) {
     batch_release_graph(b);
   }
   return st;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Launch configurations of the pair loop, timed on the plan's own buffers and cached per
+// (device, grid edge, nocc, precision, N_k, scratch capacity) for the life of the process.
+struct TuneCfg {
+  int nkp, nstreams, b_div, split_cd;
+};
+
+std::mutex g_tune_mu;
+std::vector<std::pair<std::vector<long long>, occri_tune_t>> g_tune_cache;
+
+std::vector<long long> tune_key(const Plan* p) {
+  return {p->device, p->N[0], p->nocc, p->precision, p->nk, p->nkp_cap};
+}
+
+void apply_tune(Plan* p, const occri_tune_t& t) {
+  p->nkp_wave = std::max(1, std::min(t.k_per_wave, p->nkp_cap));
+  p->nstreams = t.streams == 1 ? 1 : 2;
+  p->b_div = std::max(1, t.pass_b_div);
+  p->split_cd = t.split_cd ? 1 : 0;
+  p->tuned = 1;
+}
+
+bool tune_lookup(Plan* p, occri_tune_t* out) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const auto key = tune_key(p);
+  for (const auto& e : g_tune_cache)
+    if (e.first == key) {
+      if (out) *out = e.second;
+      return true;
+    }
+  return false;
+}
+
+// Microseconds per pair field of `reps` consecutive waves of the build's loop (the waves of
+// k = 0 with k' = 1, 2, ... wrapped over the mesh; diagonal waves where N_k = 1), under cfg.
+template <typename T>
+int tune_time(Plan* p, const TuneCfg& cfg, int reps, double* us_per_field) {
+  const TuneCfg keep{p->nkp_wave, p->nstreams, p->b_div, p->split_cd};
+  p->nkp_wave = cfg.nkp;
+  p->nstreams = cfg.nstreams;
+  p->b_div = cfg.b_div;
+  p->split_cd = cfg.split_cd;
+  cudaStream_t s = p->stream;
+  cudaStream_t st[2] = {s, p->aux};
+  void* sc[2] = {p->scratch, p->scratch2};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = OCCRI_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = OCCRI_ECUDA;
+  double fields = 0.0;
+  if (rc == OCCRI_OK) {
+    bool ok = cudaEventRecord(e0, s) == cudaSuccess && cudaEventRecord(p->ev_fork, s) == cudaSuccess &&
+              cudaStreamWaitEvent(p->aux, p->ev_fork, 0) == cudaSuccess &&
+              cudaEventRecord(p->ev_y, s) == cudaSuccess;
+    int kp0 = p->nk > 1 ? 1 : 0;
+    for (int w = 0; w < reps && ok; ++w) {
+      const int diag = p->nk > 1 ? 0 : 1;
+      const int nkp = diag ? 1 : std::min(cfg.nkp, p->nk - kp0);
+      const int sw = cfg.nstreams == 2 ? (w & 1) : 0;
+      ok = occri::launch_pair_wave<T>(*p, 0, kp0, nkp, diag, st[sw], sc[sw], nullptr,
+                                      p->ev_y) == cudaSuccess;
+      fields += (double)occri::wave_fields(p->nocc, nkp, diag);
+      if (!diag) {
+        kp0 += nkp;
+        if (kp0 >= p->nk) kp0 = 1;
+      }
+    }
+    ok = ok && cudaEventRecord(p->ev_join, p->aux) == cudaSuccess &&
+         cudaStreamWaitEvent(s, p->ev_join, 0) == cudaSuccess && cudaEventRecord(e1, s) == cudaSuccess;
+    float ms = 0.f;
+    ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      rc = OCCRI_ECUDA;
+    } else {
+      *us_per_field = 1e3 * (double)ms / std::max(1.0, fields);
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  p->nkp_wave = keep.nkp;
+  p->nstreams = keep.nstreams;
+  p->b_div = keep.b_div;
+  p->split_cd = keep.split_cd;
+  return rc;
+}
+
+template <typename T>
+int autotune(Plan* p, occri_tune_t* out) {
+  std::vector<int> nkps;
+  for (int v = 1; v < p->nkp_cap; v *= 2) nkps.push_back(v);
+  nkps.push_back(p->nkp_cap);
+  const bool can_fuse = occri::pair_wave_launches<T>(p->nocc, 0) == 4;
+  // enough waves for every candidate to cover the same fields (and both streams)
+  const int reps = std::max(4, 2 * p->nkp_cap);
+  const TuneCfg def{p->nkp_cap, 2, 1, 0};
+  double t_def = 0.0, best = 0.0;
+  TuneCfg pick = def;
+  int count = 0;
+  for (int nkp : nkps)
+    for (int ns = 1; ns <= 2; ++ns)
+      for (int bd = 1; bd <= 2; ++bd)
+        for (int sp = 0; sp <= (can_fuse ? 1 : 0); ++sp) {
+          const TuneCfg c{nkp, ns, bd, sp};
+          const int r = std::max(1, reps * p->nkp_cap / nkp);   // equal fields per candidate
+          double us = 0.0;
+          int st = tune_time<T>(p, c, 1, &us);   // warm-up (attributes, caches)
+          if (st == OCCRI_OK) st = tune_time<T>(p, c, r, &us);
+          if (st != OCCRI_OK) return st;
+          ++count;
+          const bool is_def = c.nkp == def.nkp && c.nstreams == def.nstreams &&
+                              c.b_div == def.b_div && c.split_cd == def.split_cd;
+          if (is_def) t_def = us;
+          if (count == 1 || us < best) {
+            best = us;
+            pick = c;
+          }
+        }
+  // the build leaves Y to be overwritten; the timed waves only touched scratch and Y
+  occri_tune_t t{};
+  t.k_per_wave = pick.nkp;
+  t.streams = pick.nstreams;
+  t.pass_b_div = pick.b_div;
+  t.split_cd = pick.split_cd;
+  t.us_per_field = best;
+  t.us_default = t_def;
+  t.candidates = count;
+  apply_tune(p, t);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const auto key = tune_key(p);
+    bool found = false;
+    for (auto& e : g_tune_cache)
+      if (e.first == key) {
+        e.second = t;
+        found = true;
+      }
+    if (!found) g_tune_cache.emplace_back(key, t);
+  }
+  if (out) *out = t;
+  return OCCRI_OK;
 }
 
 }  // namespace occri_impl
@@ -1334,6 +1480,7 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
   nkp = std::min(nkp, p->nk);
   nkp = std::max(1, std::min(nkp, 65535 / (nocc * nocc)));   // grid.y limit of the passes
   p->nkp_wave = nkp;
+  p->nkp_cap = nkp;
   p->fields_cap = nkp * nocc * nocc;
   const size_t orb = (size_t)p->nk * nocc * p->fs;
   {
@@ -1370,6 +1517,10 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     }
   }
   p->workspace_bytes = tot;
+  {
+    occri_tune_t t{};
+    if (occri_impl::tune_lookup(p, &t)) occri_impl::apply_tune(p, t);
+  }
   occri_plan* h = new (std::nothrow) occri_plan;
   if (!h) { free_plan(p); return OCCRI_ENOMEM; }
   h->p = p;
@@ -1395,10 +1546,11 @@ int occri_plan_info(const occri_plan* plan, occri_plan_info_t* info) {
   info->ng = p->ng;
   info->precision = p->precision;
   info->workspace_bytes = p->workspace_bytes;
-  info->fields_per_wave = p->fields_cap;
+  info->fields_per_wave = p->nkp_wave * p->nocc * p->nocc;
   info->launches_per_build = p->launches_per_build;
   info->contraction_tc = p->tc ? 1 : 0;
   info->tc_stages = tc_plan_stages(p->tc);
+  info->tc_flops_per_stage = p->tc ? occri::tc_flops_per_stage() : 0.0;
   return OCCRI_OK;
 }
 
@@ -1476,6 +1628,121 @@ int occri_k_build(occri_plan* plan, const void* C_dev, void* KC_dev, void* K_dev
   return p->precision == OCCRI_FP64
              ? occri_impl::build_impl<double>(p, (const double2*)C_dev, KC_dev, K_dev, Ex_dev)
              : occri_impl::build_impl<float>(p, (const double2*)C_dev, KC_dev, K_dev, Ex_dev);
+}
+
+int occri_plan_autotune(occri_plan* plan, int flags, occri_tune_t* chosen) {
+  if (!plan || (flags & ~OCCRI_TUNE_FORCE)) return OCCRI_EINVAL;
+  Plan* p = plan->p;
+  occri::DeviceGuard guard(p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
+  occri_tune_t t{};
+  if (!(flags & OCCRI_TUNE_FORCE) && occri_impl::tune_lookup(p, &t)) {
+    occri_impl::apply_tune(p, t);
+    t.candidates = 0;
+    if (chosen) *chosen = t;
+    return OCCRI_OK;
+  }
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return OCCRI_ECUDA;
+  }
+  const int st = p->precision == OCCRI_FP64 ? occri_impl::autotune<double>(p, chosen)
+                                            : occri_impl::autotune<float>(p, chosen);
+  if (st != OCCRI_OK) return st;
+  // timing may have left a device status (none is expected); report it like a build would
+  return occri_plan_sync(plan, nullptr);
+}
+
+int occri_plan_set_tuning(occri_plan* plan, const occri_tune_t* cfg) {
+  if (!plan || !cfg) return OCCRI_EINVAL;
+  if (cfg->k_per_wave < 1 || (cfg->streams != 1 && cfg->streams != 2) ||
+      (cfg->pass_b_div != 1 && cfg->pass_b_div != 2) || (cfg->split_cd != 0 && cfg->split_cd != 1))
+    return OCCRI_EINVAL;
+  Plan* p = plan->p;
+  occri_impl::apply_tune(p, *cfg);
+  p->tuned = 0;
+  return OCCRI_OK;
+}
+
+int occri_plan_tuning(const occri_plan* plan, occri_tune_t* current) {
+  if (!plan || !current) return OCCRI_EINVAL;
+  const Plan* p = plan->p;
+  *current = occri_tune_t{};
+  current->k_per_wave = p->nkp_wave;
+  current->streams = p->nstreams;
+  current->pass_b_div = p->b_div;
+  current->split_cd = p->split_cd;
+  current->candidates = p->tuned ? -1 : 0;
+  return OCCRI_OK;
+}
+
+int occri_k_assemble_paper(occri_plan* plan, int ncol, const void* S_dev, const void* C_dev,
+                           const void* KC_dev, void* K_dev) {
+  if (!plan || !S_dev || !C_dev || !KC_dev || !K_dev) return OCCRI_EINVAL;
+  Plan* p = plan->p;
+  if (ncol < 1 || ncol > p->nao) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
+  const cudaError_t e = occri::launch_assemble_paper(*p, ncol, (const double2*)S_dev,
+                                                     (const double2*)C_dev, (const double2*)KC_dev,
+                                                     (double2*)K_dev);
+  if (e == cudaErrorMemoryAllocation) return OCCRI_ENOMEM;
+  return e == cudaSuccess ? OCCRI_OK : OCCRI_ECUDA;
+}
+
+int occri_k_build_conduction(occri_plan* plan_all, occri_plan* plan_r, const void* C_all_dev,
+                             void* KCr_dev) {
+  if (!plan_all || !plan_r || !C_all_dev || !KCr_dev || plan_all == plan_r) return OCCRI_EINVAL;
+  Plan* pa = plan_all->p;
+  Plan* pr = plan_r->p;
+  // the two plans must describe the same cell, k-mesh, basis, grid, kernel and precision
+  bool same = pa->nk == pr->nk && pa->nao == pr->nao && pa->natm == pr->natm &&
+              pa->nshell == pr->nshell && pa->precision == pr->precision &&
+              pa->device == pr->device && pa->nocc > pr->nocc &&
+              pa->kernel.kind == pr->kernel.kind && pa->kernel.omega == pr->kernel.omega &&
+              pa->g0_4pi == pr->g0_4pi && pa->rc == pr->rc;
+  for (int d = 0; d < 3; ++d) same = same && pa->N[d] == pr->N[d] && pa->D[d] == pr->D[d];
+  for (int i = 0; i < 3 && same; ++i)
+    for (int j = 0; j < 3; ++j) same = same && pa->lat[i][j] == pr->lat[i][j];
+  same = same && pa->kint_h == pr->kint_h;
+  if (!same) return OCCRI_EINVAL;
+  occri::DeviceGuard guard(pa->device);
+  if (!guard.ok) return OCCRI_ECUDA;
+  const int nr = pr->nocc, nocc = pa->nocc - nr;
+  const long long rows = (long long)pa->nk * pa->nao;
+  void* buf = nullptr;
+  const size_t b_all = sizeof(double2) * (size_t)rows * pa->nocc;
+  const size_t b_r = sizeof(double2) * (size_t)rows * nr;
+  if (occri::device_malloc(&buf, b_all + 2 * b_r) != cudaSuccess) {
+    cudaGetLastError();
+    return OCCRI_ENOMEM;
+  }
+  double2* kc_all = (double2*)buf;
+  double2* c_r = (double2*)((unsigned char*)buf + b_all);
+  double2* kc_r = (double2*)((unsigned char*)buf + b_all + b_r);
+  int st = OCCRI_OK;
+  // both builds run on plan_all's stream, one after the other
+  cudaStream_t keep = pr->stream;
+  pr->stream = pa->stream;
+  if (occri::launch_gather_cols((const double2*)C_all_dev, c_r, rows, nocc, nr, pa->stream) !=
+      cudaSuccess)
+    st = OCCRI_ECUDA;
+  if (st == OCCRI_OK) st = occri_k_build(plan_all, C_all_dev, kc_all, nullptr, nullptr);
+  if (st == OCCRI_OK) st = occri_k_build(plan_r, c_r, kc_r, nullptr, nullptr);
+  if (st == OCCRI_OK &&
+      occri::launch_band_diff(kc_all, kc_r, (double2*)KCr_dev, rows, nocc, nr, pa->stream) !=
+          cudaSuccess)
+    st = OCCRI_ECUDA;
+  if (cudaStreamSynchronize(pa->stream) != cudaSuccess && st == OCCRI_OK) st = OCCRI_ECUDA;
+  pr->stream = keep;
+  cudaFree(buf);
+  if (st != OCCRI_OK) {
+    cudaGetLastError();
+    return st;
+  }
+  const int s1 = occri_plan_sync(plan_all, nullptr);
+  const int s2 = occri_plan_sync(plan_r, nullptr);
+  return s1 != OCCRI_OK ? s1 : s2;
 }
 
 int occri_k_build_once(const occri_cell* cell, const occri_kmesh* kmesh,

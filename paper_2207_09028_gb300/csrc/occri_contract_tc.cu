@@ -7,7 +7,7 @@
 // (e^{ik.S} = 1 there). Then conj(chi_{mu k}(r)) = sum_l e^{-ik.L_l} Phi_mu(r - L_l), and
 //   K_{mu i}(k) = scale sum_l e^{-ik.L_l} P_l[mu, (k,i)],   P_l = sum_r Phi_mu(r - L_l) Y_ik(r).
 // P_l is a real-by-complex GEMM: rows mu (128 AOs per tile, sorted by screening radius so that
-// tight AOs share tiles), columns the (Re, Im) of 128 (k, i) pairs (N = 256), reduction over the
+// tight AOs share tiles), columns the (Re, Im) of 96 (k, i) pairs (N = 192), reduction over the
 // cell's grid points. A stage is one tile of 32 grid points r at one offset l: A = Phi at the
 // points r - L_l, B = Y at the points r. Both operands are split hi + lo in FP16 (power-of-two
 // scalings per row and column), and three FP16 MMAs (hi.hi + hi.lo + lo.hi) with FP32
@@ -21,7 +21,7 @@
 //   contract_tc_kernel              the GEMM over the slab's stages: one producer thread copies
 //                                   each stage's A and B blocks with the bulk-copy engine, one
 //                                   thread issues the MMAs into one of two tensor-memory
-//                                   accumulators, and 16 epilogue warps take every stage's
+//                                   accumulators, and 12 epilogue warps take every stage's
 //                                   product out at once (times the phases e^{-ik.L_l}) into
 //                                   FP32 running sums held in registers, which go to K_{mu i}
 //                                   by FP64 atomics. Each product leaves tensor memory after
@@ -38,6 +38,7 @@
 #include <numeric>
 #include <vector>
 
+#include "fft_reg.cuh"
 #include "occri_device.cuh"
 #include "occri_internal.h"
 #include "occri_tc.cuh"
@@ -45,15 +46,18 @@
 namespace occri {
 namespace tcc {
 
+namespace pk = fft::pk;
+using pk::u64;
+
 constexpr int kM = 128;             // AO rows per tile (TMEM lanes)
-constexpr int kNC = 128;            // complex (k, i) columns per tile
+constexpr int kNC = 96;             // complex (k, i) columns per tile (a multiple of 32)
 constexpr int kN = 2 * kNC;         // real columns (Re, Im)
 constexpr int kKP = 32;             // grid points per stage (MMA K, two slices of 16)
 constexpr int kStages = 4;
 constexpr int kFlushTiles = 16;     // point tiles summed in FP32 before the FP64 atomics
 constexpr int kSlabBlocks = 1 << 18;     // A blocks generated at a time (4 GiB)
 constexpr int kMaxImg = 128;        // supercell images of one stage, all atoms
-constexpr int kEWarps = 16;         // epilogue: four per lane quarter, 32 complex columns each
+constexpr int kEWarps = kNC / 8;    // epilogue: per 32 complex columns one warp per lane quarter
 constexpr int kEThreads = 32 * kEWarps;
 constexpr int kThreads = 64 + kEThreads;     // + MMA warp and bulk-copy warp
 constexpr int kGenThreads = 256;             // threads of the block-generation kernel
@@ -65,6 +69,9 @@ constexpr int kABlock = 2 * kABytes;          // one generated A block (hi then 
 constexpr int kBBlock = 2 * kBBytes;          // one converted Y block (hi then lo): 32 KB
 constexpr int kStageBytes = kABlock + kBBlock;
 constexpr uint32_t kIdesc = tc::idesc_f16_f32(kM, kN);
+constexpr int kPhaseRow = 3 * kNC;      // floats of the phases of one (column tile, l)
+constexpr int kAccCols = 256;           // tensor-memory columns between the two accumulators
+static_assert(kNC % 32 == 0 && kN <= kAccCols, "column tile");
 // Descriptor strides of the no-swizzle K-major layout used below: inside one 16-wide K slice,
 // an 8-row group holds its two 8-column core matrices at +0 and +128 bytes and groups follow
 // every 256 bytes.
@@ -104,10 +111,11 @@ struct TcParams {
   const int* perm;               // tile row -> AO (or -1)
   const float* reach;            // [tile][natm] largest screening radius of the tile's shells
   const float4* rtiles;          // [ntile_r] centre (x, y, z) and radius of the point tile
-  const float2* phase;           // [ct][nl][128] e^{-ik.L_l} of the tile's columns (0 past ncol)
+  const float* phase;            // [ct][nl][3][128] cos, sin, -sin of the phase e^{-ik.L_l}
+                                 // of the tile's columns (0 past ncol)
   const uint2* stages;           // the slab's stages, CTA by CTA
   const long long* cta_stage0;   // stages of CTA b: [cta_stage0[b], cta_stage0[b+1])
-  const unsigned* colmax;        // [ncol] max over r of |Re Y| + |Im Y| (float bits)
+  const double* colf;            // [ncol] 2^(e - 13): undoes the column scaling of Y (e as below)
   double2* kc;
   double scale;
   float lat[9], sc[9], scinv[9]; // rows a_d; supercell rows D_d a_d; cart -> supercell frac
@@ -374,12 +382,20 @@ __global__ void __launch_bounds__(kGenThreads) gen_blocks_kernel(TcParams p) {
   }
 }
 
+// The phases of each stage's (column tile, l) row travel with the stage, in a ring of their
+// own: the A/B slot is free once the MMA is done, the phases only once the epilogue is.
+constexpr int kPhRing = 8;
+constexpr int kPhBytes = kPhaseRow * 4;
+
 struct __align__(16) Smem {
   unsigned long long full[kStages], empty[kStages], acc_full[2], acc_empty[2], done;
+  unsigned long long ph_full[kPhRing], ph_empty[kPhRing];
   uint32_t tmem_slot;
 };
 
-static_assert(kStages * kStageBytes + sizeof(Smem) <= 227 * 1024, "shared memory of one CTA");
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + (size_t)kPhRing * kPhBytes + sizeof(Smem);
+static_assert(kSmemBytes <= 227 * 1024, "shared memory of one CTA");
+static_assert(kPhBytes % 16 == 0, "bulk copies of whole 16-byte pieces");
 
 __device__ __forceinline__ int st_ablk(uint2 e) { return (int)(e.x & 0x3fffffu); }
 __device__ __forceinline__ int st_l(uint2 e) { return (int)(e.x >> 22); }
@@ -401,7 +417,8 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
 __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* stage0 = smraw;   // kStages x (A hi | A lo | B hi | B lo)
-  Smem& sm = *reinterpret_cast<Smem*>(smraw + kStages * kStageBytes);
+  float* ph0 = reinterpret_cast<float*>(smraw + kStages * kStageBytes);   // kPhRing phase rows
+  Smem& sm = *reinterpret_cast<Smem*>(smraw + kStages * kStageBytes + kPhRing * kPhBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long s_begin = p.cta_stage0[blockIdx.x];
   const long long nst = p.cta_stage0[blockIdx.x + 1] - s_begin;
@@ -417,13 +434,17 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
       tc::mbar_init(tc::smem_u32(&sm.acc_empty[b]), kEThreads);
     }
     tc::mbar_init(tc::smem_u32(&sm.done), 1);
+    for (int j = 0; j < kPhRing; ++j) {
+      tc::mbar_init(tc::smem_u32(&sm.ph_full[j]), 1);
+      tc::mbar_init(tc::smem_u32(&sm.ph_empty[j]), kEWarps);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(&sm.tmem_slot), 512);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tmem = sm.tmem_slot;   // accumulators: columns [0, 256) and [256, 512)
+  const uint32_t tmem = sm.tmem_slot;   // accumulators: columns [0, kN) and [256, 256 + kN)
 
   if (warp == 0) {
     // ------------------------------------------------------------ MMA issuer
@@ -446,17 +467,24 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
         tc::tc_fence_after();
         const uint32_t a_hi = tc::smem_u32(stage0 + (size_t)s * kStageBytes);
         const uint32_t a_lo = a_hi + kABytes, b_hi = a_hi + kABlock, b_lo = b_hi + kBBytes;
-        const uint32_t t_acc = tmem + (uint32_t)(ab * kN);
+        const uint32_t t_acc = tmem + (uint32_t)(ab * kAccCols);
+        // the two small cross terms of both K slices first, the hi x hi products last: each
+        // accumulation into tensor memory rounds toward zero at the running sum's magnitude,
+        // so only the last two additions happen at full magnitude
+        uint64_t ah[2], al[2], bh[2], bl[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-          const uint64_t ah = tc::smem_desc(a_hi + k * kASlice, kLBO, kSBO);
-          const uint64_t al = tc::smem_desc(a_lo + k * kASlice, kLBO, kSBO);
-          const uint64_t bh = tc::smem_desc(b_hi + k * kBSlice, kLBO, kSBO);
-          const uint64_t bl = tc::smem_desc(b_lo + k * kBSlice, kLBO, kSBO);
-          tc::mma_f16(t_acc, ah, bh, kIdesc, k == 0 ? 0u : 1u);
-          tc::mma_f16(t_acc, ah, bl, kIdesc, 1u);
-          tc::mma_f16(t_acc, al, bh, kIdesc, 1u);
+          ah[k] = tc::smem_desc(a_hi + k * kASlice, kLBO, kSBO);
+          al[k] = tc::smem_desc(a_lo + k * kASlice, kLBO, kSBO);
+          bh[k] = tc::smem_desc(b_hi + k * kBSlice, kLBO, kSBO);
+          bl[k] = tc::smem_desc(b_lo + k * kBSlice, kLBO, kSBO);
         }
+        tc::mma_f16(t_acc, ah[0], bl[0], kIdesc, 0u);
+        tc::mma_f16(t_acc, al[0], bh[0], kIdesc, 1u);
+        tc::mma_f16(t_acc, ah[1], bl[1], kIdesc, 1u);
+        tc::mma_f16(t_acc, al[1], bh[1], kIdesc, 1u);
+        tc::mma_f16(t_acc, ah[0], bh[0], kIdesc, 1u);
+        tc::mma_f16(t_acc, ah[1], bh[1], kIdesc, 1u);
         tc::mma_commit(tc::smem_u32(&sm.empty[s]));
         tc::mma_commit(tc::smem_u32(&sm.acc_full[ab]));
       }
@@ -479,7 +507,18 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
           good = false;
           break;
         }
+        const int j = (int)(sidx % kPhRing);
+        const long long v = sidx / kPhRing;
+        if (v > 0 && !tc::mbar_wait(tc::smem_u32(&sm.ph_empty[j]), (unsigned)((v - 1) & 1),
+                                    p.wait_ns)) {
+          good = false;
+          break;
+        }
         const uint2 e = stages[sidx];
+        const uint32_t pb = tc::smem_u32(&sm.ph_full[j]);
+        tc::mbar_expect_tx(pb, kPhBytes);
+        tc::bulk_g2s(tc::smem_u32(ph0 + (size_t)j * kPhaseRow),
+                     p.phase + ((size_t)st_ct(e) * p.nl + st_l(e)) * kPhaseRow, kPhBytes, pb);
         const uint32_t fb = tc::smem_u32(&sm.full[s]);
         tc::mbar_expect_tx(fb, kStageBytes);
         const uint32_t dst = tc::smem_u32(stage0 + (size_t)s * kStageBytes);
@@ -487,10 +526,18 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
         tc::bulk_g2s(dst + kABlock, p.yh + ((size_t)st_ct(e) * p.ntile_r + st_rt(e)) * kBBlock,
                      kBBlock, fb);
       }
-      // no copy may be in flight when the CTA leaves: wait for the last ones issued
+      // no copy may be in flight when the CTA leaves: wait for the last ones issued (a stage
+      // whose phase copy was issued also had its A/B copies issued, and the other way round,
+      // except when the loop stopped between the two waits above)
       for (long long last = std::max<long long>(0, sidx - kStages); last < sidx; ++last) {
         const int s = (int)(last % kStages);
         if (!tc::mbar_wait(tc::smem_u32(&sm.full[s]), (unsigned)((last / kStages) & 1),
+                           p.wait_ns))
+          good = false;
+      }
+      for (long long last = std::max<long long>(0, sidx - kPhRing); last < sidx; ++last) {
+        const int j = (int)(last % kPhRing);
+        if (!tc::mbar_wait(tc::smem_u32(&sm.ph_full[j]), (unsigned)((last / kPhRing) & 1),
                            p.wait_ns))
           good = false;
       }
@@ -504,11 +551,13 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
     const int cs = ew >> 2;                     // complex columns [32 cs, 32 cs + 32)
     const int row = 32 * quarter + lane;
     const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
-    float sr[32], si[32];
+    // running sums of the warp's 32 complex columns as packed pairs of columns:
+    // SR[p] = (Re c_2p, Re c_2p+1), SI[p] = (Im c_2p, Im c_2p+1)
+    u64 SR[16], SI[16];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) { sr[j] = 0.f; si[j] = 0.f; }
+    for (int j = 0; j < 16; ++j) { SR[j] = 0ull; SI[j] = 0ull; }
     bool good = true;
-    for (long long sidx = 0; sidx < nst; ++sidx) {
+    for (int sidx = 0; sidx < (int)nst; ++sidx) {
       const uint2 e = stages[sidx];
       const int ab = (int)(sidx & 1);
       const int flags = st_flags(e), ct = st_ct(e), l = st_l(e);
@@ -520,25 +569,50 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
       tc::tc_fence_after();
       if (flags & kFirstSum) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) { sr[j] = 0.f; si[j] = 0.f; }
+        for (int j = 0; j < 16; ++j) { SR[j] = 0ull; SI[j] = 0ull; }
       }
-      const float2* ph = p.phase + ((size_t)ct * p.nl + l) * kNC + 32 * cs;
-      const uint32_t ta = tmem + (uint32_t)(ab * kN) + lane_off + (uint32_t)(64 * cs);
+      // cos, sin and -sin of the phases of the warp's columns, from the stage's slot of the
+      // phase ring (copied in by the producer with the stage's operands)
+      const int jp = sidx % kPhRing;
+      if (!warp_wait(tc::smem_u32(&sm.ph_full[jp]), (unsigned)((sidx / kPhRing) & 1), p.wait_ns,
+                     lane)) {
+        good = false;
+        break;
+      }
+      const u64* wc = reinterpret_cast<const u64*>(ph0 + (size_t)jp * kPhaseRow) + 16 * cs;
+      const u64* ws = wc + kNC / 2;
+      const u64* wn = wc + kNC;
+      const uint32_t ta = tmem + (uint32_t)(ab * kAccCols) + lane_off + (uint32_t)(64 * cs);
+      // eight groups of 4 complex columns (Re at ta + 32 (q/4) + 4 (q%4), Im 16 columns on),
+      // software-pipelined: the tensor-memory and phase loads of group q + 1 are in flight
+      // while group q is added in
+      uint32_t vr[2][4], vi[2][4];
+      auto load = [&](int q, int b) {
+        const uint32_t tq = ta + 32 * (q >> 2) + 4 * (q & 3);
+        tc::tmem_ld4(tq, vr[b]);
+        tc::tmem_ld4(tq + 16, vi[b]);
+      };
+      load(0, 0);
+      tc::tmem_wait_ld();
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {             // 16 real columns = 8 complex per load
-        uint32_t va[16];
-        tc::tmem_ld16(ta + 16 * q, va);
-        tc::tmem_wait_ld();
+      for (int q = 0; q < 8; ++q) {
+        const int b = q & 1;
+        if (q + 1 < 8) load(q + 1, b ^ 1);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float2 w = __ldg(ph + 8 * q + j);
-          const float ar = __uint_as_float(va[2 * j]), ai = __uint_as_float(va[2 * j + 1]);
-          sr[8 * q + j] += w.x * ar - w.y * ai;
-          si[8 * q + j] += w.x * ai + w.y * ar;
+        for (int u = 0; u < 2; ++u) {
+          const int pi = 2 * q + u;
+          const u64 ar = pk::pack(__uint_as_float(vr[b][2 * u]), __uint_as_float(vr[b][2 * u + 1]));
+          const u64 ai = pk::pack(__uint_as_float(vi[b][2 * u]), __uint_as_float(vi[b][2 * u + 1]));
+          const u64 c = wc[pi], sn = ws[pi], ns = wn[pi];
+          SR[pi] = pk::fma(ns, ai, pk::fma(c, ar, SR[pi]));
+          SI[pi] = pk::fma(sn, ar, pk::fma(c, ai, SI[pi]));
         }
+        if (q + 1 < 8) tc::tmem_wait_ld();
       }
       tc::tc_fence_before();
       tc::mbar_arrive(tc::smem_u32(&sm.acc_empty[ab]));
+      __syncwarp();   // every lane has read the phase slot
+      if (lane == 0) tc::mbar_arrive(tc::smem_u32(&sm.ph_empty[jp]));
       if (flags & kToGlobal) {
         const int tl = (int)((e.y >> 26) & 3u);
         const int mu = p.perm[tl * kM + row];
@@ -548,14 +622,14 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
           for (int j = 0; j < 32; ++j) {
             const int c = ct * kNC + 32 * cs + j;
             if (c >= p.ncol) continue;
-            const float mx = __uint_as_float(p.colmax[c]);
-            int e2 = 0;
-            if (mx > 0.f) frexpf(mx, &e2);
-            const double f = rf * ldexp(1.0, e2 - 13);
+            const double f = rf * p.colf[c];
             const int k = c / p.nocc, i = c - k * p.nocc;
+            float r0, r1, i0, i1;
+            pk::unpack(SR[j >> 1], r0, r1);
+            pk::unpack(SI[j >> 1], i0, i1);
             double* dst = reinterpret_cast<double*>(p.kc + ((size_t)k * p.nao + mu) * p.nocc + i);
-            atomicAdd(dst, f * (double)sr[j]);
-            atomicAdd(dst + 1, f * (double)si[j]);
+            atomicAdd(dst, f * (double)((j & 1) ? r1 : r0));
+            atomicAdd(dst + 1, f * (double)((j & 1) ? i1 : i0));
           }
         }
       }
@@ -572,8 +646,9 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
 }
 
 // max over the points of |Re| + |Im| of every (k, i) field of Y, as float bits
+// and colf = 2^(e - 13), e the exponent of that max (frexp)
 __global__ void colmax_kernel(const float2* __restrict__ Y, unsigned* __restrict__ colmax,
-                              long long ng, long long fs) {
+                              double* __restrict__ colf, long long ng, long long fs) {
   const int c = blockIdx.x;
   float m = 0.f;
   for (long long q = threadIdx.x; q < ng; q += blockDim.x) {
@@ -587,11 +662,18 @@ __global__ void colmax_kernel(const float2* __restrict__ Y, unsigned* __restrict
   if (threadIdx.x < 32) {
     m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) colmax[c] = __float_as_uint(m);
+    if (threadIdx.x == 0) {
+      colmax[c] = __float_as_uint(m);
+      int e2 = 0;
+      if (m > 0.f) frexpf(m, &e2);
+      colf[c] = ldexp(1.0, e2 - 13);
+    }
   }
 }
 
-// Y -> FP16 hi/lo B blocks: block (ct, rt) row 2c + {0: Re, 1: Im} of column c of the tile,
+// Y -> FP16 hi/lo B blocks: in block (ct, rt), column c of the tile is row 32 (c / 16) + c % 16
+// (Re) and that row + 16 (Im), so that a tensor-memory load of 8 consecutive columns gives
+// the real (or imaginary) parts of 8 consecutive columns;
 // K index = point q - 32 rt; scaled by 2^(13 - e) with e the column's max exponent.
 __global__ void convert_y_kernel(const float2* __restrict__ Y, const unsigned* __restrict__ colmax,
                                  unsigned char* __restrict__ yh, int ncol, int n_ct, int ntile_r,
@@ -628,7 +710,9 @@ __global__ void convert_y_kernel(const float2* __restrict__ Y, const unsigned* _
     split2(xi[0], xi[1], ih.x, il.x); split2(xi[2], xi[3], ih.y, il.y);
     split2(xi[4], xi[5], ih.z, il.z); split2(xi[6], xi[7], ih.w, il.w);
     unsigned char* blk = yh + ((size_t)ct * ntile_r + rt) * kBBlock;
-    const int o_re = op_off(2 * cl, g * 8, kBSlice), o_im = op_off(2 * cl + 1, g * 8, kBSlice);
+    // rows of the 16-column group of cl: Re of its columns, then Im
+    const int r_re = 32 * (cl >> 4) + (cl & 15);
+    const int o_re = op_off(r_re, g * 8, kBSlice), o_im = op_off(r_re + 16, g * 8, kBSlice);
     *reinterpret_cast<uint4*>(blk + o_re) = rh;
     *reinterpret_cast<uint4*>(blk + o_im) = ih;
     *reinterpret_cast<uint4*>(blk + kBBytes + o_re) = rl;
@@ -690,9 +774,12 @@ struct TcPlan {
   unsigned char* ablk = nullptr;
   uint2* blocks = nullptr;
   unsigned* colmax = nullptr;
+  double* colf = nullptr;
 };
 
 long long tc_plan_stages(const TcPlan* t) { return t ? t->stages : 0; }
+int tc_plan_launches(const TcPlan* t) { return t ? 2 + 2 * (int)t->slabs.size() : 0; }
+double tc_flops_per_stage() { return 6.0 * tcc::kM * tcc::kN * tcc::kKP; }
 
 void tc_plan_free(TcPlan* t) {
   if (!t) return;
@@ -976,7 +1063,6 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
       slab.stage0 = (long long)stages.size();
       slab.cta0 = (int)cta_stage0.size();
       const int ncta = std::max(1, std::min<int>(nsm, (int)(st.size() / 64 + 1)));
-      long long cut = 0;
       int b = 0;
       cta_stage0.push_back(slab.stage0);
       for (size_t i = 0; i < st.size(); ++i) {
@@ -986,7 +1072,6 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
           cta_stage0.push_back(slab.stage0 + (long long)i + 1);
           ++b;
         }
-        (void)cut;
       }
       slab.ncta = b + 1;
       stages.insert(stages.end(), st.begin(), st.end());
@@ -996,7 +1081,7 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
   }
   cta_stage0.push_back((long long)stages.size());
   // per (column tile, l): the phases e^{-ik.L_l} of the tile's 128 columns
-  std::vector<float2> phase((size_t)q.n_ct * NL * kNC, make_float2(0.f, 0.f));
+  std::vector<float> phase((size_t)q.n_ct * NL * kPhaseRow, 0.f);
   {
     const int Dc = NL;
     for (int ct = 0; ct < q.n_ct; ++ct)
@@ -1011,8 +1096,10 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
             num += (long long)p->kint_h[3 * k + d] * l3[d] * (Dc / p->D[d]);
           num %= Dc;
           const double ang = -2.0 * 3.14159265358979323846 * (double)num / (double)Dc;
-          phase[((size_t)ct * NL + l) * kNC + j] =
-              make_float2((float)std::cos(ang), (float)std::sin(ang));
+          float* row = &phase[((size_t)ct * NL + l) * kPhaseRow];
+          row[j] = (float)std::cos(ang);
+          row[kNC + j] = (float)std::sin(ang);
+          row[2 * kNC + j] = -(float)std::sin(ang);
         }
       }
   }
@@ -1023,7 +1110,7 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
   TcShell* d_sh = nullptr; int* d_ts = nullptr; float* d_rs = nullptr; double* d_rf = nullptr;
   int* d_perm = nullptr; float* d_reach = nullptr; float4* d_rt = nullptr;
   uint2* d_st = nullptr; long long* d_s0 = nullptr; uint2* d_bl = nullptr;
-  float* d_pts = nullptr; float* d_tb = nullptr; float2* d_ph = nullptr;
+  float* d_pts = nullptr; float* d_tb = nullptr; float* d_ph = nullptr;
   chk(put(&d_pts, pts, total)); t->bufs.push_back(d_pts);
   chk(put(&d_tb, tbase, total)); t->bufs.push_back(d_tb);
   chk(put(&d_sh, shells, total)); t->bufs.push_back(d_sh);
@@ -1048,7 +1135,11 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
     chk(device_malloc(&b, ab)); t->bufs.push_back(b); t->ablk = (unsigned char*)b;
     b = nullptr;
     *total += (size_t)q.ncol * 4;
-    chk(device_malloc(&b, (size_t)q.ncol * 4)); t->bufs.push_back(b); t->colmax = (unsigned*)b;
+    const size_t cm = ((size_t)q.ncol * 4 + 15) / 16 * 16;
+    *total += (size_t)q.ncol * 8;
+    chk(device_malloc(&b, cm + (size_t)q.ncol * 8)); t->bufs.push_back(b);
+    t->colmax = (unsigned*)b;
+    t->colf = b ? (double*)((unsigned char*)b + cm) : nullptr;
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1057,12 +1148,12 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
   }
   q.yh = t->yh; q.ablk = t->ablk; q.shells = d_sh; q.tile_shell0 = d_ts; q.rowscale = d_rs;
   q.rowf = d_rf; q.perm = d_perm; q.reach = d_reach; q.rtiles = d_rt; q.stages = d_st;
-  q.cta_stage0 = d_s0; q.colmax = t->colmax; q.pts = d_pts; q.tbase = d_tb; q.phase = d_ph;
+  q.cta_stage0 = d_s0; q.colf = t->colf; q.pts = d_pts; q.tbase = d_tb; q.phase = d_ph;
   q.ntile = ntile;
   q.nentries = (int)shells.size();
   t->blocks = d_bl;
   t->stages = total_st;
-  t->smem = (size_t)kStages * kStageBytes + sizeof(Smem);
+  t->smem = kSmemBytes;
   p->tc = t;
   return OCCRI_OK;
 }
@@ -1077,7 +1168,7 @@ cudaError_t launch_contract_tc(const Plan& p, cudaStream_t s) {
   q.status = p.status;
   q.wait_ns = p.wait_ns;
   const float2* Y = (const float2*)p.Y;
-  colmax_kernel<<<q.ncol, 256, 0, s>>>(Y, t->colmax, p.ng, p.fs);
+  colmax_kernel<<<q.ncol, 256, 0, s>>>(Y, t->colmax, t->colf, p.ng, p.fs);
   convert_y_kernel<<<8 * 152, 256, 0, s>>>(Y, t->colmax, t->yh, q.ncol, q.n_ct, q.ntile_r, p.ng,
                                            p.fs);
   static DeviceCache attr;

@@ -92,6 +92,8 @@ struct PairParams {
   double g0;                 // value at G+q = 0, in units of 4 pi
   double dg0;                // d g0 / d omega, in units of 4 pi
   double rc;                 // truncation radius of OCCRI_COULOMB_TRUNC
+  int b_div;                 // pass-B CTAs = resident slots / b_div (set by the autotuner)
+  int split_cd;              // 1: passes C and D even where the fused pass CD applies
   // FP32 copies (hi/lo for the metric) made on the host, so FP32 kernels never
   // convert from double on the device (FP64 issue is 1/64 rate)
   float gh[6], gl[6];
@@ -119,6 +121,12 @@ struct Plan {
   int fields_cap;            // pair fields held by the transform scratch
   long long fs;              // scratch field stride in points (ng rounded up to 64)
   int nkp_wave;              // k' per wave
+  int nkp_cap = 1;           // k' per wave the scratch buffers hold
+  // launch configuration of the pair loop (occri_plan_autotune may change it)
+  int nstreams = 2;          // 2: consecutive waves alternate between two streams
+  int b_div = 1;             // pass-B CTAs = resident slots / b_div
+  int split_cd = 0;          // 1: passes C and D instead of the fused pass CD
+  int tuned = 0;             // 1: the configuration came from the autotuner (or its cache)
   std::vector<int> shells_by_l[4];
 
   // device tables
@@ -171,6 +179,8 @@ struct Plan {
   int* status = nullptr;     // [2]: first device error code, k index
   bool have_kc = false;
   TcPlan* tc = nullptr;      // OCCRI_MIXED_TC: the tensor-core contraction's tables
+  void* asm_scratch = nullptr;   // paper-form assembly: M, T, D (grown on demand)
+  size_t asm_bytes = 0;
   double* ao_norm = nullptr; // [nao] N_lm per AO
   void* cs = nullptr;        // scaled coefficients (see AOParams::cs)
 
@@ -251,8 +261,8 @@ cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, do
 // fused pass. A wave launches the kernel-table fill and passes A and B, then the fused
 // pass or passes C and D.
 constexpr int kFusedCdNoc = 8;
-template <typename T> constexpr int pair_wave_launches(int nocc) {
-  return (std::is_same<T, float>::value && nocc <= kFusedCdNoc) ? 4 : 5;
+template <typename T> constexpr int pair_wave_launches(int nocc, int split_cd = 0) {
+  return (std::is_same<T, float>::value && nocc <= kFusedCdNoc && !split_cd) ? 4 : 5;
 }
 
 // scratch per wave (MB): how many k' one wave takes when nocc^2 fields of a k' fit
@@ -272,7 +282,16 @@ cudaError_t launch_widen(const Plan& p, void* out, cudaStream_t s);
 int tc_plan_create(Plan* p, const std::vector<ShellDev>& shells, const double* xyz,
                    const std::vector<double>& rcut, size_t* total);
 void tc_plan_free(TcPlan* t);
-long long tc_plan_stages(const TcPlan* t);   // stages of one contraction (0 without a plan)
+long long tc_plan_stages(const TcPlan* t);
+int tc_plan_launches(const TcPlan* t);      // kernels one tensor-core contraction launches
+double tc_flops_per_stage();
+// Paper-form assembly and conduction-band helpers (occri_assemble.cu), on the plan's stream.
+cudaError_t launch_assemble_paper(Plan& p, int ncol, const double2* S, const double2* C,
+                                  const double2* KC, double2* K);
+cudaError_t launch_gather_cols(const double2* all, double2* cr, long long rows, int nocc, int nr,
+                               cudaStream_t s);
+cudaError_t launch_band_diff(const double2* all, const double2* rr, double2* out, long long rows,
+                             int nocc, int nr, cudaStream_t s);   // MMA flops of one stage of the tensor-core contraction   // stages of one contraction (0 without a plan)
 cudaError_t launch_contract_tc(const Plan& p, cudaStream_t s);
 
 // Launch settings derived once per kernel instantiation and device (function attributes,

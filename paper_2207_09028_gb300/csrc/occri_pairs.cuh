@@ -62,9 +62,10 @@ constexpr int threads_for(int n) {
 constexpr int min_blocks(int n, int elem_bytes) {
   return elem_bytes > 8 ? (n <= 32 ? 4 : 2) : (n <= 32 ? 8 : 4);
 }
-// pass A (29 KB of shared memory at 60^3, FP32) gains from a fifth CTA per SM
+// pass A (29 KB of shared memory at 60^3, FP32) runs six CTAs per SM (80 registers, no
+// spills): 4 % faster than five at 60^3; a seventh (72 registers) was 7 % slower
 constexpr int min_blocks_a(int n, int elem_bytes) {
-  return elem_bytes > 8 ? min_blocks(n, elem_bytes) : (n <= 32 ? 8 : 5);
+  return elem_bytes > 8 ? min_blocks(n, elem_bytes) : (n <= 32 ? 8 : 6);
 }
 // f(|G+q|)/(4 pi) of Eq. recipcoul for |G+q|^2 = g2 = g2h + g2l > 0 (a hi + lo pair).
 // The truncated Coulomb kernel (1 - cos(x R_c))/x^2 = 2 sin^2(x R_c/2)/x^2 is evaluated in
@@ -1493,10 +1494,11 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   if (ev) chk(cudaEventRecord(ev[1], st));
   T* vt = reinterpret_cast<T*>(reinterpret_cast<char*>(S) + p.vt_off);
   vtab_kernel<T, N><<<dim3(N, p.diag ? 1 : p.nkp, kVtabSplit), nt, 0, st>>>(vt, p);
-  pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S, p, vt);
+  pass_b<T, N><<<std::min(N * nf, std::max(1, slots_b / std::max(1, p.b_div))), nt, sb, st>>>(
+      S, p, vt);
   if (ev) chk(cudaEventRecord(ev[2], st));
   // FP32 waves of nocc <= kCdNoc: passes C and D fused (the potentials stay on chip)
-  const bool fused = pair_wave_launches<T>(p.nocc) == 4;
+  const bool fused = pair_wave_launches<T>(p.nocc, p.split_cd) == 4;
   if (!fused) pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S, p);
   if (ev_y) chk(cudaStreamWaitEvent(st, ev_y, 0));   // the previous wave's Y updates
   if constexpr (std::is_same<T, float>::value) {

@@ -82,6 +82,11 @@ def test_null_arguments(lib):
     assert lib.occri_k_build(None, None, None, None, None) == occri.OCCRI_EINVAL
     assert lib.occri_vjp(None, None, 1.0, None, None) == occri.OCCRI_EINVAL
     assert lib.occri_plan_sync(None, None) == occri.OCCRI_EINVAL
+    assert lib.occri_k_assemble_paper(None, 1, None, None, None, None) == occri.OCCRI_EINVAL
+    assert lib.occri_k_build_conduction(None, None, None, None) == occri.OCCRI_EINVAL
+    assert lib.occri_plan_autotune(None, 0, None) == occri.OCCRI_EINVAL
+    assert lib.occri_plan_tuning(None, None) == occri.OCCRI_EINVAL
+    assert lib.occri_plan_set_tuning(None, None) == occri.OCCRI_EINVAL
 
 
 def test_batch_rejects_invalid_arguments_on_the_host(lib):
