@@ -80,8 +80,9 @@ typedef enum {
  * OCCRI_MIXED_TC: as OCCRI_MIXED, but the contraction (e) runs on the tensor cores as
  *   one GEMM over the grid points of the k-mesh's supercell: the AOs periodised over the
  *   supercell (generated on the fly) times Y, both split into FP16 hi + lo parts with
- *   power-of-two scalings, three FP16 products with FP32 accumulation per term, FP32 sums
- *   over at most 512 points before the phases of the supercell offsets, FP64 sums beyond.
+ *   power-of-two scalings, three FP16 products with FP32 accumulation per term; each
+ *   32-point product leaves tensor memory at once, times the phase of its supercell offset,
+ *   into FP32 running sums over at most 16 point tiles, and FP64 sums beyond.
  *   Where the supercell has more than 512 cells, the cell more than 8 atoms, or a tile of 32
  *   grid points more than 128 supercell images in reach (small supercells), the plan keeps
  *   the CUDA-core contraction of OCCRI_MIXED; occri_plan_info reports which one it uses. */
@@ -191,7 +192,8 @@ int occri_k_build(occri_plan *plan, const void *C_dev, void *KC_dev, void *K_dev
  * accumulations, i.e. the rounding. */
 typedef struct {
   int k_per_wave;       /* k' per wave (1 .. the plan's scratch capacity) */
-  int streams;          /* 2: consecutive waves alternate between two streams; 1: one stream */
+  int streams;          /* 1, 2 or 3: consecutive waves go round-robin over that many streams,
+                           each with its own scratch (the third is allocated on first use) */
   int pass_b_div;       /* pass-B CTAs = resident CTA slots / pass_b_div (1 or 2) */
   int split_cd;         /* 1: separate passes C and D where the fused pass CD applies */
   double us_per_field;  /* autotuner: measured microseconds per pair field of this choice */
@@ -203,7 +205,7 @@ typedef struct {
 enum { OCCRI_TUNE_FORCE = 1 };   /* time again even if the cache holds this shape */
 
 /* Autotuner (not in the paper): times every candidate launch configuration of the pair loop
- * (k' per wave in powers of two up to the scratch capacity, one or two streams, pass-B CTAs
+ * (k' per wave in powers of two up to the scratch capacity, one to three streams, pass-B CTAs
  * per resident slot 1 or 1/2, fused or separate passes C and D) on the plan's own buffers,
  * with CUDA events on the plan's stream, over the same number of pair fields each, and
  * keeps the fastest. The choice is cached per (device, grid edge, nocc, precision, N_k,
@@ -211,15 +213,17 @@ enum { OCCRI_TUNE_FORCE = 1 };   /* time again even if the cache holds this shap
  * the same shape, take it from the cache unless flags has OCCRI_TUNE_FORCE.
  * Synchronises the plan's stream. Leaves the plan's accumulators in an undefined state
  * (every build overwrites them). chosen (may be NULL) receives the configuration.
- * OCCRI_EINVAL for a NULL plan or unknown flags. */
+ * OCCRI_EINVAL for a NULL plan or unknown flags; OCCRI_ENOMEM if a third stream's scratch
+ * cannot be had (candidates with three streams are then skipped, not an error). */
 int occri_plan_autotune(occri_plan *plan, int flags, occri_tune_t *chosen);
 
 /* The plan's current launch configuration (us_* fields 0). */
 int occri_plan_tuning(const occri_plan *plan, occri_tune_t *current);
 
 /* Set the launch configuration by hand (k_per_wave >= 1, clamped to the scratch capacity;
- * streams 1 or 2; pass_b_div 1 or 2; split_cd 0 or 1; other fields ignored), else
- * OCCRI_EINVAL. Takes effect at the next build. */
+ * streams 1, 2 or 3; pass_b_div 1 or 2; split_cd 0 or 1; other fields ignored), else
+ * OCCRI_EINVAL; OCCRI_ENOMEM if three streams are asked for and the third scratch cannot be
+ * allocated. Takes effect at the next build. */
 int occri_plan_set_tuning(occri_plan *plan, const occri_tune_t *cfg);
 
 /* The paper's form of the assembly (Sec. II.C, Eq. occrikop): K ~ PKP + PKQ + QKP, where

@@ -607,12 +607,15 @@ void free_plan(Plan* p) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->scratch2) cudaFree(p->scratch2);
+  if (p->scratch3) cudaFree(p->scratch3);
   if (p->asm_scratch) cudaFree(p->asm_scratch);
   for (void* b : {p->gam, p->gpsi, p->cs_g, (void*)p->gkc, (void*)p->gcf, (void*)p->gacc})
     if (b) cudaFree(b);
-  for (cudaEvent_t e : {p->ev_fork, p->ev_join, p->ev_y, p->ev_iso})
+  for (cudaEvent_t e : {p->ev_fork, p->ev_join, p->ev_y, p->ev_iso, p->ev_join2, p->ev_iso2,
+                        p->ev_iso3})
     if (e) cudaEventDestroy(e);
   if (p->aux) cudaStreamDestroy(p->aux);
+  if (p->aux2) cudaStreamDestroy(p->aux2);
   if (p->tc) tc_plan_free(p->tc);
   for (cudaEvent_t e : p->ev_used) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev_free) cudaEventDestroy(e);
@@ -693,52 +696,62 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
     launches += 2 + (p->nocc + kOrbChunk - 1) / kOrbChunk;
   }
   {
-    // Waves alternate between the plan's stream and the auxiliary one, each with its own
-    // scratch; the accumulation passes (which update Y_k) are chained across the two
-    // streams by ev_y. A sampled wave runs alone (both streams wait for each other
-    // around it) so that its pass times are not mixed with the other stream's work.
+    // Waves go round-robin over the plan's stream and one or two auxiliary ones, each with
+    // its own scratch; the accumulation passes (which update Y_k) are chained across the
+    // streams by ev_y. A sampled wave runs alone (the streams wait for each other around
+    // it) so that its pass times are not mixed with another stream's work.
     StageTimer all(p, timed);
-    cudaStream_t st[2] = {s, p->aux};
-    void* sc[2] = {p->scratch, p->scratch2};
+    const int ns = p->nstreams;
+    cudaStream_t st[3] = {s, p->aux, p->aux2};
+    void* sc[3] = {p->scratch, p->scratch2, p->scratch3};
+    cudaEvent_t join[3] = {nullptr, p->ev_join, p->ev_join2};
+    cudaEvent_t iso[3] = {p->ev_iso, p->ev_iso2, p->ev_iso3};
     if (cudaEventRecord(p->ev_fork, s) != cudaSuccess) return OCCRI_ECUDA;
-    if (cudaStreamWaitEvent(p->aux, p->ev_fork, 0) != cudaSuccess) return OCCRI_ECUDA;
+    for (int o = 1; o < ns; ++o)
+      if (cudaStreamWaitEvent(st[o], p->ev_fork, 0) != cudaSuccess) return OCCRI_ECUDA;
     // the first wave's accumulation waits on this record (within the same build, which
     // keeps the chain inside a captured graph when the build is captured)
     if (cudaEventRecord(p->ev_y, s) != cudaSuccess) return OCCRI_ECUDA;
+    // every other stream's work so far precedes the next work of stream w
+    auto isolate = [&](int w) {
+      for (int o = 0; o < ns; ++o)
+        if (o != w && (cudaEventRecord(iso[o], st[o]) != cudaSuccess ||
+                       cudaStreamWaitEvent(st[w], iso[o], 0) != cudaSuccess))
+          return false;
+      return true;
+    };
     double fields = 0.0;
     long long wave = 0;
     for (int k = 0; k < p->nk; ++k)
       for (int kp0 = k; kp0 < p->nk; ++wave) {   // unordered pairs: (k, k), then k' > k
         const int diag = (kp0 == k) ? 1 : 0;
         const int nkp = diag ? 1 : std::min(p->nkp_wave, p->nk - kp0);
-        const int w = p->nstreams == 2 ? (int)(wave & 1) : 0;
+        const int w = (int)(wave % ns);
         cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
         bool sample = p->timing_every > 0 && (wave % p->timing_every == 0);
         if (sample)
           for (int i = 0; i < 4 && sample; ++i) sample = (ev[i] = take_event(p)) != nullptr;
-        if (sample && p->nstreams == 2) {   // wait for the other stream's work
-          if (cudaEventRecord(p->ev_iso, st[w ^ 1]) != cudaSuccess ||
-              cudaStreamWaitEvent(st[w], p->ev_iso, 0) != cudaSuccess)
-            return OCCRI_ECUDA;
-        }
+        if (sample && !isolate(w)) return OCCRI_ECUDA;   // wait for the other streams' work
         if (launch_pair_wave<T>(*p, k, kp0, nkp, diag, st[w], sc[w], sample ? ev : nullptr,
                                 p->ev_y) != cudaSuccess)
           return OCCRI_ECUDA;
         launches += pair_wave_launches<T>(p->nocc, p->split_cd);
         const double nf = (double)wave_fields(p->nocc, nkp, diag);
         fields += nf;
-        if (sample) {   // and keep the other stream waiting until this wave is done
-          if (p->nstreams == 2 && (cudaEventRecord(p->ev_iso, st[w]) != cudaSuccess ||
-                                   cudaStreamWaitEvent(st[w ^ 1], p->ev_iso, 0) != cudaSuccess))
-            return OCCRI_ECUDA;
+        if (sample) {   // and keep the other streams waiting until this wave is done
+          if (cudaEventRecord(iso[w], st[w]) != cudaSuccess) return OCCRI_ECUDA;
+          for (int o = 0; o < ns; ++o)
+            if (o != w && cudaStreamWaitEvent(st[o], iso[w], 0) != cudaSuccess) return OCCRI_ECUDA;
           p->ev_pending.push_back(Plan::TimedSpan{ev[0], ev[1], OCCRI_STAGE_PAIR_A, nf});
           p->ev_pending.push_back(Plan::TimedSpan{ev[1], ev[2], OCCRI_STAGE_PAIR_B, nf});
           p->ev_pending.push_back(Plan::TimedSpan{ev[2], ev[3], OCCRI_STAGE_PAIR_C, nf});
         }
         kp0 += nkp;
       }
-    if (cudaEventRecord(p->ev_join, p->aux) != cudaSuccess) return OCCRI_ECUDA;
-    if (cudaStreamWaitEvent(s, p->ev_join, 0) != cudaSuccess) return OCCRI_ECUDA;
+    for (int o = 1; o < ns; ++o)
+      if (cudaEventRecord(join[o], st[o]) != cudaSuccess ||
+          cudaStreamWaitEvent(s, join[o], 0) != cudaSuccess)
+        return OCCRI_ECUDA;
     all.done(OCCRI_STAGE_PAIRS, fields);
   }
   {
@@ -984,12 +997,36 @@ std::vector<long long> tune_key(const Plan* p) {
   return {p->device, p->N[0], p->nocc, p->precision, p->nk, p->nkp_cap};
 }
 
-void apply_tune(Plan* p, const occri_tune_t& t) {
+// The third stream, its scratch and events, made on first use.
+int ensure_third_stream(Plan* p) {
+  if (p->scratch3) return OCCRI_OK;
+  cudaError_t e = occri::device_malloc(&p->scratch3, p->scratch_bytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join2, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_iso3, cudaEventDisableTiming);
+  if (e == cudaSuccess) return OCCRI_OK;
+  cudaGetLastError();
+  if (p->scratch3) cudaFree(p->scratch3);
+  if (p->aux2) cudaStreamDestroy(p->aux2);
+  if (p->ev_join2) cudaEventDestroy(p->ev_join2);
+  if (p->ev_iso3) cudaEventDestroy(p->ev_iso3);
+  p->scratch3 = nullptr;
+  p->aux2 = nullptr;
+  p->ev_join2 = p->ev_iso3 = nullptr;
+  return e == cudaErrorMemoryAllocation ? OCCRI_ENOMEM : OCCRI_ECUDA;
+}
+
+int apply_tune(Plan* p, const occri_tune_t& t) {
+  if (t.streams == 3) {
+    const int st = ensure_third_stream(p);
+    if (st != OCCRI_OK) return st;
+  }
   p->nkp_wave = std::max(1, std::min(t.k_per_wave, p->nkp_cap));
-  p->nstreams = t.streams == 1 ? 1 : 2;
+  p->nstreams = std::max(1, std::min(t.streams, 3));
   p->b_div = std::max(1, t.pass_b_div);
   p->split_cd = t.split_cd ? 1 : 0;
   p->tuned = 1;
+  return OCCRI_OK;
 }
 
 bool tune_lookup(Plan* p, occri_tune_t* out) {
@@ -1013,21 +1050,23 @@ int tune_time(Plan* p, const TuneCfg& cfg, int reps, double* us_per_field) {
   p->b_div = cfg.b_div;
   p->split_cd = cfg.split_cd;
   cudaStream_t s = p->stream;
-  cudaStream_t st[2] = {s, p->aux};
-  void* sc[2] = {p->scratch, p->scratch2};
+  cudaStream_t st[3] = {s, p->aux, p->aux2};
+  void* sc[3] = {p->scratch, p->scratch2, p->scratch3};
+  cudaEvent_t join[3] = {nullptr, p->ev_join, p->ev_join2};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = OCCRI_OK;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = OCCRI_ECUDA;
   double fields = 0.0;
   if (rc == OCCRI_OK) {
-    bool ok = cudaEventRecord(e0, s) == cudaSuccess && cudaEventRecord(p->ev_fork, s) == cudaSuccess &&
-              cudaStreamWaitEvent(p->aux, p->ev_fork, 0) == cudaSuccess &&
-              cudaEventRecord(p->ev_y, s) == cudaSuccess;
+    bool ok = cudaEventRecord(e0, s) == cudaSuccess && cudaEventRecord(p->ev_fork, s) == cudaSuccess;
+    for (int o = 1; o < cfg.nstreams && ok; ++o)
+      ok = cudaStreamWaitEvent(st[o], p->ev_fork, 0) == cudaSuccess;
+    ok = ok && cudaEventRecord(p->ev_y, s) == cudaSuccess;
     int kp0 = p->nk > 1 ? 1 : 0;
     for (int w = 0; w < reps && ok; ++w) {
       const int diag = p->nk > 1 ? 0 : 1;
       const int nkp = diag ? 1 : std::min(cfg.nkp, p->nk - kp0);
-      const int sw = cfg.nstreams == 2 ? (w & 1) : 0;
+      const int sw = w % cfg.nstreams;
       ok = occri::launch_pair_wave<T>(*p, 0, kp0, nkp, diag, st[sw], sc[sw], nullptr,
                                       p->ev_y) == cudaSuccess;
       fields += (double)occri::wave_fields(p->nocc, nkp, diag);
@@ -1036,8 +1075,10 @@ int tune_time(Plan* p, const TuneCfg& cfg, int reps, double* us_per_field) {
         if (kp0 >= p->nk) kp0 = 1;
       }
     }
-    ok = ok && cudaEventRecord(p->ev_join, p->aux) == cudaSuccess &&
-         cudaStreamWaitEvent(s, p->ev_join, 0) == cudaSuccess && cudaEventRecord(e1, s) == cudaSuccess;
+    for (int o = 1; o < cfg.nstreams && ok; ++o)
+      ok = cudaEventRecord(join[o], st[o]) == cudaSuccess &&
+           cudaStreamWaitEvent(s, join[o], 0) == cudaSuccess;
+    ok = ok && cudaEventRecord(e1, s) == cudaSuccess;
     float ms = 0.f;
     ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
     if (!ok) {
@@ -1062,14 +1103,15 @@ int autotune(Plan* p, occri_tune_t* out) {
   for (int v = 1; v < p->nkp_cap; v *= 2) nkps.push_back(v);
   nkps.push_back(p->nkp_cap);
   const bool can_fuse = occri::pair_wave_launches<T>(p->nocc, 0) == 4;
+  const bool has_third = ensure_third_stream(p) == OCCRI_OK;   // else two streams at most
   // enough waves for every candidate to cover the same fields (and both streams)
-  const int reps = std::max(4, 2 * p->nkp_cap);
+  const int reps = std::max(12, 2 * p->nkp_cap);
   const TuneCfg def{p->nkp_cap, 2, 1, 0};
   double t_def = 0.0, best = 0.0;
   TuneCfg pick = def;
   int count = 0;
   for (int nkp : nkps)
-    for (int ns = 1; ns <= 2; ++ns)
+    for (int ns = 1; ns <= (has_third ? 3 : 2); ++ns)
       for (int bd = 1; bd <= 2; ++bd)
         for (int sp = 0; sp <= (can_fuse ? 1 : 0); ++sp) {
           const TuneCfg c{nkp, ns, bd, sp};
@@ -1096,7 +1138,8 @@ int autotune(Plan* p, occri_tune_t* out) {
   t.us_per_field = best;
   t.us_default = t_def;
   t.candidates = count;
-  apply_tune(p, t);
+  const int st = apply_tune(p, t);
+  if (st != OCCRI_OK) return st;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     const auto key = tune_key(p);
@@ -1489,11 +1532,12 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     chk(dalloc(&b, orb * csz, &tot)); p->Y = b; b = nullptr;
     // behind each scratch buffer, the kernel tables v/(4 pi) of one wave (one per k')
     const size_t sbytes = (size_t)p->fields_cap * field_bytes + (size_t)nkp * ng * (csz / 2);
+    p->scratch_bytes = sbytes;
     chk(dalloc(&b, sbytes, &tot)); p->scratch = b; b = nullptr;
     chk(dalloc(&b, sbytes, &tot)); p->scratch2 = b;
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
-  for (cudaEvent_t* ev : {&p->ev_fork, &p->ev_join, &p->ev_y, &p->ev_iso})
+  for (cudaEvent_t* ev : {&p->ev_fork, &p->ev_join, &p->ev_y, &p->ev_iso, &p->ev_iso2})
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   chk(dalloc(&p->kc, (size_t)p->nk * nao * nocc, &tot));
   chk(dalloc(&p->xi, (size_t)p->nk * nao * nocc, &tot));
@@ -1519,7 +1563,8 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
   p->workspace_bytes = tot;
   {
     occri_tune_t t{};
-    if (occri_impl::tune_lookup(p, &t)) occri_impl::apply_tune(p, t);
+    if (occri_impl::tune_lookup(p, &t) && occri_impl::apply_tune(p, t) != OCCRI_OK)
+      p->nstreams = 2;   // the cached choice needed memory that is not there: keep the default
   }
   occri_plan* h = new (std::nothrow) occri_plan;
   if (!h) { free_plan(p); return OCCRI_ENOMEM; }
@@ -1637,7 +1682,8 @@ int occri_plan_autotune(occri_plan* plan, int flags, occri_tune_t* chosen) {
   if (!guard.ok) return OCCRI_ECUDA;
   occri_tune_t t{};
   if (!(flags & OCCRI_TUNE_FORCE) && occri_impl::tune_lookup(p, &t)) {
-    occri_impl::apply_tune(p, t);
+    const int st = occri_impl::apply_tune(p, t);
+    if (st != OCCRI_OK) return st;
     t.candidates = 0;
     if (chosen) *chosen = t;
     return OCCRI_OK;
@@ -1655,11 +1701,14 @@ int occri_plan_autotune(occri_plan* plan, int flags, occri_tune_t* chosen) {
 
 int occri_plan_set_tuning(occri_plan* plan, const occri_tune_t* cfg) {
   if (!plan || !cfg) return OCCRI_EINVAL;
-  if (cfg->k_per_wave < 1 || (cfg->streams != 1 && cfg->streams != 2) ||
+  if (cfg->k_per_wave < 1 || cfg->streams < 1 || cfg->streams > 3 ||
       (cfg->pass_b_div != 1 && cfg->pass_b_div != 2) || (cfg->split_cd != 0 && cfg->split_cd != 1))
     return OCCRI_EINVAL;
   Plan* p = plan->p;
-  occri_impl::apply_tune(p, *cfg);
+  occri::DeviceGuard guard(p->device);
+  if (!guard.ok) return OCCRI_ECUDA;
+  const int st = occri_impl::apply_tune(p, *cfg);
+  if (st != OCCRI_OK) return st;
   p->tuned = 0;
   return OCCRI_OK;
 }

@@ -92,9 +92,11 @@ constexpr int kMaxTiles = 4;             // AO tiles of a plan (nao <= 512)
 constexpr int kMaxEntries = 192;         // shell entries of all tiles
 
 // A stage of the GEMM: x = A slot in the slab | l << 22; y = point tile | column tile << 16
-// | flags << 24 | AO tile << 26 (kFirstSum: the running sums start here; kToGlobal: they go
+// | flags << 24 | AO tile << 27 (kFirstSum: the running sums start here; kToGlobal: they go
 // to K_{mu i} after this stage).
-enum { kFirstSum = 1, kToGlobal = 2 };
+// kChain: this stage and the next one (same column tile and offset l, the next point tile)
+// share one accumulator, and the epilogue takes their sum out once.
+enum { kFirstSum = 1, kToGlobal = 2, kChain = 4 };
 
 struct TcParams {
   int nk, nao, nocc, natm, N, ncol, n_ct, ntile_r, nl, ntile, nentries;
@@ -401,7 +403,8 @@ __device__ __forceinline__ int st_ablk(uint2 e) { return (int)(e.x & 0x3fffffu);
 __device__ __forceinline__ int st_l(uint2 e) { return (int)(e.x >> 22); }
 __device__ __forceinline__ int st_rt(uint2 e) { return (int)(e.y & 0xffffu); }
 __device__ __forceinline__ int st_ct(uint2 e) { return (int)((e.y >> 16) & 0xffu); }
-__device__ __forceinline__ int st_flags(uint2 e) { return (int)((e.y >> 24) & 3u); }
+__device__ __forceinline__ int st_flags(uint2 e) { return (int)((e.y >> 24) & 7u); }
+__device__ __forceinline__ int st_tile(uint2 e) { return (int)((e.y >> 27) & 3u); }
 
 // One lane of the warp waits (bounded) for the mbarrier phase, the warp follows its verdict,
 // and the other lanes then observe the completed phase themselves (acquire).
@@ -450,43 +453,56 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       bool good = true;
-      for (long long sidx = 0; sidx < nst && good; ++sidx) {
-        const int s = (int)(sidx % kStages);
-        const long long u = sidx / kStages;
-        const int ab = (int)(sidx & 1);
-        // the epilogue has taken the product of stage sidx - 2 out of this accumulator
-        if (sidx >= 2 && !tc::mbar_wait(tc::smem_u32(&sm.acc_empty[ab]),
-                                        (unsigned)(((sidx >> 1) - 1) & 1), p.wait_ns)) {
+      long long g = 0;   // accumulator groups: one stage, or a chained pair of stages
+      for (long long sidx = 0; sidx < nst && good; ++g) {
+        const int ab = (int)(g & 1);
+        const int n = ((st_flags(stages[sidx]) & kChain) && sidx + 1 < nst) ? 2 : 1;
+        // the epilogue has taken group g - 2 out of this accumulator
+        if (g >= 2 && !tc::mbar_wait(tc::smem_u32(&sm.acc_empty[ab]),
+                                     (unsigned)(((g >> 1) - 1) & 1), p.wait_ns)) {
           good = false;
           break;
         }
-        if (!tc::mbar_wait(tc::smem_u32(&sm.full[s]), (unsigned)(u & 1), p.wait_ns)) {
-          good = false;
-          break;
+        uint64_t ah[2][2], al[2][2], bh[2][2], bl[2][2];
+        int slot[2] = {0, 0};
+        for (int q = 0; q < n && good; ++q) {
+          const long long si = sidx + q;
+          slot[q] = (int)(si % kStages);
+          if (!tc::mbar_wait(tc::smem_u32(&sm.full[slot[q]]), (unsigned)((si / kStages) & 1),
+                             p.wait_ns))
+            good = false;
         }
+        if (!good) break;
         tc::tc_fence_after();
-        const uint32_t a_hi = tc::smem_u32(stage0 + (size_t)s * kStageBytes);
-        const uint32_t a_lo = a_hi + kABytes, b_hi = a_hi + kABlock, b_lo = b_hi + kBBytes;
-        const uint32_t t_acc = tmem + (uint32_t)(ab * kAccCols);
-        // the two small cross terms of both K slices first, the hi x hi products last: each
-        // accumulation into tensor memory rounds toward zero at the running sum's magnitude,
-        // so only the last two additions happen at full magnitude
-        uint64_t ah[2], al[2], bh[2], bl[2];
+        for (int q = 0; q < n; ++q) {
+          const uint32_t a_hi = tc::smem_u32(stage0 + (size_t)slot[q] * kStageBytes);
+          const uint32_t a_lo = a_hi + kABytes, b_hi = a_hi + kABlock, b_lo = b_hi + kBBytes;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          ah[k] = tc::smem_desc(a_hi + k * kASlice, kLBO, kSBO);
-          al[k] = tc::smem_desc(a_lo + k * kASlice, kLBO, kSBO);
-          bh[k] = tc::smem_desc(b_hi + k * kBSlice, kLBO, kSBO);
-          bl[k] = tc::smem_desc(b_lo + k * kBSlice, kLBO, kSBO);
+          for (int k = 0; k < 2; ++k) {
+            ah[q][k] = tc::smem_desc(a_hi + k * kASlice, kLBO, kSBO);
+            al[q][k] = tc::smem_desc(a_lo + k * kASlice, kLBO, kSBO);
+            bh[q][k] = tc::smem_desc(b_hi + k * kBSlice, kLBO, kSBO);
+            bl[q][k] = tc::smem_desc(b_lo + k * kBSlice, kLBO, kSBO);
+          }
         }
-        tc::mma_f16(t_acc, ah[0], bl[0], kIdesc, 0u);
-        tc::mma_f16(t_acc, al[0], bh[0], kIdesc, 1u);
-        tc::mma_f16(t_acc, ah[1], bl[1], kIdesc, 1u);
-        tc::mma_f16(t_acc, al[1], bh[1], kIdesc, 1u);
-        tc::mma_f16(t_acc, ah[0], bh[0], kIdesc, 1u);
-        tc::mma_f16(t_acc, ah[1], bh[1], kIdesc, 1u);
-        tc::mma_commit(tc::smem_u32(&sm.empty[s]));
+        const uint32_t t_acc = tmem + (uint32_t)(ab * kAccCols);
+        // the small cross terms of every K slice of the group first, the hi x hi products
+        // last: each accumulation into tensor memory rounds toward zero at the running sum's
+        // magnitude, so only the hi x hi additions happen at full magnitude (two per stage)
+        uint32_t acc = 0u;
+        for (int q = 0; q < n; ++q)
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            tc::mma_f16(t_acc, ah[q][k], bl[q][k], kIdesc, acc);
+            tc::mma_f16(t_acc, al[q][k], bh[q][k], kIdesc, 1u);
+            acc = 1u;
+          }
+        for (int q = 0; q < n; ++q)
+#pragma unroll
+          for (int k = 0; k < 2; ++k) tc::mma_f16(t_acc, ah[q][k], bh[q][k], kIdesc, 1u);
+        for (int q = 0; q < n; ++q) tc::mma_commit(tc::smem_u32(&sm.empty[slot[q]]));
         tc::mma_commit(tc::smem_u32(&sm.acc_full[ab]));
+        sidx += n;
       }
       if (!good) fail(p.status);
       // every MMA issued has completed before the tensor memory is released
@@ -557,15 +573,33 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) { SR[j] = 0ull; SI[j] = 0ull; }
     bool good = true;
+    int g = 0;             // accumulator groups taken out
+    int carry_first = 0;   // kFirstSum of the first stage of a chained pair
     for (int sidx = 0; sidx < (int)nst; ++sidx) {
       const uint2 e = stages[sidx];
-      const int ab = (int)(sidx & 1);
-      const int flags = st_flags(e), ct = st_ct(e), l = st_l(e);
-      if (!warp_wait(tc::smem_u32(&sm.acc_full[ab]), (unsigned)((sidx >> 1) & 1), p.wait_ns,
+      const int jp = sidx % kPhRing;
+      const int flags = st_flags(e) | carry_first, ct = st_ct(e);
+      if ((flags & kChain) && sidx + 1 < (int)nst) {
+        // the first stage of a chained pair: its product comes out with the next stage's;
+        // only its phase-ring slot is handed back (once its copy has landed)
+        if (!warp_wait(tc::smem_u32(&sm.ph_full[jp]), (unsigned)((sidx / kPhRing) & 1),
+                       p.wait_ns, lane)) {
+          good = false;
+          break;
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(tc::smem_u32(&sm.ph_empty[jp]));
+        carry_first = flags & kFirstSum;
+        continue;
+      }
+      carry_first = 0;
+      const int ab = g & 1;
+      if (!warp_wait(tc::smem_u32(&sm.acc_full[ab]), (unsigned)((g >> 1) & 1), p.wait_ns,
                      lane)) {
         good = false;
         break;
       }
+      ++g;
       tc::tc_fence_after();
       if (flags & kFirstSum) {
 #pragma unroll
@@ -573,7 +607,6 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
       }
       // cos, sin and -sin of the phases of the warp's columns, from the stage's slot of the
       // phase ring (copied in by the producer with the stage's operands)
-      const int jp = sidx % kPhRing;
       if (!warp_wait(tc::smem_u32(&sm.ph_full[jp]), (unsigned)((sidx / kPhRing) & 1), p.wait_ns,
                      lane)) {
         good = false;
@@ -614,7 +647,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(TcParams p) {
       __syncwarp();   // every lane has read the phase slot
       if (lane == 0) tc::mbar_arrive(tc::smem_u32(&sm.ph_empty[jp]));
       if (flags & kToGlobal) {
-        const int tl = (int)((e.y >> 26) & 3u);
+        const int tl = st_tile(e);
         const int mu = p.perm[tl * kM + row];
         if (mu >= 0) {
           const double rf = p.rowf[tl * kM + row] * p.scale;
@@ -1014,8 +1047,6 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
       TcSlab slab;
       slab.block0 = (long long)blocks.size();
       const int rt0 = rt;
-      std::vector<int> slot_of;   // per (point tile - rt0, l): slot or -1
-      std::vector<int> tiles_rt;
       while (rt < q.ntile_r) {
         const long long c = cost_tile_rt[(size_t)tl * q.ntile_r + rt];
         if ((long long)blocks.size() - slab.block0 + c > kSlabBlocks && rt > rt0) break;
@@ -1031,49 +1062,78 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
       slab.nblocks = (int)((long long)blocks.size() - slab.block0);
       if (slab.nblocks == 0) continue;
       max_slab = std::max(max_slab, (size_t)slab.nblocks);
-      // stages: column tile by column tile, runs of kFlushTiles active point tiles
-      std::vector<uint2> st;
-      for (int ct = 0; ct < q.n_ct; ++ct) {
-        int slot = 0, in_run = 0;
-        size_t run_first = st.size();
+      // stages: column tile by column tile, runs of kFlushTiles active point tiles. Inside a
+      // run, point tiles go in pairs, and for each offset l active in both tiles of a pair
+      // the two stages are chained (one accumulator, one epilogue pass).
+      std::vector<int> slot_of((size_t)(rt1 - rt0) * NL, -1);   // A block slot of (r, l)
+      {
+        int sl = 0;
         for (int r = rt0; r < rt1; ++r) {
           const unsigned* act = &active[((size_t)tl * q.ntile_r + r) * nwords];
-          bool any = false;
           for (int l = 0; l < NL; ++l)
-            if ((act[l >> 5] >> (l & 31)) & 1u) {
-              st.push_back(make_uint2((unsigned)slot | ((unsigned)l << 22),
-                                      (unsigned)r | ((unsigned)ct << 16) | ((unsigned)tl << 26)));
-              ++slot;
-              any = true;
-            }
-          if (!any) continue;
-          if (++in_run == kFlushTiles || r + 1 == rt1) {
-            st[run_first].y |= (unsigned)kFirstSum << 24;
-            st.back().y |= (unsigned)kToGlobal << 24;
-            run_first = st.size();
-            in_run = 0;
-          }
-        }
-        if (st.size() > run_first) {   // a run left open by point tiles without activity
-          st[run_first].y |= (unsigned)kFirstSum << 24;
-          st.back().y |= (unsigned)kToGlobal << 24;
+            if ((act[l >> 5] >> (l & 31)) & 1u) slot_of[(size_t)(r - rt0) * NL + l] = sl++;
         }
       }
-      // CTAs: contiguous ranges of runs, cut at run ends, about equal stage counts
+      std::vector<uint2> st;
+      std::vector<size_t> ct_begin(q.n_ct + 1, 0);   // stages of column tile ct in st
+      for (int ct = 0; ct < q.n_ct; ++ct) {
+        ct_begin[ct] = st.size();
+        std::vector<int> run;   // the run's active point tiles
+        auto push = [&](int r, int l, unsigned flags) {
+          st.push_back(make_uint2((unsigned)slot_of[(size_t)(r - rt0) * NL + l] | ((unsigned)l << 22),
+                                  (unsigned)r | ((unsigned)ct << 16) | (flags << 24) |
+                                      ((unsigned)tl << 27)));
+        };
+        auto close_run = [&]() {
+          if (run.empty()) return;
+          const size_t first = st.size();
+          for (size_t i = 0; i < run.size(); i += 2) {
+            const int ra = run[i], rb = i + 1 < run.size() ? run[i + 1] : -1;
+            for (int l = 0; l < NL; ++l) {
+              const bool in_a = slot_of[(size_t)(ra - rt0) * NL + l] >= 0;
+              const bool in_b = rb >= 0 && slot_of[(size_t)(rb - rt0) * NL + l] >= 0;
+              if (in_a) push(ra, l, in_b ? (unsigned)kChain : 0u);
+              if (in_b) push(rb, l, 0u);
+            }
+          }
+          st[first].y |= (unsigned)kFirstSum << 24;
+          st.back().y |= (unsigned)kToGlobal << 24;   // never a chained first stage
+          run.clear();
+        };
+        for (int r = rt0; r < rt1; ++r) {
+          bool any = false;
+          for (int l = 0; l < NL && !any; ++l) any = slot_of[(size_t)(r - rt0) * NL + l] >= 0;
+          if (!any) continue;
+          run.push_back(r);
+          if ((int)run.size() == kFlushTiles) close_run();
+        }
+        close_run();
+      }
+      ct_begin[q.n_ct] = st.size();
+      // CTAs: every column tile's stages are cut (at run ends) into `parts` ranges of about
+      // equal length, one CTA each. The CTAs of one part but different column tiles then
+      // read the same A blocks in the same order at about the same time, so each A block
+      // comes from DRAM once and from L2 for the other column tiles.
       slab.stage0 = (long long)stages.size();
       slab.cta0 = (int)cta_stage0.size();
-      const int ncta = std::max(1, std::min<int>(nsm, (int)(st.size() / 64 + 1)));
+      const int parts = std::max(1, nsm / q.n_ct);
       int b = 0;
-      cta_stage0.push_back(slab.stage0);
-      for (size_t i = 0; i < st.size(); ++i) {
-        const bool run_end = (st[i].y >> 24) & kToGlobal;
-        if (run_end && b + 1 < ncta &&
-            (long long)(i + 1) >= (long long)((double)st.size() * (b + 1) / ncta)) {
-          cta_stage0.push_back(slab.stage0 + (long long)i + 1);
-          ++b;
+      for (int ct = 0; ct < q.n_ct; ++ct) {
+        const size_t b0 = ct_begin[ct], b1 = ct_begin[ct + 1];
+        if (b1 == b0) continue;
+        cta_stage0.push_back(slab.stage0 + (long long)b0);
+        ++b;
+        int part = 1;
+        for (size_t i = b0; i + 1 < b1 && part < parts; ++i) {
+          const bool run_end = (st[i].y >> 24) & kToGlobal;
+          if (run_end && (double)(i + 1 - b0) >= (double)(b1 - b0) * part / parts) {
+            cta_stage0.push_back(slab.stage0 + (long long)i + 1);
+            ++b;
+            ++part;
+          }
         }
       }
-      slab.ncta = b + 1;
+      slab.ncta = b;
       stages.insert(stages.end(), st.begin(), st.end());
       total_st += (long long)st.size();
       t->slabs.push_back(slab);

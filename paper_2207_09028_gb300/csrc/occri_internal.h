@@ -123,7 +123,7 @@ struct Plan {
   int nkp_wave;              // k' per wave
   int nkp_cap = 1;           // k' per wave the scratch buffers hold
   // launch configuration of the pair loop (occri_plan_autotune may change it)
-  int nstreams = 2;          // 2: consecutive waves alternate between two streams
+  int nstreams = 2;          // consecutive waves go round-robin over 1, 2 or 3 streams
   int b_div = 1;             // pass-B CTAs = resident slots / b_div
   int split_cd = 0;          // 1: passes C and D instead of the fused pass CD
   int tuned = 0;             // 1: the configuration came from the autotuner (or its cache)
@@ -164,6 +164,12 @@ struct Plan {
   // which both update Y_k, are ordered across the two streams (event ev_y).
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_y = nullptr, ev_iso = nullptr;
+  cudaEvent_t ev_iso2 = nullptr;
+  // a third stream and scratch, made when a launch configuration asks for three streams
+  cudaStream_t aux2 = nullptr;
+  void* scratch3 = nullptr;
+  size_t scratch_bytes = 0;  // bytes of each scratch buffer
+  cudaEvent_t ev_join2 = nullptr, ev_iso3 = nullptr;
   // adjoint workspaces, allocated by the first occri_vjp_full call
   void* gam = nullptr;       // [nk][nocc][fs] adjoint orbital field (periodic parts)
   void* gpsi = nullptr;      // [nk][nocc][fs] accumulated dL/dpsi (periodic parts)
