@@ -45,11 +45,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) of one full mixed-precision wave (vtab_kernel + pass_a + pass_b +
-# pass_cd), keyed by ("round_trip", grid edge, fields per wave, precision), from one ncu --set
-# full capture of the same launch shape (an off-diagonal 64-field wave at 60^3 of the 2x2x2-k
-# profiling cell of `--case 60 8 2 2 2`; cold cache, each launch replayed alone).
-TRAFFIC = {("round_trip", 60, 64, "mixed"): 425.0e6}
+# DRAM bytes (read + write) of one full mixed-precision wave (pass_a + pass_b + pass_cd; the
+# kernel tables stay in L2), keyed by ("round_trip", grid edge, fields per wave, precision),
+# from one ncu --set full capture per pass of the same launch shape (an off-diagonal 64-field
+# wave at 60^3 of the 2x2x2-k profiling cell of `--case 60 8 2 2 2`; cold cache, each launch
+# replayed alone).
+TRAFFIC = {("round_trip", 60, 64, "mixed"): 424.0e6}
 
 METRIC = "K-builds/s at 6x6x6 k, 350 AO; mixed vs FP64 GPU at |dE_x|<=1e-6 Ha/cell"
 UNIT = "K-builds/s"
@@ -283,14 +284,14 @@ def stage_ms_per_build(stages: dict, waves: int, steps: int) -> dict:
 
 
 def roofline(stages: dict, info: dict, edge: int, ng: int, nocc: int, hbm: float,
-             peak_kind: str):
+             peak_kind: str, tuning: dict = None):
     """Roofline of the dominant work, the pair round trip (steps c, d).
 
     Its unit is one transformed field; each of the two 3-D transforms reads and writes the
     field once, so the streaming model is 2 x 2 x 8 B x N_g = 32 N_g bytes per field in
     FP32 (c64). A round trip runs as four launches over a wave of fields (kernel tables,
     pass_a, pass_b and the fused pass_cd; FP64 or nocc > 8: pass_c and pass_d instead);
-    waves alternate between two streams, so the achieved rate is taken over the wall time
+    waves go round-robin over the plan's streams, so the achieved rate is taken over the wall time
     of the whole wave loop (the `pairs` stage: CUDA events on the plan's stream around the
     loop, every timed build). The per-pass split comes from the sampled waves, run alone.
     """
@@ -302,15 +303,18 @@ def roofline(stages: dict, info: dict, edge: int, ng: int, nocc: int, hbm: float
     fields = loop["units"]
     achieved = 32.0 * ng * fields / (loop["ms"] / 1e3) / 1e9
     fpw = int(info["fields_per_wave"])
-    mixed = int(info.get("precision", 1)) == 1
-    fused = mixed and nocc <= 8   # FP32 waves of nocc <= 8 fuse passes C and D
+    mixed = int(info.get("precision", 1)) in (1, 2)   # OCCRI_MIXED, OCCRI_MIXED_TC
+    tuning = tuning or {}
+    # FP32 waves of nocc <= 8 fuse passes C and D unless the tuning splits them
+    fused = mixed and nocc <= 8 and not tuning.get("split_cd", 0)
     passes = ("vtab_kernel + pass_a + pass_b + pass_cd" if fused
               else "vtab_kernel + pass_a + pass_b + pass_c + pass_d")
+    nstreams = int(tuning.get("streams", 3))
     return {"kernel": f"pair round trip: {passes} over waves of {fpw} fields of {edge}^3 "
-                      "(two streams)",
+                      f"({nstreams} streams)",
             "bound": "hbm", "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
             "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": TRAFFIC.get(("round_trip", edge, fpw, "mixed" if mixed else "fp64")),
+            "traffic": (TRAFFIC.get(("round_trip", edge, fpw, "mixed")) if fused else None),
             "bytes_per_launch": 32.0 * ng * fpw,
             "ms_per_launch": loop["ms"] * fpw / fields,
             "pass_ms_share": ({s_: stages[s_]["ms"] / rt_ms for s_ in pair} if rt_ms > 0
@@ -568,6 +572,10 @@ def main():
     ap.add_argument("--bench-precision", default="mixed_tc",
                     help="precision of the headline builds (mixed_tc: tensor-core contraction)")
     ap.add_argument("--timing", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time plain launches instead of the build's CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the default launch configuration of the pair loop")
     ap.add_argument("--configs", default=None,
                     help="'all' or a comma list: every precision of those config cells")
     args = ap.parse_args()
@@ -642,18 +650,32 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     plan = occri.Plan.from_workload(w, precision=args.bench_precision)
+    # the pair loop's launch configuration, timed once per shape before the timed region
+    tuning = None if args.no_autotune else plan.autotune()
     C = torch.from_numpy(w.C).to(dev)
     KC = torch.empty((w.nk, w.nao, w.nocc), dtype=torch.complex128, device=dev)
     K = torch.empty((w.nk, w.nao, w.nao), dtype=torch.complex128, device=dev)
     Ex = torch.zeros(1, dtype=torch.float64, device=dev)
+    # the whole build as one CUDA graph (occri_batch_* with this one cell: the first call
+    # captures it, every later call is one graph launch), unless --no-graph
+    batch = None if args.no_graph else occri.Batch([plan], stream=stream.cuda_stream)
+
+    def one_build():
+        if batch is not None:
+            batch.build([C], [KC], [K], [Ex], sync=False)
+        else:
+            plan.k_build(C, KC, K, Ex, sync=False)
+
+    def sync_builds():
+        if batch is not None:
+            batch.sync()
+        plan.sync()
+
     for _ in range(args.warmup):
-        plan.k_build(C, KC, K, Ex, sync=False)
-    plan.sync()
+        one_build()
+    sync_builds()
     ex_mixed = float(Ex.cpu()[0])
 
-    # timed builds: stage spans only (events around the stages and the whole pair loop; no
-    # wave is sampled or isolated, so the builds run exactly as untimed ones)
-    plan.set_timing(-1)
     torch.cuda.synchronize()
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -661,11 +683,16 @@ def main():
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            plan.k_build(C, KC, K, Ex, sync=False)
+            one_build()
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
     ms = ev0.elapsed_time(ev1)
+    sync_builds()
+    # stage spans (events around the stages and the whole pair loop, no wave sampled or
+    # isolated) from one more build with plain launches, untimed for the headline
+    plan.set_timing(-1)
+    plan.k_build(C, KC, K, Ex, sync=False)
     plan.sync()
     stages = plan.stage_times()
     # one more build, untimed for the headline, with every timing_every-th wave run alone
@@ -684,12 +711,13 @@ def main():
     info = plan.info()
 
     waves = pair_waves(w.nk, w.nocc, int(info["fields_per_wave"]))
-    stage_share = stage_ms_per_build(stages, waves, args.steps)
+    stage_share = stage_ms_per_build(stages, waves, 1)
     for name in ("pair_a", "pair_b", "pair_c"):   # from the one sampled build
         if name in stages:
             stage_share[name] = stages[name]["ms"] * waves / max(1, stages[name]["launches"])
     hbm, peak_kind = _peaks()
-    roof = roofline(stages, info, w.grid[0], w.ng, w.nocc, hbm, peak_kind)
+    roof = roofline(stages, info, w.grid[0], w.ng, w.nocc, hbm, peak_kind,
+                    tuning if tuning is not None else plan.tuning())
     tpeak, tpeak_kind = _tensor_peak()
     contraction_roof = tensor_roofline(info, stage_share.get("contract", 0.0), tpeak, tpeak_kind)
 
@@ -698,6 +726,9 @@ def main():
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic", "config": cfg, "roofline": roof,
            "gpu_launches": int(info["launches_per_build"]) * args.steps,
+           "tuning": tuning if tuning is not None else plan.tuning(),
+           "launch": ("one CUDA graph per build (occri_batch_* with this cell)" if batch is not None
+                      else "plain launches (occri_k_build)"),
            "stage_ms_per_build": stage_share, "E_x_mixed": ex_mixed,
            "roofline_contraction": contraction_roof}
     clocks = clk.summary()

@@ -64,13 +64,20 @@ typedef enum {
   OCCRI_EUNSUPPORTED = 6   /* valid input outside what this build implements */
 } occri_status;
 
-/* Kernels v(r) of the exchange operator (Eq. recipcoul, and the truncation of Sec. II.A):
- * OCCRI_COULOMB 1/r, OCCRI_ERFC erfc(omega r)/r, OCCRI_ERF erf(omega r)/r, and
+/* Kernels v(r) of the exchange operator (Eq. recipcoul, and the truncations of Sec. II.A):
+ * OCCRI_COULOMB 1/r, OCCRI_ERFC erfc(omega r)/r, OCCRI_ERF erf(omega r)/r,
  * OCCRI_COULOMB_TRUNC 1/r cut at R_c (Spencer-Alavi), (4 pi/3) R_c^3 = the volume of the
  * k-mesh's supercell D_1 a_1 x D_2 a_2 x D_3 a_3 (D_d: the k denominators, see occri_kmesh),
- * whose transform is (4 pi/x^2)(1 - cos(x R_c)). */
+ * whose transform is (4 pi/x^2)(1 - cos(x R_c)), and
+ * OCCRI_ERF_TRUNC erf(omega r)/r cut at the same R_c (Eq. lrtrunc, Appendix A), whose transform
+ * (4 pi/x^2)[e^{-x^2/(4 omega^2)} - e^{-omega^2 R_c^2} Re(e^{-i x R_c} w(z)) - erf(omega R_c)
+ * cos(x R_c)], z = -x/(2 omega) + i omega R_c, uses the Faddeeva function w (bounded in the
+ * upper half plane, so the cancellation of the appendix does not arise), evaluated in FP64 by
+ * Weideman's rational approximation with 40 terms (1994; ~1e-14 relative there). Its
+ * omega-derivative is not implemented: occri_vjp and occri_vjp_full return
+ * OCCRI_EUNSUPPORTED when asked for d/d omega with this kernel. */
 typedef enum {
-  OCCRI_COULOMB = 0, OCCRI_ERFC = 1, OCCRI_ERF = 2, OCCRI_COULOMB_TRUNC = 3
+  OCCRI_COULOMB = 0, OCCRI_ERFC = 1, OCCRI_ERF = 2, OCCRI_COULOMB_TRUNC = 3, OCCRI_ERF_TRUNC = 4
 } occri_kernel_kind;
 
 /* OCCRI_FP64: every step in double precision.
@@ -113,7 +120,9 @@ typedef struct {
   double omega;            /* range-separation parameter (bohr^-1), > 0 for erfc / erf */
   int g0_mode;             /* the G+q = 0 term (Eq. VGao's chi):
                               0: dropped;
-                              1: f(x -> 0): pi/omega^2 (erfc), 2 pi R_c^2 (truncated Coulomb);
+                              1: f(x -> 0): pi/omega^2 (erfc), 2 pi R_c^2 (truncated Coulomb),
+                                 4 pi [(R_c^2/2 - 1/(4 omega^2)) erf(omega R_c) + R_c
+                                 e^{-omega^2 R_c^2}/(2 omega sqrt(pi))] (truncated erf);
                               2: the Madelung correction of the supercell of volume V
                                  (Coulomb: chi = -V v_M, v_M the Ewald potential at a unit
                                  point charge from its images in a neutralising background;
@@ -193,11 +202,11 @@ int occri_k_build(occri_plan *plan, const void *C_dev, void *KC_dev, void *K_dev
 typedef struct {
   int k_per_wave;       /* k' per wave (1 .. the plan's scratch capacity) */
   int streams;          /* 1, 2 or 3: consecutive waves go round-robin over that many streams,
-                           each with its own scratch (the third is allocated on first use) */
+                           each with its own scratch (default 3) */
   int pass_b_div;       /* pass-B CTAs = resident CTA slots / pass_b_div (1 or 2) */
   int split_cd;         /* 1: separate passes C and D where the fused pass CD applies */
   double us_per_field;  /* autotuner: measured microseconds per pair field of this choice */
-  double us_default;    /* autotuner: the same for the default (widest wave, 2 streams, 1, 0) */
+  double us_default;    /* autotuner: the same for the default (widest wave, 3 streams, 1, 0) */
   int candidates;       /* autotuner: configurations timed; 0: taken from the cache;
                            occri_plan_tuning: -1 if the autotuner set it, else 0 */
 } occri_tune_t;
@@ -213,8 +222,7 @@ enum { OCCRI_TUNE_FORCE = 1 };   /* time again even if the cache holds this shap
  * the same shape, take it from the cache unless flags has OCCRI_TUNE_FORCE.
  * Synchronises the plan's stream. Leaves the plan's accumulators in an undefined state
  * (every build overwrites them). chosen (may be NULL) receives the configuration.
- * OCCRI_EINVAL for a NULL plan or unknown flags; OCCRI_ENOMEM if a third stream's scratch
- * cannot be had (candidates with three streams are then skipped, not an error). */
+ * OCCRI_EINVAL for a NULL plan or unknown flags. */
 int occri_plan_autotune(occri_plan *plan, int flags, occri_tune_t *chosen);
 
 /* The plan's current launch configuration (us_* fields 0). */
@@ -222,8 +230,7 @@ int occri_plan_tuning(const occri_plan *plan, occri_tune_t *current);
 
 /* Set the launch configuration by hand (k_per_wave >= 1, clamped to the scratch capacity;
  * streams 1, 2 or 3; pass_b_div 1 or 2; split_cd 0 or 1; other fields ignored), else
- * OCCRI_EINVAL; OCCRI_ENOMEM if three streams are asked for and the third scratch cannot be
- * allocated. Takes effect at the next build. */
+ * OCCRI_EINVAL. Takes effect at the next build. */
 int occri_plan_set_tuning(occri_plan *plan, const occri_tune_t *cfg);
 
 /* The paper's form of the assembly (Sec. II.C, Eq. occrikop): K ~ PKP + PKQ + QKP, where

@@ -27,9 +27,9 @@ OCCRI_EUNSUPPORTED = 6
 
 OCCRI_COULOMB, OCCRI_ERFC, OCCRI_ERF = 0, 1, 2
 OCCRI_FP64, OCCRI_MIXED, OCCRI_MIXED_TC = 0, 1, 2
-OCCRI_COULOMB_TRUNC = 3
+OCCRI_COULOMB_TRUNC, OCCRI_ERF_TRUNC = 3, 4
 KERNELS = {"coulomb": OCCRI_COULOMB, "erfc": OCCRI_ERFC, "erf": OCCRI_ERF,
-           "coulomb_trunc": OCCRI_COULOMB_TRUNC}
+           "coulomb_trunc": OCCRI_COULOMB_TRUNC, "erf_trunc": OCCRI_ERF_TRUNC}
 PRECISIONS = {"fp64": OCCRI_FP64, "mixed": OCCRI_MIXED, "mixed_tc": OCCRI_MIXED_TC}
 
 

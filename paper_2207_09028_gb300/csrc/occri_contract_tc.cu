@@ -1111,16 +1111,17 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
       }
       ct_begin[q.n_ct] = st.size();
       // CTAs: every column tile's stages are cut (at run ends) into `parts` ranges of about
-      // equal length, one CTA each. The CTAs of one part but different column tiles then
-      // read the same A blocks in the same order at about the same time, so each A block
-      // comes from DRAM once and from L2 for the other column tiles.
+      // equal length, one CTA each, with parts = SMs / column tiles (one more for the first
+      // SMs % column tiles tiles, so that every SM has a CTA). The CTAs of one part but
+      // different column tiles then read the same A blocks in about the same order at about
+      // the same time, so an A block comes from DRAM once and from L2 for the others.
       slab.stage0 = (long long)stages.size();
       slab.cta0 = (int)cta_stage0.size();
-      const int parts = std::max(1, nsm / q.n_ct);
       int b = 0;
       for (int ct = 0; ct < q.n_ct; ++ct) {
         const size_t b0 = ct_begin[ct], b1 = ct_begin[ct + 1];
         if (b1 == b0) continue;
+        const int parts = std::max(1, nsm / q.n_ct + (ct < nsm % q.n_ct ? 1 : 0));
         cta_stage0.push_back(slab.stage0 + (long long)b0);
         ++b;
         int part = 1;

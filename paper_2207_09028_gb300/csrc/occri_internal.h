@@ -71,6 +71,8 @@ constexpr int kMaxTcAtoms = 8;
 struct TcPlan;   // tables and buffers of the tensor-core contraction (occri_contract_tc.cu)
 
 // Parameters of one wave of pair fields (steps c, d): output k, a block of k'.
+constexpr int kFadN = 40;   // terms of the Faddeeva approximation (OCCRI_ERF_TRUNC)
+
 struct PairParams {
   int nk, nocc, N1;          // N1: cubic grid edge
   long long ng;
@@ -92,6 +94,11 @@ struct PairParams {
   double g0;                 // value at G+q = 0, in units of 4 pi
   double dg0;                // d g0 / d omega, in units of 4 pi
   double rc;                 // truncation radius of OCCRI_COULOMB_TRUNC
+  // OCCRI_ERF_TRUNC: Weideman's coefficients of the Faddeeva function w(z) (Im z > 0),
+  // w = 2 P(Z)/(L - i z)^2 + 1/(sqrt(pi) (L - i z)), Z = (L + i z)/(L - i z),
+  // P(Z) = sum_n fad_a[n] Z^n; erf(omega R_c) and e^{-omega^2 R_c^2}
+  double fad_a[kFadN];
+  double fad_L, lr_erf, lr_exp;
   int b_div;                 // pass-B CTAs = resident slots / b_div (set by the autotuner)
   int split_cd;              // 1: passes C and D even where the fused pass CD applies
   // FP32 copies (hi/lo for the metric) made on the host, so FP32 kernels never
@@ -112,7 +119,8 @@ struct Plan {
   occri_kernel kernel;
   cudaStream_t stream;
   double g0_4pi = 0.0, dg0_4pi = 0.0;   // the G+q = 0 value and its omega-derivative / (4 pi)
-  double rc = 0.0;                       // truncation radius (OCCRI_COULOMB_TRUNC)
+  double rc = 0.0;                       // truncation radius (OCCRI_COULOMB_TRUNC, _ERF_TRUNC)
+  double fad_a[kFadN] = {}, fad_L = 0.0, lr_erf = 0.0, lr_exp = 0.0;   // OCCRI_ERF_TRUNC
   int device = 0;            // the CUDA device current at plan creation; every call runs on it
   int fault = 0;             // test-only fault injection (occri_plan_inject_fault)
   long long wait_ns = 2000000000LL;   // limit of the bounded device waits
@@ -123,7 +131,7 @@ struct Plan {
   int nkp_wave;              // k' per wave
   int nkp_cap = 1;           // k' per wave the scratch buffers hold
   // launch configuration of the pair loop (occri_plan_autotune may change it)
-  int nstreams = 2;          // consecutive waves go round-robin over 1, 2 or 3 streams
+  int nstreams = 3;          // consecutive waves go round-robin over 1, 2 or 3 streams
   int b_div = 1;             // pass-B CTAs = resident slots / b_div
   int split_cd = 0;          // 1: passes C and D instead of the fused pass CD
   int tuned = 0;             // 1: the configuration came from the autotuner (or its cache)
@@ -165,7 +173,7 @@ struct Plan {
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_y = nullptr, ev_iso = nullptr;
   cudaEvent_t ev_iso2 = nullptr;
-  // a third stream and scratch, made when a launch configuration asks for three streams
+  // the third stream and scratch (three waves in flight)
   cudaStream_t aux2 = nullptr;
   void* scratch3 = nullptr;
   size_t scratch_bytes = 0;  // bytes of each scratch buffer

@@ -86,6 +86,36 @@ __device__ __forceinline__ T kernel_f(T g2h, T g2l, int kind, T inv4w2, double r
   return base * exp_t(-y);
 }
 
+// f(|G+q|)/(4 pi) of the truncated erf kernel (Eq. lrtrunc) for |G+q|^2 = g2 > 0, in FP64:
+//   [e^{-y} - e^{-omega^2 R_c^2} Re(e^{-i x R_c} w(z)) - erf(omega R_c) cos(x R_c)] / x^2,
+// y = x^2/(4 omega^2), z = -x/(2 omega) + i omega R_c, with the Faddeeva function w from
+// Weideman's rational approximation (coefficients made on the host).
+__device__ __forceinline__ double kernel_lr_trunc(double g2, const PairParams& p) {
+  const double x = sqrt(g2), w = p.omega, R = p.rc;
+  const double zr = -x / (2.0 * w), zi = w * R;
+  // d = L - i z, n = L + i z (i z = -zi + i zr)
+  const double L = p.fad_L;
+  const double dr = L + zi, di = -zr, nr = L - zi, ni = zr;
+  const double den = dr * dr + di * di;
+  const double Zr = (nr * dr + ni * di) / den, Zi = (ni * dr - nr * di) / den;
+  double pr = p.fad_a[kFadN - 1], pi = 0.0;
+#pragma unroll 4
+  for (int n = kFadN - 2; n >= 0; --n) {
+    const double tr = pr * Zr - pi * Zi + p.fad_a[n];
+    pi = pr * Zi + pi * Zr;
+    pr = tr;
+  }
+  const double ir = dr / den, ii = -di / den;            // 1/d
+  const double i2r = ir * ir - ii * ii, i2i = 2.0 * ir * ii;
+  constexpr double kInvSqrtPi = 0.56418958354775628694807945156077259;
+  const double fr = 2.0 * (pr * i2r - pi * i2i) + kInvSqrtPi * ir;
+  const double fi = 2.0 * (pr * i2i + pi * i2r) + kInvSqrtPi * ii;
+  double sn, cs;
+  sincos(x * R, &sn, &cs);
+  const double t = exp(-g2 / (4.0 * w * w)) - p.lr_exp * (cs * fr + sn * fi);
+  return (t - p.lr_erf * cs) / g2;
+}
+
 // (d f/d omega)/(4 pi) = -/+ e^{-x^2/(4 omega^2)} / (2 omega^3) (erfc / erf).
 template <typename T>
 __device__ __forceinline__ T kernel_df(T g2, int kind, T inv4w2, T omega) {
@@ -467,6 +497,8 @@ __device__ __forceinline__ T bin_value(const PairParams& p, const Consts<T>& k,
                                        const Axis1<T>& a, const ColumnConst<T>& c) {
   if ((a.flags & 2) && c.zero) return DERIV ? k.dg0 : k.g0;
   auto f = [&](T g2h, T g2l) {
+    if (!DERIV && p.kind == OCCRI_ERF_TRUNC)
+      return T(kernel_lr_trunc((double)g2h + (double)g2l, p));
     return DERIV ? kernel_df<T>(g2h + g2l, p.kind, k.inv4w2, k.omega)
                  : kernel_f<T>(g2h, g2l, p.kind, k.inv4w2, p.rc);
   };

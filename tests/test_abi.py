@@ -61,6 +61,9 @@ def _create(w, **over):
     (dict(kernel="erfc", omega=0.0), occri.OCCRI_EINVAL),
     (dict(kernel="erf", omega=0.3, g0_mode=1), occri.OCCRI_EINVAL),
     (dict(kernel="coulomb", g0_mode=1), occri.OCCRI_EINVAL),
+    (dict(kernel="erf_trunc", omega=0.0), occri.OCCRI_EINVAL),
+    (dict(kernel="erf_trunc", omega=0.3, g0_mode=2), occri.OCCRI_EINVAL),
+    (dict(kernel=5, omega=0.3), occri.OCCRI_EINVAL),
     (dict(precision=7), occri.OCCRI_EINVAL),
     (dict(lattice=np.zeros((3, 3))), occri.OCCRI_EINVAL),
     (dict(shell_atom=np.array([1, 0, 0, 1, 1, 1])), occri.OCCRI_EINVAL),

@@ -133,7 +133,28 @@ SINGULAR = [
          g0_mode=1),
     dict(mesh=(1, 1, 1), grid=(16, 16, 16), counts=(2, 1), nocc=2, kernel="coulomb_trunc",
          g0_mode=1),
+    dict(mesh=(1, 1, 2), grid=(12, 12, 12), counts=(2, 1, 1), nocc=3, kernel="erf_trunc",
+         omega=0.5, g0_mode=1),
+    dict(mesh=(2, 1, 1), grid=(10, 10, 10), counts=(2, 1), nocc=2, kernel="erf_trunc",
+         omega=0.3, g0_mode=1),
 ]
+
+
+def test_truncated_erf_has_no_omega_gradient(torch_cuda):
+    """The omega-derivative of the truncated erf kernel is not implemented: asking for it is
+    refused instead of returning zero."""
+    import paper_2207_09028_gb300 as occri
+    torch = torch_cuda
+    w = small_workload(mesh=(1, 1, 1), grid=(8, 8, 8), counts=(2, 1), nocc=2, kernel="erf_trunc",
+                       omega=0.5, g0_mode=1, seed=320)
+    plan = occri.Plan.from_workload(w, precision="fp64")
+    C = torch.from_numpy(w.C).cuda()
+    plan.build(C, want_k=False)
+    with pytest.raises(occri.OccriError) as e:
+        plan.vjp(C, 1.0, want_c=False, want_omega=True)
+    assert e.value.status == occri.OCCRI_EUNSUPPORTED
+    g, _ = plan.vjp(C, 1.0, want_omega=False)   # the C gradient is available
+    assert g is not None
 
 
 @pytest.mark.parametrize("case", range(len(SINGULAR)))
