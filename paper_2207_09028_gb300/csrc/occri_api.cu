@@ -616,6 +616,20 @@ ace_adjoint_kernel(const double2* __restrict__ C, const double2* __restrict__ kc
   }
 }
 
+// y += a + b over n complex values (the streams' private accumulators into Y)
+template <typename C2>
+__global__ void add3_kernel(C2* __restrict__ y, const C2* __restrict__ a, const C2* __restrict__ b,
+                            long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    C2 v = y[i];
+    const C2 u = a[i], w = b[i];
+    v.x += u.x + w.x;
+    v.y += u.y + w.y;
+    y[i] = v;
+  }
+}
+
 __global__ void add_kernel(const double2* __restrict__ a, const double2* __restrict__ b,
                            double2* __restrict__ out, long long n) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -634,6 +648,8 @@ void free_plan(Plan* p) {
     if (b) cudaFree(b);
   if (p->scratch2) cudaFree(p->scratch2);
   if (p->scratch3) cudaFree(p->scratch3);
+  for (void* yx : p->Yx)
+    if (yx) cudaFree(yx);
   if (p->asm_scratch) cudaFree(p->asm_scratch);
   for (void* b : {p->gam, p->gpsi, p->cs_g, (void*)p->gkc, (void*)p->gcf, (void*)p->gacc})
     if (b) cudaFree(b);
@@ -708,6 +724,9 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
   long long launches = 0;
   const size_t orb = (size_t)p->nk * p->nocc * p->fs;
   if (cudaMemsetAsync(p->Y, 0, orb * sizeof(cplx_t<T>), s) != cudaSuccess) return OCCRI_ECUDA;
+  for (void* yx : p->Yx)
+    if (yx && cudaMemsetAsync(yx, 0, orb * sizeof(cplx_t<T>), s) != cudaSuccess)
+      return OCCRI_ECUDA;
   if (cudaMemsetAsync(p->kc, 0, sizeof(double2) * (size_t)p->nk * p->nao * p->nocc, s) != cudaSuccess)
     return OCCRI_ECUDA;
   {
@@ -730,6 +749,10 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
     const int ns = p->nstreams;
     cudaStream_t st[3] = {s, p->aux, p->aux2};
     void* sc[3] = {p->scratch, p->scratch2, p->scratch3};
+    // with private accumulators per stream, no wave waits for another stream's Y updates
+    const bool split_y = p->Yx[0] && p->Yx[1];
+    void* yacc[3] = {p->Y, split_y ? p->Yx[0] : p->Y, split_y ? p->Yx[1] : p->Y};
+    cudaEvent_t ev_y = split_y ? nullptr : p->ev_y;
     cudaEvent_t join[3] = {nullptr, p->ev_join, p->ev_join2};
     cudaEvent_t iso[3] = {p->ev_iso, p->ev_iso2, p->ev_iso3};
     if (cudaEventRecord(p->ev_fork, s) != cudaSuccess) return OCCRI_ECUDA;
@@ -758,8 +781,8 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
         if (sample)
           for (int i = 0; i < 4 && sample; ++i) sample = (ev[i] = take_event(p)) != nullptr;
         if (sample && !isolate(w)) return OCCRI_ECUDA;   // wait for the other streams' work
-        if (launch_pair_wave<T>(*p, k, kp0, nkp, diag, st[w], sc[w], sample ? ev : nullptr,
-                                p->ev_y) != cudaSuccess)
+        if (launch_pair_wave<T>(*p, k, kp0, nkp, diag, st[w], sc[w], yacc[w],
+                                sample ? ev : nullptr, ev_y) != cudaSuccess)
           return OCCRI_ECUDA;
         launches += pair_wave_launches<T>(p->nocc, p->split_cd);
         const double nf = (double)wave_fields(p->nocc, nkp, diag);
@@ -778,6 +801,11 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
       if (cudaEventRecord(join[o], st[o]) != cudaSuccess ||
           cudaStreamWaitEvent(s, join[o], 0) != cudaSuccess)
         return OCCRI_ECUDA;
+    if (split_y) {
+      add3_kernel<<<8 * 152, 256, 0, s>>>((cplx_t<T>*)p->Y, (const cplx_t<T>*)p->Yx[0],
+                                          (const cplx_t<T>*)p->Yx[1], (long long)orb);
+      ++launches;
+    }
     all.done(OCCRI_STAGE_PAIRS, fields);
   }
   {
@@ -1033,6 +1061,8 @@ int ensure_third_stream(Plan* p) {
   if (e == cudaSuccess) return OCCRI_OK;
   cudaGetLastError();
   if (p->scratch3) cudaFree(p->scratch3);
+  for (void* yx : p->Yx)
+    if (yx) cudaFree(yx);
   if (p->aux2) cudaStreamDestroy(p->aux2);
   if (p->ev_join2) cudaEventDestroy(p->ev_join2);
   if (p->ev_iso3) cudaEventDestroy(p->ev_iso3);
@@ -1093,8 +1123,10 @@ int tune_time(Plan* p, const TuneCfg& cfg, int reps, double* us_per_field) {
       const int diag = p->nk > 1 ? 0 : 1;
       const int nkp = diag ? 1 : std::min(cfg.nkp, p->nk - kp0);
       const int sw = w % cfg.nstreams;
-      ok = occri::launch_pair_wave<T>(*p, 0, kp0, nkp, diag, st[sw], sc[sw], nullptr,
-                                      p->ev_y) == cudaSuccess;
+      const bool split_y = p->Yx[0] && p->Yx[1];
+      void* ya = split_y && sw > 0 ? p->Yx[sw - 1] : p->Y;
+      ok = occri::launch_pair_wave<T>(*p, 0, kp0, nkp, diag, st[sw], sc[sw], ya, nullptr,
+                                      split_y ? nullptr : p->ev_y) == cudaSuccess;
       fields += (double)occri::wave_fields(p->nocc, nkp, diag);
       if (!diag) {
         kp0 += nkp;
@@ -1568,6 +1600,11 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     unsigned char* b = nullptr;
     chk(dalloc(&b, orb * csz, &tot)); p->psi = b; b = nullptr;
     chk(dalloc(&b, orb * csz, &tot)); p->Y = b; b = nullptr;
+    // the second and third streams' private accumulators, where they cost at most 16 GiB
+    if (2 * orb * csz <= ((size_t)16 << 30)) {
+      chk(dalloc(&b, orb * csz, &tot)); p->Yx[0] = b; b = nullptr;
+      chk(dalloc(&b, orb * csz, &tot)); p->Yx[1] = b; b = nullptr;
+    }
     // behind each scratch buffer, the kernel tables v/(4 pi) of one wave (one per k')
     const size_t sbytes = (size_t)p->fields_cap * field_bytes + (size_t)nkp * ng * (csz / 2);
     p->scratch_bytes = sbytes;

@@ -164,6 +164,10 @@ struct Plan {
   // long, so each starts 512-byte aligned (whole-tile bulk copies).
   void* psi = nullptr;       // [nk][nocc][fs] cplx_t<T>
   void* Y = nullptr;         // [nk][nocc][fs] cplx_t<T>
+  // private accumulators of the second and third streams (same layout), added into Y after
+  // the wave loop, so that waves on different streams never wait for each other's updates;
+  // null when they would take too much memory (the streams' updates of Y are then chained)
+  void* Yx[2] = {nullptr, nullptr};
   void* scratch = nullptr;   // [fields_cap][fs] cplx_t<T>, waves on the plan's stream, then
                              // the wave's kernel tables [nkp_wave][m3][m1][m2] T
   void* scratch2 = nullptr;  // the same for the waves on the second stream
@@ -256,12 +260,14 @@ cudaError_t launch_phase_fields(const Plan& p, void* F, int sign, cudaStream_t s
                                 int nkk = -1);
 // Pair-wave launches over unordered pairs: diag = 1 is the wave (k, k) with fields
 // i <= j; diag = 0 covers k' in [kp0, kp0 + nkp), all kp0 > k, with every (i, j).
-// S is the wave's scratch. When ev != nullptr, ev[0..3] are recorded before pass A,
-// before pass B, before pass C and after pass D. When ev_y != nullptr, pass D first
-// waits for it and then records it (orders the Y updates of waves on two streams).
+// S is the wave's scratch and Y the accumulator the wave adds into (the plan's Y, or the
+// private one of the wave's stream). When ev != nullptr, ev[0..3] are recorded before pass
+// A, before pass B, before pass C and after pass D. When ev_y != nullptr, pass D first
+// waits for it and then records it (orders the updates of one Y by waves on several streams).
 template <typename T>
 cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s,
-                             void* S, cudaEvent_t* ev = nullptr, cudaEvent_t ev_y = nullptr);
+                             void* S, void* Y, cudaEvent_t* ev = nullptr,
+                             cudaEvent_t ev_y = nullptr);
 template <typename T>
 cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s);
 // One wave of the adjoint build: forward potentials in scratch, adjoint potentials in

@@ -5,7 +5,7 @@ namespace occri {
 
 template <typename T>
 cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s,
-                             void* scratch, cudaEvent_t* ev, cudaEvent_t ev_y) {
+                             void* scratch, void* Yacc, cudaEvent_t* ev, cudaEvent_t ev_y) {
   PairParams pp = p.pair_params();
   pp.k = k;
   pp.kp0 = kp0;
@@ -13,7 +13,7 @@ cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, int diag, c
   pp.diag = diag;
   const cplx_t<T>* psi = (const cplx_t<T>*)p.psi;
   cplx_t<T>* S = (cplx_t<T>*)scratch;
-  cplx_t<T>* Y = (cplx_t<T>*)p.Y;
+  cplx_t<T>* Y = (cplx_t<T>*)Yacc;
   switch (p.N[0]) {
 #define OCCRI_PAIR_CASE(NN) \
   case NN:                  \
@@ -75,9 +75,9 @@ template cudaError_t launch_vjp_wave<float>(const Plan&, int, int, int, int, dou
 template cudaError_t launch_vjp_wave<double>(const Plan&, int, int, int, int, double*,
                                              cudaStream_t);
 template cudaError_t launch_pair_wave<float>(const Plan&, int, int, int, int, cudaStream_t, void*,
-                                             cudaEvent_t*, cudaEvent_t);
+                                             void*, cudaEvent_t*, cudaEvent_t);
 template cudaError_t launch_pair_wave<double>(const Plan&, int, int, int, int, cudaStream_t, void*,
-                                              cudaEvent_t*, cudaEvent_t);
+                                              void*, cudaEvent_t*, cudaEvent_t);
 template cudaError_t launch_domega_wave<float>(const Plan&, int, int, int, int, cudaStream_t);
 template cudaError_t launch_domega_wave<double>(const Plan&, int, int, int, int, cudaStream_t);
 
