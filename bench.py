@@ -343,10 +343,12 @@ def alu_roofline(fields: float, ng: int, ms: float, peak_tflops: float, kind: st
 # M = 128 AO rows, N = 256 real columns, K = 32 grid points
 
 
-def tensor_roofline(info: dict, contract_ms: float, peak_tflops: float, peak_kind: str):
-    """Roofline of the tensor-core contraction: the MMA flops of its stages over the
-    contraction stage's time, against the measured dense bf16 rate (FP16 runs at the same
-    rate on these tensor cores)."""
+def tensor_roofline(info: dict, contract_ms: float, peak_tflops: float, peak_kind: str,
+                    stage_ms: float = 0.0):
+    """Roofline of the tensor-core contraction: the MMA flops of its stages over the time of
+    its GEMM kernels (CUDA events around each launch), against the measured dense bf16 rate
+    (FP16 runs at the same rate on these tensor cores). `stage_ms`, the whole contraction
+    stage (with the Y conversion and the A-block generation), is reported beside it."""
     st = int(info.get("tc_stages", 0))
     fps = float(info.get("tc_flops_per_stage", 0.0))
     if not info.get("contraction_tc") or st <= 0 or contract_ms <= 0 or fps <= 0:
@@ -355,7 +357,9 @@ def tensor_roofline(info: dict, contract_ms: float, peak_tflops: float, peak_kin
     return {"kernel": "contract_tc_kernel (tcgen05.mma kind::f16, FP16 hi/lo x3, FP32 accumulate)",
             "bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "peak_kind": peak_kind, "stages": st,
-            "flops_per_stage": fps,
+            "flops_per_stage": fps, "gemm_ms": contract_ms, "stage_ms": stage_ms,
+            "frac_of_stage": (fps * st / (stage_ms / 1e3) / 1e12 / peak_tflops
+                              if stage_ms > 0 else None),
             "useful_frac": achieved / 3.0 / peak_tflops}
 
 
@@ -719,7 +723,8 @@ def main():
     roof = roofline(stages, info, w.grid[0], w.ng, w.nocc, hbm, peak_kind,
                     tuning if tuning is not None else plan.tuning())
     tpeak, tpeak_kind = _tensor_peak()
-    contraction_roof = tensor_roofline(info, stage_share.get("contract", 0.0), tpeak, tpeak_kind)
+    contraction_roof = tensor_roofline(info, stage_share.get("contract_gemm", 0.0), tpeak,
+                                       tpeak_kind, stage_share.get("contract", 0.0))
 
     out = {"impl": "occri", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -775,7 +780,7 @@ def main():
         ms64 = e0.elapsed_time(e1) / args.fp64_steps
         ex64 = float(Ex64.cpu()[0])
         peaks = {k: occri.measure_fma_peak(k) for k in ("fp64", "fp32", "fp32x2")}
-        fields = stages.get("pairs", {}).get("units", 0.0) / max(1, args.steps)
+        fields = stages.get("pairs", {}).get("units", 0.0)   # one build with stage spans
         out["fp64_gpu"] = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
                            "steps": args.fp64_steps, "E_x": ex64,
                            "mixed_speedup": ms64 / ms_per_step,

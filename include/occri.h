@@ -158,7 +158,10 @@ enum {
   OCCRI_STAGE_CONTRACT = 4,  /* (e) */
   OCCRI_STAGE_ASSEMBLE = 5,  /* (f) */
   OCCRI_STAGE_PAIRS = 6,     /* (c)+(d): the whole loop over pair waves, wall time */
-  OCCRI_NSTAGES = 7
+  OCCRI_STAGE_CONTRACT_GEMM = 7,  /* (e) on the tensor cores: the GEMM kernels alone (inside
+                                     OCCRI_STAGE_CONTRACT, which also holds the Y conversion
+                                     and the A-block generation) */
+  OCCRI_NSTAGES = 8
 };
 
 typedef struct occri_plan occri_plan;

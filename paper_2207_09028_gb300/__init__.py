@@ -81,7 +81,8 @@ EXPORTED = ["occri_plan_create", "occri_plan_destroy", "occri_plan_info", "occri
 
 OCCRI_FAULT_NONE, OCCRI_FAULT_WAIT = 0, 1
 
-STAGES = ["orbitals", "pair_a", "pair_b", "pair_c", "contract", "assemble", "pairs"]
+STAGES = ["orbitals", "pair_a", "pair_b", "pair_c", "contract", "assemble", "pairs",
+          "contract_gemm"]
 
 _lib_handle = None
 

@@ -813,7 +813,23 @@ int build_impl(Plan* p, const double2* C, void* KC, void* K, double* Ex) {
     if (launch_phase_fields<T>(*p, p->Y, +1, s) != cudaSuccess) return OCCRI_ECUDA;
     ++launches;
     if (p->tc) {
-      if (launch_contract_tc(*p, s) != cudaSuccess) return OCCRI_ECUDA;
+      // the GEMM kernels alone, one span per slab (stage OCCRI_STAGE_CONTRACT_GEMM)
+      struct GemmSpans : LaunchHook {
+        Plan* p;
+        cudaStream_t s;
+        bool on;
+        StageTimer* t = nullptr;
+        GemmSpans(Plan* pl, cudaStream_t st, bool timed) : p(pl), s(st), on(timed) {}
+        void before() override {
+          if (on) t = new StageTimer(p, true, s);
+        }
+        void after() override {
+          if (t) t->done(OCCRI_STAGE_CONTRACT_GEMM, 1.0);
+          delete t;
+          t = nullptr;
+        }
+      } spans(p, s, timed);
+      if (launch_contract_tc(*p, s, &spans) != cudaSuccess) return OCCRI_ECUDA;
       launches += tc_plan_launches(p->tc);
     } else {
       if (launch_contract<T>(*p, s) != cudaSuccess) return OCCRI_ECUDA;

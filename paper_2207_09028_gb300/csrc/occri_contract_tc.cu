@@ -1219,7 +1219,7 @@ int tc_plan_create(Plan* p, const std::vector<ShellDev>& sh, const double* xyz,
   return OCCRI_OK;
 }
 
-cudaError_t launch_contract_tc(const Plan& p, cudaStream_t s) {
+cudaError_t launch_contract_tc(const Plan& p, cudaStream_t s, LaunchHook* hook) {
   using namespace tcc;
   TcPlan* t = p.tc;
   TcParams q = t->prm;
@@ -1244,7 +1244,9 @@ cudaError_t launch_contract_tc(const Plan& p, cudaStream_t s) {
     qs.nblocks = sl.nblocks;
     qs.cta_stage0 = q.cta_stage0 + sl.cta0;
     gen_blocks_kernel<<<std::min(sl.nblocks, 152 * 8), kGenThreads, 0, s>>>(qs);
+    if (hook) hook->before();
     contract_tc_kernel<<<sl.ncta, kThreads, t->smem, s>>>(qs);
+    if (hook) hook->after();
   }
   return cudaGetLastError();
 }

@@ -312,7 +312,13 @@ cudaError_t launch_gather_cols(const double2* all, double2* cr, long long rows, 
                                cudaStream_t s);
 cudaError_t launch_band_diff(const double2* all, const double2* rr, double2* out, long long rows,
                              int nocc, int nr, cudaStream_t s);   // MMA flops of one stage of the tensor-core contraction   // stages of one contraction (0 without a plan)
-cudaError_t launch_contract_tc(const Plan& p, cudaStream_t s);
+// Called around every GEMM launch of the tensor-core contraction (stage timing).
+struct LaunchHook {
+  virtual void before() = 0;
+  virtual void after() = 0;
+  virtual ~LaunchHook() = default;
+};
+cudaError_t launch_contract_tc(const Plan& p, cudaStream_t s, LaunchHook* hook = nullptr);
 
 // Launch settings derived once per kernel instantiation and device (function attributes,
 // resident-slot counts): each entry is filled under a lock the first time a plan on that
