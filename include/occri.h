@@ -343,8 +343,8 @@ int occri_plan_stage_times(occri_plan *plan, double *ms, long long *launches, do
 #define OCCRI_STATIC_SCRATCH_BYTES (32u << 20)
 
 /* occri_orbitals for callers that cannot allocate device memory at call time -- for
- * example code running while a stream is being captured into a CUDA graph, or hosts
- * whose device memory is owned by another allocator. No counterpart in the paper.
+ * example hosts whose device memory is owned by another allocator. No counterpart in the
+ * paper.
  * Same inputs, output and result as occri_orbitals, but the call's scratch (the
  * normalised coefficients and the orbitals before widening) lives in one static
  * device array of OCCRI_STATIC_SCRATCH_BYTES instead of the plan's workspaces; the
@@ -353,7 +353,7 @@ int occri_plan_stage_times(occri_plan *plan, double *ms, long long *launches, do
  * or 8*nk*nocc*F (mixed) bytes of it, F being N_g rounded up to a multiple of 64;
  * larger problems return OCCRI_EINVAL before anything is launched.
  * The first call on each device looks up the array's device address (with that device
- * current); make that first call before any stream capture. All calls share the one
+ * current). All calls share the one
  * array and it keeps the previous call's contents (every byte a call reads it has
  * written first, so nothing needs clearing); calls whose work overlaps on the GPU --
  * on different streams, or from different host threads -- race on it and must be

@@ -343,7 +343,8 @@ __device__ __forceinline__ void block_tables(const TcParams& p, StageTab& tb, in
 // 32 points r - L_l of point tile rt, FP16 hi then lo, in the tensor cores' layout. One CTA
 // per block at a time; warp 0 builds the tables, every thread generates (shell entry, four
 // points) items into shared memory, and the block is stored with 16-byte coalesced stores.
-__global__ void __launch_bounds__(kGenThreads) gen_blocks_kernel(TcParams p) {
+// Three CTAs per SM (80 registers) hide the block barriers a little better than two.
+__global__ void __launch_bounds__(kGenThreads, 3) gen_blocks_kernel(TcParams p) {
   __shared__ __align__(16) unsigned char a[kABlock];
   __shared__ StageTab tb;
   __shared__ TcShell shells[kMaxEntries];

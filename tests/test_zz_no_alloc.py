@@ -1,5 +1,5 @@
 """occri_orbitals_noalloc: the orbital stage for callers that cannot allocate device
-memory during the call (e.g. while a stream is captured into a CUDA graph). It must
+memory during the call. It must
 give what the allocating entry point occri_orbitals gives, call after call, although
 every call reuses the library's one static scratch array.
 
