@@ -583,6 +583,24 @@ pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams 
       const C2 b = cmulc<T>(__ldg(gj + off), __ldg(pi + off));
       pl[n2 * P + n3] = mk<T>(a.x + b.x, a.y + b.y);
     });
+  } else if constexpr (std::is_same<T, float>::value && N % 2 == 0) {
+    // two points per 16-byte load: N/2 threads per row, more bytes in flight per thread
+    // (every plane row starts 16-byte aligned: fs, N and the column are even)
+    constexpr int H = N / 2;
+    constexpr int RT2 = threads_for(N) / H;
+    const int t = threadIdx.x;
+    if (t < RT2 * H) {
+      const int c = 2 * (t % H);
+      const float4* pj4 = reinterpret_cast<const float4*>(pj);
+      const float4* pi4 = reinterpret_cast<const float4*>(pi);
+#pragma unroll 4
+      for (int r = t / H; r < N; r += RT2) {
+        const size_t off = ((size_t)r * N * N + c) / 2;
+        const float4 a = __ldg(pj4 + off), b = __ldg(pi4 + off);
+        pl[c * P + r] = cmulc<T>(make_float2(a.x, a.y), make_float2(b.x, b.y));
+        pl[(c + 1) * P + r] = cmulc<T>(make_float2(a.z, a.w), make_float2(b.z, b.w));
+      }
+    }
   } else {
     plane_loop<N>([&](int n3, int n2) {
       const size_t off = (size_t)n3 * N * N + n2;
