@@ -247,9 +247,14 @@ __device__ __forceinline__ void line_fft(cplx_t<T>* base, int stride, bool inver
 // its loads and its stores: __syncwarp for adjacent lanes, else named barrier `bar`
 // (1 or 2: at most two pairs of warps per CTA, N <= 64), or with bar = 0 the whole CTA
 // (every thread of the CTA then calls it).
-template <typename T, int N, typename Post>
+struct NoMid {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+template <typename T, int N, typename Post, typename Mid = NoMid>
 __device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool inverse, bool store,
-                                          int h, bool valid, int bar, Post&& post) {
+                                          int h, bool valid, int bar, Post&& post,
+                                          Mid&& mid = Mid()) {
   constexpr int M = N / 2;
   auto pair_barrier = [&]() {
     if constexpr (kPairLanes) {
@@ -297,6 +302,7 @@ __device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool inve
       });
     }
     pair_barrier();
+    mid();   // every line of the CTA is in registers when bar == 0
     fft::pfft_dif<M, -1>(x);
     fft::static_for<M>([&](auto I) {
       constexpr int q = decltype(I)::value;
@@ -334,6 +340,7 @@ __device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool inve
       });
     }
     pair_barrier();
+    mid();   // every line of the CTA is in registers when bar == 0
     fft::fft_dif<M, -1>(re, im);
     fft::static_for<M>([&](auto I) {
       constexpr int q = decltype(I)::value;
@@ -349,6 +356,21 @@ __device__ __forceinline__ void line_fft2(cplx_t<T>* base, int stride, bool inve
 
 // One transform job over the N lines of a plane (rows: along the contiguous index;
 // columns: along the pitched index); every thread of the CTA must call it.
+// As run_lines for even N, with the pair barrier made CTA-wide and mid() called after it by
+// every thread: the plane in shared memory is free from then on (every line is in registers).
+template <typename T, int N, typename Post, typename Mid>
+__device__ __forceinline__ void run_lines_then(cplx_t<T>* plane, int P, bool rows, bool inverse,
+                                               Post&& post, Mid&& mid) {
+  static_assert(line_split(N) == 2, "even edges");
+  const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+  const int line0 = kPairLanes ? (int)threadIdx.x >> 1 : (w >> 1) * 32 + lane;
+  const int h = kPairLanes ? (int)threadIdx.x & 1 : w & 1;
+  const bool valid = line0 < N;
+  const int line = valid ? line0 : N - 1;
+  line_fft2<T, N>(rows ? plane + line * P : plane + line, rows ? 1 : P, inverse, false, h, valid,
+                  0, [&](int k, T& re, T& im) { post(line, k, re, im); }, mid);
+}
+
 template <typename T, int N, typename Post>
 __device__ __forceinline__ void run_lines(cplx_t<T>* plane, int P, bool rows, bool inverse,
                                           bool store, Post&& post) {
@@ -704,13 +726,24 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
       run_lines<T, N>(plane, P, true, true, true, [](int, int, T&, T&) {});
       __syncthreads();
       C2* buf = S + (size_t)f * p.fs + (size_t)m3 * N * N;
-      run_lines<T, N>(plane, P, false, true, false, [&](int line, int k, T& re, T& im) {
-        buf[(size_t)k * N + line] = mk<T>(re, im);
-      });
-      __syncthreads();   // releases the buffers for the next item's copies
+      auto out = [&](int line, int k, T& re, T& im) { buf[(size_t)k * N + line] = mk<T>(re, im); };
+      if constexpr (line_split(N) == 2) {
+        // the next item's copies start as soon as every line of this last transform is in
+        // registers, and overlap its arithmetic and stores
+        run_lines_then<T, N>(plane, P, false, true, out, [&]() {
+          if (it + 1 < i1) stage(it + 1);
+          cp_async_commit();
+        });
+      } else {
+        run_lines<T, N>(plane, P, false, true, false, out);
+        __syncthreads();   // releases the buffers for the next item's copies
+        if (it + 1 < i1) stage(it + 1);
+        cp_async_commit();
+      }
+    } else {
+      if (it + 1 < i1) stage(it + 1);
+      cp_async_commit();
     }
-    if (it + 1 < i1) stage(it + 1);
-    cp_async_commit();
   }
   if constexpr (DOMEGA) {
     double part = double(dsum);
