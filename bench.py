@@ -289,8 +289,9 @@ def roofline(stages: dict, info: dict, edge: int, ng: int, nocc: int, hbm: float
 
     Its unit is one transformed field; each of the two 3-D transforms reads and writes the
     field once, so the streaming model is 2 x 2 x 8 B x N_g = 32 N_g bytes per field in
-    FP32 (c64). A round trip runs as four launches over a wave of fields (kernel tables,
-    pass_a, pass_b and the fused pass_cd; FP64 or nocc > 8: pass_c and pass_d instead);
+    FP32 (c64). A round trip runs as three launches over a wave of fields (pass_a, whose extra
+    CTAs fill the kernel tables, pass_b and the fused pass_cd; FP64 or nocc > 8: pass_c and
+    pass_d instead);
     waves go round-robin over the plan's streams, so the achieved rate is taken over the wall time
     of the whole wave loop (the `pairs` stage: CUDA events on the plan's stream around the
     loop, every timed build). The per-pass split comes from the sampled waves, run alone.
@@ -307,8 +308,8 @@ def roofline(stages: dict, info: dict, edge: int, ng: int, nocc: int, hbm: float
     tuning = tuning or {}
     # FP32 waves of nocc <= 8 fuse passes C and D unless the tuning splits them
     fused = mixed and nocc <= 8 and not tuning.get("split_cd", 0)
-    passes = ("vtab_kernel + pass_a + pass_b + pass_cd" if fused
-              else "vtab_kernel + pass_a + pass_b + pass_c + pass_d")
+    passes = ("pass_a (with the kernel tables) + pass_b + pass_cd" if fused
+              else "pass_a (with the kernel tables) + pass_b + pass_c + pass_d")
     nstreams = int(tuning.get("streams", 3))
     return {"kernel": f"pair round trip: {passes} over waves of {fpw} fields of {edge}^3 "
                       f"({nstreams} streams)",

@@ -150,9 +150,9 @@ typedef struct {
 /* Stages reported by occri_plan_stage_times. */
 enum {
   OCCRI_STAGE_ORBITALS = 0,  /* (a)+(b) */
-  OCCRI_STAGE_PAIR_A = 1,    /* (c)+(d) pass A: pair density, FFT along n3 and n2 */
-  OCCRI_STAGE_PAIR_B = 2,    /* (d) kernel tables; pass B: FFT along n1, kernel, inverse
-                                along m2, m1 */
+  OCCRI_STAGE_PAIR_A = 1,    /* (c)+(d) pass A: pair density, FFT along n3 and n2; and the
+                                wave's kernel tables, filled by extra CTAs of the same launch */
+  OCCRI_STAGE_PAIR_B = 2,    /* (d) pass B: FFT along n1, kernel, inverse along m2, m1 */
   OCCRI_STAGE_PAIR_C = 3,    /* (d) inverse along m3 and the Y accumulation (one fused pass
                                 for FP32 waves of nocc <= 8, else passes C and D) */
   OCCRI_STAGE_CONTRACT = 4,  /* (e) */

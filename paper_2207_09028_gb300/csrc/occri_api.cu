@@ -1176,7 +1176,7 @@ int autotune(Plan* p, occri_tune_t* out) {
   std::vector<int> nkps;
   for (int v = 1; v < p->nkp_cap; v *= 2) nkps.push_back(v);
   nkps.push_back(p->nkp_cap);
-  const bool can_fuse = occri::pair_wave_launches<T>(p->nocc, 0) == 4;
+  const bool can_fuse = occri::pair_wave_launches<T>(p->nocc, 0) == 3;
   const bool has_third = ensure_third_stream(p) == OCCRI_OK;   // else two streams at most
   // enough waves for every candidate to cover the same fields (and both streams)
   const int reps = std::max(12, 2 * p->nkp_cap);

@@ -282,7 +282,7 @@ cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, do
 // pass or passes C and D.
 constexpr int kFusedCdNoc = 8;
 template <typename T> constexpr int pair_wave_launches(int nocc, int split_cd = 0) {
-  return (std::is_same<T, float>::value && nocc <= kFusedCdNoc && !split_cd) ? 4 : 5;
+  return (std::is_same<T, float>::value && nocc <= kFusedCdNoc && !split_cd) ? 3 : 4;
 }
 
 // scratch per wave (MB): how many k' one wave takes when nocc^2 fields of a k' fit

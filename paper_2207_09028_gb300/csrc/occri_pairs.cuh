@@ -584,10 +584,23 @@ vtab_kernel(T* __restrict__ vt, PairParams p) {
 template <typename T, int N, bool ADJ = false>
 __global__ void __launch_bounds__(threads_for(N), min_blocks_a(N, sizeof(cplx_t<T>)))
 pass_a(const cplx_t<T>* __restrict__ psi, cplx_t<T>* __restrict__ S, PairParams p,
-       const cplx_t<T>* __restrict__ gam = nullptr) {
+       const cplx_t<T>* __restrict__ gam = nullptr, T* __restrict__ vt = nullptr) {
   using C2 = cplx_t<T>;
   constexpr int P = pitch(N);
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (vt != nullptr) {
+    // CTAs past the wave's fields fill the wave's kernel tables vt[kpl][m3][m1][m2] (rows
+    // m1 = z mod kVtabSplit of plane m3 = blockIdx.x), alongside the density transforms
+    const int nf = wave_fields(p.nocc, p.nkp, p.diag);
+    if ((int)blockIdx.y >= nf) {
+      const int y = (int)blockIdx.y - nf;
+      const int kpl = y / kVtabSplit, z = y % kVtabSplit, m3 = blockIdx.x;
+      const MetricHL<T> gm(p);
+      fill_vtab<T, N, false>(p, gm, m3, kpl, reinterpret_cast<Axis1<T>*>(smem_raw),
+                             vt + ((size_t)kpl * N + m3) * N * N, z, kVtabSplit);
+      return;
+    }
+  }
   C2* pl = reinterpret_cast<C2*>(smem_raw);   // rho, then its 2-D transform
   const int n1 = blockIdx.x;
   const int f = blockIdx.y;
@@ -1573,15 +1586,16 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
   if (ev) chk(cudaEventRecord(ev[0], st));
-  pass_a<T, N><<<dim3(N, nf), nt, sa, st>>>(psi, S, p);
-  if (ev) chk(cudaEventRecord(ev[1], st));
+  // pass A and the wave's kernel tables in one launch (extra rows of CTAs fill the tables)
   T* vt = reinterpret_cast<T*>(reinterpret_cast<char*>(S) + p.vt_off);
-  vtab_kernel<T, N><<<dim3(N, p.diag ? 1 : p.nkp, kVtabSplit), nt, 0, st>>>(vt, p);
+  pass_a<T, N><<<dim3(N, nf + (p.diag ? 1 : p.nkp) * kVtabSplit), nt, sa, st>>>(psi, S, p,
+                                                                             nullptr, vt);
+  if (ev) chk(cudaEventRecord(ev[1], st));
   pass_b<T, N><<<std::min(N * nf, std::max(1, slots_b / std::max(1, p.b_div))), nt, sb, st>>>(
       S, p, vt);
   if (ev) chk(cudaEventRecord(ev[2], st));
   // FP32 waves of nocc <= kCdNoc: passes C and D fused (the potentials stay on chip)
-  const bool fused = pair_wave_launches<T>(p.nocc, p.split_cd) == 4;
+  const bool fused = pair_wave_launches<T>(p.nocc, p.split_cd) == 3;
   if (!fused) pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S, p);
   if (ev_y) chk(cudaStreamWaitEvent(st, ev_y, 0));   // the previous wave's Y updates
   if constexpr (std::is_same<T, float>::value) {
