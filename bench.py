@@ -45,12 +45,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) of one full mixed-precision wave (pass_a with its kernel-table CTAs,
-# pass_b and pass_cd), keyed by ("round_trip", grid edge, fields per wave, precision),
+# DRAM bytes (read + write) of one full mixed-precision wave (pass_a, pass_b reading the plan's
+# kernel tables, and pass_cd), keyed by ("round_trip", grid edge, fields per wave, precision),
 # from one ncu --set full capture per pass of the same launch shape (an off-diagonal 64-field
 # wave at 60^3 of the 2x2x2-k profiling cell of `--case 60 8 2 2 2`; cold cache, each launch
 # replayed alone).
-TRAFFIC = {("round_trip", 60, 64, "mixed"): 425.9e6}
+TRAFFIC = {("round_trip", 60, 64, "mixed"): 425.0e6}
 
 METRIC = "K-builds/s at 6x6x6 k, 350 AO; mixed vs FP64 GPU at |dE_x|<=1e-6 Ha/cell"
 UNIT = "K-builds/s"

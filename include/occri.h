@@ -150,8 +150,9 @@ typedef struct {
 /* Stages reported by occri_plan_stage_times. */
 enum {
   OCCRI_STAGE_ORBITALS = 0,  /* (a)+(b) */
-  OCCRI_STAGE_PAIR_A = 1,    /* (c)+(d) pass A: pair density, FFT along n3 and n2; and the
-                                wave's kernel tables, filled by extra CTAs of the same launch */
+  OCCRI_STAGE_PAIR_A = 1,    /* (c)+(d) pass A: pair density, FFT along n3 and n2; where the
+                                plan holds no kernel tables (occri_tune_t.wave_tables), also
+                                the wave's, filled by extra CTAs of the same launch */
   OCCRI_STAGE_PAIR_B = 2,    /* (d) pass B: FFT along n1, kernel, inverse along m2, m1 */
   OCCRI_STAGE_PAIR_C = 3,    /* (d) inverse along m3 and the Y accumulation (one fused pass
                                 for FP32 waves of nocc <= 8, else passes C and D) */
@@ -174,8 +175,10 @@ typedef struct occri_plan occri_plan;
  * compiled for its length, and the pair passes are compiled per cubic edge. cuda_stream: a
  * cudaStream_t or NULL (legacy default stream). The plan lives on the device current at
  * this call: every later call on it makes that device current for its duration and then
- * restores the caller's. On success *out owns a plan to be destroyed with
- * occri_plan_destroy; on failure *out is NULL. */
+ * restores the caller's. Among its workspaces are the kernel tables v/(4 pi) of every integer
+ * k - k' on the mesh, formed here where they take at most 4 GiB (occri_tune_t.wave_tables).
+ * On success *out owns a plan to be destroyed with occri_plan_destroy; on failure *out is
+ * NULL. */
 int occri_plan_create(occri_plan **out, const occri_cell *cell, const occri_kmesh *kmesh,
                       const occri_basis *basis, int nocc, const int grid[3],
                       const occri_kernel *kernel, int precision, void *cuda_stream);
@@ -208,6 +211,12 @@ typedef struct {
                            each with its own scratch (default 3) */
   int pass_b_div;       /* pass-B CTAs = resident CTA slots / pass_b_div (1 or 2) */
   int split_cd;         /* 1: separate passes C and D where the fused pass CD applies */
+  int wave_tables;      /* 1: every wave forms its own kernel tables v/(4 pi); 0 (default): the
+                           waves read the plan's tables, one per integer k - k' on the mesh,
+                           formed once at plan creation where they take at most 4 GiB
+                           ((2 D_1 - 1)(2 D_2 - 1)(2 D_3 - 1) N_g values of the plan's real
+                           type, D_d the mesh's k denominators). occri_plan_tuning reports 1
+                           when the plan holds no tables. Same values either way */
   double us_per_field;  /* autotuner: measured microseconds per pair field of this choice */
   double us_default;    /* autotuner: the same for the default (widest wave, 3 streams, 1, 0) */
   int candidates;       /* autotuner: configurations timed; 0: taken from the cache;
@@ -232,8 +241,9 @@ int occri_plan_autotune(occri_plan *plan, int flags, occri_tune_t *chosen);
 int occri_plan_tuning(const occri_plan *plan, occri_tune_t *current);
 
 /* Set the launch configuration by hand (k_per_wave >= 1, clamped to the scratch capacity;
- * streams 1, 2 or 3; pass_b_div 1 or 2; split_cd 0 or 1; other fields ignored), else
- * OCCRI_EINVAL. Takes effect at the next build. */
+ * streams 1, 2 or 3; pass_b_div 1 or 2; split_cd 0 or 1; wave_tables 0 or 1; other fields
+ * ignored), else OCCRI_EINVAL. Takes effect at the next build. The autotuner and its cache
+ * leave wave_tables as it is. */
 int occri_plan_set_tuning(occri_plan *plan, const occri_tune_t *cfg);
 
 /* The paper's form of the assembly (Sec. II.C, Eq. occrikop): K ~ PKP + PKQ + QKP, where

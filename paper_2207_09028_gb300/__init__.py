@@ -54,7 +54,7 @@ class occri_kernel(ctypes.Structure):
 class occri_tune_t(ctypes.Structure):
     _fields_ = [("k_per_wave", ctypes.c_int), ("streams", ctypes.c_int),
                 ("pass_b_div", ctypes.c_int), ("split_cd", ctypes.c_int),
-                ("us_per_field", ctypes.c_double), ("us_default", ctypes.c_double),
+                ("wave_tables", ctypes.c_int), ("us_per_field", ctypes.c_double), ("us_default", ctypes.c_double),
                 ("candidates", ctypes.c_int)]
 
 
@@ -323,10 +323,11 @@ class Plan:
         _check(self._lib.occri_plan_tuning(self._h, ctypes.byref(t)), "occri_plan_tuning")
         return {f: getattr(t, f) for f, _ in occri_tune_t._fields_}
 
-    def force_tuning(self, k_per_wave: int, streams: int, pass_b_div: int, split_cd: int):
+    def force_tuning(self, k_per_wave: int, streams: int, pass_b_div: int, split_cd: int,
+                     wave_tables: int = 0):
         """occri_plan_set_tuning: set the pair loop's launch configuration by hand."""
         t = occri_tune_t(k_per_wave=k_per_wave, streams=streams, pass_b_div=pass_b_div,
-                         split_cd=split_cd)
+                         split_cd=split_cd, wave_tables=wave_tables)
         _check(self._lib.occri_plan_set_tuning(self._h, ctypes.byref(t)), "occri_plan_set_tuning")
 
     def assemble_paper(self, S, C, KC, K=None):

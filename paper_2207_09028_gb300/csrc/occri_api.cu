@@ -77,6 +77,7 @@ PairParams Plan::pair_params() const {
   q.b_div = b_div;
   q.split_cd = split_cd;
   q.vt_off = (long long)fields_cap * fs * (precision == OCCRI_FP64 ? 16 : 8);
+  q.vq = wave_tables ? nullptr : vq;
   for (int d = 0; d < 3; ++d) q.D[d] = D[d];
   q.kint = kint;
   // reciprocal vectors b_i (rows): B = 2 pi (A^{-1})^T
@@ -648,6 +649,7 @@ void free_plan(Plan* p) {
     if (b) cudaFree(b);
   if (p->scratch2) cudaFree(p->scratch2);
   if (p->scratch3) cudaFree(p->scratch3);
+  if (p->vq) cudaFree(p->vq);
   for (void* yx : p->Yx)
     if (yx) cudaFree(yx);
   if (p->asm_scratch) cudaFree(p->asm_scratch);
@@ -1098,7 +1100,7 @@ int apply_tune(Plan* p, const occri_tune_t& t) {
   p->b_div = std::max(1, t.pass_b_div);
   p->split_cd = t.split_cd ? 1 : 0;
   p->tuned = 1;
-  return OCCRI_OK;
+  return OCCRI_OK;   // wave_tables is set by occri_plan_set_tuning only
 }
 
 bool tune_lookup(Plan* p, occri_tune_t* out) {
@@ -1209,6 +1211,7 @@ int autotune(Plan* p, occri_tune_t* out) {
   t.streams = pick.nstreams;
   t.pass_b_div = pick.b_div;
   t.split_cd = pick.split_cd;
+  t.wave_tables = (p->wave_tables || !p->vq) ? 1 : 0;
   t.us_per_field = best;
   t.us_default = t_def;
   t.candidates = count;
@@ -1628,7 +1631,13 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
     chk(dalloc(&b, sbytes, &tot)); p->scratch2 = b; b = nullptr;
     // three waves in flight by default: one more scratch buffer (a wave, ~110 MB at 60^3
     // FP32) measured 1.5 % faster builds at 6x6x6 k than two
-    chk(dalloc(&b, sbytes, &tot)); p->scratch3 = b;
+    chk(dalloc(&b, sbytes, &tot)); p->scratch3 = b; b = nullptr;
+    // the kernel tables of every k - k', where they fit: waves then form none of their own
+    const size_t qbytes = (size_t)(2 * p->D[0] - 1) * (2 * p->D[1] - 1) * (2 * p->D[2] - 1) *
+                          (size_t)ng * (csz / 2);
+    if (qbytes <= kQTabMaxBytes) {
+      chk(dalloc(&b, qbytes, &tot)); p->vq = b; b = nullptr;
+    }
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux2, cudaStreamNonBlocking);
@@ -1643,6 +1652,9 @@ int occri_plan_create(occri_plan** out, const occri_cell* cell, const occri_kmes
   chk(dalloc(&p->dacc, 2, &tot));
   chk(dalloc(&p->status, 2, &tot));
   if (e == cudaSuccess) e = cudaMemset(p->status, 0, 2 * sizeof(int));
+  if (e == cudaSuccess && p->vq)
+    e = precision == OCCRI_FP64 ? launch_qtables<double>(*p, p->stream)
+                                : launch_qtables<float>(*p, p->stream);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? OCCRI_ENOMEM : OCCRI_ECUDA;
@@ -1799,13 +1811,15 @@ int occri_plan_autotune(occri_plan* plan, int flags, occri_tune_t* chosen) {
 int occri_plan_set_tuning(occri_plan* plan, const occri_tune_t* cfg) {
   if (!plan || !cfg) return OCCRI_EINVAL;
   if (cfg->k_per_wave < 1 || cfg->streams < 1 || cfg->streams > 3 ||
-      (cfg->pass_b_div != 1 && cfg->pass_b_div != 2) || (cfg->split_cd != 0 && cfg->split_cd != 1))
+      (cfg->pass_b_div != 1 && cfg->pass_b_div != 2) || (cfg->split_cd != 0 && cfg->split_cd != 1) ||
+      (cfg->wave_tables != 0 && cfg->wave_tables != 1))
     return OCCRI_EINVAL;
   Plan* p = plan->p;
   occri::DeviceGuard guard(p->device);
   if (!guard.ok) return OCCRI_ECUDA;
   const int st = occri_impl::apply_tune(p, *cfg);
   if (st != OCCRI_OK) return st;
+  p->wave_tables = cfg->wave_tables ? 1 : 0;
   p->tuned = 0;
   return OCCRI_OK;
 }
@@ -1818,6 +1832,7 @@ int occri_plan_tuning(const occri_plan* plan, occri_tune_t* current) {
   current->streams = p->nstreams;
   current->pass_b_div = p->b_div;
   current->split_cd = p->split_cd;
+  current->wave_tables = (p->wave_tables || !p->vq) ? 1 : 0;
   current->candidates = p->tuned ? -1 : 0;
   return OCCRI_OK;
 }

@@ -81,6 +81,8 @@ struct PairParams {
   int k, kp0, nkp;
   int diag;                  // 1: the wave is (k, k) and holds the fields i <= j only
   long long vt_off;          // bytes from a scratch buffer's start to its kernel tables
+  const void* vq;            // the plan's kernel tables of every k - k' (qtab_index order), or
+                             // null: each wave forms its own behind its scratch (vt_off)
   int* status;               // plan status word (first device error, k), for bounded waits
   long long wait_ns;         // limit of every bounded device wait (nanoseconds)
   int fault;                 // test-only fault injection (OCCRI_FAULT_*), 0 in normal use
@@ -134,6 +136,7 @@ struct Plan {
   int nstreams = 3;          // consecutive waves go round-robin over 1, 2 or 3 streams
   int b_div = 1;             // pass-B CTAs = resident slots / b_div
   int split_cd = 0;          // 1: passes C and D instead of the fused pass CD
+  int wave_tables = 0;       // 1: each wave forms its kernel tables even where vq is held
   int tuned = 0;             // 1: the configuration came from the autotuner (or its cache)
   std::vector<int> shells_by_l[4];
 
@@ -171,6 +174,10 @@ struct Plan {
   void* scratch = nullptr;   // [fields_cap][fs] cplx_t<T>, waves on the plan's stream, then
                              // the wave's kernel tables [nkp_wave][m3][m1][m2] T
   void* scratch2 = nullptr;  // the same for the waves on the second stream
+  // kernel tables v/(4 pi) of every integer difference kint[k] - kint[k'] ((2 D_d - 1) per
+  // axis, each [m3][m1][m2] T), formed once at creation where they take at most
+  // kQTabMaxBytes; null otherwise
+  void* vq = nullptr;
   // Consecutive waves alternate between the plan's stream and `aux`, each with its own
   // scratch, so one wave's passes overlap the next one's; only the accumulation passes,
   // which both update Y_k, are ordered across the two streams (event ev_y).
@@ -270,6 +277,11 @@ cudaError_t launch_pair_wave(const Plan& p, int k, int kp0, int nkp, int diag, c
                              cudaEvent_t ev_y = nullptr);
 template <typename T>
 cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag, cudaStream_t s);
+// The plan's kernel tables of every k - k' into p.vq (allocated by the caller), on stream s.
+template <typename T>
+cudaError_t launch_qtables(const Plan& p, cudaStream_t s);
+// Most device memory the plan's kernel tables may take; beyond it every wave forms its own.
+constexpr size_t kQTabMaxBytes = (size_t)4 << 30;
 // One wave of the adjoint build: forward potentials in scratch, adjoint potentials in
 // scratch2, their contributions added to gpsi (uses psi and gam); with dacc != nullptr
 // also the omega term sum (dv/d omega)/(4 pi) Re(conj(sigma^) rho^) added to *dacc.
@@ -278,8 +290,8 @@ cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, do
                             cudaStream_t s);
 
 // Largest nocc whose FP32 waves run the inverse along m3 and the Y accumulation as one
-// fused pass. A wave launches the kernel-table fill and passes A and B, then the fused
-// pass or passes C and D.
+// fused pass. A wave launches passes A (with the wave's kernel tables where the plan holds
+// none) and B, then the fused pass or passes C and D.
 constexpr int kFusedCdNoc = 8;
 template <typename T> constexpr int pair_wave_launches(int nocc, int split_cd = 0) {
   return (std::is_same<T, float>::value && nocc <= kFusedCdNoc && !split_cd) ? 3 : 4;

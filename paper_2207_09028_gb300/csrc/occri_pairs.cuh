@@ -541,12 +541,9 @@ __device__ __forceinline__ T bin_value(const PairParams& p, const Consts<T>& k,
 // N-entry scratch table in shared memory; every thread of the CTA calls this (one
 // __syncthreads inside, between the axis-1 table and its use).
 template <typename T, int N, bool DERIV>
-__device__ __forceinline__ void fill_vtab(const PairParams& p, const MetricHL<T>& gm, int m3,
-                                          int kpl, Axis1<T>* ax1, T* out, int r0, int rs) {
-  const int kp = p.kp0 + kpl;
-  int Q[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
+__device__ __forceinline__ void fill_vtab_q(const PairParams& p, const MetricHL<T>& gm, int m3,
+                                            const int (&Q)[3], Axis1<T>* ax1, T* out, int r0,
+                                            int rs) {
   for (int t = threadIdx.x; t < N; t += blockDim.x)
     ax1[t] = axis1_entry<T>(gm, axis_int(t, Q[0], p.D[0], N));
   __syncthreads();
@@ -562,6 +559,29 @@ __device__ __forceinline__ void fill_vtab(const PairParams& p, const MetricHL<T>
   }
 }
 
+// The same for the wave's k' = kp0 + kpl: q = k - k' is Q / D per axis.
+template <typename T, int N, bool DERIV>
+__device__ __forceinline__ void fill_vtab(const PairParams& p, const MetricHL<T>& gm, int m3,
+                                          int kpl, Axis1<T>* ax1, T* out, int r0, int rs) {
+  const int kp = p.kp0 + kpl;
+  int Q[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) Q[d] = p.kint[p.k * 3 + d] - p.kint[kp * 3 + d];
+  fill_vtab_q<T, N, DERIV>(p, gm, m3, Q, ax1, out, r0, rs);
+}
+
+// The plan's kernel tables: one per integer difference Q = kint[k] - kint[k'], each axis
+// in -(D - 1) .. D - 1, stored in row-major (Q_1, Q_2, Q_3) order, each [m3][m1][m2].
+// Table index of the wave's k' = kp0 + kpl.
+__device__ __forceinline__ long long qtab_index(const PairParams& p, int kpl) {
+  const int kp = p.kp0 + kpl;
+  long long idx = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    idx = idx * (2 * p.D[d] - 1) + (p.kint[p.k * 3 + d] - p.kint[kp * 3 + d] + p.D[d] - 1);
+  return idx;
+}
+
 // The wave's kernel tables vt[kpl][m3][m1][m2] = v/(4 pi), once per wave, for pass B to
 // copy plane by plane (instead of every pass-B CTA forming the planes it meets). CTA
 // (m3, kpl, z) fills rows m1 = z (mod kVtabSplit) of plane m3.
@@ -574,6 +594,26 @@ vtab_kernel(T* __restrict__ vt, PairParams p) {
   const MetricHL<T> gm(p);
   fill_vtab<T, N, false>(p, gm, m3, kpl, ax1, vt + ((size_t)kpl * N + m3) * N * N,
                          (int)blockIdx.z, kVtabSplit);
+}
+
+// The plan's kernel tables (qtab_index order), once at plan creation: CTA (t, m3, z) fills
+// rows m1 = z (mod kVtabSplit) of plane m3 of table t.
+template <typename T, int N>
+__global__ void __launch_bounds__(threads_for(N))
+qtab_kernel(T* __restrict__ vq, PairParams p) {
+  __shared__ Axis1<T> ax1[N];
+  const int m3 = blockIdx.y;
+  long long t = blockIdx.x;
+  int Q[3];
+#pragma unroll
+  for (int d = 2; d >= 0; --d) {
+    const int w = 2 * p.D[d] - 1;
+    Q[d] = (int)(t % w) - (p.D[d] - 1);
+    t /= w;
+  }
+  const MetricHL<T> gm(p);
+  fill_vtab_q<T, N, false>(p, gm, m3, Q, ax1, vq + ((size_t)blockIdx.x * N + m3) * N * N,
+                           (int)blockIdx.z, kVtabSplit);
 }
 
 // ------------------------------------------------------------------ pass A
@@ -699,7 +739,9 @@ __device__ __forceinline__ void pass_b_body(cplx_t<T>* __restrict__ S, const Pai
       if (m3 != m3_tab || kpl != kpl_tab) {   // uniform over the CTA
         m3_tab = m3;
         kpl_tab = kpl;
-        copy_table<T, N>(vtab, vt + ((size_t)kpl * N + m3) * N * N);
+        const T* tab = p.vq ? static_cast<const T*>(p.vq) + (size_t)qtab_index(p, kpl) * N * N * N
+                            : vt + (size_t)kpl * N * N * N;
+        copy_table<T, N>(vtab, tab + (size_t)m3 * N * N);
       }
     }
   };
@@ -1586,10 +1628,12 @@ cudaError_t run_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S, cp
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
   if (ev) chk(cudaEventRecord(ev[0], st));
-  // pass A and the wave's kernel tables in one launch (extra rows of CTAs fill the tables)
+  // pass A; without the plan's tables, the wave's kernel tables in the same launch (extra
+  // rows of CTAs fill them)
   T* vt = reinterpret_cast<T*>(reinterpret_cast<char*>(S) + p.vt_off);
-  pass_a<T, N><<<dim3(N, nf + (p.diag ? 1 : p.nkp) * kVtabSplit), nt, sa, st>>>(psi, S, p,
-                                                                             nullptr, vt);
+  const int tab_rows = p.vq ? 0 : (p.diag ? 1 : p.nkp) * kVtabSplit;
+  pass_a<T, N><<<dim3(N, nf + tab_rows), nt, sa, st>>>(psi, S, p, nullptr,
+                                                       p.vq ? nullptr : vt);
   if (ev) chk(cudaEventRecord(ev[1], st));
   pass_b<T, N><<<std::min(N * nf, std::max(1, slots_b / std::max(1, p.b_div))), nt, sb, st>>>(
       S, p, vt);
@@ -1661,13 +1705,21 @@ cudaError_t run_vjp_wave(const PairParams& p, const cplx_t<T>* psi, const cplx_t
     pass_b_domega2<T, N><<<dim3(N, nf), nt, sb + sizeof(C2) * N * pitch(N), st>>>(S0, S1, p,
                                                                                 dacc);
   T* vt = reinterpret_cast<T*>(reinterpret_cast<char*>(S0) + p.vt_off);
-  vtab_kernel<T, N><<<dim3(N, p.diag ? 1 : p.nkp, kVtabSplit), nt, 0, st>>>(vt, p);
+  if (!p.vq) vtab_kernel<T, N><<<dim3(N, p.diag ? 1 : p.nkp, kVtabSplit), nt, 0, st>>>(vt, p);
   pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S0, p, vt);
   pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S0, p);
   pass_b<T, N><<<std::min(N * nf, slots_b), nt, sb, st>>>(S1, p, vt);
   pass_c<T, N><<<dim3(N, nf), nt, sc, st>>>(S1, p);
   const cudaError_t e = launch_pass_e<T>(p, S0, S1, psi, gam, G, st);
   return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// The plan's kernel tables into vq: (2 D_1 - 1)(2 D_2 - 1)(2 D_3 - 1) tables of N^3 values.
+template <typename T, int N>
+cudaError_t run_qtables(const PairParams& p, T* vq, cudaStream_t st) {
+  const unsigned nq = (unsigned)((2 * p.D[0] - 1) * (2 * p.D[1] - 1) * (2 * p.D[2] - 1));
+  qtab_kernel<T, N><<<dim3(nq, N, kVtabSplit), threads_for(N), 0, st>>>(vq, p);
+  return cudaGetLastError();
 }
 
 }  // namespace pairs

@@ -15,6 +15,8 @@ template <typename T, int N>
 cudaError_t run_domega_wave(const PairParams& p, const cplx_t<T>* psi, cplx_t<T>* S,
                             double* dacc, cudaStream_t st);
 template <typename T, int N>
+cudaError_t run_qtables(const PairParams& p, T* vq, cudaStream_t st);
+template <typename T, int N>
 cudaError_t run_vjp_wave(const PairParams& p, const cplx_t<T>* psi, const cplx_t<T>* gam,
                          cplx_t<T>* S0, cplx_t<T>* S1, cplx_t<T>* G, double* dacc,
                          cudaStream_t st);

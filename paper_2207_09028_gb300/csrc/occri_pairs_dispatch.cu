@@ -47,6 +47,20 @@ cudaError_t launch_domega_wave(const Plan& p, int k, int kp0, int nkp, int diag,
 }
 
 template <typename T>
+cudaError_t launch_qtables(const Plan& p, cudaStream_t s) {
+  const PairParams pp = p.pair_params();
+  switch (p.N[0]) {
+#define OCCRI_QTAB_CASE(NN) \
+  case NN:                  \
+    return pairs::run_qtables<T, NN>(pp, (T*)p.vq, s);
+    OCCRI_FOR_EACH_N(OCCRI_QTAB_CASE)
+#undef OCCRI_QTAB_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
 cudaError_t launch_vjp_wave(const Plan& p, int k, int kp0, int nkp, int diag, double* dacc,
                             cudaStream_t s) {
   PairParams pp = p.pair_params();
@@ -78,6 +92,8 @@ template cudaError_t launch_pair_wave<float>(const Plan&, int, int, int, int, cu
                                              void*, cudaEvent_t*, cudaEvent_t);
 template cudaError_t launch_pair_wave<double>(const Plan&, int, int, int, int, cudaStream_t, void*,
                                               void*, cudaEvent_t*, cudaEvent_t);
+template cudaError_t launch_qtables<float>(const Plan&, cudaStream_t);
+template cudaError_t launch_qtables<double>(const Plan&, cudaStream_t);
 template cudaError_t launch_domega_wave<float>(const Plan&, int, int, int, int, cudaStream_t);
 template cudaError_t launch_domega_wave<double>(const Plan&, int, int, int, int, cudaStream_t);
 

@@ -6,8 +6,10 @@ namespace occri {
 namespace pairs {
 template cudaError_t run_wave<float, 40>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t, cudaEvent_t*, cudaEvent_t);
 template cudaError_t run_domega_wave<float, 40>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_qtables<float, 40>(const PairParams&, float*, cudaStream_t);
 template cudaError_t run_wave<float, 45>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cudaStream_t, cudaEvent_t*, cudaEvent_t);
 template cudaError_t run_domega_wave<float, 45>(const PairParams&, const cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
+template cudaError_t run_qtables<float, 45>(const PairParams&, float*, cudaStream_t);
 template cudaError_t run_vjp_wave<float, 40>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
 template cudaError_t run_vjp_wave<float, 45>(const PairParams&, const cplx_t<float>*, const cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, cplx_t<float>*, double*, cudaStream_t);
 }  // namespace pairs

@@ -6,6 +6,7 @@ namespace occri {
 namespace pairs {
 template cudaError_t run_wave<double, 54>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, cplx_t<double>*, cudaStream_t, cudaEvent_t*, cudaEvent_t);
 template cudaError_t run_domega_wave<double, 54>(const PairParams&, const cplx_t<double>*, cplx_t<double>*, double*, cudaStream_t);
+template cudaError_t run_qtables<double, 54>(const PairParams&, double*, cudaStream_t);
 template cudaError_t run_vjp_wave<double, 54>(const PairParams&, const cplx_t<double>*, const cplx_t<double>*, cplx_t<double>*, cplx_t<double>*, cplx_t<double>*, double*, cudaStream_t);
 }  // namespace pairs
 }  // namespace occri

@@ -37,7 +37,9 @@ def test_autotuned_build_matches_default(prec, tol):
 
 @pytest.mark.parametrize("cfg", [dict(k_per_wave=1, streams=1, pass_b_div=2, split_cd=1),
                                  dict(k_per_wave=3, streams=2, pass_b_div=1, split_cd=0),
-                                 dict(k_per_wave=2, streams=3, pass_b_div=1, split_cd=0)])
+                                 dict(k_per_wave=2, streams=3, pass_b_div=1, split_cd=0),
+                                 dict(k_per_wave=2, streams=3, pass_b_div=1, split_cd=0,
+                                      wave_tables=1)])
 def test_every_configuration_gives_the_same_result(cfg, monkeypatch):
     """Each knob on its own: builds under forced configurations agree with the default."""
     w = _wl(nocc=3, grid=(20, 20, 20))
@@ -67,3 +69,24 @@ def test_tuning_is_cached_per_shape():
     assert c.tuning()["candidates"] in (0, -1)
     for p in (a, b, c):
         p.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_plan_tables_match_wave_tables(prec, tol):
+    """The plan's kernel tables (one per integer k - k', formed at creation) and the tables each
+    wave forms for itself hold the same values: both builds agree, at the 60^3 grid edge of the
+    benchmark and on an uneven mesh (k - k' differs per axis)."""
+    w = small_workload(mesh=(3, 2, 1), grid=(60, 60, 60), nocc=3, counts=(2, 1), seed=91)
+    plan = occri.Plan.from_workload(w, precision=prec)
+    assert plan.tuning()["wave_tables"] == 0          # the plan holds its tables
+    C = torch.from_numpy(w.C).cuda()
+    kc0, _, ex0 = plan.build(C, want_k=False)
+    kc0 = kc0.cpu().numpy()
+    cur = plan.tuning()
+    plan.force_tuning(cur["k_per_wave"], cur["streams"], cur["pass_b_div"], cur["split_cd"],
+                      wave_tables=1)
+    assert plan.tuning()["wave_tables"] == 1
+    kc1, _, ex1 = plan.build(C, want_k=False)
+    assert np.abs(kc1.cpu().numpy() - kc0).max() <= tol * np.abs(kc0).max()
+    assert abs(float(ex1.cpu()[0]) - float(ex0.cpu()[0])) <= tol * abs(float(ex0.cpu()[0]))
+    plan.close()
