@@ -54,8 +54,8 @@ class occri_kernel(ctypes.Structure):
 class occri_tune_t(ctypes.Structure):
     _fields_ = [("k_per_wave", ctypes.c_int), ("streams", ctypes.c_int),
                 ("pass_b_div", ctypes.c_int), ("split_cd", ctypes.c_int),
-                ("wave_tables", ctypes.c_int), ("us_per_field", ctypes.c_double), ("us_default", ctypes.c_double),
-                ("candidates", ctypes.c_int)]
+                ("wave_tables", ctypes.c_int), ("us_per_field", ctypes.c_double),
+                ("us_default", ctypes.c_double), ("candidates", ctypes.c_int)]
 
 
 OCCRI_TUNE_FORCE = 1
