@@ -5,9 +5,9 @@ One step = one full exchange build (steps a-f: AO/orbital evaluation, every
 (k,k',i,j) pair-density FFT round trip with the Coulomb kernel, the contraction
 and the FP64 ACE assembly) on the paper-scale synthetic cell: fcc a = 5.43 A,
 2 atoms, 6x6x6 Gamma-centred k-mesh (216 k), 350 uncontracted s/p/d/f AOs,
-nocc = 8, 60^3 grid, mixed precision with the tensor-core contraction. Inputs (C, plan tables) are resident in
-HBM before the timed region; the orbital and accumulator fields (3 GB each)
-exceed L2, so no flush is needed between steps.
+nocc = 8, 60^3 grid, mixed precision with the tensor-core contraction. Inputs
+(C, plan tables) are resident in HBM before the timed region; the orbital and
+accumulator fields (3 GB each) exceed L2, so no flush is needed between steps.
 
 Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead
 (bounded sample on every host core, extrapolated to a full build).
