@@ -341,7 +341,7 @@ def alu_roofline(fields: float, ng: int, ms: float, peak_tflops: float, kind: st
 
 
 # one stage of the tensor-core contraction: three FP16 MMAs (hi.hi, hi.lo, lo.hi) of
-# M = 128 AO rows, N = 256 real columns, K = 32 grid points
+# M = 128 AO rows, N = 192 real columns (96 complex), K = 32 grid points
 
 
 def tensor_roofline(info: dict, contract_ms: float, peak_tflops: float, peak_kind: str,

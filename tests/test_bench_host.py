@@ -76,3 +76,34 @@ def test_l2_note_follows_the_field_sizes(bench):
     assert big.startswith("no flush") and "3 GB" in big
     small = bench.l2_note(1, 4, 24 ** 3)
     assert small.startswith("fields fit L2")
+
+
+def test_tensor_roofline_counts_stage_flops_over_gemm_time(bench):
+    fps = 3 * 2 * 128 * 192 * 32                   # one stage: three MMAs of M 128, N 192, K 32
+    info = {"contraction_tc": 1, "tc_stages": 1_000_000, "tc_flops_per_stage": float(fps)}
+    r = bench.tensor_roofline(info, 4.0, 1000.0, "measured", stage_ms=8.0)
+    assert r["achieved"] == pytest.approx(fps * 1e6 / 4e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1000.0)
+    assert r["frac_of_stage"] == pytest.approx(r["frac"] / 2.0)   # twice the time, same flops
+    assert r["useful_frac"] == pytest.approx(r["frac"] / 3.0)     # only hi.hi is the product
+    assert bench.tensor_roofline(info, 4.0, 1000.0, "measured")["frac_of_stage"] is None
+    assert bench.tensor_roofline(dict(info, contraction_tc=0), 4.0, 1000.0, "m") is None
+    assert bench.tensor_roofline(info, 0.0, 1000.0, "m") is None
+
+
+def test_alu_roofline_of_the_fp64_pair_loop(bench):
+    ng = 8 ** 3
+    assert bench.pair_field_flops(ng) == pytest.approx((10.0 * 9 + 24.0) * ng)
+    r = bench.alu_roofline(2000.0, ng, 10.0, 1.25, "fp64")
+    assert r["achieved"] == pytest.approx(bench.pair_field_flops(ng) * 2000.0 / 0.01 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1.25) and r["bound"] == "alu"
+    assert bench.alu_roofline(2000.0, ng, 10.0, 0.0, "fp64") is None
+
+
+def test_sweep_slope_and_job_throughput(bench):
+    xs = [1, 8, 27, 64, 125, 216]
+    assert bench.loglog_slope(xs, [3.0 * x ** 2 for x in xs]) == pytest.approx(2.0)
+    assert bench.loglog_slope(xs, [7.0 * x ** 0.5 for x in xs]) == pytest.approx(0.5)
+    # replicas: every rank runs `steps` builds; the job's rate is the sum over ranks
+    assert bench.job_throughput(4, 3, 1500.0) == pytest.approx(8.0)
+    assert bench.max_over_ranks(12.5) == 12.5
